@@ -1,0 +1,194 @@
+/*
+ * ugp.h -- C ABI of the GB300 (sm_103a) Gaussian-primitive ray tracer.
+ *
+ * Implements the scene queries of "Unified Gaussian Primitives for Scene
+ * Representation and Rendering" (Zhou, Wu, Yan; arXiv 2406.09733):
+ * primitives are scaled anisotropic 3D Gaussians (Eq. 1, Eq. 2) truncated to
+ * their k-sigma bounding ellipsoid (Eq. 4); light is attenuated by the linear
+ * transmittance of Eq. 7 and scattered by whole primitives sampled from the
+ * free-flight distribution of Eq. 8 (Sec. 5.2).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are DEVICE pointers unless a comment says "host".  The caller
+ *    owns all memory; the library never allocates device memory.  Arrays are
+ *    dense, C-contiguous, structure-of-arrays: a "float3 array" of n elements
+ *    is 3*n floats (x0,y0,z0,x1,...).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is enqueued on it and the call returns without
+ *    waiting, except where noted.  Argument errors are detected on the host
+ *    before any launch and reported synchronously.
+ *  - Rays are x_t = o + t d for t in [t0, t1]; d must be non-zero.  With a
+ *    unit d, t is Euclidean distance.
+ *  - Primitive indices in inputs and outputs are the caller's original
+ *    indices (0 .. n_prims-1), never the internal leaf order.
+ *  - Functions return a ugp_status; ugp_last_error() gives a thread-local
+ *    message for the most recent failure on the calling thread.  No C++
+ *    exception crosses this boundary.
+ *  - Device loops are bounded.  A ray whose traversal hits a bound gets a
+ *    non-zero per-ray status code (UGP_RAY_*) in status_out; the call itself
+ *    still returns UGP_OK.
+ */
+#ifndef UGP_H_
+#define UGP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ugp_status {
+  UGP_OK = 0,
+  UGP_ERR_INVALID_ARG = 1,          /* a pointer, size or value is out of range */
+  UGP_ERR_WORKSPACE_TOO_SMALL = 2,  /* workspace_bytes < the *_workspace_size() query */
+  UGP_ERR_CUDA = 3,                 /* a CUDA runtime call failed (see ugp_last_error) */
+  UGP_ERR_ITER_LIMIT = 4,           /* reported by ugp_status_of_rays: some ray hit a loop bound */
+  UGP_ERR_TIMEOUT = 5,              /* a bounded device wait gave up */
+  UGP_ERR_NOT_BUILT = 6,            /* a NULL or released BVH handle */
+  UGP_ERR_OVERFLOW = 7              /* reported by ugp_status_of_rays: a stack or buffer overflowed */
+} ugp_status;
+
+/* Per-ray status codes (uint8) written by the tracing entry points. */
+enum {
+  UGP_RAY_OK = 0,
+  UGP_RAY_STACK_OVERFLOW = 1,   /* traversal stack full: result incomplete */
+  UGP_RAY_BUFFER_OVERFLOW = 2,  /* free-flight candidate buffer held only active intervals */
+  UGP_RAY_ITER_LIMIT = 3,       /* round or root-solve bound reached */
+  UGP_RAY_BAD_NODE = 4          /* a node or leaf reference out of range (corrupt BVH) */
+};
+
+/* Input primitives (Sec. 3.1, Eq. 1-2), device float32 arrays of n rows:
+ *   mean3      mu              (n x 3)
+ *   quat4      rotation R as a unit quaternion (w, x, y, z)   (n x 4); it is
+ *              normalised by the library
+ *   scale3     diagonal of S, all > 0                          (n x 3)
+ *   magnitude  c of Eq. 1, >= 0                                (n)          */
+typedef struct ugp_prims {
+  int64_t n;
+  const float* mean3;
+  const float* quat4;
+  const float* scale3;
+  const float* magnitude;
+} ugp_prims;
+
+/* Opaque BVH handle.  The handle is a small host object; every array it
+ * refers to lives in the caller's workspace, which must stay allocated and
+ * unmodified for as long as the handle is used. */
+typedef struct ugp_bvh ugp_bvh;
+
+typedef struct ugp_bvh_info {
+  int64_t n_prims;
+  int64_t n_nodes;        /* internal binary nodes */
+  float cutoff_k;         /* sqrt(-2 ln eps) of Eq. 4 */
+  float bounds_lo[3];     /* bounds of all bounding boxes */
+  float bounds_hi[3];
+  size_t persistent_bytes;/* workspace bytes the built BVH keeps using */
+  int64_t n_invalid;      /* primitives ignored as invalid (see ugp_build_bvh) */
+} ugp_bvh_info;
+
+/* Bytes of device workspace ugp_build_bvh needs for n_prims primitives
+ * (the BVH itself plus build temporaries).  Needs a current CUDA device;
+ * returns 0 if n_prims < 0 or the query fails. */
+size_t ugp_build_bvh_workspace_size(int64_t n_prims);
+
+/* Builds the acceleration structure over the primitives' bounding ellipsoids
+ * (Eq. 4 with threshold cutoff_eps, in (0, 1); the paper uses 0.01).
+ * Per primitive it precomputes the whitening matrix W = S^-1 R^T, so that
+ * (RS)^-1 (x - mu) = W (x - mu), the normaliser g0 = c / ((2 pi)^{3/2} s_x s_y s_z)
+ * of Eq. 1, and the bounding box of the k-ellipsoid.  The structure is a
+ * binary BVH (the paper uses a kd-tree, Sec. 5.1; the exact order-free
+ * sampling of ugp_sample_free_flight does not need non-overlapping nodes).
+ *   prims       host pointer to the device SoA description above
+ *   workspace   device buffer of at least ugp_build_bvh_workspace_size(n)
+ *               bytes, 256-byte aligned; holds the BVH after the call
+ *   out         host pointer; receives a new handle (free with ugp_bvh_release)
+ * The call enqueues the build on `stream` and returns; the handle is usable
+ * by later work on the same stream.  n_prims == 0 is allowed (every ray
+ * escapes).  A primitive with a non-finite mean, a zero or non-finite
+ * quaternion, a scale that is not finite and positive, or a magnitude that is
+ * negative or not finite is ignored by every query (it is never hit); the
+ * count is reported by ugp_bvh_get_info. */
+ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, void* workspace,
+                         size_t workspace_bytes, void* stream, ugp_bvh** out);
+
+/* Frees the host handle (the workspace stays the caller's). NULL is ignored. */
+void ugp_bvh_release(ugp_bvh* bvh);
+
+/* Fills *out (host).  Synchronous: waits for the build stream, then copies
+ * the scene bounds and the invalid-primitive count from the workspace. */
+ugp_status ugp_bvh_get_info(const ugp_bvh* bvh, ugp_bvh_info* out);
+
+/* Transmittance evaluation (Sec. 5.3, Eq. 7): for each ray r,
+ *   T_out[r] = max(0, 1 - 1/2 sum_k I_k(max(t0, t_k-), min(t1, t_k+)))
+ * where I_k is the closed-form ray integral of App. A over primitive k's
+ * clipped bounding-ellipsoid interval.  Order-free; traversal stops once the
+ * sum reaches 1 (T = 0).  Russian roulette is not applied (exact T).
+ *   o3, d3        float3 arrays (n_rays)
+ *   t0, t1        float arrays (n_rays), t0 <= t1
+ *   exclude_prim  int32 array (n_rays) or NULL: primitive skipped by that
+ *                 ray (the scattering primitive of Sec. 6), -1 for none
+ *   T_out         float array (n_rays)
+ *   status_out    uint8 array (n_rays) or NULL
+ * n_rays == 0 is allowed. */
+ugp_status ugp_trace_transmittance(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
+                                   const float* d3, const float* t0, const float* t1,
+                                   const int32_t* exclude_prim, float* T_out,
+                                   uint8_t* status_out, void* stream);
+
+/* Free-flight distribution sampling (Sec. 5.2, Eq. 8-10), exact and
+ * independent of traversal order.  With F(t) = 1/2 sum_k I_k(a_k, min(t, b_k))
+ * over the clipped intervals [a_k, b_k]:
+ *  - if F(t1) <= u the ray escapes: prim_out = -1, t_u_out = t1,
+ *    t_spawn_out = t1;
+ *  - otherwise t_u solves F(t_u) = u, and the primitive is drawn among those
+ *    whose interval contains t_u with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u}),
+ *    scanning them in ascending primitive index with the second uniform u2.
+ *    t_spawn_out is the centre of the chosen primitive's clipped interval,
+ *    where the paper spawns the scattered ray (Sec. 6).
+ * The chosen primitive k has probability 1/2 I_k(a_k, min(b_k, t_sat)), the
+ * saturating-distance clamp of Eq. 8.
+ *   u, u2         float arrays (n_rays) of uniforms in [0, 1)
+ *   prim_out      int32 array (n_rays); t_u_out, t_spawn_out float arrays
+ *   other arguments as for ugp_trace_transmittance. */
+ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
+                                  const float* d3, const float* t0, const float* t1,
+                                  const float* u, const float* u2, const int32_t* exclude_prim,
+                                  int32_t* prim_out, float* t_u_out, float* t_spawn_out,
+                                  uint8_t* status_out, void* stream);
+
+/* All clipped intervals along each ray (hit-set diagnostics).  For ray r,
+ * count_out[r] receives the number of primitives whose k-ellipsoid interval
+ * meets [t0, t1] (Eq. 4 cut-off, the same test as the queries above); the
+ * first min(count, cap) of them, in traversal order, are written to
+ * ids_out[r*cap + j], a_out[r*cap + j], b_out[r*cap + j] (the clipped
+ * interval [a, b]).
+ *   cap         >= 0; ids_out, a_out, b_out hold n_rays*cap elements (may be
+ *               NULL when cap == 0)
+ *   count_out   int32 array (n_rays)
+ *   other arguments as for ugp_trace_transmittance. */
+ugp_status ugp_collect_hits(const ugp_bvh* bvh, int64_t n_rays, const float* o3, const float* d3,
+                            const float* t0, const float* t1, const int32_t* exclude_prim,
+                            int32_t cap, int32_t* ids_out, float* a_out, float* b_out,
+                            int32_t* count_out, uint8_t* status_out, void* stream);
+
+/* Optional traversal statistics: when `counters` is a device pointer to 4
+ * zero-initialised uint64, later tracing calls on any stream add
+ *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
+ *   [3] traversal rounds
+ * to it (atomically).  NULL turns counting off (the default).  Host-side
+ * setting, not thread safe against concurrent tracing calls. */
+ugp_status ugp_set_trace_counters(unsigned long long* counters);
+
+/* Static description of a status code. */
+const char* ugp_status_string(ugp_status s);
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* ugp_last_error(void);
+/* Library version string. */
+const char* ugp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UGP_H_ */

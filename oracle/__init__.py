@@ -51,6 +51,7 @@ def lib():
         L.orc_sample_free_flight.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p,
                                              f32p, f32p, f32p, i32p, f32p, f32p, i32p, f64p,
                                              f64p, f64p, i32p]
+        L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
         L.orc_erfinv.argtypes = [C.c_double]
         L.orc_erfinv.restype = C.c_double
         _post_load(L)
@@ -176,6 +177,16 @@ def sample_free_flight(scene, rays, u, u2, exclude=None, eps=0.01):
                                  _ptr(prim, i32p), _ptr(tu, f64p), _ptr(ts, f64p), _ptr(fe, f64p),
                                  _ptr(na, i32p))
     return dict(prim=prim, t_u=tu, t_spawn=ts, F_end=fe, n_active=na)
+
+
+def prim_quadratic(scene, i, o, d, _sr=None):
+    """(A, t*, d2) of App. A for primitive i along the ray (o, d), unclipped."""
+    sr = _sr or _SceneRef(scene)
+    o = _c(o, np.float32)
+    d = _c(d, np.float32)
+    out = np.zeros(3)
+    lib().orc_prim_quadratic(sr.ref, int(i), _ptr(o, f32p), _ptr(d, f32p), _ptr(out, f64p))
+    return out
 
 
 def erfinv(y: float) -> float:

@@ -141,6 +141,12 @@ void orc_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, c
   }
 }
 
+// App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.
+void orc_prim_quadratic(const orc_scene* s, int64_t i, const float* o3, const float* d3, double* out3) {
+  const Prim p = make_prim(s->mean3 + 3 * i, s->quat4 + 4 * i, s->scale3 + 3 * i, s->magnitude[i]);
+  ray_prim_quadratic(p, load3(o3), load3(d3), &out3[0], &out3[1], &out3[2]);
+}
+
 double orc_erfinv(double y) { return erfinv(y); }
 
 }  // extern "C"

@@ -1,0 +1,409 @@
+// BVH construction over the primitives' bounding ellipsoids (Sec. 4.1, Eq. 4)
+// and the per-primitive precompute of Eq. 1-2.
+//
+// Steps, all on the caller's stream:
+//   1. k_prim_bounds   per primitive: rotation from the quaternion, bounding box of
+//                      the k-ellipsoid, block-reduced centroid bounds
+//   2. k_morton        30-bit Morton code of each box centre
+//   3. radix sort      (CUB, on the caller's workspace) of (code, index)
+//   4. k_hierarchy     binary radix tree over the sorted codes (Karras, HPG 2012)
+//   5. k_records       64-byte hot records in leaf order (W = S^-1 R^T, mu, g0, index)
+//   6. k_refit         bottom-up child boxes with one atomic counter per node
+#include <cub/cub.cuh>
+
+#include <math.h>
+#include <string.h>
+
+#include "ugp_internal.cuh"
+
+namespace ugp {
+namespace {
+
+
+struct Layout {
+  size_t prims, nodes, persistent;
+  size_t aabb, keys0, keys1, vals0, vals1, parent, flags, bounds, cub, total;
+  size_t cub_bytes;
+};
+
+__device__ __forceinline__ int f2o(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Rotation matrix (row-major) of the normalised quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float4 q, float R[9]) {
+  const float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+  const float w = q.x * inv, x = q.y * inv, y = q.z * inv, z = q.w * inv;
+  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ bool prim_valid(float3 m, float4 q, float3 s, float c) {
+  const float qn = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  return isfinite(m.x) && isfinite(m.y) && isfinite(m.z) && isfinite(qn) && qn > 1e-20f &&
+         isfinite(s.x) && isfinite(s.y) && isfinite(s.z) && s.x > 0.f && s.y > 0.f && s.z > 0.f &&
+         isfinite(c) && c >= 0.f;
+}
+
+__device__ __forceinline__ float3 ld3(const float* p, int64_t i) {
+  return make_float3(p[3 * i], p[3 * i + 1], p[3 * i + 2]);
+}
+__device__ __forceinline__ float4 ld4(const float* p, int64_t i) {
+  return make_float4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+}
+
+// Bounding box of the k-ellipsoid x = mu + k R S v, |v| = 1: half extent along axis i is
+// k * sqrt(sum_j (R_ij s_j)^2).  Widened by a few float32 ulps so the box stays
+// conservative for the float32 interval test.
+__global__ void k_prim_bounds(int64_t n, const float* __restrict__ mean3, const float* __restrict__ quat4,
+                              const float* __restrict__ scale3, const float* __restrict__ mag, float k,
+                              float4* __restrict__ aabb, int* __restrict__ bounds,
+                              unsigned long long* __restrict__ n_invalid) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  bool has = false;
+  if (i < n) {
+    const float3 m = ld3(mean3, i);
+    const float4 q = ld4(quat4, i);
+    const float3 s = ld3(scale3, i);
+    const float c = mag[i];
+    if (prim_valid(m, q, s, c)) {
+      float R[9];
+      quat_rot(q, R);
+      float e[3];
+      const float mm[3] = {m.x, m.y, m.z};
+      for (int r = 0; r < 3; ++r) {
+        const float a = R[3 * r] * s.x, b = R[3 * r + 1] * s.y, d = R[3 * r + 2] * s.z;
+        e[r] = k * sqrtf(a * a + b * b + d * d) * (1.f + 4e-6f) + 2e-7f * fabsf(mm[r]);
+      }
+      aabb[2 * i] = make_float4(m.x - e[0], m.y - e[1], m.z - e[2], 0.f);
+      aabb[2 * i + 1] = make_float4(m.x + e[0], m.y + e[1], m.z + e[2], 0.f);
+      cx = m.x; cy = m.y; cz = m.z;
+      has = true;
+    } else {
+      // An invalid primitive keeps a point box; its record is flagged and never hit.
+      const float x = isfinite(m.x) ? m.x : 0.f, y = isfinite(m.y) ? m.y : 0.f,
+                  z = isfinite(m.z) ? m.z : 0.f;
+      aabb[2 * i] = make_float4(x, y, z, 0.f);
+      aabb[2 * i + 1] = make_float4(x, y, z, 0.f);
+      atomicAdd(n_invalid, 1ull);
+    }
+  }
+  // Centroid bounds: warp min-reduction of the ordered-int encodings, one atomic per warp.
+  const float big = 3.0e38f;
+  const float v[6] = {has ? cx : big, has ? cy : big, has ? cz : big,
+                      has ? -cx : big, has ? -cy : big, has ? -cz : big};
+  for (int a = 0; a < 6; ++a) {
+    const int r = __reduce_min_sync(0xffffffffu, f2o(v[a]));
+    if ((threadIdx.x & 31) == 0) atomicMin(&bounds[a], r);
+  }
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t v) {
+  v = (v * 0x00010001u) & 0xFF0000FFu;
+  v = (v * 0x00000101u) & 0x0F00F00Fu;
+  v = (v * 0x00000011u) & 0xC30C30C3u;
+  v = (v * 0x00000005u) & 0x49249249u;
+  return v;
+}
+
+__global__ void k_morton(int64_t n, const float4* __restrict__ aabb, const int* __restrict__ bounds,
+                         uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float lo[3] = {o2f(bounds[0]), o2f(bounds[1]), o2f(bounds[2])};
+  const float hi[3] = {-o2f(bounds[3]), -o2f(bounds[4]), -o2f(bounds[5])};
+  const float4 a = aabb[2 * i], b = aabb[2 * i + 1];
+  const float c[3] = {0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)};
+  uint32_t code = 0;
+  for (int ax = 0; ax < 3; ++ax) {
+    const float ext = hi[ax] - lo[ax];
+    float t = ext > 0.f ? (c[ax] - lo[ax]) / ext : 0.5f;
+    t = fminf(fmaxf(t * 1024.f, 0.f), 1023.f);
+    code |= expand10(uint32_t(t)) << (2 - ax);
+  }
+  keys[i] = code;
+  vals[i] = int32_t(i);
+}
+
+__device__ __forceinline__ int delta(const uint32_t* __restrict__ keys, int n, int i, int j) {
+  if (j < 0 || j >= n) return -1;
+  const uint32_t a = keys[i], b = keys[j];
+  if (a == b) return 32 + __clz(uint32_t(i) ^ uint32_t(j));
+  return __clz(a ^ b);
+}
+
+// One internal node per thread (n - 1 of them); node 0 is the root.
+__global__ void k_hierarchy(int n, const uint32_t* __restrict__ keys, int4* __restrict__ nodes,
+                            int32_t* __restrict__ parent_int, int32_t* __restrict__ parent_leaf) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+  const int dmin = delta(keys, n, i, i - d);
+  int lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int l = 0;
+  for (int t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  const int j = i + l * d;
+  const int dnode = delta(keys, n, i, j);
+  int s = 0;
+  for (int div = 2;; div <<= 1) {
+    const int t = (l + div - 1) / div;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    if (t <= 1) break;
+  }
+  const int g = i + s * d + min(d, 0);
+  const int lo = min(i, j), hi = max(i, j);
+  int c0, c1;
+  if (lo == g) { c0 = ~g;      parent_leaf[g] = (i << 1) | 0; }
+  else         { c0 = g;       parent_int[g] = (i << 1) | 0; }
+  if (hi == g + 1) { c1 = ~(g + 1); parent_leaf[g + 1] = (i << 1) | 1; }
+  else             { c1 = g + 1;    parent_int[g + 1] = (i << 1) | 1; }
+  nodes[4 * i + 3] = make_int4(c0, c1, 0, 0);
+  if (i == 0) parent_int[0] = -1;
+}
+
+__global__ void k_single_root(int4* nodes, int32_t* parent_leaf) {
+  nodes[3] = make_int4(~0, kEmptyChild, 0, 0);
+  parent_leaf[0] = 0;
+}
+
+// Hot record of the primitive in leaf slot `slot` (layout in ugp_internal.cuh).
+__global__ void k_records(int64_t n, const int32_t* __restrict__ order, const float* __restrict__ mean3,
+                          const float* __restrict__ quat4, const float* __restrict__ scale3,
+                          const float* __restrict__ mag, float4* __restrict__ recs) {
+  const int64_t slot = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (slot >= n) return;
+  const int64_t i = order[slot];
+  const float3 m = ld3(mean3, i);
+  const float4 q = ld4(quat4, i);
+  const float3 s = ld3(scale3, i);
+  const float c = mag[i];
+  float4 r0, r1, r2, r3;
+  if (prim_valid(m, q, s, c)) {
+    float R[9];
+    quat_rot(q, R);
+    const float is[3] = {1.f / s.x, 1.f / s.y, 1.f / s.z};
+    // W_ij = R_ji / s_i
+    r0 = make_float4(R[0] * is[0], R[3] * is[0], R[6] * is[0], m.x);
+    r1 = make_float4(R[1] * is[1], R[4] * is[1], R[7] * is[1], m.y);
+    r2 = make_float4(R[2] * is[2], R[5] * is[2], R[8] * is[2], m.z);
+    // (2 pi)^{3/2} = 15.749609945722419
+    const float g0 = c / (15.749609945722419f * s.x * s.y * s.z);
+    r3 = make_float4(g0, __int_as_float(int(i)), 1.f, 0.f);
+  } else {
+    r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r3 = make_float4(0.f, __int_as_float(int(i)), 0.f, 0.f);
+  }
+  recs[4 * slot + 0] = r0;
+  recs[4 * slot + 1] = r1;
+  recs[4 * slot + 2] = r2;
+  recs[4 * slot + 3] = r3;
+}
+
+__device__ __forceinline__ void store_child_box(float* node, int side, const float b[6]) {
+  float* p = node + (side ? 6 : 0);
+  for (int k = 0; k < 6; ++k) p[k] = b[k];
+}
+
+// Bottom-up boxes: each leaf writes its box into its parent, and the second of a node's
+// two children to arrive forms the union and continues upwards.
+__global__ void k_refit(int n, const int32_t* __restrict__ order, const float4* __restrict__ aabb,
+                        const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
+                        int* __restrict__ flags, float* __restrict__ nodes_f, float* __restrict__ root_box) {
+  const int slot = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (slot >= n) return;
+  const int i = order[slot];
+  const float4 lo = aabb[2 * i], hi = aabb[2 * i + 1];
+  float b[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+  int ps = parent_leaf[slot];
+  while (true) {
+    const int p = ps >> 1, side = ps & 1;
+    store_child_box(nodes_f + 16 * size_t(p), side, b);
+    __threadfence();
+    if (atomicAdd(&flags[p], 1) == 0) return;
+    __threadfence();
+    const float* nd = nodes_f + 16 * size_t(p);
+    float c0[6], c1[6];
+    for (int k = 0; k < 6; ++k) { c0[k] = __ldcg(nd + k); c1[k] = __ldcg(nd + 6 + k); }
+    const int4 ch = *reinterpret_cast<const int4*>(nd + 12);
+    if (ch.y == kEmptyChild) {
+      for (int k = 0; k < 6; ++k) b[k] = c0[k];
+    } else {
+      for (int k = 0; k < 3; ++k) { b[k] = fminf(c0[k], c1[k]); b[3 + k] = fmaxf(c0[3 + k], c1[3 + k]); }
+    }
+    ps = parent_int[p];
+    if (ps < 0) {
+      for (int k = 0; k < 6; ++k) root_box[k] = b[k];
+      return;
+    }
+  }
+}
+
+__global__ void k_init_bounds(int* bounds, int* n_flags_zero_dummy) {
+  if (threadIdx.x < 6) bounds[threadIdx.x] = f2o(3.0e38f);
+}
+
+// For n == 1 the single child needs its box too; the empty child gets a box nobody reaches.
+__global__ void k_single_refit(const float4* __restrict__ aabb, float* nodes_f, float* root_box) {
+  const float4 lo = aabb[0], hi = aabb[1];
+  const float b[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+  for (int k = 0; k < 6; ++k) { nodes_f[k] = b[k]; nodes_f[6 + k] = 0.f; root_box[k] = b[k]; }
+}
+
+bool layout_for(int64_t n, Layout* L) {
+  const size_t N = size_t(n);
+  const size_t ni = N > 1 ? N - 1 : 1;
+  size_t off = 0;
+  L->prims = off;      off = align256(off + N * 64);
+  L->nodes = off;      off = align256(off + ni * 64);
+  L->bounds = off;     off = align256(off + 64);   // 6 ordered-int bounds, root box, invalid count
+  L->persistent = off;
+  L->aabb = off;       off = align256(off + N * 32);
+  L->keys0 = off;      off = align256(off + N * 4);
+  L->keys1 = off;      off = align256(off + N * 4);
+  L->vals0 = off;      off = align256(off + N * 4);
+  L->vals1 = off;      off = align256(off + N * 4);
+  L->parent = off;     off = align256(off + (ni + N) * 4);
+  L->flags = off;      off = align256(off + ni * 4);
+  L->cub_bytes = 0;
+  if (N > 1) {
+    if (cub::DeviceRadixSort::SortPairs(nullptr, L->cub_bytes, (uint32_t*)nullptr, (uint32_t*)nullptr,
+                                        (int32_t*)nullptr, (int32_t*)nullptr, int(N), 0, 30) != cudaSuccess)
+      return false;
+  }
+  L->cub = off;        off = align256(off + L->cub_bytes);
+  L->total = off;
+  return true;
+}
+
+}  // namespace
+}  // namespace ugp
+
+using namespace ugp;
+
+extern "C" size_t ugp_build_bvh_workspace_size(int64_t n_prims) {
+  if (n_prims < 0 || n_prims > (int64_t(1) << 30)) return 0;
+  Layout L;
+  if (!layout_for(n_prims, &L)) return 0;
+  return L.total;
+}
+
+extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, void* workspace,
+                                    size_t workspace_bytes, void* stream_, ugp_bvh** out) {
+  clear_error();
+  if (!prims || !out) return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: prims and out must be non-NULL");
+  *out = nullptr;
+  const int64_t n = prims->n;
+  if (n < 0 || n > (int64_t(1) << 30))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: n_prims %lld out of range [0, 2^30]", (long long)n);
+  if (!(cutoff_eps > 0.f && cutoff_eps < 1.f))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: cutoff_eps %g not in (0, 1)", double(cutoff_eps));
+  if (n > 0 && (!prims->mean3 || !prims->quat4 || !prims->scale3 || !prims->magnitude))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: NULL primitive array");
+  if (n > 0 && !workspace) return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: NULL workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) & 255)
+    return fail(UGP_ERR_INVALID_ARG, "ugp_build_bvh: workspace must be 256-byte aligned");
+  Layout L;
+  if (!layout_for(n, &L)) return fail(UGP_ERR_CUDA, "ugp_build_bvh: sort workspace query failed");
+  if (workspace_bytes < L.total)
+    return fail(UGP_ERR_WORKSPACE_TOO_SMALL, "ugp_build_bvh: need %zu bytes, got %zu", L.total,
+                workspace_bytes);
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  const double kd = sqrt(-2.0 * log(double(cutoff_eps)));
+
+  ugp_bvh* b = new ugp_bvh();
+  b->magic = kBvhMagic;
+  UGP_CUDA_CHECK(cudaGetDevice(&b->device));
+  b->n_prims = n;
+  b->n_nodes = n > 1 ? n - 1 : (n == 1 ? 1 : 0);
+  b->k = float(kd);
+  b->k2 = float(kd * kd);
+  char* ws = static_cast<char*>(workspace);
+  b->prims = reinterpret_cast<const float4*>(ws + L.prims);
+  b->nodes = reinterpret_cast<const float4*>(ws + L.nodes);
+  b->persistent_bytes = L.persistent;
+  b->bounds_dev = reinterpret_cast<const float*>(ws + L.bounds);
+  if (n == 0) {
+    *out = b;
+    return UGP_OK;
+  }
+  float4* aabb = reinterpret_cast<float4*>(ws + L.aabb);
+  int* bounds = reinterpret_cast<int*>(ws + L.bounds);
+  float* root_box = reinterpret_cast<float*>(ws + L.bounds + 32);
+  unsigned long long* n_invalid = reinterpret_cast<unsigned long long*>(ws + L.bounds + 56);
+  uint32_t* k0 = reinterpret_cast<uint32_t*>(ws + L.keys0);
+  uint32_t* k1 = reinterpret_cast<uint32_t*>(ws + L.keys1);
+  int32_t* v0 = reinterpret_cast<int32_t*>(ws + L.vals0);
+  int32_t* v1 = reinterpret_cast<int32_t*>(ws + L.vals1);
+  const size_t ni = n > 1 ? size_t(n - 1) : 1;
+  int32_t* parent_int = reinterpret_cast<int32_t*>(ws + L.parent);
+  int32_t* parent_leaf = parent_int + ni;
+  int* flags = reinterpret_cast<int*>(ws + L.flags);
+
+  const int T = 256;
+  const unsigned G = unsigned((n + T - 1) / T);
+  UGP_CUDA_CHECK(cudaMemsetAsync(ws + L.bounds, 0, 64, st));
+  k_init_bounds<<<1, 32, 0, st>>>(bounds, nullptr);
+  k_prim_bounds<<<G, T, 0, st>>>(n, prims->mean3, prims->quat4, prims->scale3, prims->magnitude, b->k,
+                                 aabb, bounds, n_invalid);
+  UGP_CUDA_CHECK(cudaGetLastError());
+  int4* nodes_i = reinterpret_cast<int4*>(ws + L.nodes);
+  float* nodes_f = reinterpret_cast<float*>(ws + L.nodes);
+  int32_t* order = v0;
+  if (n == 1) {
+    UGP_CUDA_CHECK(cudaMemsetAsync(v0, 0, 4, st));
+    k_single_root<<<1, 1, 0, st>>>(nodes_i, parent_leaf);
+    k_single_refit<<<1, 1, 0, st>>>(aabb, nodes_f, root_box);
+  } else {
+    k_morton<<<G, T, 0, st>>>(n, aabb, bounds, k0, v0);
+    UGP_CUDA_CHECK(cudaGetLastError());
+    size_t cub_bytes = L.cub_bytes;
+    UGP_CUDA_CHECK(cub::DeviceRadixSort::SortPairs(ws + L.cub, cub_bytes, k0, k1, v0, v1, int(n), 0, 30, st));
+    order = v1;
+    k_hierarchy<<<unsigned((n - 1 + T - 1) / T), T, 0, st>>>(int(n), k1, nodes_i, parent_int, parent_leaf);
+    UGP_CUDA_CHECK(cudaGetLastError());
+    UGP_CUDA_CHECK(cudaMemsetAsync(flags, 0, (n - 1) * 4, st));
+    k_refit<<<G, T, 0, st>>>(int(n), order, aabb, parent_int, parent_leaf, flags, nodes_f, root_box);
+    UGP_CUDA_CHECK(cudaGetLastError());
+  }
+  k_records<<<G, T, 0, st>>>(n, order, prims->mean3, prims->quat4, prims->scale3, prims->magnitude,
+                             reinterpret_cast<float4*>(ws + L.prims));
+  UGP_CUDA_CHECK(cudaGetLastError());
+  b->stream = st;
+  *out = b;
+  return UGP_OK;
+}
+
+extern "C" void ugp_bvh_release(ugp_bvh* bvh) {
+  if (bvh && bvh->magic == kBvhMagic) {
+    bvh->magic = 0;
+    delete bvh;
+  }
+}
+
+extern "C" ugp_status ugp_bvh_get_info(const ugp_bvh* bvh, ugp_bvh_info* out) {
+  clear_error();
+  if (!valid_bvh(bvh)) return fail(UGP_ERR_NOT_BUILT, "ugp_bvh_get_info: invalid handle");
+  if (!out) return fail(UGP_ERR_INVALID_ARG, "ugp_bvh_get_info: NULL out");
+  out->n_prims = bvh->n_prims;
+  out->n_nodes = bvh->n_nodes;
+  out->cutoff_k = bvh->k;
+  out->persistent_bytes = bvh->persistent_bytes;
+  out->n_invalid = 0;
+  for (int k = 0; k < 3; ++k) { out->bounds_lo[k] = 0.f; out->bounds_hi[k] = 0.f; }
+  if (bvh->n_prims > 0) {
+    float hb[16];
+    UGP_CUDA_CHECK(cudaStreamSynchronize(bvh->stream));
+    UGP_CUDA_CHECK(cudaMemcpy(hb, bvh->bounds_dev, 64, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) { out->bounds_lo[k] = hb[8 + k]; out->bounds_hi[k] = hb[11 + k]; }
+    unsigned long long inv;
+    memcpy(&inv, reinterpret_cast<const char*>(hb) + 56, 8);
+    out->n_invalid = int64_t(inv);
+  }
+  return UGP_OK;
+}

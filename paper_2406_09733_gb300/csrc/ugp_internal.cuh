@@ -1,0 +1,68 @@
+// Internal declarations shared by the CUDA translation units of the ugp library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ugp.h"
+
+namespace ugp {
+
+constexpr uint32_t kBvhMagic = 0x55475042u;  // "UGPB"
+
+// Device layout of one primitive ("hot" record, 64 B, leaf order):
+//   r0 = (W00 W01 W02 mu.x)
+//   r1 = (W10 W11 W12 mu.y)
+//   r2 = (W20 W21 W22 mu.z)
+//   r3 = (g0, original index as int bits, 0, 0)
+// W = S^-1 R^T is the whitening matrix of Eq. 2, g0 the normaliser of Eq. 1.
+constexpr int kPrimF4 = 4;
+
+// Device layout of one binary BVH node (64 B): the bounding boxes of both
+// children and the child references.
+//   n0 = (c0.lo.x c0.lo.y c0.lo.z c0.hi.x)
+//   n1 = (c0.hi.y c0.hi.z c1.lo.x c1.lo.y)
+//   n2 = (c1.lo.z c1.hi.x c1.hi.y c1.hi.z)
+//   n3 = (child0, child1, 0, 0) as int bits; child >= 0 is an internal node,
+//        child < 0 is the leaf holding primitive slot ~child.
+constexpr int kNodeF4 = 4;
+// Child reference of the unused second child of a one-primitive tree's root.
+constexpr int kEmptyChild = INT32_MIN;
+
+}  // namespace ugp
+
+struct ugp_bvh {
+  uint32_t magic;
+  int device;
+  int64_t n_prims;
+  int64_t n_nodes;
+  float k;
+  float k2;
+  const float4* nodes;
+  const float4* prims;
+  const float* bounds_dev;   // in the workspace: ordered-int centroid bounds, root box, invalid count
+  cudaStream_t stream;       // build stream, used only by synchronous info queries
+  size_t persistent_bytes;
+};
+
+namespace ugp {
+
+// Thread-local error message helpers (defined in ugp_api.cu).
+ugp_status fail(ugp_status s, const char* fmt, ...);
+ugp_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+// Trace statistics pointer (device), or nullptr.
+unsigned long long* trace_counters();
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool valid_bvh(const ugp_bvh* b);
+
+}  // namespace ugp
+
+#define UGP_CUDA_CHECK(call)                                  \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::ugp::cuda_fail(_e, #call); \
+  } while (0)

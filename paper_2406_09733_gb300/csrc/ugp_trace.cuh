@@ -1,0 +1,35 @@
+// Launch interface of the tracing kernels (shared by the C entry points and the renderer).
+#pragma once
+
+#include "ugp_internal.cuh"
+
+namespace ugp {
+
+constexpr int kTrBlock = 128;      // transmittance: threads per block
+constexpr int kTrStack = 64;       // transmittance: traversal stack depth
+constexpr int kFFBlock = 64;       // free flight: threads per block
+constexpr int kK = 16;             // free flight: interval buffer per ray
+constexpr int kFFStack = 48;       // free flight: traversal stack depth
+constexpr int kFFMaxRounds = 256;  // free flight: collection rounds per ray
+constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
+
+struct TraceScene {
+  const float4* nodes;
+  const float4* prims;
+  int64_t n_prims;
+  int64_t n_nodes;
+  float k2;
+};
+
+TraceScene trace_scene(const ugp_bvh* b);
+
+ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
+                                const float* t0, const float* t1, const int32_t* excl, float* T,
+                                uint8_t* st, cudaStream_t stream);
+
+ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
+                              const float* t0, const float* t1, const float* u, const float* u2,
+                              const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
+                              cudaStream_t stream);
+
+}  // namespace ugp

@@ -1,0 +1,220 @@
+"""Thin Python binding of the ugp C ABI (``include/ugp.h``).
+
+Argument marshalling only: tensors are checked for device, dtype and
+contiguity, outputs are allocated with torch, and raw device pointers plus the
+current CUDA stream are handed to ``libugp.so``.  Every step of the hot path
+runs in the library's CUDA kernels; there is no fallback of any kind, and
+loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_LIB = None
+vp = C.c_void_p
+
+
+class UgpPrims(C.Structure):
+    _fields_ = [("n", C.c_int64), ("mean3", vp), ("quat4", vp), ("scale3", vp), ("magnitude", vp)]
+
+
+class UgpBvhInfo(C.Structure):
+    _fields_ = [("n_prims", C.c_int64), ("n_nodes", C.c_int64), ("cutoff_k", C.c_float),
+                ("bounds_lo", C.c_float * 3), ("bounds_hi", C.c_float * 3),
+                ("persistent_bytes", C.c_size_t), ("n_invalid", C.c_int64)]
+
+
+class UgpError(RuntimeError):
+    pass
+
+
+RAY_OK, RAY_STACK_OVERFLOW, RAY_BUFFER_OVERFLOW, RAY_ITER_LIMIT = 0, 1, 2, 3
+
+
+def lib():
+    """Loads ``libugp.so`` (built in-tree by ``build.build()``)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise UgpError(f"CUDA library not built: {_build.LIB} is missing "
+                           "(run __graft_entry__.build())")
+        L = C.CDLL(_build.LIB)
+        L.ugp_status_string.restype = C.c_char_p
+        L.ugp_status_string.argtypes = [C.c_int]
+        L.ugp_last_error.restype = C.c_char_p
+        L.ugp_version.restype = C.c_char_p
+        L.ugp_build_bvh_workspace_size.restype = C.c_size_t
+        L.ugp_build_bvh_workspace_size.argtypes = [C.c_int64]
+        L.ugp_build_bvh.restype = C.c_int
+        L.ugp_build_bvh.argtypes = [C.POINTER(UgpPrims), C.c_float, vp, C.c_size_t, vp,
+                                    C.POINTER(vp)]
+        L.ugp_bvh_release.argtypes = [vp]
+        L.ugp_bvh_release.restype = None
+        L.ugp_bvh_get_info.restype = C.c_int
+        L.ugp_bvh_get_info.argtypes = [vp, C.POINTER(UgpBvhInfo)]
+        L.ugp_trace_transmittance.restype = C.c_int
+        L.ugp_trace_transmittance.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ugp_sample_free_flight.restype = C.c_int
+        L.ugp_sample_free_flight.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                             vp, vp]
+        L.ugp_collect_hits.restype = C.c_int
+        L.ugp_collect_hits.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp,
+                                       vp, vp, vp]
+        L.ugp_set_trace_counters.restype = C.c_int
+        L.ugp_set_trace_counters.argtypes = [vp]
+        for fn in _EXTRA:
+            fn(L)
+        _LIB = L
+    return _LIB
+
+
+_EXTRA = []
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = lib()
+        raise UgpError(f"{what}: {L.ugp_status_string(status).decode()} "
+                       f"({L.ugp_last_error().decode()})")
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t, dtype, name, shape_last=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
+        raise ValueError(f"{name} must have shape (n, {shape_last})")
+    return t
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Bvh:
+    """A built BVH: the library handle plus the workspace tensor that holds it."""
+
+    def __init__(self, handle: int, workspace: torch.Tensor, n: int, inputs):
+        self.handle = handle
+        self.workspace = workspace
+        self.n = n
+        self._inputs = inputs  # keep the primitive arrays alive while the build runs
+
+    def info(self) -> dict:
+        inf = UgpBvhInfo()
+        _check(lib().ugp_bvh_get_info(C.c_void_p(self.handle), C.byref(inf)), "ugp_bvh_get_info")
+        return dict(n_prims=inf.n_prims, n_nodes=inf.n_nodes, cutoff_k=inf.cutoff_k,
+                    bounds_lo=list(inf.bounds_lo), bounds_hi=list(inf.bounds_hi),
+                    persistent_bytes=inf.persistent_bytes, n_invalid=inf.n_invalid)
+
+    def release(self):
+        if self.handle:
+            lib().ugp_bvh_release(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+def build_bvh_workspace_size(n: int) -> int:
+    return int(lib().ugp_build_bvh_workspace_size(int(n)))
+
+
+def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=None) -> Bvh:
+    n = int(mean.shape[0])
+    _dev(mean, torch.float32, "mean", 3)
+    _dev(quat, torch.float32, "quat", 4)
+    _dev(scale, torch.float32, "scale", 3)
+    _dev(magnitude, torch.float32, "magnitude")
+    ws_bytes = build_bvh_workspace_size(n)
+    if ws_bytes == 0:
+        raise UgpError("ugp_build_bvh_workspace_size failed")
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=mean.device)
+    prims = UgpPrims(n, _p(mean), _p(quat), _p(scale), _p(magnitude))
+    h = vp()
+    _check(lib().ugp_build_bvh(C.byref(prims), float(cutoff_eps), _p(ws), ws_bytes,
+                               C.c_void_p(_stream(stream)), C.byref(h)), "ugp_build_bvh")
+    return Bvh(h.value, ws, n, (mean, quat, scale, magnitude))
+
+
+def trace_transmittance(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
+    n = int(o.shape[0])
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    _dev(t0, torch.float32, "t0")
+    _dev(t1, torch.float32, "t1")
+    _dev(exclude, torch.int32, "exclude")
+    T = torch.empty(n, dtype=torch.float32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    _check(lib().ugp_trace_transmittance(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
+                                         _p(exclude), _p(T), _p(st), C.c_void_p(_stream(stream))),
+           "ugp_trace_transmittance")
+    return T, st
+
+
+def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None):
+    n = int(o.shape[0])
+    for t, nm in ((t0, "t0"), (t1, "t1"), (u, "u"), (u2, "u2")):
+        _dev(t, torch.float32, nm)
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    _dev(exclude, torch.int32, "exclude")
+    prim = torch.empty(n, dtype=torch.int32, device=o.device)
+    tu = torch.empty(n, dtype=torch.float32, device=o.device)
+    tsp = torch.empty(n, dtype=torch.float32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    _check(lib().ugp_sample_free_flight(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
+                                        _p(u), _p(u2), _p(exclude), _p(prim), _p(tu), _p(tsp),
+                                        _p(st), C.c_void_p(_stream(stream))),
+           "ugp_sample_free_flight")
+    return prim, tu, tsp, st
+
+
+def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
+    """All clipped intervals per ray: (ids, a, b) of shape (n, cap), count (n,), status."""
+    n = int(o.shape[0])
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    _dev(t0, torch.float32, "t0")
+    _dev(t1, torch.float32, "t1")
+    _dev(exclude, torch.int32, "exclude")
+    ids = torch.full((n, cap), -1, dtype=torch.int32, device=o.device)
+    a = torch.zeros((n, cap), dtype=torch.float32, device=o.device)
+    b = torch.zeros((n, cap), dtype=torch.float32, device=o.device)
+    cnt = torch.empty(n, dtype=torch.int32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    _check(lib().ugp_collect_hits(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
+                                  _p(exclude), int(cap), _p(ids), _p(a), _p(b), _p(cnt), _p(st),
+                                  C.c_void_p(_stream(stream))), "ugp_collect_hits")
+    return ids, a, b, cnt, st
+
+
+def set_trace_counters(counters=None):
+    """Turns traversal statistics on (a CUDA uint64/int64 tensor of 4 zeros) or off (None)."""
+    if counters is not None:
+        _dev(counters, torch.int64, "counters")
+        if counters.numel() < 4:
+            raise ValueError("counters needs 4 elements")
+    _check(lib().ugp_set_trace_counters(_p(counters)), "ugp_set_trace_counters")
+
+
+def version() -> str:
+    return lib().ugp_version().decode()

@@ -1,0 +1,55 @@
+"""The C-ABI library loads and exports every entry point include/ugp.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ugp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(ugp_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libugp():
+    import torch  # noqa: F401  (loads the CUDA runtime the library links against)
+    from paper_2406_09733_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for must in ("ugp_build_bvh", "ugp_trace_transmittance", "ugp_sample_free_flight"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(libugp):
+    missing = [n for n in declared_functions() if not hasattr(libugp, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_errors_without_gpu(libugp):
+    libugp.ugp_status_string.restype = ctypes.c_char_p
+    libugp.ugp_last_error.restype = ctypes.c_char_p
+    assert libugp.ugp_status_string(0) == b"ok"
+    assert libugp.ugp_status_string(6).startswith(b"BVH")
+    # argument validation happens on the host before any device work
+    libugp.ugp_trace_transmittance.restype = ctypes.c_int
+    st = libugp.ugp_trace_transmittance(None, ctypes.c_int64(1), None, None, None, None, None,
+                                        None, None, None)
+    assert st == 6
+    assert b"invalid BVH" in libugp.ugp_last_error()
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2406_09733_gb300 import ugp, build
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(ugp, "_LIB", None)
+    with pytest.raises(ugp.UgpError):
+        ugp.lib()

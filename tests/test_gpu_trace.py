@@ -1,0 +1,308 @@
+"""GPU parity of the BVH build, transmittance and free-flight sampling against the FP64 oracle.
+
+Tolerances (from the float32 arithmetic of the kernels):
+  * transmittance T: |T - T_ref| <= 1e-5 * max(T_ref, 1 - T_ref)
+  * t_u, t_spawn:    |t - t_ref| <= 1e-5 * (t1 - t0)
+  * hit sets: identical except primitives in the epsilon-band of the cut-off,
+    |sqrt(d2) - k| / k < 1e-5, or with an end point within 1e-5 (t1 - t0) of t0 / t1
+  * sampled primitive: identical except where the oracle itself changes its answer
+    when u or u2 moves by 1e-5 (a rounding-level boundary).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2406_09733_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+EPS = 0.01
+K = math.sqrt(-2 * math.log(EPS))
+REL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_09733_gb300 import build, ugp
+    build.build()
+    ugp.lib()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def build_scene(torch, s):
+    from paper_2406_09733_gb300 import ugp
+    return ugp.build_bvh(dev(torch, s.mean), dev(torch, s.quat), dev(torch, s.scale),
+                         dev(torch, s.magnitude))
+
+
+def read_bvh(torch, bvh, n):
+    """Host copies of the hot records and nodes (internal layout: records, then nodes)."""
+    ws = bvh.workspace.cpu().numpy()
+    al = lambda x: (x + 255) & ~255
+    recs = ws[: n * 64].view(np.float32).reshape(n, 16)
+    nn = max(n - 1, 1)
+    off = al(n * 64)
+    nodes = ws[off: off + nn * 64].view(np.float32).reshape(nn, 16)
+    return recs, nodes
+
+
+def test_bvh_structure_and_precompute(gpu, orc):
+    torch = gpu
+    for s in (scenes.tiny_scene(), scenes.tiny_scene(n=777, seed=3), scenes.tiny_scene(n=2, seed=4)):
+        bvh = build_scene(torch, s)
+        torch.cuda.synchronize()
+        n = s.n
+        recs, nodes = read_bvh(torch, bvh, n)
+        W_ref, g0_ref, aabb_ref = orc.prim_setup(s, EPS)
+        ids = recs[:, 13].view(np.int32)
+        assert sorted(ids.tolist()) == list(range(n))
+        W = np.stack([recs[:, 0:3], recs[:, 4:7], recs[:, 8:11]], 1).astype(np.float64)
+        np.testing.assert_allclose(W, W_ref[ids], rtol=2e-6, atol=2e-6 * np.abs(W_ref).max())
+        np.testing.assert_allclose(recs[:, [3, 7, 11]], s.mean[ids], rtol=0, atol=0)
+        np.testing.assert_allclose(recs[:, 12], g0_ref[ids], rtol=2e-6)
+        # tree: every leaf reached once, child boxes contain what is below them
+        ch = nodes[:, 12:14].view(np.int32)
+        seen = np.zeros(n, int)
+        stack = [0]
+        visited = 0
+        while stack:
+            i = stack.pop()
+            visited += 1
+            for c in range(2):
+                ref = ch[i, c]
+                if ref == np.iinfo(np.int32).min:
+                    continue
+                box = nodes[i, 6 * c: 6 * c + 6].astype(np.float64)
+                if ref < 0:
+                    slot = ~ref
+                    seen[slot] += 1
+                    pid = ids[slot]
+                    assert np.all(box[:3] <= aabb_ref[pid, :3] + 1e-6)
+                    assert np.all(box[3:] >= aabb_ref[pid, 3:] - 1e-6)
+                else:
+                    sub = nodes[ref]
+                    for cc in range(2):
+                        if ch[ref, cc] == np.iinfo(np.int32).min:
+                            continue
+                        b2 = sub[6 * cc: 6 * cc + 6]
+                        assert np.all(box[:3] <= b2[:3]) and np.all(box[3:] >= b2[3:])
+                    stack.append(ref)
+        assert np.all(seen == 1)
+        info = bvh.info()
+        assert info["n_prims"] == n and info["n_invalid"] == 0
+        np.testing.assert_allclose(info["bounds_lo"], aabb_ref[:, :3].min(0), atol=1e-5)
+        np.testing.assert_allclose(info["bounds_hi"], aabb_ref[:, 3:].max(0), atol=1e-5)
+
+
+def _t_check(T, T_ref):
+    err = np.abs(T.astype(np.float64) - T_ref) / np.maximum(np.maximum(T_ref, 1 - T_ref), 1e-30)
+    return err
+
+
+def test_transmittance_parity_tiny(gpu, orc):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene()
+    bvh = build_scene(torch, s)
+    r = scenes.random_rays(20011, seed=11)       # several blocks and a ragged tail
+    T, st = ugp.trace_transmittance(bvh, dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0),
+                                    dev(torch, r.t1))
+    T_ref, tau, nh = orc.transmittance(s, r)
+    assert st.cpu().numpy().max() == 0
+    err = _t_check(T.cpu().numpy(), T_ref)
+    assert err.max() <= REL, (err.max(), np.argmax(err))
+    assert (nh > 0).mean() > 0.5 and (T_ref == 0).sum() > 0   # both regimes are exercised
+
+
+def test_transmittance_with_exclusion_and_inside_origins(gpu, orc):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene(seed=5)
+    rng = np.random.default_rng(5)
+    n = 4099
+    pid = rng.integers(0, s.n, n).astype(np.int32)
+    o = s.mean[pid] + rng.normal(scale=0.005, size=(n, 3))
+    d = rng.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t1 = rng.uniform(0.05, 1.5, n)
+    r = scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
+                    t1.astype(np.float32))
+    T, st = ugp.trace_transmittance(bvh := build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                    dev(torch, r.t0), dev(torch, r.t1), exclude=dev(torch, pid))
+    T_ref, _, _ = orc.transmittance(s, r, exclude=pid)
+    err = _t_check(T.cpu().numpy(), T_ref)
+    assert err.max() <= REL, err.max()
+    # excluding matters: without it, T changes for most rays
+    T2, _ = ugp.trace_transmittance(bvh, dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0),
+                                    dev(torch, r.t1))
+    assert (np.abs(T2.cpu().numpy() - T.cpu().numpy()) > 1e-3).mean() > 0.5
+
+
+def test_hit_sets_match_brute_force(gpu, orc):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene()
+    bvh = build_scene(torch, s)
+    r = scenes.random_rays(10000, seed=12)
+    cap = 128
+    ids, a, b, cnt, st = ugp.collect_hits(bvh, dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0),
+                                          dev(torch, r.t1), cap)
+    ids, a, b, cnt = (x.cpu().numpy() for x in (ids, a, b, cnt))
+    assert cnt.max() <= cap and st.cpu().numpy().max() == 0
+    sr = orc._SceneRef(s)
+    band = 0
+    total = 0
+    for j in range(r.n):
+        h = orc.hits(s, r.o[j], r.d[j], r.t0[j], r.t1[j], _sr=sr)
+        g = set(ids[j, : cnt[j]].tolist())
+        o = set(h["ids"].tolist())
+        total += len(g | o)
+        span = float(r.t1[j] - r.t0[j])
+        for i in g ^ o:
+            A, tstar, d2 = orc.prim_quadratic(s, i, r.o[j], r.d[j], _sr=sr)
+            near_k = abs(math.sqrt(max(d2, 0.0)) - K) / K < REL
+            half = math.sqrt(max(K * K - d2, 0.0) / A)
+            near_end = (abs(tstar - half - r.t1[j]) < REL * span or abs(tstar + half - r.t0[j]) < REL * span)
+            assert near_k or near_end, (j, i, d2)
+            band += 1
+        # intervals of common hits agree
+        for k_, i in enumerate(h["ids"]):
+            if i in g:
+                m = list(ids[j, : cnt[j]]).index(i)
+                assert abs(a[j, m] - h["a"][k_]) <= 2e-5 * max(1.0, abs(h["a"][k_]))
+                assert abs(b[j, m] - h["b"][k_]) <= 2e-5 * max(1.0, abs(h["b"][k_]))
+    assert band <= 1e-3 * total, (band, total)
+
+
+def _ff_compare(orc, s, r, u, u2, prim, tu, tsp, exclude=None, max_frac=1e-3):
+    ref = orc.sample_free_flight(s, r, u, u2, exclude=exclude)
+    mism = np.nonzero(prim != ref["prim"])[0]
+    unexplained = []
+    for j in mism:
+        ok = False
+        for du in (-REL, 0.0, REL):
+            for du2 in (-REL, 0.0, REL):
+                rj = scenes.Rays(r.o[j:j + 1], r.d[j:j + 1], r.t0[j:j + 1], r.t1[j:j + 1])
+                f = orc.sample_free_flight(s, rj, np.clip(u[j:j + 1] + du, 0, 1 - 2 ** -24),
+                                           np.clip(u2[j:j + 1] + du2, 0, 1 - 2 ** -24),
+                                           exclude=None if exclude is None else exclude[j:j + 1])
+                ok |= f["prim"][0] == prim[j]
+        if not ok:
+            unexplained.append(j)
+    assert not unexplained, [(j, prim[j], ref["prim"][j], u[j], u2[j]) for j in unexplained[:5]]
+    assert len(mism) <= max_frac * r.n + 1, (len(mism), r.n)
+    same = (prim == ref["prim"]) & (prim >= 0)
+    span = (r.t1 - r.t0).astype(np.float64)
+    e_tu = np.abs(tu[same] - ref["t_u"][same]) / span[same]
+    e_ts = np.abs(tsp[same] - ref["t_spawn"][same]) / span[same]
+    assert e_tu.max() <= REL, e_tu.max()
+    assert e_ts.max() <= REL, e_ts.max()
+    esc = prim < 0
+    assert np.all(tu[esc] == r.t1[esc])
+    return ref
+
+
+def test_free_flight_parity_tiny(gpu, orc):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene()
+    bvh = build_scene(torch, s)
+    r = scenes.random_rays(20011, seed=13)
+    u, u2 = scenes.uniforms24(14, r.n), scenes.uniforms24(15, r.n)
+    prim, tu, tsp, st = ugp.sample_free_flight(bvh, dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0),
+                                               dev(torch, r.t1), dev(torch, u), dev(torch, u2))
+    assert st.cpu().numpy().max() == 0
+    ref = _ff_compare(orc, s, r, u, u2, prim.cpu().numpy(), tu.cpu().numpy().astype(np.float64),
+                      tsp.cpu().numpy().astype(np.float64))
+    assert (ref["prim"] >= 0).mean() > 0.2 and (ref["n_active"] >= 2).sum() > 100
+
+
+def test_free_flight_dense_overlaps_and_exclusion(gpu, orc):
+    """Saturating clusters (many intervals per window, several rounds) and excluded origins."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene(n=3000, seed=21)
+    s.magnitude[:] *= 4.0
+    rng = np.random.default_rng(21)
+    n = 8192
+    pid = rng.integers(0, s.n, n).astype(np.int32)
+    o = s.mean[pid].astype(np.float64)
+    d = rng.normal(size=(n, 3)); d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
+                    np.full(n, 2.0, np.float32))
+    u, u2 = scenes.uniforms24(22, n), scenes.uniforms24(23, n)
+    prim, tu, tsp, st = ugp.sample_free_flight(build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                               dev(torch, r.t0), dev(torch, r.t1), dev(torch, u),
+                                               dev(torch, u2), exclude=dev(torch, pid))
+    assert st.cpu().numpy().max() == 0
+    _ff_compare(orc, s, r, u, u2, prim.cpu().numpy(), tu.cpu().numpy().astype(np.float64),
+                tsp.cpu().numpy().astype(np.float64), exclude=pid)
+
+
+def test_edge_cases(gpu, orc):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    r = scenes.random_rays(300, seed=31)
+    u, u2 = scenes.uniforms24(32, r.n), scenes.uniforms24(33, r.n)
+    args = lambda: (dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0), dev(torch, r.t1))
+    # empty scene: everything escapes, T = 1
+    s0 = scenes.tiny_scene(n=1).subset(np.zeros(0, int))
+    b0 = build_scene(torch, s0)
+    T, st = ugp.trace_transmittance(b0, *args())
+    assert np.all(T.cpu().numpy() == 1.0)
+    prim, tu, _, _ = ugp.sample_free_flight(b0, *args(), dev(torch, u), dev(torch, u2))
+    assert np.all(prim.cpu().numpy() == -1)
+    # one primitive
+    s1 = scenes.tiny_scene(n=1, seed=34)
+    s1.mean[0] = [0.5, 0.5, 0.5]
+    s1.scale[0] = [0.2, 0.1, 0.3]
+    b1 = build_scene(torch, s1)
+    T, st = ugp.trace_transmittance(b1, *args())
+    T_ref, _, nh = orc.transmittance(s1, r)
+    assert nh.sum() > 20
+    assert _t_check(T.cpu().numpy(), T_ref).max() <= REL
+    prim, tu, tsp, st = ugp.sample_free_flight(b1, *args(), dev(torch, u), dev(torch, u2))
+    _ff_compare(orc, s1, r, u, u2, prim.cpu().numpy(), tu.cpu().numpy().astype(np.float64),
+                tsp.cpu().numpy().astype(np.float64))
+    # zero rays
+    z = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    z1 = torch.zeros(0, dtype=torch.float32, device="cuda")
+    T, st = ugp.trace_transmittance(b1, z, z, z1, z1)
+    assert T.numel() == 0
+    # empty ray intervals t0 == t1
+    rr = scenes.Rays(r.o, r.d, r.t0, r.t0.copy())
+    T, st = ugp.trace_transmittance(b1, dev(torch, rr.o), dev(torch, rr.d), dev(torch, rr.t0),
+                                    dev(torch, rr.t1))
+    assert np.all(T.cpu().numpy() == 1.0)
+    # invalid primitives are ignored: same result as the scene without them
+    s = scenes.tiny_scene(n=200, seed=35)
+    bad = s.subset(np.arange(s.n))
+    bad.scale[3] = [0.0, 0.01, 0.01]
+    bad.scale[7, 1] = np.nan
+    bad.magnitude[11] = -1.0
+    bad.quat[13] = 0.0
+    bb = build_scene(torch, bad)
+    assert bb.info()["n_invalid"] == 4
+    keep = np.setdiff1d(np.arange(s.n), [3, 7, 11, 13])
+    T, st = ugp.trace_transmittance(bb, *args())
+    T_ref, _, _ = orc.transmittance(s.subset(keep), r)
+    assert _t_check(T.cpu().numpy(), T_ref).max() <= REL
+
+
+def test_api_errors(gpu):
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene(n=10)
+    m = dev(torch, s.mean)
+    with pytest.raises(ugp.UgpError):
+        ugp.build_bvh(m, dev(torch, s.quat), dev(torch, s.scale), dev(torch, s.magnitude),
+                      cutoff_eps=1.5)
+    with pytest.raises(TypeError):
+        ugp.build_bvh(m.double(), dev(torch, s.quat), dev(torch, s.scale), dev(torch, s.magnitude))
