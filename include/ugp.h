@@ -54,8 +54,9 @@ enum {
   UGP_RAY_OK = 0,
   UGP_RAY_STACK_OVERFLOW = 1,   /* traversal stack full: result incomplete */
   UGP_RAY_BUFFER_OVERFLOW = 2,  /* free-flight candidate buffer held only active intervals */
-  UGP_RAY_ITER_LIMIT = 3,       /* round or root-solve bound reached */
-  UGP_RAY_BAD_NODE = 4          /* a node or leaf reference out of range (corrupt BVH) */
+  UGP_RAY_ITER_LIMIT = 3,       /* free flight: collection-round bound reached */
+  UGP_RAY_BAD_NODE = 4,         /* a node or leaf reference out of range (corrupt BVH) */
+  UGP_RAY_SOLVE_LIMIT = 5       /* free flight: root solve did not converge in its bound */
 };
 
 /* Input primitives (Sec. 3.1, Eq. 1-2), device float32 arrays of n rows:

@@ -256,7 +256,10 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
     }
     if (F_c + dF > u) {
       // ---- root of F(t) = u in [t_c, t_w], bracketed Newton ----
+      // Safeguarded Newton: a Newton step is taken only if it stays inside the bracket and
+      // the previous-but-one step shows it converges at least as fast as bisection.
       float lo = t_c, hi = t_w, t = 0.5f * (t_c + t_w);
+      float dx_old = hi - lo, dx = dx_old;
       bool conv = false;
       for (int it = 0; it < kFFNewtonIters; ++it) {
         float f = F_c - u, fp = 0.f;
@@ -269,12 +272,21 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
         if (f == 0.f) { conv = true; break; }
         if (f < 0.f) lo = t; else hi = t;
         if (!(nextafterf(lo, INFINITY) < hi)) { conv = true; break; }  // bracket is one ulp wide
-        float tnew = fp > 0.f ? t - f / fp : 0.5f * (lo + hi);
-        if (!(tnew > lo && tnew < hi)) tnew = 0.5f * (lo + hi);
+        const float tn_ = fp > 0.f ? t - f / fp : lo;
+        float tnew;
+        if (fp > 0.f && tn_ > lo && tn_ < hi && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
+          dx_old = dx;
+          dx = f / fp;
+          tnew = tn_;
+        } else {
+          dx_old = dx;
+          dx = 0.5f * (hi - lo);
+          tnew = lo + dx;
+        }
         if (tnew == t) { conv = true; break; }
         t = tnew;
       }
-      if (!conv) st = UGP_RAY_ITER_LIMIT;
+      if (!conv) st = UGP_RAY_SOLVE_LIMIT;
       // ---- choose among the intervals containing t, proportional to G, ascending index ----
       float tot = 0.f;
       for (int e = 0; e < nE; ++e)

@@ -33,7 +33,7 @@ class UgpError(RuntimeError):
     pass
 
 
-RAY_OK, RAY_STACK_OVERFLOW, RAY_BUFFER_OVERFLOW, RAY_ITER_LIMIT = 0, 1, 2, 3
+RAY_OK, RAY_STACK_OVERFLOW, RAY_BUFFER_OVERFLOW, RAY_ITER_LIMIT, RAY_BAD_NODE, RAY_SOLVE_LIMIT = 0, 1, 2, 3, 4, 5
 
 
 def lib():
