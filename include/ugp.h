@@ -53,7 +53,7 @@ typedef enum ugp_status {
 enum {
   UGP_RAY_OK = 0,
   UGP_RAY_STACK_OVERFLOW = 1,   /* traversal stack full: result incomplete */
-  UGP_RAY_BUFFER_OVERFLOW = 2,  /* free-flight candidate buffer held only active intervals */
+  UGP_RAY_BUFFER_OVERFLOW = 2,  /* reserved (the free-flight buffer falls back to binning) */
   UGP_RAY_ITER_LIMIT = 3,       /* free flight: collection-round bound reached */
   UGP_RAY_BAD_NODE = 4,         /* a node or leaf reference out of range (corrupt BVH) */
   UGP_RAY_SOLVE_LIMIT = 5       /* free flight: root solve did not converge in its bound */
@@ -173,10 +173,11 @@ ugp_status ugp_collect_hits(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
                             int32_t cap, int32_t* ids_out, float* a_out, float* b_out,
                             int32_t* count_out, uint8_t* status_out, void* stream);
 
-/* Optional traversal statistics: when `counters` is a device pointer to 4
+/* Optional traversal statistics: when `counters` is a device pointer to 6
  * zero-initialised uint64, later tracing calls on any stream add
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
- *   [3] traversal rounds
+ *   [3] traversal rounds, [4] free-flight rays that needed the binned mode,
+ *   [5] reserved
  * to it (atomically).  NULL turns counting off (the default).  Host-side
  * setting, not thread safe against concurrent tracing calls. */
 ugp_status ugp_set_trace_counters(unsigned long long* counters);

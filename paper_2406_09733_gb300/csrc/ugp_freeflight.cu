@@ -1,0 +1,562 @@
+// Exact free-flight distribution sampling over the BVH (Sec. 5.2, Eq. 8-10).
+//
+// Definition (order-free).  With the clipped intervals [a_k, b_k] of the primitives along the
+// ray and F(t) = 1/2 sum_k I_k(a_k, min(t, b_k)): the ray escapes if F(t1) <= u; otherwise
+// t_u solves F(t_u) = u and the primitive is drawn among those whose interval contains t_u
+// with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u}), scanning them in ascending index with
+// the second uniform u2.  Since u < 1, t_u lies before the saturating distance, so primitive k
+// is chosen with probability 1/2 I_k(a_k, min(b_k, t_sat)).
+//
+// A BVH gives no front-to-back order (the paper's reason for a kd-tree, Sec. 5.1), so the
+// kernel finds t_u in one of two ways, both exact:
+//
+//  * rounds (fast path).  A traversal collects the intervals with the smallest (a, index)
+//    keys after a cursor into a per-ray shared-memory buffer of kK entries, next to the
+//    intervals still active from the previous round.  Everything not kept starts at or after
+//    t_w (the smallest dropped start, or the entry of a pruned subtree), so F on [t_c, t_w] is
+//    known from the buffer; if it crosses u there, a safeguarded Newton iteration with
+//    F' = 1/2 sum G (Eq. 9) finds t_u, else the window advances.
+//  * binned refinement (fallback when more than kK intervals overlap, as in dense aggregates).
+//    In the spirit of the paper's GPU binning (Sec. 5.2), one traversal adds each interval's
+//    contribution to kB equal bins of the current window [lo, hi], pruning subtrees that start
+//    after the bin where the running sum passes u.  The window then shrinks to the crossing
+//    bin, until the intervals meeting it fit the buffer (Newton as above) or the window is one
+//    float wide.  Memory per ray stays fixed whatever the overlap depth.
+//
+// The choice at t_u uses the buffer when it holds every interval containing t_u, and otherwise
+// id-ordered passes that each collect the next kK smallest indices containing t_u.
+#include "ugp_gauss.cuh"
+#include "ugp_trace.cuh"
+
+namespace ugp {
+namespace {
+
+struct FFSmem {
+  float a[kK][kFFBlock];
+  float b[kK][kFFBlock];
+  float tn[kK][kFFBlock];
+  float ts[kK][kFFBlock];
+  float s[kK][kFFBlock];
+  float e0[kK][kFFBlock];
+  int id[kK][kFFBlock];
+  float bin[kB][kFFBlock];
+  int stk[kFFStack][kFFBlock];
+};
+
+struct Ctx {
+  FFSmem& sm;
+  int tid;
+  const TraceScene& sc;
+  Ray ray;
+  float t0, t1;
+  int ex;
+  unsigned n_nodes, n_prims;
+  uint8_t st;
+};
+
+#define FB(arr, i) c.sm.arr[(i)][c.tid]
+
+__device__ __forceinline__ bool key_less(float a0, int i0, float a1, int i1) {
+  return a0 < a1 || (a0 == a1 && i0 < i1);
+}
+
+__device__ __forceinline__ void put(Ctx& c, int pos, const PrimHit& h) {
+  FB(a, pos) = h.a;
+  FB(b, pos) = h.b;
+  FB(tn, pos) = h.tn;
+  FB(ts, pos) = h.ts;
+  FB(s, pos) = h.s;
+  FB(e0, pos) = h.e0;
+  FB(id, pos) = h.id;
+}
+
+__device__ __forceinline__ void move(Ctx& c, int to, int from) {
+  FB(a, to) = FB(a, from);
+  FB(b, to) = FB(b, from);
+  FB(tn, to) = FB(tn, from);
+  FB(ts, to) = FB(ts, from);
+  FB(s, to) = FB(s, from);
+  FB(e0, to) = FB(e0, from);
+  FB(id, to) = FB(id, from);
+}
+
+// Nearest-first traversal of the leaves whose boxes meet [lo, hi].  The visitor may lower
+// `limit`; children whose clipped entry lies beyond it are skipped and reported through
+// vis.pruned(entry).
+template <class V>
+__device__ void traverse(Ctx& c, float lo, float hi, float& limit, V& vis) {
+  int sp = 0, node = 0;
+  while (true) {
+    if (unsigned(node) >= unsigned(c.sc.n_nodes)) {
+      c.st = UGP_RAY_BAD_NODE;
+      return;
+    }
+    const float4* nd = c.sc.nodes + 4 * node;
+    const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+    const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
+    ++c.n_nodes;
+    const int ch[2] = {n3.x, n3.y};
+    if ((ch[0] < 0 && ~ch[0] >= c.sc.n_prims) ||
+        (ch[1] < 0 && ch[1] != kEmptyChild && ~ch[1] >= c.sc.n_prims)) {
+      c.st = UGP_RAY_BAD_NODE;
+      return;
+    }
+    float en[2];
+    bool hc[2];
+    hc[0] = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, c.ray, lo, hi, en[0]);
+    hc[1] = ch[1] != kEmptyChild && slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, c.ray, lo, hi, en[1]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!hc[k]) continue;
+      if (en[k] > limit) {
+        vis.pruned(en[k]);
+        hc[k] = false;
+        continue;
+      }
+      if (ch[k] >= 0) continue;
+      hc[k] = false;
+      ++c.n_prims;
+      vis.leaf(~ch[k], limit);
+    }
+    if (hc[0] && hc[1]) {
+      const bool first0 = en[0] <= en[1];
+      if (sp == kFFStack) {
+        c.st = UGP_RAY_STACK_OVERFLOW;
+        return;
+      }
+      FB(stk, sp) = first0 ? ch[1] : ch[0];
+      ++sp;
+      node = first0 ? ch[0] : ch[1];
+    } else if (hc[0]) {
+      node = ch[0];
+    } else if (hc[1]) {
+      node = ch[1];
+    } else {
+      if (sp == 0) return;
+      --sp;
+      node = FB(stk, sp);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- rounds: collection visitor
+struct RoundVisitor {
+  Ctx& c;
+  float t_c, cur_a;
+  int cur_id, nC, cap, nNew;
+  float t_next;
+  __device__ void pruned(float en) { t_next = fminf(t_next, en); }
+  __device__ void leaf(int slot, float& limit) {
+    PrimHit h;
+    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    if (h.b <= t_c) return;                           // ends before the window
+    if (!key_less(cur_a, cur_id, h.a, h.id)) return;  // kept in an earlier round
+    int pos;
+    if (nNew < cap) {
+      pos = nC + nNew;
+      ++nNew;
+    } else {
+      const int last = nC + nNew - 1;
+      if (!key_less(h.a, h.id, FB(a, last), FB(id, last))) {
+        t_next = fminf(t_next, h.a);
+        return;
+      }
+      t_next = fminf(t_next, FB(a, last));  // the evicted interval starts here
+      pos = last;
+    }
+    while (pos > nC && key_less(h.a, h.id, FB(a, pos - 1), FB(id, pos - 1))) {
+      move(c, pos, pos - 1);
+      --pos;
+    }
+    put(c, pos, h);
+    if (nNew == cap) limit = FB(a, nC + nNew - 1);
+  }
+};
+
+// ---------------------------------------------------------------- binned refinement visitor
+struct BinVisitor {
+  Ctx& c;
+  float lo, hi, w, target;  // bins of width w over [lo, hi]; target = u - F(lo)
+  int count;
+  __device__ float edge(int j) const { return j >= kB ? hi : lo + w * float(j); }
+  __device__ void pruned(float) {}
+  __device__ void leaf(int slot, float& limit) {
+    PrimHit h;
+    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    const float x = fmaxf(h.a, lo), y = fminf(h.b, hi);
+    if (!(x < y)) return;
+    if (count < kK) put(c, count, h);
+    ++count;
+    int j = min(kB - 1, max(0, int((x - lo) / w)));
+    while (j > 0 && x < edge(j)) --j;
+    while (j < kB - 1 && x >= edge(j + 1)) ++j;
+    for (; j < kB && edge(j) < y; ++j) {
+      const float xa = fmaxf(x, edge(j)), ya = fminf(y, edge(j + 1));
+      if (xa < ya) FB(bin, j) += half_integral(xa, ya, h.tn, h.ts, h.s, h.e0);
+    }
+    // the partial sums only grow, so once they pass the target the crossing is known to lie
+    // at or before that bin's upper edge
+    float acc = 0.f;
+    for (int k = 0; k < kB; ++k) {
+      acc += FB(bin, k);
+      if (acc > target) {
+        limit = fminf(limit, edge(k + 1));
+        break;
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------- choice passes visitor
+struct ChoiceVisitor {
+  Ctx& c;
+  float t;
+  int last_id, n;  // collect the kK smallest indices above last_id among intervals containing t
+  int total;       // number of intervals containing t
+  float S;         // sum of G over them
+  __device__ void pruned(float) {}
+  __device__ void leaf(int slot, float&) {
+    PrimHit h;
+    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    if (!(h.a <= t && t <= h.b)) return;
+    const float g = gauss_at(t, h.tn, h.ts, h.s, h.e0);
+    ++total;
+    S += g;
+    if (h.id <= last_id) return;
+    int pos;
+    if (n < kK) {
+      pos = n++;
+    } else {
+      if (h.id >= FB(id, kK - 1)) return;
+      pos = kK - 1;
+    }
+    while (pos > 0 && h.id < FB(id, pos - 1)) {
+      FB(id, pos) = FB(id, pos - 1);
+      FB(a, pos) = FB(a, pos - 1);
+      --pos;
+    }
+    FB(id, pos) = h.id;
+    FB(a, pos) = g;
+  }
+};
+
+// F(t) - u and F'(t) from the buffer entries [0, nE) on a window starting at lo with F(lo) = Flo.
+__device__ __forceinline__ void eval_F(Ctx& c, int nE, float lo, float Flo, float u, float t, float& f,
+                                       float& fp) {
+  f = Flo - u;
+  fp = 0.f;
+  for (int e = 0; e < nE; ++e) {
+    const float x0 = fmaxf(FB(a, e), lo), x1 = fminf(FB(b, e), t);
+    if (x0 < x1) f += half_integral(x0, x1, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+    if (FB(a, e) <= t && t <= FB(b, e)) fp += 0.5f * gauss_at(t, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+  }
+}
+
+// Root of F = u on [lo, hi] (F(lo) <= u < F(hi)) by Newton's method safeguarded with bisection:
+// a Newton step is taken only if it stays in the bracket and shrinks it at least as fast as
+// bisection would have two steps earlier.
+__device__ float solve_buffer(Ctx& c, int nE, float lo, float hi, float Flo, float u) {
+  const float w_lo = lo;
+  float t = 0.5f * (lo + hi);
+  float dx_old = hi - lo, dx = dx_old;
+  for (int it = 0; it < kFFNewtonIters; ++it) {
+    float f, fp;
+    eval_F(c, nE, w_lo, Flo, u, t, f, fp);
+    if (f == 0.f) return t;
+    if (f < 0.f) lo = t; else hi = t;
+    if (!(nextafterf(lo, INFINITY) < hi)) return t;  // bracket one float wide
+    const float tn = fp > 0.f ? t - f / fp : lo;
+    float tnew;
+    if (fp > 0.f && tn > lo && tn < hi && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
+      dx_old = dx;
+      dx = f / fp;
+      tnew = tn;
+    } else {
+      dx_old = dx;
+      dx = 0.5f * (hi - lo);
+      tnew = lo + dx;
+    }
+    if (tnew == t) return t;
+    t = tnew;
+  }
+  c.st = UGP_RAY_SOLVE_LIMIT;
+  return t;
+}
+
+// Choice among buffer entries [0, nE) containing t: proportional to G, ascending index.
+__device__ int choose_buffer(Ctx& c, int nE, float t, float u2) {
+  float tot = 0.f;
+  for (int e = 0; e < nE; ++e)
+    if (FB(a, e) <= t && t <= FB(b, e)) tot += gauss_at(t, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+  const float target = u2 * tot;
+  float cum = 0.f;
+  int last_id = -1, pick = -1, any = -1;
+  while (true) {
+    int best = -1, best_id = INT32_MAX;
+    for (int e = 0; e < nE; ++e) {
+      const int idv = FB(id, e);
+      if (FB(a, e) <= t && t <= FB(b, e) && idv > last_id && idv < best_id) {
+        best = e;
+        best_id = idv;
+      }
+    }
+    if (best < 0) break;
+    any = best;
+    cum += gauss_at(t, FB(tn, best), FB(ts, best), FB(s, best), FB(e0, best));
+    last_id = best_id;
+    if (cum > target) {
+      pick = best;
+      break;
+    }
+  }
+  return pick >= 0 ? pick : any;
+}
+
+// Choice by id-ordered traversal passes (any number of intervals containing t).  Returns the
+// chosen primitive index and its clipped interval through a_out / b_out.
+struct FindVisitor {
+  Ctx& c;
+  int want;
+  float a, b;
+  __device__ void pruned(float) {}
+  __device__ void leaf(int slot, float&) {
+    PrimHit h;
+    if (prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h) && h.id == want) {
+      a = h.a;
+      b = h.b;
+    }
+  }
+};
+
+__device__ int choose_passes(Ctx& c, float t, float u2, float& a_out, float& b_out) {
+  float S = -1.f, target = 0.f, cum = 0.f;
+  int last_id = -1, any = -1, pick = -1;
+  for (int pass = 0; pass < kChoicePasses && pick < 0; ++pass) {
+    ChoiceVisitor v{c, t, last_id, 0, 0, 0.f};
+    float limit = t;
+    traverse(c, t, t, limit, v);
+    if (c.st != UGP_RAY_OK) return -1;
+    if (S < 0.f) {
+      S = v.S;
+      target = u2 * S;
+    }
+    for (int e = 0; e < v.n && pick < 0; ++e) {
+      any = FB(id, e);
+      cum += FB(a, e);
+      if (cum > target) pick = any;
+    }
+    if (v.n < kK) break;  // every interval containing t has been seen
+    last_id = FB(id, v.n - 1);
+  }
+  if (pick < 0) pick = any;  // rounding left the sum just short of u2 * S
+  if (pick < 0) return -1;
+  FindVisitor f{c, pick, t, t};
+  float limit = t;
+  traverse(c, t, t, limit, f);
+  a_out = f.a;
+  b_out = f.b;
+  return pick;
+}
+
+// Exit distance of the ray from the scene's bounding box (both children of the root).
+__device__ float scene_exit(const Ctx& c, float lo, float hi) {
+  const float4* nd = c.sc.nodes;
+  const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+  const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
+  const float lx = fminf(n0.x, n3.y != kEmptyChild ? n1.z : n0.x);
+  const float ly = fminf(n0.y, n3.y != kEmptyChild ? n1.w : n0.y);
+  const float lz = fminf(n0.z, n3.y != kEmptyChild ? n2.x : n0.z);
+  const float hx = fmaxf(n0.w, n3.y != kEmptyChild ? n2.y : n0.w);
+  const float hy = fmaxf(n1.x, n3.y != kEmptyChild ? n2.z : n1.x);
+  const float hz = fmaxf(n1.y, n3.y != kEmptyChild ? n2.w : n1.y);
+  const Ray& r = c.ray;
+  const float x0 = (lx - r.o.x) * r.inv.x, x1 = (hx - r.o.x) * r.inv.x;
+  const float y0 = (ly - r.o.y) * r.inv.y, y1 = (hy - r.o.y) * r.inv.y;
+  const float z0 = (lz - r.o.z) * r.inv.z, z1 = (hz - r.o.z) * r.inv.z;
+  const float th = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+  return fminf(hi, fmaxf(lo, th * (1.f + 1e-6f) + 1e-6f));
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kFFBlock)
+k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const float* __restrict__ d3,
+              const float* __restrict__ t0a, const float* __restrict__ t1a, const float* __restrict__ ua,
+              const float* __restrict__ u2a, const int32_t* __restrict__ excl,
+              int32_t* __restrict__ prim_out, float* __restrict__ tu_out, float* __restrict__ tsp_out,
+              uint8_t* __restrict__ st_out, unsigned long long* __restrict__ ctr) {
+  __shared__ FFSmem sm;
+  const int64_t r = int64_t(blockIdx.x) * kFFBlock + threadIdx.x;
+  if (r >= n_rays) return;
+  Ctx c{sm, int(threadIdx.x), sc, make_ray(ld3(o3, r), ld3(d3, r)), __ldg(t0a + r), __ldg(t1a + r),
+        excl ? __ldg(excl + r) : -1, 0u, 0u, UGP_RAY_OK};
+  const float u = __ldg(ua + r), u2 = __ldg(u2a + r);
+  unsigned n_rounds = 0;
+  int out_prim = -1;
+  float out_tu = c.t1, out_tsp = c.t1;
+
+  float t_c = c.t0, F_c = 0.f;
+  float cur_a = -INFINITY;
+  int cur_id = -1, nC = 0;
+  bool done = !(sc.n_prims > 0 && c.t0 < c.t1);
+  bool dense = false;
+  // ---------------- rounds ----------------
+  while (!done) {
+    if (n_rounds >= kFFMaxRounds || nC == kK) {
+      dense = true;
+      break;
+    }
+    ++n_rounds;
+    RoundVisitor v{c, t_c, cur_a, cur_id, nC, kK - nC, 0, c.t1};
+    float limit = c.t1;
+    traverse(c, t_c, c.t1, limit, v);
+    if (c.st != UGP_RAY_OK) break;
+    const int nE = nC + v.nNew;
+    const float t_w = fmaxf(v.t_next, t_c);
+    float dF = 0.f;
+    for (int e = 0; e < nE; ++e) {
+      const float lo = fmaxf(FB(a, e), t_c), hi = fminf(FB(b, e), t_w);
+      if (lo < hi) dF += half_integral(lo, hi, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+    }
+    if (F_c + dF > u) {
+      const float t = solve_buffer(c, nE, t_c, t_w, F_c, u);
+      const int pick = choose_buffer(c, nE, t, u2);
+      if (pick >= 0) {
+        out_prim = FB(id, pick);
+        out_tu = t;
+        out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
+      }
+      done = true;
+      break;
+    }
+    F_c += dF;
+    t_c = t_w;
+    if (t_w >= c.t1) {
+      done = true;  // escape
+      break;
+    }
+    if (v.nNew > 0) {
+      cur_a = FB(a, nE - 1);
+      cur_id = FB(id, nE - 1);
+    }
+    int m = 0;  // carry the intervals still active after t_w
+    for (int e = 0; e < nE; ++e) {
+      if (FB(b, e) > t_w) {
+        if (m != e) move(c, m, e);
+        ++m;
+      }
+    }
+    nC = m;
+  }
+  // ---------------- binned refinement ----------------
+  if (dense && c.st == UGP_RAY_OK) {
+    float lo = t_c, hi = scene_exit(c, t_c, c.t1), Flo = F_c;
+    bool solved = false;
+    float t_u = hi;
+    for (int level = 0; level < kDenseLevels && !solved; ++level) {
+      for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
+      BinVisitor v{c, lo, hi, (hi - lo) / float(kB), u - Flo, 0};
+      float limit = hi;
+      traverse(c, lo, hi, limit, v);
+      if (c.st != UGP_RAY_OK) break;
+      if (v.count <= kK) {
+        // every interval meeting [lo, limit] is in the buffer
+        float f, fp;
+        eval_F(c, v.count, lo, Flo, u, limit, f, fp);
+        if (f <= 0.f) {
+          if (level == 0 && limit >= hi) {  // F(end) <= u: escape
+            solved = true;
+            t_u = -1.f;
+            break;
+          }
+          t_u = limit;  // rounding put the crossing at the window's end
+        } else {
+          t_u = solve_buffer(c, v.count, lo, limit, Flo, u);
+        }
+        const int pick = choose_buffer(c, v.count, t_u, u2);
+        if (pick >= 0) {
+          out_prim = FB(id, pick);
+          out_tu = t_u;
+          out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
+        }
+        solved = true;
+        break;
+      }
+      // crossing bin
+      float acc = 0.f;
+      int jx = -1;
+      for (int j = 0; j < kB; ++j) {
+        const float nxt = acc + FB(bin, j);
+        if (nxt > u - Flo) {
+          jx = j;
+          break;
+        }
+        acc = nxt;
+      }
+      if (jx < 0) {
+        if (level == 0) {  // F(end) <= u: escape
+          solved = true;
+          t_u = -1.f;
+          break;
+        }
+        jx = kB - 1;  // rounding: the crossing is at the window's end
+      }
+      const float nlo = v.edge(jx), nhi = v.edge(jx + 1);
+      Flo += acc;
+      lo = nlo;
+      hi = nhi;
+      t_u = 0.5f * (lo + hi);
+      if (!(nextafterf(lo, INFINITY) < hi)) break;  // window one float wide
+    }
+    if (!solved && c.st == UGP_RAY_OK) {
+      float a_k = t_u, b_k = t_u;
+      const int pid = choose_passes(c, t_u, u2, a_k, b_k);
+      if (pid >= 0) {
+        out_prim = pid;
+        out_tu = t_u;
+        out_tsp = 0.5f * (a_k + b_k);
+      }
+    }
+  }
+  prim_out[r] = out_prim;
+  tu_out[r] = out_tu;
+  tsp_out[r] = out_tsp;
+  if (st_out) st_out[r] = c.st;
+  if (STATS) add_counters(ctr, c.n_nodes, c.n_prims, 1u, n_rounds, dense ? 1u : 0u);
+}
+
+#undef FB
+
+}  // namespace
+
+ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
+                              const float* t0, const float* t1, const float* u, const float* u2,
+                              const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
+                              cudaStream_t stream) {
+  const unsigned grid = unsigned((n + kFFBlock - 1) / kFFBlock);
+  unsigned long long* ctr = trace_counters();
+  if (ctr)
+    k_free_flight<true><<<grid, kFFBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, u, u2, excl, prim, tu, tsp, st, ctr);
+  else
+    k_free_flight<false><<<grid, kFFBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, u, u2, excl, prim, tu, tsp, st, ctr);
+  UGP_CUDA_CHECK(cudaGetLastError());
+  return UGP_OK;
+}
+
+}  // namespace ugp
+
+using namespace ugp;
+
+extern "C" ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
+                                             const float* d3, const float* t0, const float* t1,
+                                             const float* u, const float* u2, const int32_t* exclude_prim,
+                                             int32_t* prim_out, float* t_u_out, float* t_spawn_out,
+                                             uint8_t* status_out, void* stream) {
+  clear_error();
+  ugp_status s = check_rays("ugp_sample_free_flight", bvh, n_rays, o3, d3, t0, t1);
+  if (s != UGP_OK) return s;
+  if (n_rays > 0 && (!u || !u2 || !prim_out || !t_u_out || !t_spawn_out))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_sample_free_flight: NULL uniform or output array");
+  if (n_rays == 0) return UGP_OK;
+  return launch_free_flight(trace_scene(bvh), n_rays, o3, d3, t0, t1, u, u2, exclude_prim, prim_out, t_u_out,
+                            t_spawn_out, status_out, static_cast<cudaStream_t>(stream));
+}

@@ -136,19 +136,22 @@ __device__ __forceinline__ float3 ld3(const float* __restrict__ p, int64_t i) {
   return make_float3(__ldg(p + 3 * i), __ldg(p + 3 * i + 1), __ldg(p + 3 * i + 2));
 }
 
-// Warp-aggregated statistics update (threads of a warp that already returned are left out).
+// Warp-aggregated statistics update (threads of a warp that already returned are left out):
+// nodes loaded, primitive records loaded, rays, traversal rounds, rays that needed the binned mode.
 __device__ __forceinline__ void add_counters(unsigned long long* ctr, unsigned a, unsigned b,
-                                             unsigned c, unsigned d) {
+                                             unsigned c, unsigned d, unsigned e) {
   const unsigned mask = __activemask();
   a = __reduce_add_sync(mask, a);
   b = __reduce_add_sync(mask, b);
   c = __reduce_add_sync(mask, c);
   d = __reduce_add_sync(mask, d);
+  e = __reduce_add_sync(mask, e);
   if ((threadIdx.x & 31) == unsigned(__ffs(mask) - 1)) {
     atomicAdd(ctr + 0, (unsigned long long)a);
     atomicAdd(ctr + 1, (unsigned long long)b);
     atomicAdd(ctr + 2, (unsigned long long)c);
     atomicAdd(ctr + 3, (unsigned long long)d);
+    if (e) atomicAdd(ctr + 4, (unsigned long long)e);
   }
 }
 

@@ -10,7 +10,10 @@ constexpr int kTrStack = 64;       // transmittance: traversal stack depth
 constexpr int kFFBlock = 64;       // free flight: threads per block
 constexpr int kK = 16;             // free flight: interval buffer per ray
 constexpr int kFFStack = 48;       // free flight: traversal stack depth
-constexpr int kFFMaxRounds = 256;  // free flight: collection rounds per ray
+constexpr int kFFMaxRounds = 8;    // free flight: collection rounds before the binned mode
+constexpr int kB = 16;             // free flight: bins per refinement level of the binned mode
+constexpr int kDenseLevels = 16;   // free flight: refinement levels of the binned mode
+constexpr int kChoicePasses = 64;  // free flight: id-ordered passes of the final choice
 constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
 
 struct TraceScene {
@@ -22,6 +25,9 @@ struct TraceScene {
 };
 
 TraceScene trace_scene(const ugp_bvh* b);
+
+ugp_status check_rays(const char* fn, const ugp_bvh* bvh, int64_t n, const void* o3, const void* d3,
+                      const void* t0, const void* t1);
 
 ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
                                 const float* t0, const float* t1, const int32_t* excl, float* T,

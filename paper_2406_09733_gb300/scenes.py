@@ -186,12 +186,14 @@ def _tangent_frame(rng, nrm):
 
 def room_scene(n: int = 1_000_000, seed: int = 0, width: int = 1024, height: int = 1024,
                near_specular_frac: float = 0.0, lighting: str = "A",
-               n_small_emitters: int = 12000) -> Scene:
+               n_small_emitters: int = 12000, n_clusters: int = 300) -> Scene:
     """Procedural room of surface splats and aggregate clusters (mixed materials).
 
     lighting "A": one 0.3 x 0.3 quad light below the ceiling (L_e = 20) plus
     background radiance 0.2.  lighting "B": ``n_small_emitters`` small emissive
-    aggregate primitives, no quad, black background.
+    aggregate primitives, no quad, black background.  ``n_clusters`` sets how many
+    aggregate clusters share the 30 % aggregate primitives (smaller scenes keep the
+    per-cluster density of the 1M scene with n_clusters = 300 * n / 1e6).
     """
     rng = _rng(seed)
     n_surf = int(round(0.7 * n))
@@ -267,7 +269,7 @@ def room_scene(n: int = 1_000_000, seed: int = 0, width: int = 1024, height: int
     surf_sggx = _sggx_from_frame(t1, t2, nrm, 0.01)
 
     # --- aggregates: 300 Gaussian clusters of isotropic primitives ------------------------------
-    n_cl = 300
+    n_cl = max(1, int(n_clusters))
     centres = rng.uniform(0.1, 0.9, (n_cl, 3))
     cl = rng.integers(0, n_cl, n_aggr)
     ap = centres[cl] + rng.normal(scale=0.03, size=(n_aggr, 3))

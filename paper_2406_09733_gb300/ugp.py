@@ -208,11 +208,11 @@ def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
 
 
 def set_trace_counters(counters=None):
-    """Turns traversal statistics on (a CUDA uint64/int64 tensor of 4 zeros) or off (None)."""
+    """Turns traversal statistics on (a CUDA int64 tensor of 6 zeros) or off (None)."""
     if counters is not None:
         _dev(counters, torch.int64, "counters")
-        if counters.numel() < 4:
-            raise ValueError("counters needs 4 elements")
+        if counters.numel() < 6:
+            raise ValueError("counters needs 6 elements")
     _check(lib().ugp_set_trace_counters(_p(counters)), "ugp_set_trace_counters")
 
 

@@ -247,6 +247,45 @@ def test_free_flight_dense_overlaps_and_exclusion(gpu, orc):
                 tsp.cpu().numpy().astype(np.float64), exclude=pid)
 
 
+def test_free_flight_room_scene_binned_mode(gpu, orc):
+    """Surface splats plus dense aggregate clusters: many rays need the binned refinement."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.room_scene(100_000, seed=3, n_clusters=30)
+    bvh = build_scene(torch, s)
+    rng = np.random.default_rng(40)
+    n = 3001
+    eye = np.array(s.camera.eye)
+    tgt = rng.uniform(0.02, 0.98, (n, 3))
+    o = np.tile(eye, (n, 1))
+    half = n // 2
+    o[half:] = rng.uniform(0.05, 0.95, (n - half, 3))      # secondary-like rays inside the room
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
+                    np.full(n, 4.0, np.float32))
+    u, u2 = scenes.uniforms24(41, n), scenes.uniforms24(42, n)
+    ctr = torch.zeros(6, dtype=torch.int64, device="cuda")
+    ugp.set_trace_counters(ctr)
+    try:
+        prim, tu, tsp, st = ugp.sample_free_flight(bvh, dev(torch, r.o), dev(torch, r.d),
+                                                   dev(torch, r.t0), dev(torch, r.t1), dev(torch, u),
+                                                   dev(torch, u2))
+        torch.cuda.synchronize()
+    finally:
+        ugp.set_trace_counters(None)
+    stn = st.cpu().numpy()
+    assert stn.max() == 0, np.bincount(stn)
+    c = ctr.cpu().numpy()
+    assert c[2] == n and c[4] > 0.01 * n, c      # the binned mode ran on a real share of rays
+    T, _ = ugp.trace_transmittance(bvh, dev(torch, r.o), dev(torch, r.d), dev(torch, r.t0),
+                                   dev(torch, r.t1))
+    T_ref, _, _ = orc.transmittance(s, r)
+    assert _t_check(T.cpu().numpy(), T_ref).max() <= REL
+    _ff_compare(orc, s, r, u, u2, prim.cpu().numpy(), tu.cpu().numpy().astype(np.float64),
+                tsp.cpu().numpy().astype(np.float64))
+
+
 def test_edge_cases(gpu, orc):
     from paper_2406_09733_gb300 import ugp
     torch = gpu
