@@ -191,3 +191,150 @@ def prim_quadratic(scene, i, o, d, _sr=None):
 
 def erfinv(y: float) -> float:
     return float(lib().orc_erfinv(float(y)))
+
+
+# ------------------------------------------------------------------ appearance and rendering
+def _register_phase(L):
+    d = f64p
+    L.orc_sggx_eval.argtypes = [d, C.c_int64, d, d, d]
+    L.orc_sggx_dvis.argtypes = [d, d, C.c_int64, d, d]
+    L.orc_sggx_sample_vndf.argtypes = [d, d, C.c_int64, d, d]
+    L.orc_sggx_roughen.argtypes = [d, C.c_double, d]
+    L.orc_base_bsdf.argtypes = [C.c_int, d, C.c_double, C.c_int64, d, d, d, d]
+    L.orc_ggx_sample_vn.argtypes = [C.c_double, d, d, C.c_int64, d, d]
+    L.orc_micro_sample.argtypes = [C.c_double, d, C.c_int64, d, d]
+    L.orc_phase_eval.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d, C.c_int, d]
+    L.orc_phase_sample.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d, d, i32p]
+    L.orc_phase_pdf_approx.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d]
+    L.orc_render.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.POINTER(OrcLights),
+                             C.POINTER(OrcParams), C.c_int64, C.c_int64, d, d,
+                             C.POINTER(C.c_int64)]
+
+
+_REGISTRY.append(_register_phase)
+
+
+class OrcCamera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class OrcLights(C.Structure):
+    _fields_ = [("has_quad", C.c_int32), ("corner", C.c_float * 3), ("e1", C.c_float * 3),
+                ("e2", C.c_float * 3), ("Le", C.c_float * 3), ("bg", C.c_float * 3)]
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
+                ("seed", C.c_uint64), ("cutoff_eps", C.c_double), ("nee", C.c_int32),
+                ("spawn_mode", C.c_int32)]
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def sggx_eval(S6, w):
+    S6, w = _d(S6), _d(w).reshape(-1, 3)
+    n = w.shape[0]
+    sig, D = np.zeros(n), np.zeros(n)
+    lib().orc_sggx_eval(_ptr(S6, f64p), n, _ptr(w, f64p), _ptr(sig, f64p), _ptr(D, f64p))
+    return sig, D
+
+
+def sggx_dvis(S6, wo, nrm):
+    S6, wo, nrm = _d(S6), _d(wo), _d(nrm).reshape(-1, 3)
+    out = np.zeros(nrm.shape[0])
+    lib().orc_sggx_dvis(_ptr(S6, f64p), _ptr(wo, f64p), nrm.shape[0], _ptr(nrm, f64p), _ptr(out, f64p))
+    return out
+
+
+def sggx_sample_vndf(S6, wo, U2):
+    S6, wo, U2 = _d(S6), _d(wo), _d(U2).reshape(-1, 2)
+    out = np.zeros((U2.shape[0], 3))
+    lib().orc_sggx_sample_vndf(_ptr(S6, f64p), _ptr(wo, f64p), U2.shape[0], _ptr(U2, f64p), _ptr(out, f64p))
+    return out
+
+
+def sggx_roughen(S6, alpha):
+    S6 = _d(S6)
+    out = np.zeros(6)
+    lib().orc_sggx_roughen(_ptr(S6, f64p), float(alpha), _ptr(out, f64p))
+    return out
+
+
+def base_bsdf(mtype, albedo, alpha, wi, wo, nrm):
+    albedo, wi, wo, nrm = _d(albedo), _d(wi).reshape(-1, 3), _d(wo), _d(nrm)
+    out = np.zeros((wi.shape[0], 3))
+    lib().orc_base_bsdf(int(mtype), _ptr(albedo, f64p), float(alpha), wi.shape[0], _ptr(wi, f64p),
+                        _ptr(wo, f64p), _ptr(nrm, f64p), _ptr(out, f64p))
+    return out
+
+
+def ggx_sample_vn(alpha, wo, nrm, U2):
+    wo, nrm, U2 = _d(wo), _d(nrm), _d(U2).reshape(-1, 2)
+    out = np.zeros((U2.shape[0], 3))
+    lib().orc_ggx_sample_vn(float(alpha), _ptr(wo, f64p), _ptr(nrm, f64p), U2.shape[0], _ptr(U2, f64p),
+                            _ptr(out, f64p))
+    return out
+
+
+def micro_sample(alpha, h, U2):
+    h, U2 = _d(h), _d(U2).reshape(-1, 2)
+    out = np.zeros((U2.shape[0], 3))
+    lib().orc_micro_sample(float(alpha), _ptr(h, f64p), U2.shape[0], _ptr(U2, f64p), _ptr(out, f64p))
+    return out
+
+
+def phase_eval(mtype, albedo, alpha, S6, wo, wi, U6=None, mode=0):
+    albedo, S6, wo, wi = _d(albedo), _d(S6), _d(wo), _d(wi).reshape(-1, 3)
+    n = wi.shape[0]
+    U6 = np.zeros((n, 6)) if U6 is None else _d(U6).reshape(n, 6)
+    out = np.zeros((n, 3))
+    lib().orc_phase_eval(int(mtype), _ptr(albedo, f64p), float(alpha), _ptr(S6, f64p), _ptr(wo, f64p), n,
+                         _ptr(wi, f64p), _ptr(U6, f64p), int(mode), _ptr(out, f64p))
+    return out
+
+
+def phase_sample(mtype, albedo, alpha, S6, wo, U4):
+    albedo, S6, wo, U4 = _d(albedo), _d(S6), _d(wo), _d(U4).reshape(-1, 4)
+    n = U4.shape[0]
+    wi, w = np.zeros((n, 3)), np.zeros((n, 3))
+    ok = np.zeros(n, np.int32)
+    lib().orc_phase_sample(int(mtype), _ptr(albedo, f64p), float(alpha), _ptr(S6, f64p), _ptr(wo, f64p), n,
+                           _ptr(U4, f64p), _ptr(wi, f64p), _ptr(w, f64p), _ptr(ok, i32p))
+    return wi, w, ok.astype(bool)
+
+
+def phase_pdf_approx(mtype, albedo, alpha, S6, wo, wi):
+    albedo, S6, wo, wi = _d(albedo), _d(S6), _d(wo), _d(wi).reshape(-1, 3)
+    out = np.zeros(wi.shape[0])
+    lib().orc_phase_pdf_approx(int(mtype), _ptr(albedo, f64p), float(alpha), _ptr(S6, f64p), _ptr(wo, f64p),
+                               wi.shape[0], _ptr(wi, f64p), _ptr(out, f64p))
+    return out
+
+
+def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1, spawn_mode=0,
+           pixels=None, threads=None):
+    """Per-pixel sums of sample values and squares, shape (H, W, 3) each, plus query counts.
+
+    ``pixels`` = (p_begin, p_end) renders only that row-major pixel range (others stay zero).
+    """
+    cam, li = scene.camera, scene.lights
+    W, H = cam.width, cam.height
+    c = OrcCamera((C.c_float * 3)(*cam.eye), (C.c_float * 3)(*cam.look), (C.c_float * 3)(*cam.up),
+                  cam.vfov_deg, W, H)
+    l = OrcLights(int(li.has_quad), (C.c_float * 3)(*li.quad_corner), (C.c_float * 3)(*li.quad_e1),
+                  (C.c_float * 3)(*li.quad_e2), (C.c_float * 3)(*li.quad_Le), (C.c_float * 3)(*li.bg))
+    p = OrcParams(int(spp), int(spp_begin), int(max_depth), int(seed), float(cutoff_eps), int(nee),
+                  int(spawn_mode))
+    acc = np.zeros((H, W, 3))
+    acc2 = np.zeros((H, W, 3))
+    counts = (C.c_int64 * 2)(0, 0)
+    pb, pe = (0, W * H) if pixels is None else pixels
+    sr = _SceneRef(scene)
+    if threads:
+        set_num_threads(threads)
+    lib().orc_render(sr.ref, C.byref(c), C.byref(l), C.byref(p), int(pb), int(pe), _ptr(acc, f64p),
+                     _ptr(acc2, f64p), counts)
+    return acc, acc2, (int(counts[0]), int(counts[1]))

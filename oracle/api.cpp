@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "oracle_internal.h"
+#include "oracle_phase.h"
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -148,5 +149,118 @@ void orc_prim_quadratic(const orc_scene* s, int64_t i, const float* o3, const fl
 }
 
 double orc_erfinv(double y) { return erfinv(y); }
+
+// ------------------------------------------------------------------ appearance (Sec. 6, App. B)
+static V3 d3v(const double* p) { return v3(p[0], p[1], p[2]); }
+static void put3(double* p, V3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+static Material mat_of(int type, const double* albedo3, double alpha, const double* S6) {
+  Material m;
+  m.type = type;
+  m.albedo = d3v(albedo3);
+  m.alpha = alpha;
+  m.emission = v3(0, 0, 0);
+  for (int k = 0; k < 6; ++k) m.S[k] = S6[k];
+  return m;
+}
+
+// sigma(w) and D(n = w) of the SGGX distribution S6 for n directions.
+void orc_sggx_eval(const double* S6, int64_t n, const double* w3, double* sigma, double* D) {
+  for (int64_t i = 0; i < n; ++i) {
+    sigma[i] = sggx_sigma(S6, d3v(w3 + 3 * i));
+    D[i] = sggx_D(S6, d3v(w3 + 3 * i));
+  }
+}
+void orc_sggx_dvis(const double* S6, const double* wo, int64_t n, const double* n3, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = sggx_Dvis(S6, d3v(wo), d3v(n3 + 3 * i));
+}
+void orc_sggx_sample_vndf(const double* S6, const double* wo, int64_t n, const double* U2, double* n3) {
+  for (int64_t i = 0; i < n; ++i) put3(n3 + 3 * i, sggx_sample_vndf(S6, d3v(wo), U2[2 * i], U2[2 * i + 1]));
+}
+void orc_sggx_roughen(const double* S6, double alpha, double* out6) { sggx_roughen(S6, alpha, out6); }
+
+// Cosine-weighted base BSDF f(wi, wo; n) <n.wi> for type 0 (Lambertian) or 1 (GGX).
+void orc_base_bsdf(int type, const double* albedo3, double alpha, int64_t n, const double* wi3,
+                   const double* wo, const double* nrm, double* out3) {
+  for (int64_t i = 0; i < n; ++i) {
+    const V3 wi = d3v(wi3 + 3 * i);
+    const V3 f = type == kMatGGX ? ggx_f(d3v(albedo3), alpha, wi, d3v(wo), d3v(nrm))
+                                 : lambert_f(d3v(albedo3), wi, d3v(wo), d3v(nrm));
+    put3(out3 + 3 * i, f);
+  }
+}
+// GGX visible-normal samples h (n3 out) and micro-normal samples around a half vector.
+void orc_ggx_sample_vn(double alpha, const double* wo, const double* nrm, int64_t n, const double* U2,
+                       double* h3) {
+  for (int64_t i = 0; i < n; ++i) put3(h3 + 3 * i, ggx_sample_vn(alpha, d3v(wo), d3v(nrm), U2[2 * i], U2[2 * i + 1]));
+}
+void orc_micro_sample(double alpha, const double* h, int64_t n, const double* U2, double* n3) {
+  for (int64_t i = 0; i < n; ++i) put3(n3 + 3 * i, micro_sample(alpha, d3v(h), U2[2 * i], U2[2 * i + 1]));
+}
+
+// Phase function values for n incident directions.  mode 0: as used by the renderer (closed form
+// for isotropic flakes with a Lambertian base, else stochastic), 1: stochastic estimator,
+// 2: Lambert-sphere closed form.  U6 holds six uniforms per direction.
+void orc_phase_eval(int type, const double* albedo3, double alpha, const double* S6, const double* wo,
+                    int64_t n, const double* wi3, const double* U6, int mode, double* out3) {
+  const Material m = mat_of(type, albedo3, alpha, S6);
+  for (int64_t i = 0; i < n; ++i) {
+    const V3 wi = d3v(wi3 + 3 * i);
+    V3 f;
+    if (mode == 1) f = phase_eval_stochastic(m, wi, d3v(wo), U6 + 6 * i);
+    else if (mode == 2) f = phase_eval_lambert_sphere(m.albedo, wi, d3v(wo));
+    else f = phase_eval(m, wi, d3v(wo), U6 + 6 * i);
+    put3(out3 + 3 * i, f);
+  }
+}
+
+void orc_phase_sample(int type, const double* albedo3, double alpha, const double* S6, const double* wo,
+                      int64_t n, const double* U4, double* wi3, double* weight3, int32_t* ok) {
+  const Material m = mat_of(type, albedo3, alpha, S6);
+  for (int64_t i = 0; i < n; ++i) {
+    V3 wi = v3(0, 0, 0), w = v3(0, 0, 0);
+    ok[i] = phase_sample(m, d3v(wo), U4 + 4 * i, &wi, &w) ? 1 : 0;
+    put3(wi3 + 3 * i, wi);
+    put3(weight3 + 3 * i, w);
+  }
+}
+
+void orc_phase_pdf_approx(int type, const double* albedo3, double alpha, const double* S6, const double* wo,
+                          int64_t n, const double* wi3, double* out) {
+  const Material m = mat_of(type, albedo3, alpha, S6);
+  for (int64_t i = 0; i < n; ++i) out[i] = phase_pdf_approx(m, d3v(wi3 + 3 * i), d3v(wo));
+}
+
+// ------------------------------------------------------------------ path tracer (Table 1)
+typedef struct {
+  float eye[3], look[3], up[3];
+  float vfov_deg;
+  int32_t width, height;
+} orc_camera;
+typedef struct {
+  int32_t has_quad;
+  float corner[3], e1[3], e2[3], Le[3], bg[3];
+} orc_lights;
+typedef struct {
+  int32_t spp, spp_begin, max_depth;
+  uint64_t seed;
+  double cutoff_eps;
+  int32_t nee, spawn_mode;
+} orc_params;
+
+// Adds the per-pixel sums of sample values and of their squares (3 channels) for pixels
+// [p_begin, p_end) into accum / accum_sq (full-image arrays).  counts[0] += extend queries,
+// counts[1] += shadow queries.
+void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, const orc_params* p,
+                int64_t p_begin, int64_t p_end, double* accum, double* accum_sq, int64_t* counts) {
+  Camera cam{load3(c->eye), load3(c->look), load3(c->up), c->vfov_deg, c->width, c->height};
+  Lights L{l->has_quad != 0, load3(l->corner), load3(l->e1), load3(l->e2), load3(l->Le), load3(l->bg)};
+  RenderParams P{p->spp, p->spp_begin, p->max_depth, p->seed, p->cutoff_eps, p->nee, p->spawn_mode};
+  int64_t ne = 0, ns = 0;
+  render_pixels(scene_in(s), cam, L, P, p_begin, p_end, accum, accum_sq, &ne, &ns);
+  if (counts) {
+    counts[0] += ne;
+    counts[1] += ns;
+  }
+}
 
 }  // extern "C"

@@ -7,7 +7,8 @@
 //   2. k_morton        30-bit Morton code of each box centre
 //   3. radix sort      (CUB, on the caller's workspace) of (code, index)
 //   4. k_hierarchy     binary radix tree over the sorted codes (Karras, HPG 2012)
-//   5. k_records       64-byte hot records in leaf order (W = S^-1 R^T, mu, g0, index)
+//   5. k_records       64-byte hot records in leaf order (W = S^-1 R^T, mu, g0, index) and
+//                      the low float parts of W (48 B, read only by ill-conditioned hits)
 //   6. k_refit         bottom-up child boxes with one atomic counter per node
 #include <cub/cub.cuh>
 
@@ -21,7 +22,7 @@ namespace {
 
 
 struct Layout {
-  size_t prims, nodes, persistent;
+  size_t prims, nodes, wlo, persistent;
   size_t aabb, keys0, keys1, vals0, vals1, parent, flags, bounds, cub, total;
   size_t cub_bytes;
 };
@@ -172,10 +173,13 @@ __global__ void k_single_root(int4* nodes, int32_t* parent_leaf) {
   parent_leaf[0] = 0;
 }
 
-// Hot record of the primitive in leaf slot `slot` (layout in ugp_internal.cuh).
+// Hot record of the primitive in leaf slot `slot` (layout in ugp_internal.cuh), plus the
+// low-order float parts of W for the double-float refinement of ill-conditioned hits.  W is
+// formed in double precision from the float32 inputs and split as W = hi + lo.
 __global__ void k_records(int64_t n, const int32_t* __restrict__ order, const float* __restrict__ mean3,
                           const float* __restrict__ quat4, const float* __restrict__ scale3,
-                          const float* __restrict__ mag, float4* __restrict__ recs) {
+                          const float* __restrict__ mag, float4* __restrict__ recs,
+                          float4* __restrict__ wlo) {
   const int64_t slot = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (slot >= n) return;
   const int64_t i = order[slot];
@@ -183,26 +187,41 @@ __global__ void k_records(int64_t n, const int32_t* __restrict__ order, const fl
   const float4 q = ld4(quat4, i);
   const float3 s = ld3(scale3, i);
   const float c = mag[i];
-  float4 r0, r1, r2, r3;
+  float4 r0, r1, r2, r3, l0, l1, l2;
   if (prim_valid(m, q, s, c)) {
-    float R[9];
-    quat_rot(q, R);
-    const float is[3] = {1.f / s.x, 1.f / s.y, 1.f / s.z};
-    // W_ij = R_ji / s_i
-    r0 = make_float4(R[0] * is[0], R[3] * is[0], R[6] * is[0], m.x);
-    r1 = make_float4(R[1] * is[1], R[4] * is[1], R[7] * is[1], m.y);
-    r2 = make_float4(R[2] * is[2], R[5] * is[2], R[8] * is[2], m.z);
+    const double qn = sqrt(double(q.x) * q.x + double(q.y) * q.y + double(q.z) * q.z + double(q.w) * q.w);
+    const double w = q.x / qn, x = q.y / qn, y = q.z / qn, z = q.w / qn;
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z),     2 * (x * z + w * y),
+                         2 * (x * y + w * z),     1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y),     2 * (y * z + w * x),     1 - 2 * (x * x + y * y)};
+    const double is[3] = {1.0 / s.x, 1.0 / s.y, 1.0 / s.z};
+    float hi[9], lo[9];
+    for (int r = 0; r < 3; ++r)
+      for (int cc = 0; cc < 3; ++cc) {
+        const double v = R[3 * cc + r] * is[r];  // W_rc = R_cr / s_r
+        hi[3 * r + cc] = float(v);
+        lo[3 * r + cc] = float(v - double(hi[3 * r + cc]));
+      }
+    r0 = make_float4(hi[0], hi[1], hi[2], m.x);
+    r1 = make_float4(hi[3], hi[4], hi[5], m.y);
+    r2 = make_float4(hi[6], hi[7], hi[8], m.z);
+    l0 = make_float4(lo[0], lo[1], lo[2], 0.f);
+    l1 = make_float4(lo[3], lo[4], lo[5], 0.f);
+    l2 = make_float4(lo[6], lo[7], lo[8], 0.f);
     // (2 pi)^{3/2} = 15.749609945722419
-    const float g0 = c / (15.749609945722419f * s.x * s.y * s.z);
+    const float g0 = float(double(c) / (15.749609945722419 * double(s.x) * double(s.y) * double(s.z)));
     r3 = make_float4(g0, __int_as_float(int(i)), 1.f, 0.f);
   } else {
-    r0 = r1 = r2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r0 = r1 = r2 = l0 = l1 = l2 = make_float4(0.f, 0.f, 0.f, 0.f);
     r3 = make_float4(0.f, __int_as_float(int(i)), 0.f, 0.f);
   }
   recs[4 * slot + 0] = r0;
   recs[4 * slot + 1] = r1;
   recs[4 * slot + 2] = r2;
   recs[4 * slot + 3] = r3;
+  wlo[3 * slot + 0] = l0;
+  wlo[3 * slot + 1] = l1;
+  wlo[3 * slot + 2] = l2;
 }
 
 __device__ __forceinline__ void store_child_box(float* node, int side, const float b[6]) {
@@ -261,6 +280,7 @@ bool layout_for(int64_t n, Layout* L) {
   size_t off = 0;
   L->prims = off;      off = align256(off + N * 64);
   L->nodes = off;      off = align256(off + ni * 64);
+  L->wlo = off;        off = align256(off + N * 48);
   L->bounds = off;     off = align256(off + 64);   // 6 ordered-int bounds, root box, invalid count
   L->persistent = off;
   L->aabb = off;       off = align256(off + N * 32);
@@ -325,6 +345,7 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   b->k2 = float(kd * kd);
   char* ws = static_cast<char*>(workspace);
   b->prims = reinterpret_cast<const float4*>(ws + L.prims);
+  b->wlo = reinterpret_cast<const float4*>(ws + L.wlo);
   b->nodes = reinterpret_cast<const float4*>(ws + L.nodes);
   b->persistent_bytes = L.persistent;
   b->bounds_dev = reinterpret_cast<const float*>(ws + L.bounds);
@@ -372,7 +393,7 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
     UGP_CUDA_CHECK(cudaGetLastError());
   }
   k_records<<<G, T, 0, st>>>(n, order, prims->mean3, prims->quat4, prims->scale3, prims->magnitude,
-                             reinterpret_cast<float4*>(ws + L.prims));
+                             reinterpret_cast<float4*>(ws + L.prims), reinterpret_cast<float4*>(ws + L.wlo));
   UGP_CUDA_CHECK(cudaGetLastError());
   b->stream = st;
   *out = b;

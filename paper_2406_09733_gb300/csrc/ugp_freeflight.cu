@@ -148,7 +148,7 @@ struct RoundVisitor {
   __device__ void pruned(float en) { t_next = fminf(t_next, en); }
   __device__ void leaf(int slot, float& limit) {
     PrimHit h;
-    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     if (h.b <= t_c) return;                           // ends before the window
     if (!key_less(cur_a, cur_id, h.a, h.id)) return;  // kept in an earlier round
     int pos;
@@ -182,7 +182,7 @@ struct BinVisitor {
   __device__ void pruned(float) {}
   __device__ void leaf(int slot, float& limit) {
     PrimHit h;
-    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     const float x = fmaxf(h.a, lo), y = fminf(h.b, hi);
     if (!(x < y)) return;
     if (count < kK) put(c, count, h);
@@ -217,7 +217,7 @@ struct ChoiceVisitor {
   __device__ void pruned(float) {}
   __device__ void leaf(int slot, float&) {
     PrimHit h;
-    if (!prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     if (!(h.a <= t && t <= h.b)) return;
     const float g = gauss_at(t, h.tn, h.ts, h.s, h.e0);
     ++total;
@@ -321,7 +321,7 @@ struct FindVisitor {
   __device__ void pruned(float) {}
   __device__ void leaf(int slot, float&) {
     PrimHit h;
-    if (prim_test(c.sc.prims, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h) && h.id == want) {
+    if (prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h) && h.id == want) {
       a = h.a;
       b = h.b;
     }

@@ -52,11 +52,91 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// ---- double-float helpers (value = h + l), built from correctly rounded intrinsics so the
+// compiler cannot contract them into FMAs ---------------------------------------------------
+struct dsf {
+  float h, l;
+};
+__device__ __forceinline__ dsf ds_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ dsf ds_norm(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dsf ds_add(dsf a, dsf b) {
+  const dsf s = ds_two_sum(a.h, b.h);
+  return ds_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dsf ds_mul(dsf a, dsf b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = __fmaf_rn(a.h, b.h, -p);
+  return ds_norm(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.h, b.l), __fmul_rn(a.l, b.h))));
+}
+__device__ __forceinline__ dsf ds_div(dsf a, dsf b) {
+  const float q1 = __fdiv_rn(a.h, b.h);
+  const dsf r = ds_add(a, ds_mul({-q1, 0.f}, b));
+  return ds_norm(q1, __fdiv_rn(r.h, b.h));
+}
+
+// Whitened coordinates of a ray relative to one primitive, in double-float arithmetic:
+// q = p + tn d (p = o - mu as an exact pair), o' = W q, d' = W d with W = hi + lo, then the
+// closest approach t_s = -(o'.d')/A and d2 = |o' + t_s d'|^2.  Used only for hits whose float32
+// evaluation is ill-conditioned (large whitened terms cancelling to a small result).
+__device__ __noinline__ void refine_ds(const float4 r0, const float4 r1, const float4 r2,
+                                       const float4* __restrict__ lo3, const float3 ph, const float3 pl,
+                                       float tn, const float3 d, float& A_out, float& ts_out, float& d2_out) {
+  const float4 l0 = __ldg(lo3), l1 = __ldg(lo3 + 1), l2 = __ldg(lo3 + 2);
+  const float phv[3] = {ph.x, ph.y, ph.z}, plv[3] = {pl.x, pl.y, pl.z}, dv[3] = {d.x, d.y, d.z};
+  dsf q[3];
+  for (int j = 0; j < 3; ++j) {
+    const float P = __fmul_rn(tn, dv[j]);
+    const float Pe = __fmaf_rn(tn, dv[j], -P);
+    const dsf S = ds_two_sum(phv[j], P);
+    q[j] = ds_norm(S.h, __fadd_rn(S.l, __fadd_rn(Pe, plv[j])));
+  }
+  const float Wh[9] = {r0.x, r0.y, r0.z, r1.x, r1.y, r1.z, r2.x, r2.y, r2.z};
+  const float Wl[9] = {l0.x, l0.y, l0.z, l1.x, l1.y, l1.z, l2.x, l2.y, l2.z};
+  dsf o[3], w[3];
+  for (int i = 0; i < 3; ++i) {
+    dsf so = {0.f, 0.f}, sd = {0.f, 0.f};
+    for (int j = 0; j < 3; ++j) {
+      const dsf W = {Wh[3 * i + j], Wl[3 * i + j]};
+      so = ds_add(so, ds_mul(W, q[j]));
+      sd = ds_add(sd, ds_mul(W, {dv[j], 0.f}));
+    }
+    o[i] = so;
+    w[i] = sd;
+  }
+  dsf A = {0.f, 0.f}, od = {0.f, 0.f};
+  for (int i = 0; i < 3; ++i) {
+    A = ds_add(A, ds_mul(w[i], w[i]));
+    od = ds_add(od, ds_mul(o[i], w[i]));
+  }
+  dsf ts = ds_div(od, A);
+  ts = {-ts.h, -ts.l};
+  dsf d2 = {0.f, 0.f};
+  for (int i = 0; i < 3; ++i) {
+    const dsf ci = ds_add(o[i], ds_mul(ts, w[i]));
+    d2 = ds_add(d2, ds_mul(ci, ci));
+  }
+  A_out = A.h;
+  ts_out = ts.h;
+  d2_out = __fadd_rn(d2.h, d2.l);
+}
+
+// Whitened magnitude above which a hit is recomputed in double-float arithmetic: the float32
+// error of d is about 1e-7 times the largest |W_ij q_j|, so below this it stays under 1e-6.
+constexpr float kRefineAbove = 8.f;
+
 // Tests primitive `slot` against the ray over [t0, t1].  Returns false if the ray misses the
 // k-ellipsoid (d2 >= k^2), if the clipped interval is empty, if the primitive is the
 // excluded one, or if it was flagged invalid at build time.
-__device__ __forceinline__ bool prim_test(const float4* __restrict__ recs, int slot, const Ray& r,
-                                          float t0, float t1, float k2, int exclude, PrimHit& h) {
+__device__ __forceinline__ bool prim_test(const float4* __restrict__ recs, const float4* __restrict__ wlo,
+                                          int slot, const Ray& r, float t0, float t1, float k2, int exclude,
+                                          PrimHit& h) {
   const float4 r3 = __ldg(recs + 4 * slot + 3);
   const int id = __float_as_int(r3.y);
   if (id == exclude || r3.z == 0.f) return false;
@@ -77,13 +157,20 @@ __device__ __forceinline__ bool prim_test(const float4* __restrict__ recs, int s
   const float dx = fmaf(r0.x, r.d.x, fmaf(r0.y, r.d.y, r0.z * r.d.z));
   const float dy = fmaf(r1.x, r.d.x, fmaf(r1.y, r.d.y, r1.z * r.d.z));
   const float dz = fmaf(r2.x, r.d.x, fmaf(r2.y, r.d.y, r2.z * r.d.z));
-  const float A = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  const float invA = 1.f / A;
-  const float ts = -fmaf(ox, dx, fmaf(oy, dy, oz * dz)) * invA;
+  float A = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float ts = -fmaf(ox, dx, fmaf(oy, dy, oz * dz)) / A;
   const float cx = fmaf(ts, dx, ox), cy = fmaf(ts, dy, oy), cz = fmaf(ts, dz, oz);
-  const float d2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  float d2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
+  if (!(d2 < k2 * 1.0001f)) return false;
+  // conditioning: largest whitened term that took part in a cancellation
+  const float aqx = fabsf(qx), aqy = fabsf(qy), aqz = fabsf(qz);
+  const float m0 = fabsf(r0.x) * aqx + fabsf(r0.y) * aqy + fabsf(r0.z) * aqz;
+  const float m1 = fabsf(r1.x) * aqx + fabsf(r1.y) * aqy + fabsf(r1.z) * aqz;
+  const float m2 = fabsf(r2.x) * aqx + fabsf(r2.y) * aqy + fabsf(r2.z) * aqz;
+  if (fmaxf(m0, fmaxf(m1, m2)) > kRefineAbove)
+    refine_ds(r0, r1, r2, wlo + 3 * slot, make_float3(px, py, pz), make_float3(lx, ly, lz), tn, r.d, A, ts, d2);
   if (!(d2 < k2)) return false;
-  const float half = sqrtf((k2 - d2) * invA);
+  const float half = sqrtf((k2 - d2) / A);
   const float tc = tn + ts;
   const float a = fmaxf(t0, tc - half), b = fminf(t1, tc + half);
   if (!(a < b)) return false;

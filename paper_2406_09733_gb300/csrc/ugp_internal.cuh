@@ -40,6 +40,7 @@ struct ugp_bvh {
   float k2;
   const float4* nodes;
   const float4* prims;
+  const float4* wlo;         // low float parts of W, 3 float4 per leaf slot
   const float* bounds_dev;   // in the workspace: ordered-int centroid bounds, root box, invalid count
   cudaStream_t stream;       // build stream, used only by synchronous info queries
   size_t persistent_bytes;

@@ -47,13 +47,13 @@ k_transmittance(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, con
       }
       if (h0 && n3.x < 0) {
         ++n_prims;
-        if (prim_test(sc.prims, ~n3.x, ray, t0, t1, sc.k2, ex, h))
+        if (prim_test(sc.prims, sc.wlo, ~n3.x, ray, t0, t1, sc.k2, ex, h))
           acc += half_integral(h.a, h.b, h.tn, h.ts, h.s, h.e0);
         h0 = false;
       }
       if (h1 && n3.y < 0) {
         ++n_prims;
-        if (prim_test(sc.prims, ~n3.y, ray, t0, t1, sc.k2, ex, h))
+        if (prim_test(sc.prims, sc.wlo, ~n3.y, ray, t0, t1, sc.k2, ex, h))
           acc += half_integral(h.a, h.b, h.tn, h.ts, h.s, h.e0);
         h1 = false;
       }
@@ -122,7 +122,7 @@ k_collect_hits(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, cons
         if (!hc[c] || ch[c] >= 0) continue;
         hc[c] = false;
         PrimHit h;
-        if (!prim_test(sc.prims, ~ch[c], ray, t0, t1, sc.k2, ex, h)) continue;
+        if (!prim_test(sc.prims, sc.wlo, ~ch[c], ray, t0, t1, sc.k2, ex, h)) continue;
         if (count < cap) {
           ids[r * cap + count] = h.id;
           aa[r * cap + count] = h.a;
@@ -157,6 +157,7 @@ TraceScene trace_scene(const ugp_bvh* b) {
   TraceScene s;
   s.nodes = b->nodes;
   s.prims = b->prims;
+  s.wlo = b->wlo;
   s.n_prims = b->n_prims;
   s.n_nodes = b->n_nodes;
   s.k2 = b->k2;

@@ -19,6 +19,7 @@ constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
 struct TraceScene {
   const float4* nodes;
   const float4* prims;
+  const float4* wlo;
   int64_t n_prims;
   int64_t n_nodes;
   float k2;

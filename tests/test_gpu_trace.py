@@ -145,6 +145,43 @@ def test_transmittance_with_exclusion_and_inside_origins(gpu, orc):
     assert (np.abs(T2.cpu().numpy() - T.cpu().numpy()) > 1e-3).mean() > 0.5
 
 
+def thin_splat_scene(n=400, seed=50, ratio=100.0):
+    """Surface-like primitives (thin axis = scale / ratio) with random orientations."""
+    rng = np.random.default_rng(seed)
+    s = scenes.tiny_scene(n=n, seed=seed)
+    st = np.exp(rng.uniform(np.log(5e-4), np.log(5e-3), n))
+    s.scale[:] = np.stack([st, st * rng.uniform(0.5, 1.0, n), st / ratio], 1).astype(np.float32)
+    s.magnitude[:] = (3.0 * 2 * np.pi * s.scale[:, 0].astype(np.float64) * s.scale[:, 1]).astype(np.float32)
+    s.mean[:] = rng.uniform(0.3, 0.7, (n, 3)).astype(np.float32)
+    return s, rng
+
+
+def test_transmittance_thin_splats_grazing(gpu, orc):
+    """Thin primitives hit steeply and at grazing angles: the double-float refinement path."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s, rng = thin_splat_scene()
+    from scipy.spatial.transform import Rotation
+    n = 6000
+    pid = rng.integers(0, s.n, n)
+    w, x, y, z = s.quat[pid].astype(np.float64).T
+    R = Rotation.from_quat(np.stack([x, y, z, w], 1)).as_matrix()
+    nrm, t1v = R[:, :, 2], R[:, :, 0]
+    ang = np.where(rng.random(n) < 0.5, rng.uniform(0.2, 5.0, n), rng.uniform(5.0, 90.0, n)) * np.pi / 180
+    d = np.cos(ang)[:, None] * t1v + np.sin(ang)[:, None] * nrm
+    off = rng.normal(size=(n, 3)) * s.scale[pid, :1].astype(np.float64) * 0.8
+    target = s.mean[pid].astype(np.float64) + off
+    o = target - rng.uniform(0.05, 1.0, n)[:, None] * d
+    r = scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
+                    np.full(n, 2.0, np.float32))
+    T, st = ugp.trace_transmittance(build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                    dev(torch, r.t0), dev(torch, r.t1))
+    T_ref, tau, nh = orc.transmittance(s, r)
+    assert (nh > 0).mean() > 0.5
+    err = _t_check(T.cpu().numpy(), T_ref)
+    assert err.max() <= REL, (err.max(), int(np.argmax(err)))
+
+
 def test_hit_sets_match_brute_force(gpu, orc):
     from paper_2406_09733_gb300 import ugp
     torch = gpu
