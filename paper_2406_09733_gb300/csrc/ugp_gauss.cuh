@@ -85,7 +85,7 @@ __device__ __forceinline__ dsf ds_div(dsf a, dsf b) {
 // q = p + tn d (p = o - mu as an exact pair), o' = W q, d' = W d with W = hi + lo, then the
 // closest approach t_s = -(o'.d')/A and d2 = |o' + t_s d'|^2.  Used only for hits whose float32
 // evaluation is ill-conditioned (large whitened terms cancelling to a small result).
-__device__ __noinline__ void refine_ds(const float4 r0, const float4 r1, const float4 r2,
+static __device__ __noinline__ void refine_ds(const float4 r0, const float4 r1, const float4 r2,
                                        const float4* __restrict__ lo3, const float3 ph, const float3 pl,
                                        float tn, const float3 d, float& A_out, float& ts_out, float& d2_out) {
   const float4 l0 = __ldg(lo3), l1 = __ldg(lo3 + 1), l2 = __ldg(lo3 + 2);
