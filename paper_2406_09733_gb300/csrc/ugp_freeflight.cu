@@ -38,12 +38,13 @@ struct FFSmem {
   float ts[kK][kFFBlock];
   float s[kK][kFFBlock];
   float e0[kK][kFFBlock];
-  int id[kK][kFFBlock];
+  float th[kK][kFFBlock];
+  int id[kK][kFFBlock];   // index with the end-point flags (pack_id)
   float bin[kB][kFFBlock];
   int stk[kFFStack][kFFBlock];
 };
 
-struct Ctx {
+struct Ctx {  // per-ray state shared by the traversal visitors
   FFSmem& sm;
   int tid;
   const TraceScene& sc;
@@ -67,7 +68,8 @@ __device__ __forceinline__ void put(Ctx& c, int pos, const PrimHit& h) {
   FB(ts, pos) = h.ts;
   FB(s, pos) = h.s;
   FB(e0, pos) = h.e0;
-  FB(id, pos) = h.id;
+  FB(th, pos) = h.th;
+  FB(id, pos) = pack_id(h);
 }
 
 __device__ __forceinline__ void move(Ctx& c, int to, int from) {
@@ -77,7 +79,15 @@ __device__ __forceinline__ void move(Ctx& c, int to, int from) {
   FB(ts, to) = FB(ts, from);
   FB(s, to) = FB(s, from);
   FB(e0, to) = FB(e0, from);
+  FB(th, to) = FB(th, from);
   FB(id, to) = FB(id, from);
+}
+
+// 1/2 I of buffer entry e over [x, y].
+__device__ __forceinline__ float entry_integral(const Ctx& c, int e, float x, float y) {
+  const int p = FB(id, e);
+  return seg_half_integral(x, y, FB(a, e), FB(b, e), packed_a_end(p), packed_b_end(p), FB(tn, e), FB(ts, e),
+                           FB(s, e), FB(e0, e), FB(th, e));
 }
 
 // Nearest-first traversal of the leaves whose boxes meet [lo, hi].  The visitor may lower
@@ -157,14 +167,14 @@ struct RoundVisitor {
       ++nNew;
     } else {
       const int last = nC + nNew - 1;
-      if (!key_less(h.a, h.id, FB(a, last), FB(id, last))) {
+      if (!key_less(h.a, h.id, FB(a, last), unpack_id(FB(id, last)))) {
         t_next = fminf(t_next, h.a);
         return;
       }
       t_next = fminf(t_next, FB(a, last));  // the evicted interval starts here
       pos = last;
     }
-    while (pos > nC && key_less(h.a, h.id, FB(a, pos - 1), FB(id, pos - 1))) {
+    while (pos > nC && key_less(h.a, h.id, FB(a, pos - 1), unpack_id(FB(id, pos - 1)))) {
       move(c, pos, pos - 1);
       --pos;
     }
@@ -192,7 +202,8 @@ struct BinVisitor {
     while (j < kB - 1 && x >= edge(j + 1)) ++j;
     for (; j < kB && edge(j) < y; ++j) {
       const float xa = fmaxf(x, edge(j)), ya = fminf(y, edge(j + 1));
-      if (xa < ya) FB(bin, j) += half_integral(xa, ya, h.tn, h.ts, h.s, h.e0);
+      if (xa < ya)
+        FB(bin, j) += seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
     }
     // the partial sums only grow, so once they pass the target the crossing is known to lie
     // at or before that bin's upper edge
@@ -247,7 +258,7 @@ __device__ __forceinline__ void eval_F(Ctx& c, int nE, float lo, float Flo, floa
   fp = 0.f;
   for (int e = 0; e < nE; ++e) {
     const float x0 = fmaxf(FB(a, e), lo), x1 = fminf(FB(b, e), t);
-    if (x0 < x1) f += half_integral(x0, x1, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+    if (x0 < x1) f += entry_integral(c, e, x0, x1);
     if (FB(a, e) <= t && t <= FB(b, e)) fp += 0.5f * gauss_at(t, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
   }
 }
@@ -294,7 +305,7 @@ __device__ int choose_buffer(Ctx& c, int nE, float t, float u2) {
   while (true) {
     int best = -1, best_id = INT32_MAX;
     for (int e = 0; e < nE; ++e) {
-      const int idv = FB(id, e);
+      const int idv = unpack_id(FB(id, e));
       if (FB(a, e) <= t && t <= FB(b, e) && idv > last_id && idv < best_id) {
         best = e;
         best_id = idv;
@@ -415,13 +426,13 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
     float dF = 0.f;
     for (int e = 0; e < nE; ++e) {
       const float lo = fmaxf(FB(a, e), t_c), hi = fminf(FB(b, e), t_w);
-      if (lo < hi) dF += half_integral(lo, hi, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+      if (lo < hi) dF += entry_integral(c, e, lo, hi);
     }
     if (F_c + dF > u) {
       const float t = solve_buffer(c, nE, t_c, t_w, F_c, u);
       const int pick = choose_buffer(c, nE, t, u2);
       if (pick >= 0) {
-        out_prim = FB(id, pick);
+        out_prim = unpack_id(FB(id, pick));
         out_tu = t;
         out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
       }
@@ -436,7 +447,7 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
     }
     if (v.nNew > 0) {
       cur_a = FB(a, nE - 1);
-      cur_id = FB(id, nE - 1);
+      cur_id = unpack_id(FB(id, nE - 1));
     }
     int m = 0;  // carry the intervals still active after t_w
     for (int e = 0; e < nE; ++e) {
@@ -474,7 +485,7 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
         }
         const int pick = choose_buffer(c, v.count, t_u, u2);
         if (pick >= 0) {
-          out_prim = FB(id, pick);
+          out_prim = unpack_id(FB(id, pick));
           out_tu = t_u;
           out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
         }

@@ -43,8 +43,22 @@ struct PrimHit {
   float tn, ts; // t* = tn + ts
   float s;      // sqrt(A / 2)
   float e0;     // g0 exp(-d2 / 2): peak of G along the ray
+  float th;     // tau at the ellipsoid's exit, sqrt((k^2 - d2) / 2) (-th at its entry)
   int id;       // caller's primitive index
+  bool a_end;   // a is the ellipsoid entry (not clipped by t0)
+  bool b_end;   // b is the ellipsoid exit (not clipped by t1)
 };
+
+// An interval end that is the ellipsoid boundary has the exact erf argument -th / +th; taking
+// it from the float32 end point instead would cost s * ulp(t), large for thin primitives.
+// Flags travel in the two top bits of a stored index (indices are below 2^30).
+constexpr int kIdMask = 0x3fffffff;
+__device__ __forceinline__ int pack_id(const PrimHit& h) {
+  return h.id | (h.a_end ? 0x40000000 : 0) | (h.b_end ? int(0x80000000u) : 0);
+}
+__device__ __forceinline__ int unpack_id(int p) { return p & kIdMask; }
+__device__ __forceinline__ bool packed_a_end(int p) { return (p & 0x40000000) != 0; }
+__device__ __forceinline__ bool packed_b_end(int p) { return (p & int(0x80000000u)) != 0; }
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -180,16 +194,18 @@ __device__ __forceinline__ bool prim_test(const float4* __restrict__ recs, const
   h.ts = ts;
   h.s = sqrtf(0.5f * A);
   h.e0 = r3.x * expf(-0.5f * d2);
+  h.th = sqrtf(0.5f * (k2 - d2));
   h.id = id;
+  h.a_end = tc - half >= t0;
+  h.b_end = tc + half <= t1;
   return true;
 }
 
 __device__ __forceinline__ float tau_at(float t, float tn, float ts, float s) { return s * ((t - tn) - ts); }
 
-// 1/2 I(x, y) of App. A: 1/2 g0 e^{-d2/2} sqrt(pi / 2A) [erf(tau_y) - erf(tau_x)], with
-// sqrt(pi / 2A) = sqrt(pi) / (2 s).  Same-sign arguments use erfc to avoid cancellation.
-__device__ __forceinline__ float half_integral(float x, float y, float tn, float ts, float s, float e0) {
-  const float tx = tau_at(x, tn, ts, s), ty = tau_at(y, tn, ts, s);
+// 1/2 I between erf arguments tx <= ty (App. A): 1/2 g0 e^{-d2/2} sqrt(pi / 2A) [erf(ty) - erf(tx)],
+// with sqrt(pi / 2A) = sqrt(pi) / (2 s).  Same-sign arguments use erfc to avoid cancellation.
+__device__ __forceinline__ float half_integral_tau(float tx, float ty, float s, float e0) {
   float diff;
   if (tx >= 0.f)
     diff = erfcf(tx) - erfcf(ty);
@@ -198,6 +214,19 @@ __device__ __forceinline__ float half_integral(float x, float y, float tn, float
   else
     diff = erff(ty) - erff(tx);
   return e0 * (0.25f * kSqrtPi) / s * diff;
+}
+
+// 1/2 I(x, y) for a sub-range [x, y] of a clipped interval [a, b].
+__device__ __forceinline__ float seg_half_integral(float x, float y, float a, float b, bool a_end, bool b_end,
+                                                   float tn, float ts, float s, float e0, float th) {
+  const float tx = (a_end && x == a) ? -th : tau_at(x, tn, ts, s);
+  const float ty = (b_end && y == b) ? th : tau_at(y, tn, ts, s);
+  return half_integral_tau(tx, ty, s, e0);
+}
+
+// 1/2 I over a hit's whole clipped interval.
+__device__ __forceinline__ float hit_half_integral(const PrimHit& h) {
+  return seg_half_integral(h.a, h.b, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
 }
 
 // G(x_t) of Eq. 1 along the ray: e0 exp(-tau^2).

@@ -48,13 +48,13 @@ k_transmittance(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, con
       if (h0 && n3.x < 0) {
         ++n_prims;
         if (prim_test(sc.prims, sc.wlo, ~n3.x, ray, t0, t1, sc.k2, ex, h))
-          acc += half_integral(h.a, h.b, h.tn, h.ts, h.s, h.e0);
+          acc += hit_half_integral(h);
         h0 = false;
       }
       if (h1 && n3.y < 0) {
         ++n_prims;
         if (prim_test(sc.prims, sc.wlo, ~n3.y, ray, t0, t1, sc.k2, ex, h))
-          acc += half_integral(h.a, h.b, h.tn, h.ts, h.s, h.e0);
+          acc += hit_half_integral(h);
         h1 = false;
       }
       if (acc >= 1.f) break;  // saturated: T = 0 whatever follows
