@@ -143,8 +143,10 @@ ugp_status ugp_trace_transmittance(const ugp_bvh* bvh, int64_t n_rays, const flo
  *  - if F(t1) <= u the ray escapes: prim_out = -1, t_u_out = t1,
  *    t_spawn_out = t1;
  *  - otherwise t_u solves F(t_u) = u, and the primitive is drawn among those
- *    whose interval contains t_u with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u}),
- *    scanning them in ascending primitive index with the second uniform u2.
+ *    whose interval contains t_u with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u})
+ *    by an exponential race: candidate k gets E_k = -ln U_k, U_k = ((x0 >> 8) + 1) / 2^24
+ *    where x = Philox4x32-10(counter (k, 0, 0, 0), key (bit pattern of u2, 0x2406C0DE)),
+ *    and the smallest E_k / G_k(x_{t_u}) wins (ties: smaller index).
  *    t_spawn_out is the centre of the chosen primitive's clipped interval,
  *    where the paper spawns the scattered ray (Sec. 6).
  * The chosen primitive k has probability 1/2 I_k(a_k, min(b_k, t_sat)), the

@@ -50,7 +50,9 @@ def lib():
                                         f32p, f32p, i32p, f64p, f64p, i32p]
         L.orc_sample_free_flight.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p,
                                              f32p, f32p, f32p, i32p, f32p, f32p, i32p, f64p,
-                                             f64p, f64p, i32p]
+                                             f64p, f64p, i32p, f64p]
+        L.orc_race_exponential.argtypes = [C.c_double, C.c_int32]
+        L.orc_race_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
         L.orc_erfinv.argtypes = [C.c_double]
         L.orc_erfinv.restype = C.c_double
@@ -172,11 +174,17 @@ def sample_free_flight(scene, rays, u, u2, exclude=None, eps=0.01):
     prim = np.zeros(n, np.int32)
     tu, ts, fe = np.zeros(n), np.zeros(n), np.zeros(n)
     na = np.zeros(n, np.int32)
+    mg = np.zeros(n)
     lib().orc_sample_free_flight(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
                                  _ptr(t1, f32p), _ptr(ex, i32p), _ptr(u, f32p), _ptr(u2, f32p),
                                  _ptr(prim, i32p), _ptr(tu, f64p), _ptr(ts, f64p), _ptr(fe, f64p),
-                                 _ptr(na, i32p))
-    return dict(prim=prim, t_u=tu, t_spawn=ts, F_end=fe, n_active=na)
+                                 _ptr(na, i32p), _ptr(mg, f64p))
+    return dict(prim=prim, t_u=tu, t_spawn=ts, F_end=fe, n_active=na, race_margin=mg)
+
+
+def race_exponential(u2: float, k: int) -> float:
+    """The race variate E_k = -ln U_k of primitive k for the uniform u2 (free-flight choice)."""
+    return float(lib().orc_race_exponential(float(np.float32(u2)), int(k)))
 
 
 def prim_quadratic(scene, i, o, d, _sr=None):

@@ -126,7 +126,7 @@ void orc_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, c
                             const float* d3, const float* t0, const float* t1,
                             const int32_t* exclude, const float* u, const float* u2,
                             int32_t* prim_out, double* t_u_out, double* t_spawn_out,
-                            double* F_end_out, int32_t* n_active_out) {
+                            double* F_end_out, int32_t* n_active_out, double* race_margin_out) {
   const std::vector<Prim> prims = make_prims(scene_in(s));
   const double k = cutoff_k(cutoff_eps);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -139,6 +139,7 @@ void orc_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, c
     t_spawn_out[r] = f.t_spawn;
     if (F_end_out) F_end_out[r] = f.F_end;
     if (n_active_out) n_active_out[r] = f.n_active;
+    if (race_margin_out) race_margin_out[r] = f.race_margin;
   }
 }
 
@@ -149,6 +150,7 @@ void orc_prim_quadratic(const orc_scene* s, int64_t i, const float* o3, const fl
 }
 
 double orc_erfinv(double y) { return erfinv(y); }
+double orc_race_exponential(double u2, int32_t k) { return race_exponential(u2, k); }
 
 // ------------------------------------------------------------------ appearance (Sec. 6, App. B)
 static V3 d3v(const double* p) { return v3(p[0], p[1], p[2]); }

@@ -5,6 +5,7 @@
 // and shares no code with, the CUDA library.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <limits>
 
 #include "oracle_internal.h"
@@ -125,6 +126,20 @@ double transmittance(const std::vector<Prim>& prims, V3 o, V3 d, double t0, doub
   return std::max(0.0, 1.0 - tau);
 }
 
+// Exponential variate of primitive k in the race that picks the scattering primitive: Philox4x32-10
+// with key (bits of u2, 0x2406C0DE) and counter (k, 0, 0, 0); U = (x0 >> 8 + 1) / 2^24 in (0, 1].
+double race_exponential(double u2, int32_t k) {
+  const float f = float(u2);
+  uint32_t bits;
+  std::memcpy(&bits, &f, 4);
+  const uint32_t ctr[4] = {uint32_t(k), 0u, 0u, 0u};
+  const uint32_t key[2] = {bits, 0x2406C0DEu};
+  uint32_t x[4];
+  philox4x32_10(ctr, key, x);
+  const double U = double((x[0] >> 8) + 1u) * (1.0 / 16777216.0);
+  return -std::log(U);
+}
+
 // erf^-1 by Newton's method on std::erf, started from a bisection bracket.
 double erfinv(double y) {
   if (y <= -1.0) return -std::numeric_limits<double>::infinity();
@@ -152,12 +167,12 @@ double erfinv(double y) {
 //     bracketed Newton iteration with F' = 1/2 sum_active G_k (Eq. 9); with a single active
 //     primitive the erf^-1 closed form is tried first.
 //  5. The primitive is chosen among the primitives active at t_u with probability
-//     G_k(x_{t_u}) / sum_active G_j(x_{t_u}), walking them in ascending primitive id.
+//     G_k(x_{t_u}) / sum_active G_j(x_{t_u}) by an exponential race keyed by u2 (race_exponential).
 //  Since u < 1, t_u lies before the saturating distance, so primitive k is returned with
 //  probability 1/2 I_k(a_k, min(b_k, t_sat)).
 FreeFlight sample_free_flight_hits(const std::vector<Hit>& hits, double t0, double t1, double u,
                                    double u2) {
-  FreeFlight r{-1, 0.0, 0.0, 0.0, 0};
+  FreeFlight r{-1, 0.0, 0.0, 0.0, 0, std::numeric_limits<double>::infinity()};
   std::vector<double> ev;
   ev.reserve(2 * hits.size() + 2);
   for (const Hit& h : hits) {
@@ -221,20 +236,22 @@ FreeFlight sample_free_flight_hits(const std::vector<Hit>& hits, double t0, doub
       }
     }
     r.t_u = t;
-    // Choose among the primitives active at t_u, proportionally to G_k(x_{t_u}).
-    std::vector<const Hit*> by_id(act.begin(), act.end());
-    std::sort(by_id.begin(), by_id.end(), [](const Hit* x, const Hit* y) { return x->id < y->id; });
-    double tot = 0.0;
-    for (const Hit* h : by_id) tot += gauss_at(*h, t);
-    double cum = 0.0;
-    const Hit* pick = by_id.back();
-    for (const Hit* h : by_id) {
-      cum += gauss_at(*h, t);
-      if (cum > u2 * tot) {
+    // Choose among the primitives active at t_u, proportionally to G_k(x_{t_u}), by an
+    // exponential race: primitive k draws E_k = -ln U_k and the smallest E_k / G_k wins, which
+    // happens with probability G_k / sum_j G_j whatever the order the candidates are seen in.
+    const Hit* pick = nullptr;
+    double best = std::numeric_limits<double>::infinity(), second = best;
+    for (const Hit* h : act) {
+      const double key = race_exponential(u2, h->id) / gauss_at(*h, t);
+      if (key < best || (key == best && pick && h->id < pick->id)) {
+        second = best;
+        best = key;
         pick = h;
-        break;
+      } else if (key < second) {
+        second = key;
       }
     }
+    r.race_margin = act.size() > 1 ? (second - best) / best : std::numeric_limits<double>::infinity();
     r.prim = pick->id;
     r.t_spawn = 0.5 * (pick->a + pick->b);
     r.n_active = int32_t(act.size());

@@ -92,6 +92,7 @@ struct FreeFlight {
   double t_spawn; // centre of the chosen primitive's clipped interval
   double F_end;   // F(t1) = 1/2 sum_k I_k(clip) (unclamped optical depth)
   int32_t n_active;
+  double race_margin;  // relative gap between the two smallest race keys (inf if one candidate)
 };
 FreeFlight sample_free_flight(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
                               double k, int32_t exclude, double u, double u2);
@@ -99,6 +100,7 @@ FreeFlight sample_free_flight_hits(const std::vector<Hit>& hits, double t0, doub
                                    double u2);
 
 double erfinv(double y);
+double race_exponential(double u2, int32_t k);
 
 // Philox4x32-10 (Salmon et al., SC'11).
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -3,9 +3,11 @@
 // Definition (order-free).  With the clipped intervals [a_k, b_k] of the primitives along the
 // ray and F(t) = 1/2 sum_k I_k(a_k, min(t, b_k)): the ray escapes if F(t1) <= u; otherwise
 // t_u solves F(t_u) = u and the primitive is drawn among those whose interval contains t_u
-// with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u}), scanning them in ascending index with
-// the second uniform u2.  Since u < 1, t_u lies before the saturating distance, so primitive k
-// is chosen with probability 1/2 I_k(a_k, min(b_k, t_sat)).
+// with probability G_k(x_{t_u}) / sum_j G_j(x_{t_u}).  The draw is an exponential race: each
+// candidate k gets E_k = -ln U_k with U_k from Philox keyed by u2 and counter k, and the
+// smallest E_k / G_k wins, so the result does not depend on the order candidates are seen in.
+// Since u < 1, t_u lies before the saturating distance, so primitive k is chosen with
+// probability 1/2 I_k(a_k, min(b_k, t_sat)).
 //
 // A BVH gives no front-to-back order (the paper's reason for a kd-tree, Sec. 5.1), so the
 // kernel finds t_u in one of two ways, both exact:
@@ -16,16 +18,15 @@
 //    t_w (the smallest dropped start, or the entry of a pruned subtree), so F on [t_c, t_w] is
 //    known from the buffer; if it crosses u there, a safeguarded Newton iteration with
 //    F' = 1/2 sum G (Eq. 9) finds t_u, else the window advances.
-//  * binned refinement (fallback when more than kK intervals overlap, as in dense aggregates).
-//    In the spirit of the paper's GPU binning (Sec. 5.2), one traversal adds each interval's
-//    contribution to kB equal bins of the current window [lo, hi], pruning subtrees that start
-//    after the bin where the running sum passes u.  The window then shrinks to the crossing
-//    bin, until the intervals meeting it fit the buffer (Newton as above) or the window is one
-//    float wide.  Memory per ray stays fixed whatever the overlap depth.
-//
-// The choice at t_u uses the buffer when it holds every interval containing t_u, and otherwise
-// id-ordered passes that each collect the next kK smallest indices containing t_u.
+//  * dense mode (when more than kK intervals overlap, as in dense aggregates, or after
+//    kFFMaxRounds rounds).  In the spirit of the paper's GPU binning (Sec. 5.2), one traversal
+//    adds each interval's contribution to kB equal bins of [t_c, scene exit], pruning subtrees
+//    that start after the bin where the running sum passes u; this brackets t_u in one bin.  A
+//    safeguarded Newton iteration then evaluates F and F' on the bracket by order-free
+//    traversals, which need no per-ray storage whatever the overlap depth, and one more
+//    traversal runs the race at t_u.
 #include "ugp_gauss.cuh"
+#include "ugp_philox.cuh"
 #include "ugp_trace.cuh"
 
 namespace ugp {
@@ -218,36 +219,44 @@ struct BinVisitor {
   }
 };
 
-// ---------------------------------------------------------------- choice passes visitor
-struct ChoiceVisitor {
+// ---------------------------------------------------------------- dense mode: F by traversal
+// F(t) - F(lo) = sum over all intervals of 1/2 I(max(a, lo), min(b, t)) and F'(t) = 1/2 sum G(t),
+// accumulated in any order (no buffer).
+struct FVisitor {
   Ctx& c;
-  float t;
-  int last_id, n;  // collect the kK smallest indices above last_id among intervals containing t
-  int total;       // number of intervals containing t
-  float S;         // sum of G over them
+  float lo, t;
+  float f, fp;
+  __device__ void pruned(float) {}
+  __device__ void leaf(int slot, float&) {
+    PrimHit h;
+    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
+    const float x = fmaxf(h.a, lo), y = fminf(h.b, t);
+    if (x < y) f += seg_half_integral(x, y, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
+    if (h.a <= t && t <= h.b) fp += 0.5f * gauss_at(t, h.tn, h.ts, h.s, h.e0);
+  }
+};
+
+// ---------------------------------------------------------------- the choice at t_u
+// Exponential race among the primitives whose interval contains t: the smallest
+// E_k / G_k(x_t) wins, i.e. primitive k with probability G_k / sum_j G_j, in one pass.
+struct RaceVisitor {
+  Ctx& c;
+  float t, u2;
+  float best;
+  int best_id;
+  float a, b;
   __device__ void pruned(float) {}
   __device__ void leaf(int slot, float&) {
     PrimHit h;
     if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     if (!(h.a <= t && t <= h.b)) return;
-    const float g = gauss_at(t, h.tn, h.ts, h.s, h.e0);
-    ++total;
-    S += g;
-    if (h.id <= last_id) return;
-    int pos;
-    if (n < kK) {
-      pos = n++;
-    } else {
-      if (h.id >= FB(id, kK - 1)) return;
-      pos = kK - 1;
+    const float key = race_exponential(u2, h.id) / gauss_at(t, h.tn, h.ts, h.s, h.e0);
+    if (key < best || (key == best && h.id < best_id)) {
+      best = key;
+      best_id = h.id;
+      a = h.a;
+      b = h.b;
     }
-    while (pos > 0 && h.id < FB(id, pos - 1)) {
-      FB(id, pos) = FB(id, pos - 1);
-      FB(a, pos) = FB(a, pos - 1);
-      --pos;
-    }
-    FB(id, pos) = h.id;
-    FB(a, pos) = g;
   }
 };
 
@@ -294,78 +303,20 @@ __device__ float solve_buffer(Ctx& c, int nE, float lo, float hi, float Flo, flo
   return t;
 }
 
-// Choice among buffer entries [0, nE) containing t: proportional to G, ascending index.
+// Choice among buffer entries [0, nE) containing t by the exponential race (RaceVisitor).
 __device__ int choose_buffer(Ctx& c, int nE, float t, float u2) {
-  float tot = 0.f;
-  for (int e = 0; e < nE; ++e)
-    if (FB(a, e) <= t && t <= FB(b, e)) tot += gauss_at(t, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
-  const float target = u2 * tot;
-  float cum = 0.f;
-  int last_id = -1, pick = -1, any = -1;
-  while (true) {
-    int best = -1, best_id = INT32_MAX;
-    for (int e = 0; e < nE; ++e) {
-      const int idv = unpack_id(FB(id, e));
-      if (FB(a, e) <= t && t <= FB(b, e) && idv > last_id && idv < best_id) {
-        best = e;
-        best_id = idv;
-      }
-    }
-    if (best < 0) break;
-    any = best;
-    cum += gauss_at(t, FB(tn, best), FB(ts, best), FB(s, best), FB(e0, best));
-    last_id = best_id;
-    if (cum > target) {
-      pick = best;
-      break;
+  int pick = -1, pick_id = INT32_MAX;
+  float best = INFINITY;
+  for (int e = 0; e < nE; ++e) {
+    if (!(FB(a, e) <= t && t <= FB(b, e))) continue;
+    const int idv = unpack_id(FB(id, e));
+    const float key = race_exponential(u2, idv) / gauss_at(t, FB(tn, e), FB(ts, e), FB(s, e), FB(e0, e));
+    if (pick < 0 || key < best || (key == best && idv < pick_id)) {
+      best = key;
+      pick = e;
+      pick_id = idv;
     }
   }
-  return pick >= 0 ? pick : any;
-}
-
-// Choice by id-ordered traversal passes (any number of intervals containing t).  Returns the
-// chosen primitive index and its clipped interval through a_out / b_out.
-struct FindVisitor {
-  Ctx& c;
-  int want;
-  float a, b;
-  __device__ void pruned(float) {}
-  __device__ void leaf(int slot, float&) {
-    PrimHit h;
-    if (prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h) && h.id == want) {
-      a = h.a;
-      b = h.b;
-    }
-  }
-};
-
-__device__ int choose_passes(Ctx& c, float t, float u2, float& a_out, float& b_out) {
-  float S = -1.f, target = 0.f, cum = 0.f;
-  int last_id = -1, any = -1, pick = -1;
-  for (int pass = 0; pass < kChoicePasses && pick < 0; ++pass) {
-    ChoiceVisitor v{c, t, last_id, 0, 0, 0.f};
-    float limit = t;
-    traverse(c, t, t, limit, v);
-    if (c.st != UGP_RAY_OK) return -1;
-    if (S < 0.f) {
-      S = v.S;
-      target = u2 * S;
-    }
-    for (int e = 0; e < v.n && pick < 0; ++e) {
-      any = FB(id, e);
-      cum += FB(a, e);
-      if (cum > target) pick = any;
-    }
-    if (v.n < kK) break;  // every interval containing t has been seen
-    last_id = FB(id, v.n - 1);
-  }
-  if (pick < 0) pick = any;  // rounding left the sum just short of u2 * S
-  if (pick < 0) return -1;
-  FindVisitor f{c, pick, t, t};
-  float limit = t;
-  traverse(c, t, t, limit, f);
-  a_out = f.a;
-  b_out = f.b;
   return pick;
 }
 
@@ -458,73 +409,79 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
     }
     nC = m;
   }
-  // ---------------- binned refinement ----------------
+  // ---------------- dense mode: binned bracket, then Newton by traversal ----------------
   if (dense && c.st == UGP_RAY_OK) {
-    float lo = t_c, hi = scene_exit(c, t_c, c.t1), Flo = F_c;
-    bool solved = false;
-    float t_u = hi;
-    for (int level = 0; level < kDenseLevels && !solved; ++level) {
-      for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
-      BinVisitor v{c, lo, hi, (hi - lo) / float(kB), u - Flo, 0};
-      float limit = hi;
-      traverse(c, lo, hi, limit, v);
-      if (c.st != UGP_RAY_OK) break;
-      if (v.count <= kK) {
-        // every interval meeting [lo, limit] is in the buffer
-        float f, fp;
-        eval_F(c, v.count, lo, Flo, u, limit, f, fp);
-        if (f <= 0.f) {
-          if (level == 0 && limit >= hi) {  // F(end) <= u: escape
-            solved = true;
-            t_u = -1.f;
-            break;
-          }
-          t_u = limit;  // rounding put the crossing at the window's end
-        } else {
-          t_u = solve_buffer(c, v.count, lo, limit, Flo, u);
-        }
+    const float lo0 = t_c, hi0 = scene_exit(c, t_c, c.t1);
+    for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
+    BinVisitor v{c, lo0, hi0, (hi0 - lo0) / float(kB), u - F_c, 0};
+    float limit = hi0;
+    traverse(c, lo0, hi0, limit, v);
+    float t_u = -1.f;
+    if (c.st == UGP_RAY_OK && v.count <= kK) {
+      // every interval meeting [lo0, limit] is in the buffer
+      float f, fp;
+      eval_F(c, v.count, lo0, F_c, u, limit, f, fp);
+      if (f > 0.f || limit < hi0) {
+        t_u = f > 0.f ? solve_buffer(c, v.count, lo0, limit, F_c, u) : limit;
         const int pick = choose_buffer(c, v.count, t_u, u2);
         if (pick >= 0) {
           out_prim = unpack_id(FB(id, pick));
           out_tu = t_u;
           out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
         }
-        solved = true;
-        break;
       }
-      // crossing bin
+    } else if (c.st == UGP_RAY_OK) {
       float acc = 0.f;
       int jx = -1;
       for (int j = 0; j < kB; ++j) {
         const float nxt = acc + FB(bin, j);
-        if (nxt > u - Flo) {
+        if (nxt > u - F_c) {
           jx = j;
           break;
         }
         acc = nxt;
       }
-      if (jx < 0) {
-        if (level == 0) {  // F(end) <= u: escape
-          solved = true;
-          t_u = -1.f;
-          break;
+      if (jx >= 0) {   // otherwise F(end) <= u: escape
+        float lo = v.edge(jx), hi = v.edge(jx + 1);
+        const float Flo = F_c + acc;
+        const float inbin = FB(bin, jx);
+        float t = inbin > 0.f ? lo + (u - Flo) / inbin * (hi - lo) : 0.5f * (lo + hi);
+        if (!(t > lo && t < hi)) t = 0.5f * (lo + hi);
+        const float w_lo = lo;
+        float dx_old = hi - lo, dx = dx_old;
+        bool conv = false;
+        for (int it = 0; it < kDenseNewtonIters && c.st == UGP_RAY_OK; ++it) {
+          FVisitor fv{c, w_lo, t, Flo - u, 0.f};
+          float lim = t;
+          traverse(c, w_lo, t, lim, fv);
+          const float f = fv.f, fp = fv.fp;
+          if (f == 0.f) { conv = true; break; }
+          if (f < 0.f) lo = t; else hi = t;
+          if (!(nextafterf(lo, INFINITY) < hi)) { conv = true; break; }
+          const float tn = fp > 0.f ? t - f / fp : lo;
+          float tnew;
+          if (fp > 0.f && tn > lo && tn < hi && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
+            dx_old = dx;
+            dx = f / fp;
+            tnew = tn;
+          } else {
+            dx_old = dx;
+            dx = 0.5f * (hi - lo);
+            tnew = lo + dx;
+          }
+          if (tnew == t) { conv = true; break; }
+          t = tnew;
         }
-        jx = kB - 1;  // rounding: the crossing is at the window's end
-      }
-      const float nlo = v.edge(jx), nhi = v.edge(jx + 1);
-      Flo += acc;
-      lo = nlo;
-      hi = nhi;
-      t_u = 0.5f * (lo + hi);
-      if (!(nextafterf(lo, INFINITY) < hi)) break;  // window one float wide
-    }
-    if (!solved && c.st == UGP_RAY_OK) {
-      float a_k = t_u, b_k = t_u;
-      const int pid = choose_passes(c, t_u, u2, a_k, b_k);
-      if (pid >= 0) {
-        out_prim = pid;
-        out_tu = t_u;
-        out_tsp = 0.5f * (a_k + b_k);
+        if (!conv && c.st == UGP_RAY_OK) c.st = UGP_RAY_SOLVE_LIMIT;
+        t_u = t;
+        RaceVisitor rv{c, t_u, u2, INFINITY, INT32_MAX, t_u, t_u};
+        float lim = t_u;
+        traverse(c, t_u, t_u, lim, rv);
+        if (rv.best_id != INT32_MAX) {
+          out_prim = rv.best_id;
+          out_tu = t_u;
+          out_tsp = 0.5f * (rv.a + rv.b);
+        }
       }
     }
   }

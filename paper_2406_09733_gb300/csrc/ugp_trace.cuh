@@ -11,9 +11,8 @@ constexpr int kFFBlock = 64;       // free flight: threads per block
 constexpr int kK = 16;             // free flight: interval buffer per ray
 constexpr int kFFStack = 48;       // free flight: traversal stack depth
 constexpr int kFFMaxRounds = 8;    // free flight: collection rounds before the binned mode
-constexpr int kB = 16;             // free flight: bins per refinement level of the binned mode
-constexpr int kDenseLevels = 16;   // free flight: refinement levels of the binned mode
-constexpr int kChoicePasses = 64;  // free flight: id-ordered passes of the final choice
+constexpr int kB = 16;             // free flight: bins of the dense mode's bracketing pass
+constexpr int kDenseNewtonIters = 32;  // free flight: traversal-evaluated Newton steps (dense mode)
 constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
 
 struct TraceScene {

@@ -219,18 +219,19 @@ def test_hit_sets_match_brute_force(gpu, orc):
 
 
 def _ff_compare(orc, s, r, u, u2, prim, tu, tsp, exclude=None, max_frac=1e-3):
+    """Free-flight parity.  A differing primitive is accepted only at a rounding-level
+    boundary: the oracle flips to the GPU's answer when u moves by 1e-5 (escape / interval
+    boundaries), or its exponential race had a near-tie (margin < 1e-4)."""
     ref = orc.sample_free_flight(s, r, u, u2, exclude=exclude)
     mism = np.nonzero(prim != ref["prim"])[0]
     unexplained = []
     for j in mism:
-        ok = False
-        for du in (-REL, 0.0, REL):
-            for du2 in (-REL, 0.0, REL):
-                rj = scenes.Rays(r.o[j:j + 1], r.d[j:j + 1], r.t0[j:j + 1], r.t1[j:j + 1])
-                f = orc.sample_free_flight(s, rj, np.clip(u[j:j + 1] + du, 0, 1 - 2 ** -24),
-                                           np.clip(u2[j:j + 1] + du2, 0, 1 - 2 ** -24),
-                                           exclude=None if exclude is None else exclude[j:j + 1])
-                ok |= f["prim"][0] == prim[j]
+        ok = prim[j] >= 0 and ref["prim"][j] >= 0 and ref["race_margin"][j] < 1e-4
+        for du in (-REL, REL):
+            rj = scenes.Rays(r.o[j:j + 1], r.d[j:j + 1], r.t0[j:j + 1], r.t1[j:j + 1])
+            f = orc.sample_free_flight(s, rj, np.clip(u[j:j + 1] + du, 0, 1 - 2 ** -24), u2[j:j + 1],
+                                       exclude=None if exclude is None else exclude[j:j + 1])
+            ok |= f["prim"][0] == prim[j]
         if not ok:
             unexplained.append(j)
     assert not unexplained, [(j, prim[j], ref["prim"][j], u[j], u2[j]) for j in unexplained[:5]]
