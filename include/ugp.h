@@ -175,6 +175,72 @@ ugp_status ugp_collect_hits(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
                             int32_t cap, int32_t* ids_out, float* a_out, float* b_out,
                             int32_t* count_out, uint8_t* status_out, void* stream);
 
+/* ------------------------------------------------------------------ rendering
+ * Per-primitive appearance (Sec. 6), device arrays in the caller's order:
+ *   sggx6      SGGX matrix S (Sxx, Syy, Szz, Sxy, Sxz, Syz), positive definite (n x 6)
+ *   type       0 Lambertian base, 1 GGX base, 2 emissive (pure emitter)      (n, uint8)
+ *   albedo3    Lambertian rho, or the GGX base's Schlick F0                  (n x 3)
+ *   roughness  GGX alpha in (0, 1]                                          (n)
+ *   emission3  radiance of emissive primitives (isotropic)                  (n x 3) */
+typedef struct ugp_materials {
+  const float* sggx6;
+  const uint8_t* type;
+  const float* albedo3;
+  const float* roughness;
+  const float* emission3;
+} ugp_materials;
+
+/* Pinhole camera (host struct).  Pixel (px, py), row 0 at the top, is sampled at
+ * (px + jx, py + jy) with a Philox jitter (bounce 15, slot 0). */
+typedef struct ugp_camera {
+  float eye[3], look[3], up[3];
+  float vfov_deg;
+  int32_t width, height;
+} ugp_camera;
+
+/* Lights (host struct): an optional one-sided parallelogram area light
+ * {corner + a e1 + b e2, a, b in [0, 1]} emitting quad_Le towards e1 x e2, and a
+ * constant background radiance bg seen by rays that escape without reaching the light. */
+typedef struct ugp_lights {
+  int32_t has_quad;
+  float quad_corner[3], quad_e1[3], quad_e2[3], quad_Le[3];
+  float bg[3];
+} ugp_lights;
+
+/* Render parameters (host struct).
+ *   spp, spp_begin  samples [spp_begin, spp_begin + spp) of every pixel (resumable)
+ *   max_depth       at most max_depth scattering vertices per path (>= 0)
+ *   nee             1: light sampling with balance-heuristic MIS (Table 1), 0: none
+ *   seed            Philox key (low, high 32 bits)
+ *   spawn_mode      0: scattered rays start at the centre of the chosen primitive's
+ *                   clipped interval (Sec. 6), 1: at x_{t_u} */
+typedef struct ugp_render_params {
+  int32_t spp, spp_begin, max_depth, nee;
+  uint64_t seed;
+  int32_t spawn_mode, reserved;
+} ugp_render_params;
+
+/* Workspace bytes ugp_render needs for a width x height image (path state and
+ * queues, 128 bytes per pixel plus alignment). */
+size_t ugp_render_workspace_size(int32_t width, int32_t height);
+
+/* Path-traces the image with the volumetric path tracer of Table 1 (right column)
+ * as a wavefront: per bounce, an extend pass (free-flight sampling,
+ * ugp_sample_free_flight), a shade pass (emission, light sampling, phase
+ * sampling) and a shadow pass (ugp_trace_transmittance), with live paths
+ * compacted between bounces.  Random numbers are Philox4x32-10 with counter
+ * (pixel, sample, 16 * bounce + slot, 0); slots: 0 free flight, 1 phase
+ * sampling, 3 light point, 4-5 stochastic phase evaluation.
+ *   accum_rgb, accum_sq_rgb  device float arrays (height x width x 3) to which the
+ *                per-pixel sums of sample values and of their squares are ADDED
+ *   ray_counts   device uint64[3] or NULL: [0] += free-flight queries,
+ *                [1] += shadow queries, [2] += queries with a non-zero ray status
+ * Asynchronous on `stream`. */
+ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const ugp_camera* camera,
+                      const ugp_lights* lights, const ugp_render_params* params, float* accum_rgb,
+                      float* accum_sq_rgb, void* workspace, size_t workspace_bytes,
+                      unsigned long long* ray_counts, void* stream);
+
 /* Optional traversal statistics: when `counters` is a device pointer to 6
  * zero-initialised uint64, later tracing calls on any stream add
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,

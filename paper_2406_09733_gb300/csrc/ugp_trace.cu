@@ -4,6 +4,7 @@
 // (stack[level][thread]) so neighbouring threads hit neighbouring banks.
 #include "ugp_gauss.cuh"
 #include "ugp_trace.cuh"
+#include "ugp_transmit.cuh"
 
 namespace ugp {
 
@@ -17,72 +18,15 @@ k_transmittance(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, con
                 const int32_t* __restrict__ excl, float* __restrict__ T_out, uint8_t* __restrict__ st_out,
                 unsigned long long* __restrict__ ctr) {
   __shared__ int stk[kTrStack * kTrBlock];
-  const int tid = threadIdx.x;
-  const int64_t r = int64_t(blockIdx.x) * kTrBlock + tid;
+  const int64_t r = int64_t(blockIdx.x) * kTrBlock + threadIdx.x;
   if (r >= n_rays) return;
-  const Ray ray = make_ray(ld3(o3, r), ld3(d3, r));
-  const float t0 = __ldg(t0a + r), t1 = __ldg(t1a + r);
-  const int ex = excl ? __ldg(excl + r) : -1;
-  unsigned n_nodes = 0, n_prims = 0;
-  float acc = 0.f;
-  uint8_t st = UGP_RAY_OK;
-  if (sc.n_prims > 0 && t0 < t1) {
-    int sp = 0, node = 0;
-    while (true) {
-      if (unsigned(node) >= unsigned(sc.n_nodes)) {
-        st = UGP_RAY_BAD_NODE;
-        break;
-      }
-      const float4* nd = sc.nodes + 4 * node;
-      const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
-      const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
-      ++n_nodes;
-      float e0, e1;
-      bool h0 = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, ray, t0, t1, e0);
-      bool h1 = n3.y != kEmptyChild && slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, ray, t0, t1, e1);
-      PrimHit h;
-      if ((n3.x < 0 && ~n3.x >= sc.n_prims) || (n3.y < 0 && n3.y != kEmptyChild && ~n3.y >= sc.n_prims)) {
-        st = UGP_RAY_BAD_NODE;
-        break;
-      }
-      if (h0 && n3.x < 0) {
-        ++n_prims;
-        if (prim_test(sc.prims, sc.wlo, ~n3.x, ray, t0, t1, sc.k2, ex, h))
-          acc += hit_half_integral(h);
-        h0 = false;
-      }
-      if (h1 && n3.y < 0) {
-        ++n_prims;
-        if (prim_test(sc.prims, sc.wlo, ~n3.y, ray, t0, t1, sc.k2, ex, h))
-          acc += hit_half_integral(h);
-        h1 = false;
-      }
-      if (acc >= 1.f) break;  // saturated: T = 0 whatever follows
-      if (h0 && h1) {
-        const bool first0 = e0 <= e1;
-        if (sp == kTrStack) {
-          st = UGP_RAY_STACK_OVERFLOW;
-          break;
-        }
-        stk[sp * kTrBlock + tid] = first0 ? n3.y : n3.x;
-        ++sp;
-        node = first0 ? n3.x : n3.y;
-      } else if (h0) {
-        node = n3.x;
-      } else if (h1) {
-        node = n3.y;
-      } else {
-        if (sp == 0) break;
-        --sp;
-        node = stk[sp * kTrBlock + tid];
-      }
-    }
-  }
+  TrStats ts{0u, 0u, UGP_RAY_OK};
+  const float acc = tr_optical_depth(sc, make_ray(ld3(o3, r), ld3(d3, r)), __ldg(t0a + r), __ldg(t1a + r),
+                                     excl ? __ldg(excl + r) : -1, stk + threadIdx.x, kTrBlock, ts);
   T_out[r] = fmaxf(0.f, 1.f - acc);
-  if (st_out) st_out[r] = st;
-  if (STATS) add_counters(ctr, n_nodes, n_prims, 1u, 1u, 0u);
+  if (st_out) st_out[r] = ts.st;
+  if (STATS) add_counters(ctr, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);
 }
-
 
 // All hits along each ray, for hit-set diagnostics (no early exit).
 __global__ void __launch_bounds__(kTrBlock)

@@ -29,6 +29,26 @@ class UgpBvhInfo(C.Structure):
                 ("persistent_bytes", C.c_size_t), ("n_invalid", C.c_int64)]
 
 
+class UgpMaterials(C.Structure):
+    _fields_ = [("sggx6", vp), ("type", vp), ("albedo3", vp), ("roughness", vp), ("emission3", vp)]
+
+
+class UgpCamera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("look", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class UgpLights(C.Structure):
+    _fields_ = [("has_quad", C.c_int32), ("quad_corner", C.c_float * 3), ("quad_e1", C.c_float * 3),
+                ("quad_e2", C.c_float * 3), ("quad_Le", C.c_float * 3), ("bg", C.c_float * 3)]
+
+
+class UgpRenderParams(C.Structure):
+    _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
+                ("nee", C.c_int32), ("seed", C.c_uint64), ("spawn_mode", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class UgpError(RuntimeError):
     pass
 
@@ -65,6 +85,12 @@ def lib():
         L.ugp_collect_hits.restype = C.c_int
         L.ugp_collect_hits.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp,
                                        vp, vp, vp]
+        L.ugp_render_workspace_size.restype = C.c_size_t
+        L.ugp_render_workspace_size.argtypes = [C.c_int32, C.c_int32]
+        L.ugp_render.restype = C.c_int
+        L.ugp_render.argtypes = [vp, C.POINTER(UgpMaterials), C.POINTER(UgpCamera),
+                                 C.POINTER(UgpLights), C.POINTER(UgpRenderParams), vp, vp, vp,
+                                 C.c_size_t, vp, vp]
         L.ugp_set_trace_counters.restype = C.c_int
         L.ugp_set_trace_counters.argtypes = [vp]
         for fn in _EXTRA:
@@ -205,6 +231,82 @@ def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
                                   _p(exclude), int(cap), _p(ids), _p(a), _p(b), _p(cnt), _p(st),
                                   C.c_void_p(_stream(stream))), "ugp_collect_hits")
     return ids, a, b, cnt, st
+
+
+class Materials:
+    """Device copies of the per-primitive appearance arrays (kept alive with the struct)."""
+
+    def __init__(self, sggx6, mtype, albedo3, roughness, emission3):
+        _dev(sggx6, torch.float32, "sggx6", 6)
+        _dev(mtype, torch.uint8, "type")
+        _dev(albedo3, torch.float32, "albedo3", 3)
+        _dev(roughness, torch.float32, "roughness")
+        _dev(emission3, torch.float32, "emission3", 3)
+        self.tensors = (sggx6, mtype, albedo3, roughness, emission3)
+        self.c = UgpMaterials(*[_p(t) for t in self.tensors])
+
+
+def camera_struct(eye, look, up, vfov_deg, width, height) -> UgpCamera:
+    return UgpCamera((C.c_float * 3)(*eye), (C.c_float * 3)(*look), (C.c_float * 3)(*up),
+                     float(vfov_deg), int(width), int(height))
+
+
+def lights_struct(has_quad=False, corner=(0, 0, 0), e1=(0, 0, 0), e2=(0, 0, 0), Le=(0, 0, 0),
+                  bg=(0, 0, 0)) -> UgpLights:
+    f3 = lambda v: (C.c_float * 3)(*v)
+    return UgpLights(int(bool(has_quad)), f3(corner), f3(e1), f3(e2), f3(Le), f3(bg))
+
+
+def scene_to_device(scene, device="cuda", cutoff_eps: float = 0.01):
+    """Uploads a ``scenes.Scene`` and builds its BVH: returns (bvh, materials, camera, lights)."""
+    t = lambda a: torch.from_numpy(__import__("numpy").ascontiguousarray(a)).to(device)
+    bvh = build_bvh(t(scene.mean), t(scene.quat), t(scene.scale), t(scene.magnitude), cutoff_eps)
+    mats = Materials(t(scene.sggx), t(scene.mtype), t(scene.albedo), t(scene.roughness), t(scene.emission))
+    cam = scene.camera
+    li = scene.lights
+    return (bvh, mats, camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, cam.width, cam.height),
+            lights_struct(li.has_quad, li.quad_corner, li.quad_e1, li.quad_e2, li.quad_Le, li.bg))
+
+
+def render_workspace_size(width: int, height: int) -> int:
+    return int(lib().ugp_render_workspace_size(int(width), int(height)))
+
+
+class Renderer:
+    """Reusable render workspace for one image size."""
+
+    def __init__(self, width: int, height: int, device="cuda"):
+        self.width, self.height = int(width), int(height)
+        nb = render_workspace_size(self.width, self.height)
+        if nb == 0:
+            raise UgpError("bad image size")
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=device)
+
+    def render(self, bvh: Bvh, mats: Materials, camera: UgpCamera, lights: UgpLights, spp: int,
+               max_depth: int, seed: int = 0, spp_begin: int = 0, nee: bool = True, spawn_mode: int = 0,
+               accum=None, accum_sq=None, ray_counts=None, stream=None):
+        """Adds spp samples per pixel into accum / accum_sq ((H, W, 3) float32, created if None)."""
+        dev = self.workspace.device
+        shape = (self.height, self.width, 3)
+        if accum is None:
+            accum = torch.zeros(shape, dtype=torch.float32, device=dev)
+        if accum_sq is None:
+            accum_sq = torch.zeros(shape, dtype=torch.float32, device=dev)
+        _dev(accum, torch.float32, "accum")
+        _dev(accum_sq, torch.float32, "accum_sq")
+        if tuple(accum.shape) != shape or tuple(accum_sq.shape) != shape:
+            raise ValueError(f"accumulators must have shape {shape}")
+        if ray_counts is not None:
+            _dev(ray_counts, torch.int64, "ray_counts")
+        if camera.width != self.width or camera.height != self.height:
+            raise ValueError("camera size does not match the renderer")
+        prm = UgpRenderParams(int(spp), int(spp_begin), int(max_depth), int(bool(nee)), int(seed),
+                              int(spawn_mode), 0)
+        _check(lib().ugp_render(C.c_void_p(bvh.handle), C.byref(mats.c), C.byref(camera),
+                                C.byref(lights), C.byref(prm), _p(accum), _p(accum_sq),
+                                _p(self.workspace), self.workspace.numel(), _p(ray_counts),
+                                C.c_void_p(_stream(stream))), "ugp_render")
+        return accum, accum_sq
 
 
 def set_trace_counters(counters=None):
