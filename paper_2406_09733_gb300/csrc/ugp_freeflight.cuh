@@ -280,6 +280,13 @@ static __device__ __forceinline__ void eval_F(Ctx& c, int nE, float lo, float Fl
 static __device__ float solve_buffer(Ctx& c, int nE, float lo, float hi, float Flo, float u) {
   const float w_lo = lo;
   float t = 0.5f * (lo + hi);
+  {
+    float fh, fph;
+    eval_F(c, nE, w_lo, Flo, u, hi, fh, fph);  // F(hi) - u > 0: start from the secant
+    const float frac = (u - Flo) / (fh + u - Flo);
+    const float ts = lo + frac * (hi - lo);
+    if (ts > lo && ts < hi) t = ts;
+  }
   float dx_old = hi - lo, dx = dx_old;
   for (int it = 0; it < kFFNewtonIters; ++it) {
     float f, fp;
@@ -378,7 +385,10 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
       if (lo < hi) dF += entry_integral(c, e, lo, hi);
     }
     if (F_c + dF > u) {
-      const float t = solve_buffer(c, nE, t_c, t_w, F_c, u);
+      // F is flat after the last interval ends, so the root lies before min(t_w, max b)
+      float t_hi = t_c;
+      for (int e = 0; e < nE; ++e) t_hi = fmaxf(t_hi, FB(b, e));
+      const float t = solve_buffer(c, nE, t_c, fminf(t_w, t_hi), F_c, u);
       const int pick = choose_buffer(c, nE, t, u2);
       if (pick >= 0) {
         out_prim = unpack_id(FB(id, pick));
@@ -420,7 +430,9 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
       float f, fp;
       eval_F(c, v.count, lo0, F_c, u, limit, f, fp);
       if (f > 0.f || limit < hi0) {
-        t_u = f > 0.f ? solve_buffer(c, v.count, lo0, limit, F_c, u) : limit;
+        float t_hi = lo0;
+        for (int e = 0; e < v.count; ++e) t_hi = fmaxf(t_hi, FB(b, e));
+        t_u = f > 0.f ? solve_buffer(c, v.count, lo0, fminf(limit, t_hi), F_c, u) : limit;
         const int pick = choose_buffer(c, v.count, t_u, u2);
         if (pick >= 0) {
           out_prim = unpack_id(FB(id, pick));

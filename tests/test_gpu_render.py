@@ -60,7 +60,8 @@ def test_white_furnace_gpu(gpu):
     mean = a / 64
     assert np.all(mean <= 1 + 1e-6)
     assert (np.abs(mean - 1) < 1e-6).mean() > 0.99
-    assert cnt[0] > 1.5 * 256 * 64 and cnt[2] == 0
+    assert cnt[2] == 0
+    assert cnt[0] > 2.0 * 256 * 64   # paths scatter about 2.4 times (the oracle's rate)
 
 
 def lit_scene(n=400, seed=3, w=24, h=24):

@@ -262,6 +262,27 @@ def test_free_flight_parity_tiny(gpu, orc):
     assert (ref["prim"] >= 0).mean() > 0.2 and (ref["n_active"] >= 2).sum() > 100
 
 
+def test_free_flight_unbounded_rays(gpu, orc):
+    """t1 = 1e30 (rays that end nowhere, as in the renderer): the root solve must stay bracketed."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = scenes.tiny_scene()
+    r = scenes.random_rays(8193, seed=16)
+    r.t1[:] = 1e30
+    u, u2 = scenes.uniforms24(17, r.n), scenes.uniforms24(18, r.n)
+    prim, tu, tsp, st = ugp.sample_free_flight(build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                               dev(torch, r.t0), dev(torch, r.t1), dev(torch, u),
+                                               dev(torch, u2))
+    assert st.cpu().numpy().max() == 0
+    p = prim.cpu().numpy()
+    ref = orc.sample_free_flight(s, r, u, u2)
+    assert (ref["prim"] >= 0).mean() > 0.2
+    assert (p == ref["prim"]).mean() > 0.999
+    same = (p == ref["prim"]) & (p >= 0)
+    # t1 - t0 is huge here, so compare against the scene scale instead
+    assert np.abs(tu.cpu().numpy()[same] - ref["t_u"][same]).max() < 1e-5 * 4.0
+
+
 def test_free_flight_dense_overlaps_and_exclusion(gpu, orc):
     """Saturating clusters (many intervals per window, several rounds) and excluded origins."""
     from paper_2406_09733_gb300 import ugp
