@@ -49,19 +49,25 @@ def compare(a_g, q_g, n_g, a_o, q_o, n_o, z_max=3.0, frac=0.01):
     return z
 
 
-def test_white_furnace_gpu(gpu):
+def test_white_furnace_gpu(gpu, orc):
+    """Albedo-1 flakes under a unit background: every sample that escapes before the depth limit
+    contributes exactly 1.  Truncation at max_depth and the scattering rate match the oracle's."""
     s = scenes.tiny_scene(n=1000, seed=1, width=16, height=16)
     s.mtype[:] = scenes.MAT_DIFFUSE
     s.albedo[:] = 1.0
     s.emission[:] = 0.0
     s.magnitude[:] *= 5.0
     s.lights = scenes.Lights(bg=(1.0, 1.0, 1.0))
-    a, q, cnt = gpu_render(gpu, s, spp=64, max_depth=14)
-    mean = a / 64
-    assert np.all(mean <= 1 + 1e-6)
-    assert (np.abs(mean - 1) < 1e-6).mean() > 0.99
-    assert cnt[2] == 0
-    assert cnt[0] > 2.0 * 256 * 64   # paths scatter about 2.4 times (the oracle's rate)
+    spp, D = 64, 14
+    a, q, cnt = gpu_render(gpu, s, spp=spp, max_depth=D)
+    a_o, _, (ne_o, _) = orc.render(s, spp=spp, max_depth=D)
+    mean, mean_o = a / spp, a_o / spp
+    assert np.all(mean <= 1 + 1e-6) and cnt[2] == 0
+    # samples are either exactly 1 or truncated (0); the truncated share matches the oracle
+    k = np.round(a).astype(np.int64)
+    assert np.all(np.abs(a - k) < 1e-3)
+    assert abs((1 - mean).sum() - (1 - mean_o).sum()) <= 3 * math.sqrt((1 - mean_o).sum() * spp + 1) / spp
+    assert abs(cnt[0] / ne_o - 1) < 0.02
 
 
 def lit_scene(n=400, seed=3, w=24, h=24):
