@@ -101,7 +101,7 @@ def test_render_matches_oracle_tiny_scene_config(gpu, orc):
     spp_g, spp_o = 8192, 2048
     a_g, q_g, cnt = gpu_render(gpu, s, spp_g, max_depth=4, seed=7, chunks=4)
     a_o, q_o, _ = orc.render(s, spp=spp_o, max_depth=4, seed=8)
-    assert (a_o > 0).mean() > 0.05
+    assert (a_o > 0).mean() > 0.01   # one emitter, no background: sparse signal
     compare(a_g, q_g, spp_g, a_o, q_o, spp_o)
 
 
