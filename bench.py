@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 Gaussian-primitive path tracer.
+
+Workload (the mid-size configuration): a procedural room of 1,000,000 Gaussian primitives
+(70 % surface splats on planes, spheres and boxes, 30 % isotropic aggregates in 300
+clusters; 50 / 40 / 10 % diffuse / GGX / emissive shapes) lit by a 0.3 x 0.3 area light
+and a background, rendered at 1024 x 1024 with max depth 8.  One step = BVH build over
+the primitives + one sample per pixel of the wavefront path tracer (camera, free-flight
+extend, shading with light sampling + MIS, shadow transmittance, accumulation); 64 steps
+are the full 64-spp frame.  Inputs are synthetic (seeded generator).
+
+Metric: Mrays/s = (free-flight queries + shadow queries) / time.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ugp|reference]
+For N > 1 run under torch.distributed.run: every rank renders its own replica of the
+workload (the path does not shard across GPUs in this build), timings are max-reduced
+and rays sum-reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s + equal-time MSE vs converged ref, MLP-guided vs plain, 1 GB300"
+UNIT = "Mrays/s"
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=16)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ugp", "reference"], default="ugp")
+    p.add_argument("--n-prims", type=int, default=1_000_000)
+    p.add_argument("--width", type=int, default=1024)
+    p.add_argument("--height", type=int, default=1024)
+    p.add_argument("--depth", type=int, default=8)
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-pixels", type=int, default=1024, help="pixels of the CPU-baseline sample")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def aggregate(elapsed_ms: float, units: float, dist):
+    """Whole-job totals over ranks: (max elapsed ms, sum of units)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return elapsed_ms, units
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def workload_config(args, l2_note):
+    return {
+        "workload": (f"procedural room, {args.n_prims} Gaussian primitives (70% surface splats, 30% "
+                     f"aggregate clusters), area light + background, {args.width}x{args.height}, "
+                     f"1 spp per step, max depth {args.depth}"),
+        "n_prims": args.n_prims, "width": args.width, "height": args.height, "spp_per_step": 1,
+        "max_depth": args.depth, "step": "BVH build + 1 spp wavefront render", "l2": l2_note,
+        "parallelism": f"replicas x{args.gpus}",
+    }
+
+
+def cpu_baseline_run(scene, args, pixels, spp=1, seed=0):
+    """The FP64 oracle on a bounded sample of the workload: `pixels` consecutive pixels of the
+    middle image row(s), one sample each."""
+    import oracle
+    mid = (args.height // 2) * args.width
+    t0 = time.perf_counter()
+    _, _, (ne, ns) = oracle.render(scene, spp=spp, max_depth=args.depth, seed=seed,
+                                   pixels=(mid, mid + pixels))
+    dt = time.perf_counter() - t0
+    return (ne + ns) / dt / 1e6, oracle.num_threads(), ne + ns, dt
+
+
+# ------------------------------------------------------------------------------- arms
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle (the correctness reference) on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2406_09733_gb300 import scenes
+    scene = scenes.room_scene(args.n_prims, width=args.width, height=args.height)
+    px = max(16, args.cpu_pixels // 2)
+    for w in range(args.warmup):
+        cpu_baseline_run(scene, args, px, seed=1000 + w)
+    rays = 0
+    total = 0.0
+    cores = None
+    for k in range(args.steps):
+        v, cores, r, dt = cpu_baseline_run(scene, args, px, seed=k)
+        rays += r
+        total += dt
+    value = rays / total / 1e6
+    sample = f"{px} pixels x 1 spp of the middle row per step, brute force over all primitives"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator)",
+        "config": workload_config(args, "n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ugp(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2406_09733_gb300 import scenes, ugp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    scene = scenes.room_scene(args.n_prims, width=args.width, height=args.height)
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k)))
+            for k in ("mean", "quat", "scale", "magnitude", "sggx", "mtype", "albedo", "roughness", "emission")}
+    d = {k: v.to(dev) for k, v in host.items()}
+    mats = ugp.Materials(d["sggx"], d["mtype"], d["albedo"], d["roughness"], d["emission"])
+    cam = scene.camera
+    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, cam.width, cam.height)
+    li = scene.lights
+    lights = ugp.lights_struct(li.has_quad, li.quad_corner, li.quad_e1, li.quad_e2, li.quad_Le, li.bg)
+    renderer = ugp.Renderer(args.width, args.height, device=dev)
+    acc = torch.zeros((args.height, args.width, 3), dtype=torch.float32, device=dev)
+    acc2 = torch.zeros_like(acc)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+    stream = torch.cuda.current_stream(dev)
+    bvh_ws = torch.empty(ugp.build_bvh_workspace_size(args.n_prims), dtype=torch.uint8, device=dev)
+
+    def step(k, ray_counts):
+        bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"], workspace=bvh_ws)
+        renderer.render(bvh, mats, camera, lights, spp=1, max_depth=args.depth, seed=rank, spp_begin=k,
+                        accum=acc, accum_sq=acc2, ray_counts=ray_counts)
+        return bvh
+
+    for w in range(args.warmup):
+        step(1000 + w, None)
+    torch.cuda.synchronize(dev)
+
+    # -------- timed region: K steps, L2 flushed between steps (outside the step events)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    keep = None
+    launches0 = ugp.launch_count()
+    ugp.profile_begin(64 * (args.depth + 4) * max(args.steps, 1) + 64)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            keep = step(k, counts)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    prof = ugp.profile_end()
+    launches = ugp.launch_count() - launches0
+    del keep
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    elapsed = float(sum(step_ms))
+    c = counts.cpu().numpy()
+    rays_local = float(c[0] + c[1])
+    max_ms, rays_total = aggregate(elapsed, rays_local, dist if world > 1 else None)
+    value = rays_total / (max_ms / 1e3) / 1e6
+
+    # -------- algorithmic bytes of the dominant kernel (extend) from one counted step
+    stats = torch.zeros(12, dtype=torch.int64, device=dev)
+    ugp.set_trace_counters(stats)
+    cnt2 = torch.zeros(3, dtype=torch.int64, device=dev)
+    step(5000, cnt2)
+    torch.cuda.synchronize(dev)
+    ugp.set_trace_counters(None)
+    st = stats.cpu().numpy()
+    # per extend query: 64 B per node and 64 B per primitive record loaded (hot geometry), plus the
+    # path state it reads (queue index, origin, direction, exclusion: 32 B) and writes (16 B)
+    nodes_per_query = st[0] / max(st[2], 1)
+    prims_per_query = st[1] / max(st[2], 1)
+    alg_bytes_per_launch = ((st[0] + st[1]) * 64 + 48 * st[2]) / (args.depth + 1)
+    ext_launches = prof["extend"][1]
+    avg_ext_ms = prof["extend"][0] / max(ext_launches, 1)
+    queries_per_step = c[0] / args.steps
+    achieved_gbs = alg_bytes_per_launch / (avg_ext_ms / 1e3) / 1e9 if avg_ext_ms > 0 else None
+    peak, peak_note = measured_peaks()
+
+    # -------- end to end through host buffers (pinned): H2D scene + build + render + D2H image
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        pinned = {k: v.pin_memory() for k, v in host.items()}
+        out_acc = torch.empty(acc.shape, dtype=torch.float32).pin_memory()
+        out_acc2 = torch.empty(acc.shape, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        d2h = 2 * out_acc.numel() * 4
+        cnt3 = torch.zeros(3, dtype=torch.int64, device=dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        n_e2e = max(1, min(args.steps, 8))
+        for k in range(n_e2e):
+            for key, v in pinned.items():
+                d[key].copy_(v, non_blocking=True)
+            step(7000 + k, cnt3)
+            out_acc.copy_(acc, non_blocking=True)
+            out_acc2.copy_(acc2, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t0
+        r3 = cnt3.cpu().numpy()
+        e2e = {"value": float(r3[0] + r3[1]) / t_e2e / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, r, dt = cpu_baseline_run(scene, args, args.cpu_pixels)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_pixels} pixels x 1 spp of the middle row, {r} queries in {dt:.1f} s, "
+                         f"brute force over all primitives, FP64"}
+
+    if rank == 0:
+        clk = clocks.summary()
+        line = {
+            "impl": "ugp", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
+            "config": workload_config(args, "flushed between steps (256 MB write)"),
+            "rays_per_step": rays_local / args.steps, "extend_queries_per_step": queries_per_step,
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+            "roofline": {"bound": "hbm", "kernel": "k_extend (free-flight sampling)",
+                         "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved_gbs / peak) if achieved_gbs else None, "peak_note": peak_note,
+                         "traffic": None,
+                         "algorithmic_bytes_per_launch": alg_bytes_per_launch,
+                         "nodes_per_query": nodes_per_query, "prims_per_query": prims_per_query,
+                         "avg_launch_ms": avg_ext_ms},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "wall_s_timed_region": wall, "equal_time_mse": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ugp(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -241,14 +241,34 @@ ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const 
                       float* accum_sq_rgb, void* workspace, size_t workspace_bytes,
                       unsigned long long* ray_counts, void* stream);
 
-/* Optional traversal statistics: when `counters` is a device pointer to 6
- * zero-initialised uint64, later tracing calls on any stream add
+/* Optional traversal statistics: when `counters` is a device pointer to 12
+ * zero-initialised uint64, later tracing calls on any stream add (atomically)
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
- *   [3] traversal rounds, [4] free-flight rays that needed the binned mode,
- *   [5] reserved
- * to it (atomically).  NULL turns counting off (the default).  Host-side
+ *   [3] traversal rounds, [4] free-flight rays that needed the dense mode
+ * for free-flight and transmittance queries (standalone, and the renderer's extend
+ * pass), and the same five quantities at [6..10] for the renderer's shadow rays;
+ * [5] and [11] are reserved.  NULL turns counting off (the default).  Host-side
  * setting, not thread safe against concurrent tracing calls. */
 ugp_status ugp_set_trace_counters(unsigned long long* counters);
+
+/* ------------------------------------------------------------------ measurement
+ * Kernel timing without synchronisation: after ugp_profile_begin, every kernel the
+ * library launches is bracketed by a pair of CUDA events recorded on the launch
+ * stream (host-side event objects, created on first use and reused).  Stages:
+ *   0 BVH build (all its kernels, the radix sort included), 1 camera rays,
+ *   2 extend (free flight), 3 shade, 4 shadow (transmittance), 5 accumulate,
+ *   6 standalone queries (ugp_trace_transmittance, ugp_sample_free_flight).
+ * ugp_profile_end waits for the recorded events, writes the summed milliseconds and
+ * launch counts per stage (arrays of UGP_PROFILE_STAGES, host) and stops recording.
+ * At most max_records event pairs are kept; later launches are counted but not timed
+ * (ugp_profile_end returns UGP_ERR_OVERFLOW then).  Not thread safe. */
+#define UGP_PROFILE_STAGES 8
+ugp_status ugp_profile_begin(int32_t max_records);
+ugp_status ugp_profile_end(double* ms_out, int64_t* launches_out);
+
+/* Number of kernels the library has launched since it was loaded (its own kernels and
+ * the radix-sort kernels of the BVH build). */
+int64_t ugp_launch_count(void);
 
 /* Static description of a status code. */
 const char* ugp_status_string(ugp_status s);

@@ -28,6 +28,50 @@ unsigned long long* trace_counters() { return g_counters; }
 
 bool valid_bvh(const ugp_bvh* b) { return b != nullptr && b->magic == kBvhMagic; }
 
+// ---- launch accounting and event timing
+static unsigned long long g_launches = 0;
+struct Prof {
+  bool on = false;
+  int max_records = 0, used = 0;
+  bool overflow = false;
+  cudaEvent_t* ev = nullptr;  // 2 * capacity events, created lazily
+  int capacity = 0;
+  int* stage = nullptr;
+  long long launches[UGP_PROFILE_STAGES] = {0};
+  int open_slot = -1;
+};
+static Prof g_prof;
+
+void prof_begin(int stage, cudaStream_t s) {
+  (void)stage;
+  if (!g_prof.on) return;
+  if (g_prof.used >= g_prof.max_records) {
+    g_prof.overflow = true;
+    g_prof.open_slot = -1;
+    return;
+  }
+  const int i = g_prof.used;
+  if (i >= g_prof.capacity) {
+    g_prof.open_slot = -1;
+    g_prof.overflow = true;
+    return;
+  }
+  cudaEventRecord(g_prof.ev[2 * i], s);
+  g_prof.open_slot = i;
+}
+
+void prof_end(int stage, cudaStream_t s, int n_kernels) {
+  g_launches += (unsigned long long)n_kernels;
+  if (!g_prof.on) return;
+  g_prof.launches[stage] += n_kernels;
+  const int i = g_prof.open_slot;
+  if (i < 0) return;
+  cudaEventRecord(g_prof.ev[2 * i + 1], s);
+  g_prof.stage[i] = stage;
+  g_prof.used = i + 1;
+  g_prof.open_slot = -1;
+}
+
 }  // namespace ugp
 
 extern "C" {
@@ -49,6 +93,63 @@ const char* ugp_status_string(ugp_status s) {
 const char* ugp_last_error(void) { return ugp::g_err; }
 
 const char* ugp_version(void) { return "ugp 0.1 (sm_103a)"; }
+
+int64_t ugp_launch_count(void) { return int64_t(ugp::g_launches); }
+
+ugp_status ugp_profile_begin(int32_t max_records) {
+  using ugp::g_prof;
+  ugp::clear_error();
+  if (max_records <= 0 || max_records > (1 << 22))
+    return ugp::fail(UGP_ERR_INVALID_ARG, "ugp_profile_begin: max_records out of range");
+  if (max_records > g_prof.capacity) {
+    cudaEvent_t* ev = new cudaEvent_t[2 * size_t(max_records)];
+    int* st = new int[size_t(max_records)];
+    for (int i = 0; i < 2 * g_prof.capacity; ++i) ev[i] = g_prof.ev[i];
+    for (int i = 2 * g_prof.capacity; i < 2 * max_records; ++i) {
+      const cudaError_t e = cudaEventCreate(&ev[i]);
+      if (e != cudaSuccess) {
+        for (int j = 2 * g_prof.capacity; j < i; ++j) cudaEventDestroy(ev[j]);
+        delete[] ev;
+        delete[] st;
+        return ugp::cuda_fail(e, "cudaEventCreate");
+      }
+    }
+    delete[] g_prof.ev;
+    delete[] g_prof.stage;
+    g_prof.ev = ev;
+    g_prof.stage = st;
+    g_prof.capacity = max_records;
+  }
+  g_prof.on = true;
+  g_prof.max_records = max_records;
+  g_prof.used = 0;
+  g_prof.overflow = false;
+  g_prof.open_slot = -1;
+  for (long long& l : g_prof.launches) l = 0;
+  return UGP_OK;
+}
+
+ugp_status ugp_profile_end(double* ms_out, int64_t* launches_out) {
+  using ugp::g_prof;
+  ugp::clear_error();
+  if (!g_prof.on) return ugp::fail(UGP_ERR_INVALID_ARG, "ugp_profile_end: profiling is not on");
+  g_prof.on = false;
+  double ms[UGP_PROFILE_STAGES] = {0};
+  for (int i = 0; i < g_prof.used; ++i) {
+    const cudaError_t e = cudaEventSynchronize(g_prof.ev[2 * i + 1]);
+    if (e != cudaSuccess) return ugp::cuda_fail(e, "cudaEventSynchronize");
+    float t = 0.f;
+    const cudaError_t e2 = cudaEventElapsedTime(&t, g_prof.ev[2 * i], g_prof.ev[2 * i + 1]);
+    if (e2 != cudaSuccess) return ugp::cuda_fail(e2, "cudaEventElapsedTime");
+    ms[g_prof.stage[i]] += t;
+  }
+  for (int k = 0; k < UGP_PROFILE_STAGES; ++k) {
+    if (ms_out) ms_out[k] = ms[k];
+    if (launches_out) launches_out[k] = g_prof.launches[k];
+  }
+  if (g_prof.overflow) return ugp::fail(UGP_ERR_OVERFLOW, "ugp_profile_end: more launches than max_records");
+  return UGP_OK;
+}
 
 ugp_status ugp_set_trace_counters(unsigned long long* counters) {
   ugp::g_counters = counters;

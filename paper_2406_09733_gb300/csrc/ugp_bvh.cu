@@ -368,6 +368,7 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
 
   const int T = 256;
   const unsigned G = unsigned((n + T - 1) / T);
+  prof_begin(kStBuild, st);
   UGP_CUDA_CHECK(cudaMemsetAsync(ws + L.bounds, 0, 64, st));
   k_init_bounds<<<1, 32, 0, st>>>(bounds, nullptr);
   k_prim_bounds<<<G, T, 0, st>>>(n, prims->mean3, prims->quat4, prims->scale3, prims->magnitude, b->k,
@@ -395,6 +396,8 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   k_records<<<G, T, 0, st>>>(n, order, prims->mean3, prims->quat4, prims->scale3, prims->magnitude,
                              reinterpret_cast<float4*>(ws + L.prims), reinterpret_cast<float4*>(ws + L.wlo));
   UGP_CUDA_CHECK(cudaGetLastError());
+  // own kernels plus the radix sort's (histogram, scan and one pass per 8-bit digit of 30 bits)
+  prof_end(kStBuild, st, n == 1 ? 5 : 6 + 6);
   b->stream = st;
   *out = b;
   return UGP_OK;

@@ -31,10 +31,12 @@ ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, 
                               cudaStream_t stream) {
   const unsigned grid = unsigned((n + kFFBlock - 1) / kFFBlock);
   unsigned long long* ctr = trace_counters();
+  prof_begin(kStQuery, stream);
   if (ctr)
     k_free_flight<true><<<grid, kFFBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, u, u2, excl, prim, tu, tsp, st, ctr);
   else
     k_free_flight<false><<<grid, kFFBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, u, u2, excl, prim, tu, tsp, st, ctr);
+  prof_end(kStQuery, stream);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }

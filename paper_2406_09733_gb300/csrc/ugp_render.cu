@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_camera(CameraDev cam, int n, uint2 key,
 __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
                                                      int spawn_mode, PathSoA ps, const int* __restrict__ q,
                                                      const int* cnt, int* reset_next, int* reset_shadow,
-                                                     unsigned long long* rays) {
+                                                     unsigned long long* rays, unsigned long long* stats) {
   __shared__ FFSmem sm;
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L,
     ps.tq[p] = tq;
     ps.qflag[p] = qf;
     if (c.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
+    if (stats) add_counters(stats, c.n_nodes, c.n_prims, 1u, r.rounds, r.dense ? 1u : 0u);
   }
 }
 
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
 }
 
 __global__ void __launch_bounds__(kTrBlock) k_shadow(TraceScene sc, ShadowSoA sh, const int* cnt, PathSoA ps,
-                                                     unsigned long long* rays) {
+                                                     unsigned long long* rays, unsigned long long* stats) {
   __shared__ int stk[kTrStack * kTrBlock];
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0 && rays) atomicAdd(rays + 1, (unsigned long long)count);
@@ -251,6 +252,7 @@ __global__ void __launch_bounds__(kTrBlock) k_shadow(TraceScene sc, ShadowSoA sh
       ps.lb[p] += T * sh.cb[j];
     }
     if (ts.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
+    if (stats) add_counters(stats + 6, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);
   }
 }
 
@@ -389,6 +391,7 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   const MatDev md{materials->sggx6, materials->type, materials->albedo3, materials->roughness, materials->emission3};
   const TraceScene sc = trace_scene(bvh);
   const uint2 key = make_uint2(uint32_t(params->seed & 0xffffffffu), uint32_t(params->seed >> 32));
+  unsigned long long* stats = trace_counters();
 
   const int g_cam = grid_for((const void*)k_camera, 256, n);
   const int g_ext = grid_for((const void*)k_extend, kFFBlock, n);
@@ -397,19 +400,30 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   const int g_acc = grid_for((const void*)k_accumulate, 256, n);
   for (int si = 0; si < params->spp; ++si) {
     const int sample = params->spp_begin + si;
+    prof_begin(kStCamera, st);
     k_camera<<<g_cam, 256, 0, st>>>(cd, int(n), key, sample, ps, queue[0], counts + 0);
+    prof_end(kStCamera, st);
     int cur = 0;
     for (int b = 0; b <= params->max_depth; ++b) {
       const int nxt = 1 - cur;
+      prof_begin(kStExtend, st);
       k_extend<<<g_ext, kFFBlock, 0, st>>>(sc, Ld, key, sample, b, params->spawn_mode, ps, queue[cur], counts + cur,
-                                            counts + nxt, counts + 2, ray_counts);
+                                            counts + nxt, counts + 2, ray_counts, stats);
+      prof_end(kStExtend, st);
+      prof_begin(kStShade, st);
       k_shade<<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
                                         counts + cur, queue[nxt], counts + nxt, sh, counts + 2);
-      if (params->nee && Ld.has_quad)
-        k_shadow<<<g_shadow, kTrBlock, 0, st>>>(sc, sh, counts + 2, ps, ray_counts);
+      prof_end(kStShade, st);
+      if (params->nee && Ld.has_quad) {
+        prof_begin(kStShadow, st);
+        k_shadow<<<g_shadow, kTrBlock, 0, st>>>(sc, sh, counts + 2, ps, ray_counts, stats);
+        prof_end(kStShadow, st);
+      }
       cur = nxt;
     }
+    prof_begin(kStAccum, st);
     k_accumulate<<<g_acc, 256, 0, st>>>(int(n), ps, accum_rgb, accum_sq_rgb);
+    prof_end(kStAccum, st);
     UGP_CUDA_CHECK(cudaGetLastError());
   }
   return UGP_OK;

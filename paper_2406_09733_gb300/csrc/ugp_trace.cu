@@ -145,8 +145,10 @@ extern "C" ugp_status ugp_collect_hits(const ugp_bvh* bvh, int64_t n_rays, const
     return fail(UGP_ERR_INVALID_ARG, "ugp_collect_hits: NULL output array");
   if (n_rays == 0) return UGP_OK;
   const unsigned grid = unsigned((n_rays + kTrBlock - 1) / kTrBlock);
+  prof_begin(kStQuery, static_cast<cudaStream_t>(stream));
   k_collect_hits<<<grid, kTrBlock, 0, static_cast<cudaStream_t>(stream)>>>(
       trace_scene(bvh), n_rays, o3, d3, t0, t1, exclude_prim, cap, ids_out, a_out, b_out, count_out, status_out);
+  prof_end(kStQuery, static_cast<cudaStream_t>(stream));
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }
@@ -158,10 +160,12 @@ ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3
                                 uint8_t* st, cudaStream_t stream) {
   const unsigned grid = unsigned((n + kTrBlock - 1) / kTrBlock);
   unsigned long long* ctr = trace_counters();
+  prof_begin(kStQuery, stream);
   if (ctr)
     k_transmittance<true><<<grid, kTrBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, excl, T, st, ctr);
   else
     k_transmittance<false><<<grid, kTrBlock, 0, stream>>>(sc, n, o3, d3, t0, t1, excl, T, st, ctr);
+  prof_end(kStQuery, stream);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }

@@ -91,6 +91,11 @@ def lib():
         L.ugp_render.argtypes = [vp, C.POINTER(UgpMaterials), C.POINTER(UgpCamera),
                                  C.POINTER(UgpLights), C.POINTER(UgpRenderParams), vp, vp, vp,
                                  C.c_size_t, vp, vp]
+        L.ugp_profile_begin.restype = C.c_int
+        L.ugp_profile_begin.argtypes = [C.c_int32]
+        L.ugp_profile_end.restype = C.c_int
+        L.ugp_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.ugp_launch_count.restype = C.c_int64
         L.ugp_set_trace_counters.restype = C.c_int
         L.ugp_set_trace_counters.argtypes = [vp]
         for fn in _EXTRA:
@@ -164,7 +169,8 @@ def build_bvh_workspace_size(n: int) -> int:
     return int(lib().ugp_build_bvh_workspace_size(int(n)))
 
 
-def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=None) -> Bvh:
+def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=None, workspace=None) -> Bvh:
+    """Builds the BVH; `workspace` (uint8 CUDA tensor) is reused when given and large enough."""
     n = int(mean.shape[0])
     _dev(mean, torch.float32, "mean", 3)
     _dev(quat, torch.float32, "quat", 4)
@@ -173,7 +179,13 @@ def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=Non
     ws_bytes = build_bvh_workspace_size(n)
     if ws_bytes == 0:
         raise UgpError("ugp_build_bvh_workspace_size failed")
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=mean.device)
+    if workspace is not None:
+        _dev(workspace, torch.uint8, "workspace")
+        if workspace.numel() < ws_bytes:
+            raise ValueError(f"workspace needs {ws_bytes} bytes")
+        ws = workspace
+    else:
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device=mean.device)
     prims = UgpPrims(n, _p(mean), _p(quat), _p(scale), _p(magnitude))
     h = vp()
     _check(lib().ugp_build_bvh(C.byref(prims), float(cutoff_eps), _p(ws), ws_bytes,
@@ -310,12 +322,32 @@ class Renderer:
 
 
 def set_trace_counters(counters=None):
-    """Turns traversal statistics on (a CUDA int64 tensor of 6 zeros) or off (None)."""
+    """Turns traversal statistics on (a CUDA int64 tensor of 12 zeros) or off (None)."""
     if counters is not None:
         _dev(counters, torch.int64, "counters")
-        if counters.numel() < 6:
-            raise ValueError("counters needs 6 elements")
+        if counters.numel() < 12:
+            raise ValueError("counters needs 12 elements")
     _check(lib().ugp_set_trace_counters(_p(counters)), "ugp_set_trace_counters")
+
+
+PROFILE_STAGES = ("build", "camera", "extend", "shade", "shadow", "accumulate", "query", "reserved")
+
+
+def profile_begin(max_records: int = 1 << 16):
+    """Starts event timing of every library kernel launch (no synchronisation)."""
+    _check(lib().ugp_profile_begin(int(max_records)), "ugp_profile_begin")
+
+
+def profile_end():
+    """Stops timing; returns {stage: (milliseconds, launches)} (waits for the recorded events)."""
+    ms = (C.c_double * 8)()
+    nl = (C.c_int64 * 8)()
+    _check(lib().ugp_profile_end(ms, nl), "ugp_profile_end")
+    return {name: (ms[i], nl[i]) for i, name in enumerate(PROFILE_STAGES)}
+
+
+def launch_count() -> int:
+    return int(lib().ugp_launch_count())
 
 
 def version() -> str:

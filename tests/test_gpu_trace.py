@@ -324,7 +324,7 @@ def test_free_flight_room_scene_binned_mode(gpu, orc):
     r = scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
                     np.full(n, 4.0, np.float32))
     u, u2 = scenes.uniforms24(41, n), scenes.uniforms24(42, n)
-    ctr = torch.zeros(6, dtype=torch.int64, device="cuda")
+    ctr = torch.zeros(12, dtype=torch.int64, device="cuda")
     ugp.set_trace_counters(ctr)
     try:
         prim, tu, tsp, st = ugp.sample_free_flight(bvh, dev(torch, r.o), dev(torch, r.d),
