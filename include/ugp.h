@@ -153,12 +153,21 @@ ugp_status ugp_trace_transmittance(const ugp_bvh* bvh, int64_t n_rays, const flo
  * saturating-distance clamp of Eq. 8.
  *   u, u2         float arrays (n_rays) of uniforms in [0, 1)
  *   prim_out      int32 array (n_rays); t_u_out, t_spawn_out float arrays
+ *   workspace     device scratch of ugp_sample_free_flight_workspace_size(n_rays)
+ *                 bytes (see below)
  *   other arguments as for ugp_trace_transmittance. */
 ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
                                   const float* d3, const float* t0, const float* t1,
                                   const float* u, const float* u2, const int32_t* exclude_prim,
                                   int32_t* prim_out, float* t_u_out, float* t_spawn_out,
-                                  uint8_t* status_out, void* stream);
+                                  uint8_t* status_out, void* workspace, size_t workspace_bytes,
+                                  void* stream);
+
+/* Scratch bytes ugp_sample_free_flight needs for n_rays rays: a queue of the rays whose
+ * bracketed root has more overlapping intervals than one thread buffers (they are
+ * finished by a warp-per-ray pass).  The workspace must be 256-byte aligned and is
+ * only used during the call's device work. */
+size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
 /* All clipped intervals along each ray (hit-set diagnostics).  For ray r,
  * count_out[r] receives the number of primitives whose k-ellipsoid interval
@@ -221,7 +230,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state and
- * queues, 128 bytes per pixel plus alignment). */
+ * queues, 188 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 
 /* Path-traces the image with the volumetric path tracer of Table 1 (right column)
@@ -256,8 +265,9 @@ ugp_status ugp_set_trace_counters(unsigned long long* counters);
  * library launches is bracketed by a pair of CUDA events recorded on the launch
  * stream (host-side event objects, created on first use and reused).  Stages:
  *   0 BVH build (all its kernels, the radix sort included), 1 camera rays,
- *   2 extend (free flight), 3 shade, 4 shadow (transmittance), 5 accumulate,
- *   6 standalone queries (ugp_trace_transmittance, ugp_sample_free_flight).
+ *   2 extend (free flight, per thread), 3 shade, 4 shadow (transmittance),
+ *   5 accumulate, 6 standalone queries (ugp_trace_transmittance,
+ *   ugp_sample_free_flight), 7 free flight of dense rays (warp per ray).
  * ugp_profile_end waits for the recorded events, writes the summed milliseconds and
  * launch counts per stage (arrays of UGP_PROFILE_STAGES, host) and stops recording.
  * At most max_records event pairs are kept; later launches are counted but not timed

@@ -1,0 +1,305 @@
+// Warp-per-ray finish of free-flight sampling for rays whose bracket [lo, hi] (with F(lo) = Flo)
+// holds more intervals than one thread can buffer -- in practice rays inside dense aggregate
+// clusters, where over a hundred bounding ellipsoids can overlap at one point.
+//
+// For each queued ray one warp
+//   1. collects every clipped interval meeting [lo, hi] into a per-warp shared-memory list by a
+//      warp-parallel traversal: each step pops up to 32 nodes from a shared stack, one per lane,
+//      pushes the hit internal children with ballot-ranked slots and appends hit leaves the same
+//      way;
+//   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method safeguarded
+//      with bisection, F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive
+//      with the exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
+//   3. otherwise adds every interval's contribution to 32 sub-bins of the bracket (shared-memory
+//      atomics), moves the bracket to the crossing sub-bin and repeats.
+// The result is the same function of (u, u2) as the per-thread paths: the same F, root and race.
+#include "ugp_dense.cuh"
+#include "ugp_gauss.cuh"
+#include "ugp_philox.cuh"
+
+namespace ugp {
+namespace {
+
+constexpr int kDWarps = 4;    // rays in flight per block
+constexpr int kDCap = 512;    // intervals one warp holds
+constexpr int kDStack = 512;  // shared traversal stack of one warp
+constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
+constexpr int kDNewton = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct WarpSmem {
+  float a[kDCap], b[kDCap], tn[kDCap], ts[kDCap], s[kDCap], e0[kDCap], th[kDCap];
+  int id[kDCap];  // index with the end-point flags (pack_id)
+  int stk[kDStack];
+  float bin[32];
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return __shfl_sync(kFull, v, 0);  // lane 0's sum, identical on every lane
+}
+
+// Warp-parallel traversal of the leaves whose boxes meet [lo, hi]; `leaf(slot)` is called by all
+// lanes together (slot < 0 for lanes without a leaf), twice per step.
+template <class LeafFn>
+__device__ void warp_traverse(WarpSmem& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
+                              uint8_t& st, unsigned& nn, LeafFn&& leaf) {
+  int size = 1;
+  if (lane == 0) W.stk[0] = 0;
+  __syncwarp();
+  while (size > 0) {
+    const int m = min(size, 32);
+    const int node = lane < m ? W.stk[size - 1 - lane] : -1;
+    size -= m;
+    __syncwarp();
+    int ch[2] = {-1, -1};
+    bool h[2] = {false, false};
+    bool bad = false;
+    if (node >= 0) {
+      if (node >= sc.n_nodes) {
+        bad = true;
+      } else {
+        const float4* nd = sc.nodes + 4 * node;
+        const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
+        const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
+        ++nn;
+        ch[0] = n3.x;
+        ch[1] = n3.y;
+        bad = (ch[0] < 0 && ~ch[0] >= sc.n_prims) || (ch[1] < 0 && ch[1] != kEmptyChild && ~ch[1] >= sc.n_prims);
+        float en;
+        h[0] = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, ray, lo, hi, en);
+        h[1] = ch[1] != kEmptyChild && slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, ray, lo, hi, en);
+      }
+    }
+    if (__any_sync(kFull, bad)) {
+      st = UGP_RAY_BAD_NODE;
+      return;
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const bool push = h[c] && ch[c] >= 0;
+      const unsigned mask = __ballot_sync(kFull, push);
+      if (push) {
+        const int off = size + __popc(mask & ((1u << lane) - 1u));
+        if (off < kDStack) W.stk[off] = ch[c];
+      }
+      size += __popc(mask);
+    }
+    if (size > kDStack) {
+      st = UGP_RAY_STACK_OVERFLOW;
+      return;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) leaf((h[c] && ch[c] < 0) ? ~ch[c] : -1);
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueue q, int* __restrict__ prim_out,
+                                                        float* __restrict__ tu_out, float* __restrict__ tsp_out,
+                                                        uint8_t* __restrict__ st_out, int spawn_mode,
+                                                        unsigned long long* stats, unsigned long long* rays_err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  WarpSmem& W = reinterpret_cast<WarpSmem*>(dsm)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int count = *reinterpret_cast<const volatile int*>(q.count);
+  const int nwarps = gridDim.x * kDWarps;
+  for (int j = blockIdx.x * kDWarps + (threadIdx.x >> 5); j < count; j += nwarps) {
+    const int idx = q.idx[j];
+    float lo = q.lo[j], hi = q.hi[j], Flo = q.Flo[j];
+    const float u = q.u[j], u2 = q.u2[j], t0 = q.t0[j], t1 = q.t1[j];
+    const int excl = q.excl[j];
+    const Ray ray = make_ray(make_float3(q.ox[j], q.oy[j], q.oz[j]), make_float3(q.dx[j], q.dy[j], q.dz[j]));
+    uint8_t st = UGP_RAY_OK;
+    unsigned nn = 0, np = 0;
+    int out_prim = -1;
+    float out_tu = t1, out_tsp = t1;
+    bool done = false;
+    for (int level = 0; level < kDLevels && !done && st == UGP_RAY_OK; ++level) {
+      // ---- 1. collect the intervals meeting [lo, hi]
+      int n = 0;
+      warp_traverse(W, sc, ray, lo, hi, lane, st, nn, [&](int slot) {
+        PrimHit hh;
+        bool ok = false;
+        if (slot >= 0) {
+          ++np;
+          ok = prim_test(sc.prims, sc.wlo, slot, ray, t0, t1, sc.k2, excl, hh) && fmaxf(hh.a, lo) < fminf(hh.b, hi);
+        }
+        const unsigned mask = __ballot_sync(kFull, ok);
+        if (ok) {
+          const int i = n + __popc(mask & ((1u << lane) - 1u));
+          if (i < kDCap) {
+            W.a[i] = hh.a; W.b[i] = hh.b; W.tn[i] = hh.tn; W.ts[i] = hh.ts;
+            W.s[i] = hh.s; W.e0[i] = hh.e0; W.th[i] = hh.th; W.id[i] = pack_id(hh);
+          }
+        }
+        n += __popc(mask);
+      });
+      __syncwarp();
+      if (st != UGP_RAY_OK) break;
+      if (n <= kDCap) {
+        // ---- 2. root of F = u on [lo, min(hi, last interval end)], then the race at t_u
+        float bmax = lo;
+        for (int e = lane; e < n; e += 32) bmax = fmaxf(bmax, W.b[e]);
+        for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
+        float hi_e = fminf(hi, bmax);
+        const float w_lo = lo;
+        auto evalF = [&](float t, float& f, float& fp) {
+          float fl = 0.f, fpl = 0.f;
+          for (int e = lane; e < n; e += 32) {
+            const float x0 = fmaxf(W.a[e], w_lo), x1 = fminf(W.b[e], t);
+            const int p = W.id[e];
+            if (x0 < x1)
+              fl += seg_half_integral(x0, x1, W.a[e], W.b[e], packed_a_end(p), packed_b_end(p), W.tn[e], W.ts[e],
+                                      W.s[e], W.e0[e], W.th[e]);
+            if (W.a[e] <= t && t <= W.b[e]) fpl += 0.5f * gauss_at(t, W.tn[e], W.ts[e], W.s[e], W.e0[e]);
+          }
+          f = Flo - u + warp_sum(fl);
+          fp = warp_sum(fpl);
+        };
+        float fh, fph;
+        evalF(hi_e, fh, fph);
+        float t;
+        if (!(fh > 0.f)) {
+          t = hi_e;  // rounding placed the crossing at the end of the bracket
+        } else {
+          float a0 = lo, b0 = hi_e;
+          t = a0 + (u - Flo) / (fh + u - Flo) * (b0 - a0);
+          if (!(t > a0 && t < b0)) t = 0.5f * (a0 + b0);
+          float dx_old = b0 - a0, dx = dx_old;
+          bool conv = false;
+          for (int it = 0; it < kDNewton; ++it) {
+            float f, fp;
+            evalF(t, f, fp);
+            if (f == 0.f) { conv = true; break; }
+            if (f < 0.f) a0 = t; else b0 = t;
+            if (!(nextafterf(a0, INFINITY) < b0)) { conv = true; break; }
+            const float tn = fp > 0.f ? t - f / fp : a0;
+            float tnew;
+            if (fp > 0.f && tn > a0 && tn < b0 && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
+              dx_old = dx;
+              dx = f / fp;
+              tnew = tn;
+            } else {
+              dx_old = dx;
+              dx = 0.5f * (b0 - a0);
+              tnew = a0 + dx;
+            }
+            if (tnew == t) { conv = true; break; }
+            t = tnew;
+          }
+          if (!conv) st = UGP_RAY_SOLVE_LIMIT;
+        }
+        // race: smallest E_k / G_k(x_t) among the intervals containing t (ties: smaller index)
+        float best = INFINITY;
+        int best_id = INT32_MAX, best_e = -1;
+        for (int e = lane; e < n; e += 32) {
+          if (!(W.a[e] <= t && t <= W.b[e])) continue;
+          const int idv = unpack_id(W.id[e]);
+          const float key = race_exponential(u2, idv) / gauss_at(t, W.tn[e], W.ts[e], W.s[e], W.e0[e]);
+          if (best_e < 0 || key < best || (key == best && idv < best_id)) {
+            best = key;
+            best_id = idv;
+            best_e = e;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ok = __shfl_xor_sync(kFull, best, o);
+          const int oi = __shfl_xor_sync(kFull, best_id, o);
+          const int oe = __shfl_xor_sync(kFull, best_e, o);
+          if (oe >= 0 && (best_e < 0 || ok < best || (ok == best && oi < best_id))) {
+            best = ok;
+            best_id = oi;
+            best_e = oe;
+          }
+        }
+        if (best_e >= 0) {
+          out_prim = best_id;
+          out_tu = t;
+          out_tsp = spawn_mode == 1 ? t : 0.5f * (W.a[best_e] + W.b[best_e]);
+        }
+        done = true;
+      } else {
+        // ---- 3. too many intervals: shrink the bracket to the crossing sub-bin
+        W.bin[lane] = 0.f;
+        __syncwarp();
+        const float w = (hi - lo) / 32.f;
+        auto edge = [&](int k) { return k >= 32 ? hi : lo + w * float(k); };
+        warp_traverse(W, sc, ray, lo, hi, lane, st, nn, [&](int slot) {
+          if (slot < 0) return;
+          ++np;
+          PrimHit hh;
+          if (!prim_test(sc.prims, sc.wlo, slot, ray, t0, t1, sc.k2, excl, hh)) return;
+          const float x = fmaxf(hh.a, lo), y = fminf(hh.b, hi);
+          if (!(x < y)) return;
+          int k = min(31, max(0, int((x - lo) / w)));
+          while (k > 0 && x < edge(k)) --k;
+          while (k < 31 && x >= edge(k + 1)) ++k;
+          for (; k < 32 && edge(k) < y; ++k) {
+            const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
+            if (xa < ya)
+              atomicAdd(&W.bin[k], seg_half_integral(xa, ya, hh.a, hh.b, hh.a_end, hh.b_end, hh.tn, hh.ts, hh.s,
+                                                     hh.e0, hh.th));
+          }
+        });
+        __syncwarp();
+        if (st != UGP_RAY_OK) break;
+        float acc = 0.f;
+        int jx = 31;
+        for (int k = 0; k < 32; ++k) {
+          const float nxt = acc + W.bin[k];
+          if (nxt > u - Flo) {
+            jx = k;
+            break;
+          }
+          if (k < 31) acc = nxt;
+        }
+        const float nlo = edge(jx), nhi = edge(jx + 1);
+        Flo += acc;
+        lo = nlo;
+        hi = nhi;
+        __syncwarp();
+      }
+    }
+    if (!done && st == UGP_RAY_OK) st = UGP_RAY_ITER_LIMIT;
+    const unsigned tn_nodes = __reduce_add_sync(kFull, nn), tn_prims = __reduce_add_sync(kFull, np);
+    if (lane == 0) {
+      prim_out[idx] = out_prim;
+      tsp_out[idx] = out_tsp;
+      if (tu_out) tu_out[idx] = out_tu;
+      if (st_out) st_out[idx] = st;
+      if (st != UGP_RAY_OK && rays_err) atomicAdd(rays_err, 1ull);
+      if (stats) {
+        atomicAdd(stats + 0, (unsigned long long)tn_nodes);
+        atomicAdd(stats + 1, (unsigned long long)tn_prims);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
+                        float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
+                        unsigned long long* rays_err, cudaStream_t stream) {
+  static int grid = 0;
+  const size_t smem = sizeof(WarpSmem) * kDWarps;
+  if (grid == 0) {
+    UGP_CUDA_CHECK(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int dev = 0, sms = 0, per_sm = 0;
+    UGP_CUDA_CHECK(cudaGetDevice(&dev));
+    UGP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    UGP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, 32 * kDWarps, smem));
+    grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  }
+  prof_begin(kStDense, stream);
+  k_dense<<<grid, 32 * kDWarps, smem, stream>>>(sc, q, prim_out, t_u_out, t_spawn_out, status_out, spawn_mode, stats,
+                                               rays_err);
+  prof_end(kStDense, stream);
+  UGP_CUDA_CHECK(cudaGetLastError());
+  return UGP_OK;
+}
+
+}  // namespace ugp

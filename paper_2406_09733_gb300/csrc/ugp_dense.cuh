@@ -1,0 +1,63 @@
+// Queue of free-flight rays whose t_u is bracketed but whose bracket holds more intervals than a
+// thread's buffer: the per-thread pass appends them, a warp-per-ray pass finishes them.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "ugp_trace.cuh"
+
+namespace ugp {
+
+// Structure of arrays in caller-provided scratch memory; `count` is a device int.
+struct DenseQueue {
+  int* count;
+  int* idx;      // output slot of the ray
+  float *lo, *hi, *Flo, *u, *u2;
+  float *ox, *oy, *oz, *dx, *dy, *dz, *t0, *t1;
+  int* excl;
+};
+
+constexpr int kDenseCols = 15;
+
+// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header).
+inline size_t dense_queue_bytes(int64_t cap) { return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4); }
+
+inline DenseQueue dense_queue_at(void* base, int64_t cap) {
+  char* p = static_cast<char*>(base);
+  const size_t col = align256(size_t(cap) * 4);
+  auto F = [&](int k) { return reinterpret_cast<float*>(p + 256 + k * col); };
+  DenseQueue q;
+  q.count = reinterpret_cast<int*>(p);
+  q.idx = reinterpret_cast<int*>(F(0));
+  q.lo = F(1); q.hi = F(2); q.Flo = F(3); q.u = F(4); q.u2 = F(5);
+  q.ox = F(6); q.oy = F(7); q.oz = F(8); q.dx = F(9); q.dy = F(10); q.dz = F(11);
+  q.t0 = F(12); q.t1 = F(13);
+  q.excl = reinterpret_cast<int*>(F(14));
+  return q;
+}
+
+// Appends one ray (threads of a warp that call together share one atomic).
+__device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float lo, float hi, float Flo, float u,
+                                           float u2, float3 o, float3 d, float t0, float t1, int excl) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(q.count, int(g.size()));
+  const int j = g.shfl(base, 0) + int(g.thread_rank());
+  q.idx[j] = idx;
+  q.lo[j] = lo; q.hi[j] = hi; q.Flo[j] = Flo; q.u[j] = u; q.u2[j] = u2;
+  q.ox[j] = o.x; q.oy[j] = o.y; q.oz[j] = o.z;
+  q.dx[j] = d.x; q.dy[j] = d.y; q.dz[j] = d.z;
+  q.t0[j] = t0; q.t1[j] = t1;
+  q.excl[j] = excl;
+}
+
+// Finishes every queued ray: prim_out[idx], t_spawn_out[idx] (the spawn distance, or t_u when
+// spawn_mode == 1) and, when not NULL, t_u_out[idx] and status_out[idx].  `stats` as for the
+// trace counters (nodes, primitives of the warp pass are added to [0], [1]), `rays_err` (may be
+// NULL) counts rays that ended with a non-zero status.
+ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
+                        float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
+                        unsigned long long* rays_err, cudaStream_t stream);
+
+}  // namespace ugp

@@ -21,13 +21,14 @@
 //    t_w (the smallest dropped start, or the entry of a pruned subtree), so F on [t_c, t_w] is
 //    known from the buffer; if it crosses u there, a safeguarded Newton iteration with
 //    F' = 1/2 sum G (Eq. 9) finds t_u, else the window advances.
-//  * dense mode (when more than kK intervals overlap, as in dense aggregates, or after
-//    kFFMaxRounds rounds).  In the spirit of the paper's GPU binning (Sec. 5.2), one traversal
-//    adds each interval's contribution to kB equal bins of [t_c, scene exit], pruning subtrees
-//    that start after the bin where the running sum passes u; this brackets t_u in one bin.  A
-//    safeguarded Newton iteration then evaluates F and F' on the bracket by order-free
-//    traversals, which need no per-ray storage whatever the overlap depth, and one more
-//    traversal runs the race at t_u.
+//  * dense mode (when more than kK intervals are active at once, as in dense aggregates, or
+//    after kFFMaxRounds rounds).  In the spirit of the paper's GPU binning (Sec. 5.2), one
+//    traversal adds each interval's contribution to kB equal bins of [t_c, scene exit],
+//    pruning subtrees that start after the bin where the running sum passes u; this brackets
+//    t_u in one bin.  If the intervals meeting the window fit the buffer the thread finishes
+//    alone; otherwise the ray goes to a queue that a warp-per-ray pass (ugp_dense.cu) finishes:
+//    32 lanes collect every interval of the bracket, solve F(t_u) = u by Newton with
+//    warp-reduced F and F', and run the race as a warp argmin.
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
 #include "ugp_trace.cuh"
@@ -221,47 +222,6 @@ struct BinVisitor {
   }
 };
 
-// ---------------------------------------------------------------- dense mode: F by traversal
-// F(t) - F(lo) = sum over all intervals of 1/2 I(max(a, lo), min(b, t)) and F'(t) = 1/2 sum G(t),
-// accumulated in any order (no buffer).
-struct FVisitor {
-  Ctx& c;
-  float lo, t;
-  float f, fp;
-  __device__ void pruned(float) {}
-  __device__ void leaf(int slot, float&) {
-    PrimHit h;
-    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
-    const float x = fmaxf(h.a, lo), y = fminf(h.b, t);
-    if (x < y) f += seg_half_integral(x, y, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
-    if (h.a <= t && t <= h.b) fp += 0.5f * gauss_at(t, h.tn, h.ts, h.s, h.e0);
-  }
-};
-
-// ---------------------------------------------------------------- the choice at t_u
-// Exponential race among the primitives whose interval contains t: the smallest
-// E_k / G_k(x_t) wins, i.e. primitive k with probability G_k / sum_j G_j, in one pass.
-struct RaceVisitor {
-  Ctx& c;
-  float t, u2;
-  float best;
-  int best_id;
-  float a, b;
-  __device__ void pruned(float) {}
-  __device__ void leaf(int slot, float&) {
-    PrimHit h;
-    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
-    if (!(h.a <= t && t <= h.b)) return;
-    const float key = race_exponential(u2, h.id) / gauss_at(t, h.tn, h.ts, h.s, h.e0);
-    if (key < best || (key == best && h.id < best_id)) {
-      best = key;
-      best_id = h.id;
-      a = h.a;
-      b = h.b;
-    }
-  }
-};
-
 // F(t) - u and F'(t) from the buffer entries [0, nE) on a window starting at lo with F(lo) = Flo.
 static __device__ __forceinline__ void eval_F(Ctx& c, int nE, float lo, float Flo, float u, float t, float& f,
                                        float& fp) {
@@ -312,7 +272,7 @@ static __device__ float solve_buffer(Ctx& c, int nE, float lo, float hi, float F
   return t;
 }
 
-// Choice among buffer entries [0, nE) containing t by the exponential race (RaceVisitor).
+// Choice among buffer entries [0, nE) containing t by the exponential race (smallest E_k / G_k).
 static __device__ int choose_buffer(Ctx& c, int nE, float t, float u2) {
   int pick = -1, pick_id = INT32_MAX;
   float best = INFINITY;
@@ -353,7 +313,9 @@ struct FFResult {
   int prim;          // -1: escape
   float t_u, t_spawn;
   unsigned rounds;
-  bool dense;
+  bool dense;        // the rounds gave up (more than kK intervals active at once)
+  bool pending;      // t_u is bracketed in [lo, hi] with F(lo) = Flo; the warp pass finishes it
+  float lo, hi, Flo;
 };
 
 static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
@@ -365,7 +327,8 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
   float cur_a = -INFINITY;
   int cur_id = -1, nC = 0;
   bool done = !(c.sc.n_prims > 0 && c.t0 < c.t1);
-  bool dense = false;
+  bool dense = false, pending = false;
+  float p_lo = 0.f, p_hi = 0.f, p_Flo = 0.f;
   // ---------------- rounds ----------------
   while (!done) {
     if (n_rounds >= kFFMaxRounds || nC == kK) {
@@ -417,7 +380,7 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
     }
     nC = m;
   }
-  // ---------------- dense mode: binned bracket, then Newton by traversal ----------------
+  // ---------------- dense mode: binned bracket; the warp pass (ugp_dense.cu) finishes it ----------------
   if (dense && c.st == UGP_RAY_OK) {
     const float lo0 = t_c, hi0 = scene_exit(c, t_c, c.t1);
     for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
@@ -452,50 +415,14 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
         acc = nxt;
       }
       if (jx >= 0) {   // otherwise F(end) <= u: escape
-        float lo = v.edge(jx), hi = v.edge(jx + 1);
-        const float Flo = F_c + acc;
-        const float inbin = FB(bin, jx);
-        float t = inbin > 0.f ? lo + (u - Flo) / inbin * (hi - lo) : 0.5f * (lo + hi);
-        if (!(t > lo && t < hi)) t = 0.5f * (lo + hi);
-        const float w_lo = lo;
-        float dx_old = hi - lo, dx = dx_old;
-        bool conv = false;
-        for (int it = 0; it < kDenseNewtonIters && c.st == UGP_RAY_OK; ++it) {
-          FVisitor fv{c, w_lo, t, Flo - u, 0.f};
-          float lim = t;
-          traverse(c, w_lo, t, lim, fv);
-          const float f = fv.f, fp = fv.fp;
-          if (f == 0.f) { conv = true; break; }
-          if (f < 0.f) lo = t; else hi = t;
-          if (!(nextafterf(lo, INFINITY) < hi)) { conv = true; break; }
-          const float tn = fp > 0.f ? t - f / fp : lo;
-          float tnew;
-          if (fp > 0.f && tn > lo && tn < hi && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
-            dx_old = dx;
-            dx = f / fp;
-            tnew = tn;
-          } else {
-            dx_old = dx;
-            dx = 0.5f * (hi - lo);
-            tnew = lo + dx;
-          }
-          if (tnew == t) { conv = true; break; }
-          t = tnew;
-        }
-        if (!conv && c.st == UGP_RAY_OK) c.st = UGP_RAY_SOLVE_LIMIT;
-        t_u = t;
-        RaceVisitor rv{c, t_u, u2, INFINITY, INT32_MAX, t_u, t_u};
-        float lim = t_u;
-        traverse(c, t_u, t_u, lim, rv);
-        if (rv.best_id != INT32_MAX) {
-          out_prim = rv.best_id;
-          out_tu = t_u;
-          out_tsp = 0.5f * (rv.a + rv.b);
-        }
+        pending = true;
+        p_lo = v.edge(jx);
+        p_hi = v.edge(jx + 1);
+        p_Flo = F_c + acc;
       }
     }
   }
-  return FFResult{out_prim, out_tu, out_tsp, n_rounds, dense};
+  return FFResult{out_prim, out_tu, out_tsp, n_rounds, dense, pending, p_lo, p_hi, p_Flo};
 }
 
 #undef FB

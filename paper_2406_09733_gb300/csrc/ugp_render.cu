@@ -19,6 +19,7 @@
 
 #include <math.h>
 
+#include "ugp_dense.cuh"
 #include "ugp_freeflight.cuh"
 #include "ugp_phase.cuh"
 #include "ugp_philox.cuh"
@@ -103,7 +104,7 @@ __device__ __forceinline__ int queue_append(int* counter) {
 }
 
 __global__ void __launch_bounds__(256) k_camera(CameraDev cam, int n, uint2 key, int sample, PathSoA ps, int* q,
-                                                int* cnt) {
+                                                int* cnt, int* dense_cnt) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const int px = p % cam.width, py = p / cam.width;
     const float4 U = rng(key, p, sample, 15, 0);
@@ -118,13 +119,17 @@ __global__ void __launch_bounds__(256) k_camera(CameraDev cam, int n, uint2 key,
     ps.excl[p] = -1;
     q[p] = p;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *cnt = n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cnt = n;
+    *dense_cnt = 0;
+  }
 }
 
 __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
                                                      int spawn_mode, PathSoA ps, const int* __restrict__ q,
                                                      const int* cnt, int* reset_next, int* reset_shadow,
-                                                     unsigned long long* rays, unsigned long long* stats) {
+                                                     unsigned long long* rays, unsigned long long* stats,
+                                                     DenseQueue dq) {
   __shared__ FFSmem sm;
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L,
     const float4 U = rng(key, p, sample, bounce, 0);
     Ctx c{sm, int(threadIdx.x), sc, make_ray(o, d), 0.f, t1, ps.excl[p], 0u, 0u, UGP_RAY_OK};
     const FFResult r = ff_sample(c, U.x, U.y);
+    if (r.pending) dense_push(dq, p, r.lo, r.hi, r.Flo, U.x, U.y, o, d, 0.f, t1, c.ex);
     ps.prim[p] = r.prim;
     ps.tsp[p] = spawn_mode == 1 ? r.t_u : r.t_spawn;
     ps.tq[p] = tq;
@@ -161,8 +167,10 @@ __device__ __forceinline__ Material load_material(const MatDev& m, int k) {
 
 __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 key, int sample, int bounce, int max_depth,
                                                int nee, PathSoA ps, const int* __restrict__ q, const int* cnt,
-                                               int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow) {
+                                               int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow,
+                                               int* dense_cnt) {
   const int count = load_count(cnt);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dense_cnt = 0;  // the dense pass of this bounce has run
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const int p = q[i];
     float3 beta = f3(ps.br[p], ps.bg[p], ps.bb[p]);
@@ -270,7 +278,7 @@ __global__ void __launch_bounds__(256) k_accumulate(int n, PathSoA ps, float* __
 
 struct RenderLayout {
   size_t total;
-  size_t state, queues, shadow, counts;
+  size_t state, queues, shadow, counts, dense;
 };
 
 RenderLayout render_layout(int64_t n) {
@@ -281,6 +289,7 @@ RenderLayout render_layout(int64_t n) {
   L.queues = off;  off += 2 * col;
   L.shadow = off;  off += 12 * col;
   L.counts = off;  off += 256;
+  L.dense = off;   off += dense_queue_bytes(n);
   L.total = off;
   return L;
 }
@@ -349,6 +358,7 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
                F(RL.shadow, 10), F(RL.shadow, 11)};
   int* queue[2] = {I(RL.queues, 0), I(RL.queues, 1)};
   int* counts = reinterpret_cast<int*>(ws + RL.counts);  // [0], [1] queue lengths, [2] shadow
+  const DenseQueue dq = dense_queue_at(ws + RL.dense, n);
 
   LightsDev Ld;
   Ld.has_quad = lights->has_quad != 0;
@@ -401,18 +411,23 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   for (int si = 0; si < params->spp; ++si) {
     const int sample = params->spp_begin + si;
     prof_begin(kStCamera, st);
-    k_camera<<<g_cam, 256, 0, st>>>(cd, int(n), key, sample, ps, queue[0], counts + 0);
+    k_camera<<<g_cam, 256, 0, st>>>(cd, int(n), key, sample, ps, queue[0], counts + 0, dq.count);
     prof_end(kStCamera, st);
     int cur = 0;
     for (int b = 0; b <= params->max_depth; ++b) {
       const int nxt = 1 - cur;
       prof_begin(kStExtend, st);
       k_extend<<<g_ext, kFFBlock, 0, st>>>(sc, Ld, key, sample, b, params->spawn_mode, ps, queue[cur], counts + cur,
-                                            counts + nxt, counts + 2, ray_counts, stats);
+                                            counts + nxt, counts + 2, ray_counts, stats, dq);
       prof_end(kStExtend, st);
+      {
+        const ugp_status ds = launch_dense(sc, dq, ps.prim, nullptr, ps.tsp, nullptr, params->spawn_mode, stats,
+                                           ray_counts ? ray_counts + 2 : nullptr, st);
+        if (ds != UGP_OK) return ds;
+      }
       prof_begin(kStShade, st);
       k_shade<<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
-                                        counts + cur, queue[nxt], counts + nxt, sh, counts + 2);
+                                        counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count);
       prof_end(kStShade, st);
       if (params->nee && Ld.has_quad) {
         prof_begin(kStShadow, st);

@@ -10,9 +10,8 @@ constexpr int kTrStack = 64;       // transmittance: traversal stack depth
 constexpr int kFFBlock = 64;       // free flight: threads per block
 constexpr int kK = 16;             // free flight: interval buffer per ray
 constexpr int kFFStack = 48;       // free flight: traversal stack depth
-constexpr int kFFMaxRounds = 8;    // free flight: collection rounds before the binned mode
+constexpr int kFFMaxRounds = 3;    // free flight: collection rounds before the dense mode
 constexpr int kB = 16;             // free flight: bins of the dense mode's bracketing pass
-constexpr int kDenseNewtonIters = 32;  // free flight: traversal-evaluated Newton steps (dense mode)
 constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
 
 struct TraceScene {
@@ -36,6 +35,6 @@ ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3
 ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
                               const float* t0, const float* t1, const float* u, const float* u2,
                               const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
-                              cudaStream_t stream);
+                              void* workspace, cudaStream_t stream);
 
 }  // namespace ugp

@@ -81,7 +81,9 @@ def lib():
         L.ugp_trace_transmittance.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_sample_free_flight.restype = C.c_int
         L.ugp_sample_free_flight.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                             vp, vp]
+                                             vp, vp, C.c_size_t, vp]
+        L.ugp_sample_free_flight_workspace_size.restype = C.c_size_t
+        L.ugp_sample_free_flight_workspace_size.argtypes = [C.c_int64]
         L.ugp_collect_hits.restype = C.c_int
         L.ugp_collect_hits.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.c_int32, vp, vp, vp,
                                        vp, vp, vp]
@@ -208,8 +210,11 @@ def trace_transmittance(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
     return T, st
 
 
-def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None):
+def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None, workspace=None):
     n = int(o.shape[0])
+    nb = int(lib().ugp_sample_free_flight_workspace_size(n))
+    if workspace is None or workspace.numel() < nb:
+        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=o.device)
     for t, nm in ((t0, "t0"), (t1, "t1"), (u, "u"), (u2, "u2")):
         _dev(t, torch.float32, nm)
     _dev(o, torch.float32, "o", 3)
@@ -221,7 +226,8 @@ def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None)
     st = torch.empty(n, dtype=torch.uint8, device=o.device)
     _check(lib().ugp_sample_free_flight(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
                                         _p(u), _p(u2), _p(exclude), _p(prim), _p(tu), _p(tsp),
-                                        _p(st), C.c_void_p(_stream(stream))),
+                                        _p(st), _p(workspace), workspace.numel(),
+                                        C.c_void_p(_stream(stream))),
            "ugp_sample_free_flight")
     return prim, tu, tsp, st
 
@@ -330,7 +336,7 @@ def set_trace_counters(counters=None):
     _check(lib().ugp_set_trace_counters(_p(counters)), "ugp_set_trace_counters")
 
 
-PROFILE_STAGES = ("build", "camera", "extend", "shade", "shadow", "accumulate", "query", "reserved")
+PROFILE_STAGES = ("build", "camera", "extend", "shade", "shadow", "accumulate", "query", "dense")
 
 
 def profile_begin(max_records: int = 1 << 16):
