@@ -47,6 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-pixels", type=int, default=1024, help="pixels of the CPU-baseline sample")
+    p.add_argument("--kernel-case", choices=["ff_camera512"], default=None,
+                   help="run one small kernel case for profilers and exit (no bench line)")
     return p.parse_args(argv)
 
 
@@ -327,8 +329,42 @@ def run_ugp(args):
     return 0
 
 
+def run_kernel_case(args):
+    """One launch of each scene query on 512 x 512 pinhole camera rays of the room scene (t in
+    [0, 4]): a small, fixed case for ncu captures of the free-flight and transmittance kernels."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    s = scenes.room_scene(args.n_prims)
+    bvh = ugp.build_bvh(t(s.mean), t(s.quat), t(s.scale), t(s.magnitude))
+    W = H = 512
+    cam = s.camera
+    f = np.array(cam.look, float) - cam.eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, cam.up); r /= np.linalg.norm(r)
+    up = np.cross(r, f)
+    th = np.tan(np.radians(cam.vfov_deg) / 2)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    d = f + ((2 * px / W - 1) * th)[..., None] * r + ((1 - 2 * py / H) * th)[..., None] * up
+    d = (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3).astype(np.float32)
+    n = d.shape[0]
+    O, D = t(np.tile(np.array(cam.eye, np.float32), (n, 1))), t(d)
+    T0, T1 = torch.zeros(n, device=dev), torch.full((n,), 4.0, device=dev)
+    prim, tu, tsp, st = ugp.sample_free_flight(bvh, O, D, T0, T1, t(scenes.uniforms24(1, n)),
+                                               t(scenes.uniforms24(2, n)))
+    T, st2 = ugp.trace_transmittance(bvh, O, D, T0, T1)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "rays": n, "scattered": int((prim >= 0).sum()),
+                      "status_max": int(max(st.max(), st2.max()))}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ugp(args)

@@ -1,0 +1,54 @@
+"""Host logic of bench.py on the CPU: whole-job aggregation over ranks (gloo, world size 2)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, units = bench.aggregate(100.0 + 50.0 * rank, 1000.0 * (rank + 1), dist)
+        q.put((rank, ms, units))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_aggregate_max_time_sum_units_over_two_ranks():
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    out = sorted(q.get(timeout=5) for _ in range(2))
+    for rank, ms, units in out:
+        assert ms == 150.0 and units == 3000.0
+
+
+def test_aggregate_single_process_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate(12.5, 7.0, None) == (12.5, 7.0)
+
+
+def test_bench_arguments_and_workload_description():
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.parse_args([])
+    assert a.gpus == 1 and a.steps >= 1 and a.warmup >= 3 and a.impl == "ugp"
+    cfg = bench.workload_config(a, "flushed")
+    assert cfg["n_prims"] == 1_000_000 and cfg["width"] == 1024 and cfg["max_depth"] == 8
