@@ -169,6 +169,29 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
  * only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
+/* Free-flight sampling without any device allocation (no counterpart in the paper).
+ * Same inputs, outputs and results as ugp_sample_free_flight, for callers that cannot
+ * call cudaMalloc or hand the library a workspace -- for example code that runs while a
+ * host application owns every device allocation, or a real-time loop that must not
+ * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 3.9 MB); every GPU that
+ * loads the library holds it until the process exits.
+ *  - n_rays above UGP_NOALLOC_MAX_RAYS is rejected with UGP_ERR_INVALID_ARG.
+ *  - The first call on a device looks up the array's device address with that device
+ *    current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind; the call clears the
+ *    part that must start at zero on `stream`.  Calls whose device work overlaps (on
+ *    different streams, or from several host threads) race on the array and must be
+ *    serialised by the caller.
+ *  - No cudaMalloc, cudaFree or allocating library routine is called. */
+#define UGP_NOALLOC_MAX_RAYS 65536
+ugp_status ugp_sample_free_flight_noalloc(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
+                                          const float* d3, const float* t0, const float* t1,
+                                          const float* u, const float* u2,
+                                          const int32_t* exclude_prim, int32_t* prim_out,
+                                          float* t_u_out, float* t_spawn_out, uint8_t* status_out,
+                                          void* stream);
+
 /* All clipped intervals along each ray (hit-set diagnostics).  For ray r,
  * count_out[r] receives the number of primitives whose k-ellipsoid interval
  * meets [t0, t1] (Eq. 4 cut-off, the same test as the queries above); the
