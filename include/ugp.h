@@ -276,7 +276,8 @@ ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const 
 /* Optional traversal statistics: when `counters` is a device pointer to 12
  * zero-initialised uint64, later tracing calls on any stream add (atomically)
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
- *   [3] traversal rounds, [4] free-flight rays that needed the dense mode
+ *   [3] per-thread traversal passes, [4] free-flight rays handed to the warp-per-ray
+ *   dense pass (whose node and record loads are added to [0] and [1])
  * for free-flight and transmittance queries (standalone, and the renderer's extend
  * pass), and the same five quantities at [6..10] for the renderer's shadow rays;
  * [5] and [11] are reserved.  NULL turns counting off (the default).  Host-side

@@ -24,7 +24,7 @@ k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const
   tu_out[r] = res.t_u;
   tsp_out[r] = res.t_spawn;
   if (st_out) st_out[r] = c.st;
-  if (STATS) add_counters(ctr, c.n_nodes, c.n_prims, 1u, res.rounds, res.dense ? 1u : 0u);
+  if (STATS) add_counters(ctr, c.n_nodes, c.n_prims, 1u, 1u, res.pending ? 1u : 0u);
 }
 
 }  // namespace

@@ -12,23 +12,21 @@
 // Since u < 1, t_u lies before the saturating distance, so primitive k is chosen with
 // probability 1/2 I_k(a_k, min(b_k, t_sat)).
 //
-// A BVH gives no front-to-back order (the paper's reason for a kd-tree, Sec. 5.1), so the
-// kernel finds t_u in one of two ways, both exact:
+// A BVH gives no front-to-back order (the paper's reason for a kd-tree, Sec. 5.1), so t_u is
+// found in two exact steps, in the spirit of the paper's GPU binning (Sec. 5.2):
 //
-//  * rounds (fast path).  A traversal collects the intervals with the smallest (a, index)
-//    keys after a cursor into a per-ray shared-memory buffer of kK entries, next to the
-//    intervals still active from the previous round.  Everything not kept starts at or after
-//    t_w (the smallest dropped start, or the entry of a pruned subtree), so F on [t_c, t_w] is
-//    known from the buffer; if it crosses u there, a safeguarded Newton iteration with
-//    F' = 1/2 sum G (Eq. 9) finds t_u, else the window advances.
-//  * dense mode (when more than kK intervals are active at once, as in dense aggregates, or
-//    after kFFMaxRounds rounds).  In the spirit of the paper's GPU binning (Sec. 5.2), one
-//    traversal adds each interval's contribution to kB equal bins of [t_c, scene exit],
-//    pruning subtrees that start after the bin where the running sum passes u; this brackets
-//    t_u in one bin.  If the intervals meeting the window fit the buffer the thread finishes
-//    alone; otherwise the ray goes to a queue that a warp-per-ray pass (ugp_dense.cu) finishes:
-//    32 lanes collect every interval of the bracket, solve F(t_u) = u by Newton with
-//    warp-reduced F and F', and run the race as a warp argmin.
+//  * scan (this header, one thread per ray, one traversal).  A nearest-first traversal adds
+//    each interval's contribution to kB equal bins of [t0, scene exit].  The first bin whose
+//    prefix passes u, the crossing bin j, can only move earlier as intervals arrive, so subtrees
+//    starting after its end are pruned.  The thread also keeps the intervals that start before
+//    that end in a kK-entry buffer, evicting the one that starts last when full and remembering
+//    the smallest evicted start.  At the end F(e_j) is exact from the bins, and the buffer holds
+//    every interval meeting [e_j, e_j+1] unless an evicted one starts before e_j+1.  If it does
+//    hold them all, a safeguarded Newton iteration with F' = 1/2 sum G (Eq. 9) solves
+//    F(t_u) = u inside the bin and the race picks the primitive.
+//  * dense pass (ugp_dense.cu, one warp per ray) for the rays whose crossing bin holds more
+//    intervals than the buffer, as inside dense aggregates: 32 lanes collect every interval of
+//    the bin, solve with warp-reduced F and F', and run the race as a warp argmin.
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
 #include "ugp_trace.cuh"
@@ -60,10 +58,6 @@ struct Ctx {  // per-ray state shared by the traversal visitors
 };
 
 #define FB(arr, i) c.sm.arr[(i)][c.tid]
-
-static __device__ __forceinline__ bool key_less(float a0, int i0, float a1, int i1) {
-  return a0 < a1 || (a0 == a1 && i0 < i1);
-}
 
 static __device__ __forceinline__ void put(Ctx& c, int pos, const PrimHit& h) {
   FB(a, pos) = h.a;
@@ -153,45 +147,13 @@ __device__ void traverse(Ctx& c, float lo, float hi, float& limit, V& vis) {
   }
 }
 
-// ---------------------------------------------------------------- rounds: collection visitor
-struct RoundVisitor {
-  Ctx& c;
-  float t_c, cur_a;
-  int cur_id, nC, cap, nNew;
-  float t_next;
-  __device__ void pruned(float en) { t_next = fminf(t_next, en); }
-  __device__ void leaf(int slot, float& limit) {
-    PrimHit h;
-    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
-    if (h.b <= t_c) return;                           // ends before the window
-    if (!key_less(cur_a, cur_id, h.a, h.id)) return;  // kept in an earlier round
-    int pos;
-    if (nNew < cap) {
-      pos = nC + nNew;
-      ++nNew;
-    } else {
-      const int last = nC + nNew - 1;
-      if (!key_less(h.a, h.id, FB(a, last), unpack_id(FB(id, last)))) {
-        t_next = fminf(t_next, h.a);
-        return;
-      }
-      t_next = fminf(t_next, FB(a, last));  // the evicted interval starts here
-      pos = last;
-    }
-    while (pos > nC && key_less(h.a, h.id, FB(a, pos - 1), unpack_id(FB(id, pos - 1)))) {
-      move(c, pos, pos - 1);
-      --pos;
-    }
-    put(c, pos, h);
-    if (nNew == cap) limit = FB(a, nC + nNew - 1);
-  }
-};
-
-// ---------------------------------------------------------------- binned refinement visitor
-struct BinVisitor {
+// ---------------------------------------------------------------- scan visitor
+struct ScanVisitor {
   Ctx& c;
   float lo, hi, w, target;  // bins of width w over [lo, hi]; target = u - F(lo)
-  int count;
+  int jc;                   // current crossing bin (kB: none yet)
+  int n;                    // buffer entries
+  float lost_a;             // smallest start of an interval evicted from the full buffer
   __device__ float edge(int j) const { return j >= kB ? hi : lo + w * float(j); }
   __device__ void pruned(float) {}
   __device__ void leaf(int slot, float& limit) {
@@ -199,25 +161,47 @@ struct BinVisitor {
     if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     const float x = fmaxf(h.a, lo), y = fminf(h.b, hi);
     if (!(x < y)) return;
-    if (count < kK) put(c, count, h);
-    ++count;
     int j = min(kB - 1, max(0, int((x - lo) / w)));
     while (j > 0 && x < edge(j)) --j;
     while (j < kB - 1 && x >= edge(j + 1)) ++j;
-    for (; j < kB && edge(j) < y; ++j) {
-      const float xa = fmaxf(x, edge(j)), ya = fminf(y, edge(j + 1));
-      if (xa < ya)
-        FB(bin, j) += seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
+    for (int k = j; k < kB && edge(k) < y; ++k) {
+      const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
+      if (xa < ya) FB(bin, k) += seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
     }
-    // the partial sums only grow, so once they pass the target the crossing is known to lie
-    // at or before that bin's upper edge
-    float acc = 0.f;
-    for (int k = 0; k < kB; ++k) {
-      acc += FB(bin, k);
-      if (acc > target) {
-        limit = fminf(limit, edge(k + 1));
-        break;
+    if (j <= jc) {  // the crossing bin can only move to or before this interval's first bin
+      float acc = 0.f;
+      for (int k = 0; k < kB; ++k) {
+        acc += FB(bin, k);
+        if (acc > target) {
+          if (k < jc) {
+            jc = k;
+            limit = edge(jc + 1);
+            int m = 0;  // intervals starting after the new end can no longer matter
+            for (int e = 0; e < n; ++e) {
+              if (FB(a, e) < limit) {
+                if (m != e) move(c, m, e);
+                ++m;
+              }
+            }
+            n = m;
+          }
+          break;
+        }
       }
+    }
+    if (!(x < edge(jc + 1))) return;
+    if (n < kK) {
+      put(c, n++, h);
+      return;
+    }
+    int far = 0;  // evict whichever of the buffer and the new interval starts last
+    for (int e = 1; e < kK; ++e)
+      if (FB(a, e) > FB(a, far)) far = e;
+    if (FB(a, far) > h.a) {
+      lost_a = fminf(lost_a, FB(a, far));
+      put(c, far, h);
+    } else {
+      lost_a = fminf(lost_a, h.a);
     }
   }
 };
@@ -312,117 +296,44 @@ static __device__ float scene_exit(const Ctx& c, float lo, float hi) {
 struct FFResult {
   int prim;          // -1: escape
   float t_u, t_spawn;
-  unsigned rounds;
-  bool dense;        // the rounds gave up (more than kK intervals active at once)
   bool pending;      // t_u is bracketed in [lo, hi] with F(lo) = Flo; the warp pass finishes it
   float lo, hi, Flo;
 };
 
 static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
-  unsigned n_rounds = 0;
-  int out_prim = -1;
-  float out_tu = c.t1, out_tsp = c.t1;
-
-  float t_c = c.t0, F_c = 0.f;
-  float cur_a = -INFINITY;
-  int cur_id = -1, nC = 0;
-  bool done = !(c.sc.n_prims > 0 && c.t0 < c.t1);
-  bool dense = false, pending = false;
-  float p_lo = 0.f, p_hi = 0.f, p_Flo = 0.f;
-  // ---------------- rounds ----------------
-  while (!done) {
-    if (n_rounds >= kFFMaxRounds || nC == kK) {
-      dense = true;
-      break;
-    }
-    ++n_rounds;
-    RoundVisitor v{c, t_c, cur_a, cur_id, nC, kK - nC, 0, c.t1};
-    float limit = c.t1;
-    traverse(c, t_c, c.t1, limit, v);
-    if (c.st != UGP_RAY_OK) break;
-    const int nE = nC + v.nNew;
-    const float t_w = fmaxf(v.t_next, t_c);
-    float dF = 0.f;
-    for (int e = 0; e < nE; ++e) {
-      const float lo = fmaxf(FB(a, e), t_c), hi = fminf(FB(b, e), t_w);
-      if (lo < hi) dF += entry_integral(c, e, lo, hi);
-    }
-    if (F_c + dF > u) {
-      // F is flat after the last interval ends, so the root lies before min(t_w, max b)
-      float t_hi = t_c;
-      for (int e = 0; e < nE; ++e) t_hi = fmaxf(t_hi, FB(b, e));
-      const float t = solve_buffer(c, nE, t_c, fminf(t_w, t_hi), F_c, u);
-      const int pick = choose_buffer(c, nE, t, u2);
-      if (pick >= 0) {
-        out_prim = unpack_id(FB(id, pick));
-        out_tu = t;
-        out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
-      }
-      done = true;
-      break;
-    }
-    F_c += dF;
-    t_c = t_w;
-    if (t_w >= c.t1) {
-      done = true;  // escape
-      break;
-    }
-    if (v.nNew > 0) {
-      cur_a = FB(a, nE - 1);
-      cur_id = unpack_id(FB(id, nE - 1));
-    }
-    int m = 0;  // carry the intervals still active after t_w
-    for (int e = 0; e < nE; ++e) {
-      if (FB(b, e) > t_w) {
-        if (m != e) move(c, m, e);
-        ++m;
-      }
-    }
-    nC = m;
+  FFResult r{-1, c.t1, c.t1, false, 0.f, 0.f, 0.f};
+  if (!(c.sc.n_prims > 0 && c.t0 < c.t1)) return r;
+  const float lo = c.t0, hi = scene_exit(c, c.t0, c.t1);
+  if (!(lo < hi)) return r;
+  for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
+  ScanVisitor v{c, lo, hi, (hi - lo) / float(kB), u, kB, 0, INFINITY};
+  float limit = hi;
+  traverse(c, lo, hi, limit, v);
+  if (c.st != UGP_RAY_OK || v.jc == kB) return r;  // F(end) <= u: escape
+  float Flo = 0.f;
+  for (int k = 0; k < v.jc; ++k) Flo += FB(bin, k);
+  const float wlo = v.edge(v.jc), whi = v.edge(v.jc + 1);
+  if (v.lost_a < whi) {  // the buffer misses intervals of the crossing bin
+    r.pending = true;
+    r.lo = wlo;
+    r.hi = whi;
+    r.Flo = Flo;
+    return r;
   }
-  // ---------------- dense mode: binned bracket; the warp pass (ugp_dense.cu) finishes it ----------------
-  if (dense && c.st == UGP_RAY_OK) {
-    const float lo0 = t_c, hi0 = scene_exit(c, t_c, c.t1);
-    for (int j = 0; j < kB; ++j) FB(bin, j) = 0.f;
-    BinVisitor v{c, lo0, hi0, (hi0 - lo0) / float(kB), u - F_c, 0};
-    float limit = hi0;
-    traverse(c, lo0, hi0, limit, v);
-    float t_u = -1.f;
-    if (c.st == UGP_RAY_OK && v.count <= kK) {
-      // every interval meeting [lo0, limit] is in the buffer
-      float f, fp;
-      eval_F(c, v.count, lo0, F_c, u, limit, f, fp);
-      if (f > 0.f || limit < hi0) {
-        float t_hi = lo0;
-        for (int e = 0; e < v.count; ++e) t_hi = fmaxf(t_hi, FB(b, e));
-        t_u = f > 0.f ? solve_buffer(c, v.count, lo0, fminf(limit, t_hi), F_c, u) : limit;
-        const int pick = choose_buffer(c, v.count, t_u, u2);
-        if (pick >= 0) {
-          out_prim = unpack_id(FB(id, pick));
-          out_tu = t_u;
-          out_tsp = 0.5f * (FB(a, pick) + FB(b, pick));
-        }
-      }
-    } else if (c.st == UGP_RAY_OK) {
-      float acc = 0.f;
-      int jx = -1;
-      for (int j = 0; j < kB; ++j) {
-        const float nxt = acc + FB(bin, j);
-        if (nxt > u - F_c) {
-          jx = j;
-          break;
-        }
-        acc = nxt;
-      }
-      if (jx >= 0) {   // otherwise F(end) <= u: escape
-        pending = true;
-        p_lo = v.edge(jx);
-        p_hi = v.edge(jx + 1);
-        p_Flo = F_c + acc;
-      }
-    }
+  // F is flat after the last interval ends, so the root lies before min(whi, max b)
+  float t_hi = wlo;
+  for (int e = 0; e < v.n; ++e) t_hi = fmaxf(t_hi, FB(b, e));
+  t_hi = fminf(t_hi, whi);
+  float f, fp;
+  eval_F(c, v.n, wlo, Flo, u, t_hi, f, fp);
+  const float t = f > 0.f ? solve_buffer(c, v.n, wlo, t_hi, Flo, u) : t_hi;
+  const int pick = choose_buffer(c, v.n, t, u2);
+  if (pick >= 0) {
+    r.prim = unpack_id(FB(id, pick));
+    r.t_u = t;
+    r.t_spawn = 0.5f * (FB(a, pick) + FB(b, pick));
   }
-  return FFResult{out_prim, out_tu, out_tsp, n_rounds, dense, pending, p_lo, p_hi, p_Flo};
+  return r;
 }
 
 #undef FB

@@ -253,7 +253,7 @@ __device__ __forceinline__ float3 ld3(const float* __restrict__ p, int64_t i) {
 }
 
 // Warp-aggregated statistics update (threads of a warp that already returned are left out):
-// nodes loaded, primitive records loaded, rays, traversal rounds, rays that needed the binned mode.
+// nodes loaded, primitive records loaded, rays, traversal passes, rays handed to the dense pass.
 __device__ __forceinline__ void add_counters(unsigned long long* ctr, unsigned a, unsigned b,
                                              unsigned c, unsigned d, unsigned e) {
   const unsigned mask = __activemask();

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L,
     ps.tq[p] = tq;
     ps.qflag[p] = qf;
     if (c.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
-    if (stats) add_counters(stats, c.n_nodes, c.n_prims, 1u, r.rounds, r.dense ? 1u : 0u);
+    if (stats) add_counters(stats, c.n_nodes, c.n_prims, 1u, 1u, r.pending ? 1u : 0u);
   }
 }
 

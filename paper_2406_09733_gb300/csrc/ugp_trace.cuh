@@ -8,10 +8,9 @@ namespace ugp {
 constexpr int kTrBlock = 128;      // transmittance: threads per block
 constexpr int kTrStack = 64;       // transmittance: traversal stack depth
 constexpr int kFFBlock = 64;       // free flight: threads per block
-constexpr int kK = 16;             // free flight: interval buffer per ray
+constexpr int kK = 8;              // free flight: interval buffer per ray
 constexpr int kFFStack = 48;       // free flight: traversal stack depth
-constexpr int kFFMaxRounds = 3;    // free flight: collection rounds before the dense mode
-constexpr int kB = 16;             // free flight: bins of the dense mode's bracketing pass
+constexpr int kB = 16;             // free flight: bins of the scan
 constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
 
 struct TraceScene {
