@@ -165,8 +165,9 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
 
 /* Scratch bytes ugp_sample_free_flight needs for n_rays rays: a queue of the rays whose
  * bracketed root has more overlapping intervals than one thread buffers (they are
- * finished by a warp-per-ray pass).  The workspace must be 256-byte aligned and is
- * only used during the call's device work. */
+ * finished by a warp-per-ray pass), and per ray a list of up to 128 primitive slots met
+ * by the first pass (576 bytes per ray in all).  The workspace must be 256-byte aligned
+ * and is only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
 /* Free-flight sampling without any device allocation (no counterpart in the paper).
@@ -174,8 +175,10 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  * call cudaMalloc or hand the library a workspace -- for example code that runs while a
  * host application owns every device allocation, or a real-time loop that must not
  * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
- * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 3.9 MB); every GPU that
- * loads the library holds it until the process exits.
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.2 MB); every GPU that
+ * loads the library holds it until the process exits.  Without the per-ray slot lists of
+ * the regular entry point, its warp pass finds dense intervals by traversal; the results
+ * are the same.
  *  - n_rays above UGP_NOALLOC_MAX_RAYS is rejected with UGP_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address with that device
  *    current (cudaGetSymbolAddress); make that first call before any stream capture.
@@ -252,8 +255,8 @@ typedef struct ugp_render_params {
   int32_t spawn_mode, reserved;
 } ugp_render_params;
 
-/* Workspace bytes ugp_render needs for a width x height image (path state and
- * queues, 188 bytes per pixel plus alignment). */
+/* Workspace bytes ugp_render needs for a width x height image (path state, queues and
+ * per-path primitive-slot lists, 704 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 
 /* Path-traces the image with the volumetric path tracer of Table 1 (right column)

@@ -3,10 +3,11 @@
 // clusters, where over a hundred bounding ellipsoids can overlap at one point.
 //
 // For each queued ray one warp
-//   1. collects every clipped interval meeting [lo, hi] into a per-warp shared-memory list by a
-//      warp-parallel traversal: each step pops up to 32 nodes from a shared stack, one per lane,
-//      pushes the hit internal children with ballot-ranked slots and appends hit leaves the same
-//      way;
+//   1. collects every clipped interval meeting [lo, hi] into a per-warp shared-memory list: from
+//      the primitive slots the per-thread scan recorded for the ray when that list is complete
+//      (32 re-tests per step), else by a warp-parallel traversal that pops up to 32 nodes from a
+//      shared stack per step, one per lane, pushing the hit internal children and appending hit
+//      leaves with ballot-ranked slots;
 //   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method safeguarded
 //      with bisection, F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive
 //      with the exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
@@ -96,6 +97,22 @@ __device__ void warp_traverse(WarpSmem& W, const TraceScene& sc, const Ray& ray,
   }
 }
 
+// Calls `leaf(slot)` on all lanes for every candidate primitive of [lo, hi]: from the ray's
+// recorded slot list when it is complete (32 slots per step), else by a warp traversal.
+template <class LeafFn>
+__device__ void for_each_candidate(WarpSmem& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
+                                   uint8_t& st, unsigned& nn, const int* list, int nlist, LeafFn&& leaf) {
+  if (list) {
+    for (int base = 0; base < nlist; base += 32) {
+      const int e = base + lane;
+      leaf(e < nlist ? __ldg(list + e) : -1);
+    }
+    __syncwarp();
+    return;
+  }
+  warp_traverse(W, sc, ray, lo, hi, lane, st, nn, leaf);
+}
+
 __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueue q, int* __restrict__ prim_out,
                                                         float* __restrict__ tu_out, float* __restrict__ tsp_out,
                                                         uint8_t* __restrict__ st_out, int spawn_mode,
@@ -110,6 +127,8 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueu
     float lo = q.lo[j], hi = q.hi[j], Flo = q.Flo[j];
     const float u = q.u[j], u2 = q.u2[j], t0 = q.t0[j], t1 = q.t1[j];
     const int excl = q.excl[j];
+    const int nlist = q.nlist[j];
+    const int* list = (q.list && nlist <= kListCap) ? q.list + size_t(idx) * kListCap : nullptr;
     const Ray ray = make_ray(make_float3(q.ox[j], q.oy[j], q.oz[j]), make_float3(q.dx[j], q.dy[j], q.dz[j]));
     uint8_t st = UGP_RAY_OK;
     unsigned nn = 0, np = 0;
@@ -119,7 +138,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueu
     for (int level = 0; level < kDLevels && !done && st == UGP_RAY_OK; ++level) {
       // ---- 1. collect the intervals meeting [lo, hi]
       int n = 0;
-      warp_traverse(W, sc, ray, lo, hi, lane, st, nn, [&](int slot) {
+      for_each_candidate(W, sc, ray, lo, hi, lane, st, nn, list, nlist, [&](int slot) {
         PrimHit hh;
         bool ok = false;
         if (slot >= 0) {
@@ -226,7 +245,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueu
         __syncwarp();
         const float w = (hi - lo) / 32.f;
         auto edge = [&](int k) { return k >= 32 ? hi : lo + w * float(k); };
-        warp_traverse(W, sc, ray, lo, hi, lane, st, nn, [&](int slot) {
+        for_each_candidate(W, sc, ray, lo, hi, lane, st, nn, list, nlist, [&](int slot) {
           if (slot < 0) return;
           ++np;
           PrimHit hh;

@@ -15,11 +15,18 @@ struct DenseQueue {
   float *lo, *hi, *Flo, *u, *u2;
   float *ox, *oy, *oz, *dx, *dy, *dz, *t0, *t1;
   int* excl;
+  int* nlist;    // primitive slots the scan recorded for the ray (> kListCap: list incomplete)
+  const int* list;  // per-ray slot lists, kListCap ints at list + idx * kListCap (NULL: none)
 };
 
-constexpr int kDenseCols = 15;
+constexpr int kDenseCols = 16;
+// Slots of the primitives the scan met before its window end, kept per ray so the dense pass
+// can rebuild the window's intervals without another traversal.
+constexpr int kListCap = 128;
+inline size_t slot_list_bytes(int64_t n) { return align256(size_t(n) * kListCap * 4); }
 
-// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header).
+// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header); the slot
+// lists, when used, take slot_list_bytes(cap) more.
 inline size_t dense_queue_bytes(int64_t cap) { return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4); }
 
 inline DenseQueue dense_queue_at(void* base, int64_t cap) {
@@ -33,12 +40,14 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   q.ox = F(6); q.oy = F(7); q.oz = F(8); q.dx = F(9); q.dy = F(10); q.dz = F(11);
   q.t0 = F(12); q.t1 = F(13);
   q.excl = reinterpret_cast<int*>(F(14));
+  q.nlist = reinterpret_cast<int*>(F(15));
+  q.list = nullptr;
   return q;
 }
 
 // Appends one ray (threads of a warp that call together share one atomic).
 __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float lo, float hi, float Flo, float u,
-                                           float u2, float3 o, float3 d, float t0, float t1, int excl) {
+                                           float u2, float3 o, float3 d, float t0, float t1, int excl, int nlist) {
   namespace cg = cooperative_groups;
   cg::coalesced_group g = cg::coalesced_threads();
   int base = 0;
@@ -50,6 +59,7 @@ __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float l
   q.dx[j] = d.x; q.dy[j] = d.y; q.dz[j] = d.z;
   q.t0[j] = t0; q.t1[j] = t1;
   q.excl[j] = excl;
+  q.nlist[j] = nlist;
 }
 
 // Finishes every queued ray: prim_out[idx], t_spawn_out[idx] (the spawn distance, or t_u when

@@ -27,6 +27,7 @@
 //  * dense pass (ugp_dense.cu, one warp per ray) for the rays whose crossing bin holds more
 //    intervals than the buffer, as inside dense aggregates: 32 lanes collect every interval of
 //    the bin, solve with warp-reduced F and F', and run the race as a warp argmin.
+#include "ugp_dense.cuh"
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
 #include "ugp_trace.cuh"
@@ -55,6 +56,8 @@ struct Ctx {  // per-ray state shared by the traversal visitors
   int ex;
   unsigned n_nodes, n_prims;
   uint8_t st;
+  int* list;  // this ray's slot list (kListCap ints) or NULL
+  int nlist;
 };
 
 #define FB(arr, i) c.sm.arr[(i)][c.tid]
@@ -190,6 +193,10 @@ struct ScanVisitor {
       }
     }
     if (!(x < edge(jc + 1))) return;
+    if (c.list) {
+      if (c.nlist < kListCap) c.list[c.nlist] = slot;
+      ++c.nlist;
+    }
     if (n < kK) {
       put(c, n++, h);
       return;
@@ -298,10 +305,11 @@ struct FFResult {
   float t_u, t_spawn;
   bool pending;      // t_u is bracketed in [lo, hi] with F(lo) = Flo; the warp pass finishes it
   float lo, hi, Flo;
+  int nlist;         // slots recorded in c.list
 };
 
 static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
-  FFResult r{-1, c.t1, c.t1, false, 0.f, 0.f, 0.f};
+  FFResult r{-1, c.t1, c.t1, false, 0.f, 0.f, 0.f, 0};
   if (!(c.sc.n_prims > 0 && c.t0 < c.t1)) return r;
   const float lo = c.t0, hi = scene_exit(c, c.t0, c.t1);
   if (!(lo < hi)) return r;
@@ -318,6 +326,7 @@ static __device__ FFResult ff_sample(Ctx& c, float u, float u2) {
     r.lo = wlo;
     r.hi = whi;
     r.Flo = Flo;
+    r.nlist = c.nlist;
     return r;
   }
   // F is flat after the last interval ends, so the root lies before min(whi, max b)

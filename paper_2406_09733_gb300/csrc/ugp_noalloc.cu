@@ -13,10 +13,10 @@
 namespace ugp {
 namespace {
 
-// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header and 15 columns of
+// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header and 16 columns of
 // 4-byte entries, each padded to 256 bytes (the layout of dense_queue_at).
 constexpr int64_t kNoallocMaxRays = UGP_NOALLOC_MAX_RAYS;
-constexpr size_t kNoallocBytes = 256 + 15 * ((size_t(kNoallocMaxRays) * 4 + 255) & ~size_t(255));
+constexpr size_t kNoallocBytes = 256 + 16 * ((size_t(kNoallocMaxRays) * 4 + 255) & ~size_t(255));
 
 static __device__ __align__(256) unsigned char g_ff_scratch[kNoallocBytes];
 
@@ -72,8 +72,9 @@ extern "C" ugp_status ugp_sample_free_flight_noalloc(const ugp_bvh* bvh, int64_t
   void* scratch = nullptr;
   s = scratch_for_current_device(&scratch);
   if (s != UGP_OK) return s;
-  // The queue is laid out for n_rays entries inside the fixed array; launch_free_flight clears
+  // The queue is laid out for n_rays entries inside the fixed array (without the per-ray slot
+  // lists, so the dense pass collects its intervals by traversal); launch_free_flight clears
   // its counter on `stream` before use.
   return launch_free_flight(trace_scene(bvh), n_rays, o3, d3, t0, t1, u, u2, exclude_prim, prim_out, t_u_out,
-                            t_spawn_out, status_out, scratch, static_cast<cudaStream_t>(stream));
+                            t_spawn_out, status_out, scratch, false, static_cast<cudaStream_t>(stream));
 }

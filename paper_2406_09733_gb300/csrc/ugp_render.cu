@@ -144,9 +144,10 @@ __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L,
     const int qf = quad_hit(L, o, d, tq);
     const float t1 = qf ? tq : 1e30f;
     const float4 U = rng(key, p, sample, bounce, 0);
-    Ctx c{sm, int(threadIdx.x), sc, make_ray(o, d), 0.f, t1, ps.excl[p], 0u, 0u, UGP_RAY_OK};
+    Ctx c{sm, int(threadIdx.x), sc, make_ray(o, d), 0.f, t1, ps.excl[p], 0u, 0u, UGP_RAY_OK,
+          dq.list ? const_cast<int*>(dq.list) + size_t(p) * kListCap : nullptr, 0};
     const FFResult r = ff_sample(c, U.x, U.y);
-    if (r.pending) dense_push(dq, p, r.lo, r.hi, r.Flo, U.x, U.y, o, d, 0.f, t1, c.ex);
+    if (r.pending) dense_push(dq, p, r.lo, r.hi, r.Flo, U.x, U.y, o, d, 0.f, t1, c.ex, r.nlist);
     ps.prim[p] = r.prim;
     ps.tsp[p] = spawn_mode == 1 ? r.t_u : r.t_spawn;
     ps.tq[p] = tq;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(256) k_accumulate(int n, PathSoA ps, float* __
 
 struct RenderLayout {
   size_t total;
-  size_t state, queues, shadow, counts, dense;
+  size_t state, queues, shadow, counts, dense, lists;
 };
 
 RenderLayout render_layout(int64_t n) {
@@ -290,6 +291,7 @@ RenderLayout render_layout(int64_t n) {
   L.shadow = off;  off += 12 * col;
   L.counts = off;  off += 256;
   L.dense = off;   off += dense_queue_bytes(n);
+  L.lists = off;   off += slot_list_bytes(n);
   L.total = off;
   return L;
 }
@@ -358,7 +360,8 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
                F(RL.shadow, 10), F(RL.shadow, 11)};
   int* queue[2] = {I(RL.queues, 0), I(RL.queues, 1)};
   int* counts = reinterpret_cast<int*>(ws + RL.counts);  // [0], [1] queue lengths, [2] shadow
-  const DenseQueue dq = dense_queue_at(ws + RL.dense, n);
+  DenseQueue dq = dense_queue_at(ws + RL.dense, n);
+  dq.list = reinterpret_cast<const int*>(ws + RL.lists);
 
   LightsDev Ld;
   Ld.has_quad = lights->has_quad != 0;

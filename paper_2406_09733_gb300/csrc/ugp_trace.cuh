@@ -34,6 +34,6 @@ ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3
 ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
                               const float* t0, const float* t1, const float* u, const float* u2,
                               const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
-                              void* workspace, cudaStream_t stream);
+                              void* workspace, bool with_lists, cudaStream_t stream);
 
 }  // namespace ugp
