@@ -7,11 +7,9 @@ namespace ugp {
 
 constexpr int kTrBlock = 128;      // transmittance: threads per block
 constexpr int kTrStack = 64;       // transmittance: traversal stack depth
-constexpr int kFFBlock = 64;       // free flight: threads per block
-constexpr int kK = 8;              // free flight: interval buffer per ray
+constexpr int kFFBlock = 128;      // free flight: threads per block of the scan
 constexpr int kFFStack = 48;       // free flight: traversal stack depth
-constexpr int kB = 16;             // free flight: bins of the scan
-constexpr int kFFNewtonIters = 64; // free flight: root-solve iterations
+constexpr int kB = 32;             // free flight: bins of the scan
 
 struct TraceScene {
   const float4* nodes;
