@@ -232,10 +232,16 @@ class OrcLights(C.Structure):
                 ("e2", C.c_float * 3), ("Le", C.c_float * 3), ("bg", C.c_float * 3)]
 
 
+class OrcGuideCfg(C.Structure):
+    _fields_ = [("pos_lo", C.c_double * 3), ("pos_hi", C.c_double * 3), ("kappa_min", C.c_double),
+                ("kappa_max", C.c_double), ("round_bf16", C.c_int32)]
+
+
 class OrcParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("seed", C.c_uint64), ("cutoff_eps", C.c_double), ("nee", C.c_int32),
-                ("spawn_mode", C.c_int32)]
+                ("spawn_mode", C.c_int32), ("guide", f32p), ("guide_cfg", OrcGuideCfg),
+                ("guide_alpha", C.c_double)]
 
 
 def _d(a):
@@ -323,10 +329,11 @@ def phase_pdf_approx(mtype, albedo, alpha, S6, wo, wi):
 
 
 def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1, spawn_mode=0,
-           pixels=None, threads=None):
+           pixels=None, threads=None, guide=None, guide_alpha=0.5):
     """Per-pixel sums of sample values and squares, shape (H, W, 3) each, plus query counts.
 
     ``pixels`` = (p_begin, p_end) renders only that row-major pixel range (others stay zero).
+    ``guide`` = (params, GuideConfig) renders with the learned guide by one-sample MIS.
     """
     cam, li = scene.camera, scene.lights
     W, H = cam.width, cam.height
@@ -334,8 +341,13 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
                   cam.vfov_deg, W, H)
     l = OrcLights(int(li.has_quad), (C.c_float * 3)(*li.quad_corner), (C.c_float * 3)(*li.quad_e1),
                   (C.c_float * 3)(*li.quad_e2), (C.c_float * 3)(*li.quad_Le), (C.c_float * 3)(*li.bg))
+    gp = None
+    gcfg = OrcGuideCfg()
+    if guide is not None:
+        gp = _c(guide[0], np.float32)
+        gcfg = _guide_cfg(guide[1])
     p = OrcParams(int(spp), int(spp_begin), int(max_depth), int(seed), float(cutoff_eps), int(nee),
-                  int(spawn_mode))
+                  int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha))
     acc = np.zeros((H, W, 3))
     acc2 = np.zeros((H, W, 3))
     counts = (C.c_int64 * 2)(0, 0)
@@ -346,3 +358,108 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
     lib().orc_render(sr.ref, C.byref(c), C.byref(l), C.byref(p), int(pb), int(pe), _ptr(acc, f64p),
                      _ptr(acc2, f64p), counts)
     return acc, acc2, (int(counts[0]), int(counts[1]))
+
+
+# ------------------------------------------------------------------ learned guide
+def _register_guide(L):
+    d = f64p
+    L.orc_guide_nparams.restype = C.c_int64
+    L.orc_bf16_round.argtypes = [C.c_int64, d, d]
+    L.orc_guide_encode.argtypes = [C.POINTER(OrcGuideCfg), C.c_int64, f32p, f32p, d]
+    L.orc_guide_forward.argtypes = [C.POINTER(OrcGuideCfg), f32p, C.c_int64, f32p, f32p, d, d]
+    L.orc_mixture_pdf.argtypes = [C.c_int64, d, d, d]
+    L.orc_mixture_sample.argtypes = [C.c_int64, d, d, d, d]
+    L.orc_mixture_loss_grad.argtypes = [C.POINTER(OrcGuideCfg), d, d, C.c_double, d]
+    L.orc_mixture_loss_grad.restype = C.c_double
+    L.orc_guide_loss_grad.argtypes = [C.POINTER(OrcGuideCfg), f32p, C.c_int64, f32p, f32p, f32p, f32p, d]
+    L.orc_guide_loss_grad.restype = C.c_double
+    L.orc_adam_step.argtypes = [C.c_int64, d, d, d, d, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                C.c_double]
+
+
+_REGISTRY.append(_register_guide)
+
+
+def _guide_cfg(cfg, round_bf16=None):
+    """OrcGuideCfg from an object with pos_lo, pos_hi, kappa_min, kappa_max (and round_bf16)."""
+    rb = getattr(cfg, "round_bf16", 1) if round_bf16 is None else round_bf16
+    return OrcGuideCfg((C.c_double * 3)(*cfg.pos_lo), (C.c_double * 3)(*cfg.pos_hi), float(cfg.kappa_min),
+                       float(cfg.kappa_max), int(rb))
+
+
+def guide_nparams() -> int:
+    return int(lib().orc_guide_nparams())
+
+
+def bf16_round(x):
+    x = _d(x)
+    out = np.zeros_like(x)
+    lib().orc_bf16_round(x.size, _ptr(x, f64p), _ptr(out, f64p))
+    return out
+
+
+def guide_encode(cfg, x3, wo3, round_bf16=None):
+    x3, wo3 = _c(x3, np.float32).reshape(-1, 3), _c(wo3, np.float32).reshape(-1, 3)
+    n = x3.shape[0]
+    out = np.zeros((n, 64))
+    g = _guide_cfg(cfg, round_bf16)
+    lib().orc_guide_encode(C.byref(g), n, _ptr(x3, f32p), _ptr(wo3, f32p), _ptr(out, f64p))
+    return out
+
+
+def guide_forward(cfg, params, x3, wo3, round_bf16=None):
+    """(Y, mix): head outputs (n, 40) and mixture (n, 8, 5) = per lobe (mu xyz, kappa, pi)."""
+    params = _c(params, np.float32)
+    x3, wo3 = _c(x3, np.float32).reshape(-1, 3), _c(wo3, np.float32).reshape(-1, 3)
+    n = x3.shape[0]
+    Y = np.zeros((n, 40))
+    mix = np.zeros((n, 40))
+    g = _guide_cfg(cfg, round_bf16)
+    lib().orc_guide_forward(C.byref(g), _ptr(params, f32p), n, _ptr(x3, f32p), _ptr(wo3, f32p), _ptr(Y, f64p),
+                            _ptr(mix, f64p))
+    return Y, mix.reshape(n, 8, 5)
+
+
+def mixture_pdf(mix, wi3):
+    mix = _d(mix).reshape(-1, 40)
+    wi3 = _d(wi3).reshape(-1, 3)
+    out = np.zeros(mix.shape[0])
+    lib().orc_mixture_pdf(mix.shape[0], _ptr(mix, f64p), _ptr(wi3, f64p), _ptr(out, f64p))
+    return out
+
+
+def mixture_sample(mix, U3):
+    mix = _d(mix).reshape(-1, 40)
+    U3 = _d(U3).reshape(-1, 3)
+    n = mix.shape[0]
+    wi, pdf = np.zeros((n, 3)), np.zeros(n)
+    lib().orc_mixture_sample(n, _ptr(mix, f64p), _ptr(U3, f64p), _ptr(wi, f64p), _ptr(pdf, f64p))
+    return wi, pdf
+
+
+def mixture_loss_grad(cfg, Y, wi, w):
+    Y, wi = _d(Y), _d(wi)
+    dY = np.zeros(40)
+    g = _guide_cfg(cfg)
+    loss = lib().orc_mixture_loss_grad(C.byref(g), _ptr(Y, f64p), _ptr(wi, f64p), float(w), _ptr(dY, f64p))
+    return float(loss), dY
+
+
+def guide_loss_grad(cfg, params, x3, wo3, wi3, weight, round_bf16=None):
+    """(mean loss, gradient of the mean loss over the flat parameters)."""
+    params = _c(params, np.float32)
+    x3, wo3, wi3 = (_c(a, np.float32).reshape(-1, 3) for a in (x3, wo3, wi3))
+    weight = _c(weight, np.float32)
+    grad = np.zeros(guide_nparams())
+    g = _guide_cfg(cfg, round_bf16)
+    loss = lib().orc_guide_loss_grad(C.byref(g), _ptr(params, f32p), x3.shape[0], _ptr(x3, f32p), _ptr(wo3, f32p),
+                                     _ptr(wi3, f32p), _ptr(weight, f32p), _ptr(grad, f64p))
+    return float(loss), grad
+
+
+def adam_step(theta, m, v, g, t, lr=1e-3, b1=0.9, b2=0.99, eps=1e-8):
+    """One Adam step in place on FP64 copies; returns (theta, m, v)."""
+    theta, m, v, g = _d(theta).copy(), _d(m).copy(), _d(v).copy(), _d(g)
+    lib().orc_adam_step(theta.size, _ptr(theta, f64p), _ptr(m, f64p), _ptr(v, f64p), _ptr(g, f64p), int(t),
+                        float(lr), float(b1), float(b2), float(eps))
+    return theta, m, v

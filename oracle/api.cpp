@@ -243,11 +243,31 @@ typedef struct {
   float corner[3], e1[3], e2[3], Le[3], bg[3];
 } orc_lights;
 typedef struct {
+  double pos_lo[3], pos_hi[3];
+  double kappa_min, kappa_max;
+  int32_t round_bf16;
+} orc_guide_cfg;
+typedef struct {
   int32_t spp, spp_begin, max_depth;
   uint64_t seed;
   double cutoff_eps;
   int32_t nee, spawn_mode;
+  const float* guide;  // flat guide parameters (NULL: plain phase sampling)
+  orc_guide_cfg guide_cfg;
+  double guide_alpha;
 } orc_params;
+
+static GuideCfg guide_cfg_of(const orc_guide_cfg* g) {
+  GuideCfg c;
+  for (int a = 0; a < 3; ++a) {
+    c.pos_lo[a] = g->pos_lo[a];
+    c.pos_hi[a] = g->pos_hi[a];
+  }
+  c.kappa_min = g->kappa_min;
+  c.kappa_max = g->kappa_max;
+  c.round_bf16 = g->round_bf16;
+  return c;
+}
 
 // Adds the per-pixel sums of sample values and of their squares (3 channels) for pixels
 // [p_begin, p_end) into accum / accum_sq (full-image arrays).  counts[0] += extend queries,
@@ -257,12 +277,84 @@ void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, co
   Camera cam{load3(c->eye), load3(c->look), load3(c->up), c->vfov_deg, c->width, c->height};
   Lights L{l->has_quad != 0, load3(l->corner), load3(l->e1), load3(l->e2), load3(l->Le), load3(l->bg)};
   RenderParams P{p->spp, p->spp_begin, p->max_depth, p->seed, p->cutoff_eps, p->nee, p->spawn_mode};
+  P.guide = p->guide;
+  P.guide_cfg = guide_cfg_of(&p->guide_cfg);
+  P.guide_alpha = p->guide_alpha;
   int64_t ne = 0, ns = 0;
   render_pixels(scene_in(s), cam, L, P, p_begin, p_end, accum, accum_sq, &ne, &ns);
   if (counts) {
     counts[0] += ne;
     counts[1] += ns;
   }
+}
+
+// ------------------------------------------------------------------ learned guide
+int64_t orc_guide_nparams() { return kGNParams; }
+
+void orc_bf16_round(int64_t n, const double* x, double* out) {
+  for (int64_t i = 0; i < n; ++i) out[i] = bf16_round(x[i]);
+}
+
+void orc_guide_encode(const orc_guide_cfg* g, int64_t n, const float* x3, const float* wo3, double* out) {
+  const GuideCfg c = guide_cfg_of(g);
+  for (int64_t i = 0; i < n; ++i) guide_encode(c, load3(x3 + 3 * i), load3(wo3 + 3 * i), out + kGWidth * i);
+}
+
+// Head outputs (n x 40) and the mixture (n x 40: per lobe mu (3), kappa, pi); either may be NULL.
+void orc_guide_forward(const orc_guide_cfg* g, const float* params, int64_t n, const float* x3, const float* wo3,
+                       double* Y_out, double* mix_out) {
+  const GuideCfg c = guide_cfg_of(g);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double Y[kGOut];
+    guide_forward(c, params, load3(x3 + 3 * i), load3(wo3 + 3 * i), Y, nullptr);
+    if (Y_out) std::memcpy(Y_out + kGOut * i, Y, sizeof(Y));
+    if (mix_out) {
+      const Mixture m = guide_mixture(c, Y);
+      for (int j = 0; j < kGLobes; ++j) {
+        double* o = mix_out + kGOut * i + 5 * j;
+        o[0] = m.mu[j].x; o[1] = m.mu[j].y; o[2] = m.mu[j].z; o[3] = m.kappa[j]; o[4] = m.pi[j];
+      }
+    }
+  }
+}
+
+static Mixture mixture_of(const double* mx) {
+  Mixture m;
+  for (int j = 0; j < kGLobes; ++j) {
+    m.mu[j] = v3(mx[5 * j], mx[5 * j + 1], mx[5 * j + 2]);
+    m.kappa[j] = mx[5 * j + 3];
+    m.pi[j] = mx[5 * j + 4];
+  }
+  return m;
+}
+
+void orc_mixture_pdf(int64_t n, const double* mix, const double* wi3, double* pdf_out) {
+  for (int64_t i = 0; i < n; ++i) pdf_out[i] = mixture_pdf(mixture_of(mix + kGOut * i), d3v(wi3 + 3 * i));
+}
+
+// Directions from uniforms U3 = (lobe choice, u1, u2) per row, and their mixture pdf.
+void orc_mixture_sample(int64_t n, const double* mix, const double* U3, double* wi_out, double* pdf_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const Mixture m = mixture_of(mix + kGOut * i);
+    const V3 w = mixture_sample(m, U3 + 3 * i);
+    put3(wi_out + 3 * i, w);
+    if (pdf_out) pdf_out[i] = mixture_pdf(m, w);
+  }
+}
+
+double orc_mixture_loss_grad(const orc_guide_cfg* g, const double* Y, const double* wi, double w, double* dY) {
+  return mixture_loss_grad(guide_cfg_of(g), Y, d3v(wi), w, dY);
+}
+
+double orc_guide_loss_grad(const orc_guide_cfg* g, const float* params, int64_t n, const float* x3, const float* wo3,
+                           const float* wi3, const float* weight, double* grad) {
+  return guide_loss_grad(guide_cfg_of(g), params, n, x3, wo3, wi3, weight, grad);
+}
+
+void orc_adam_step(int64_t n, double* theta, double* m, double* v, const double* g, int64_t t, double lr, double b1,
+                   double b2, double eps) {
+  adam_step(n, theta, m, v, g, t, lr, b1, b2, eps);
 }
 
 }  // extern "C"

@@ -2,6 +2,7 @@
 //
 // TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline).
 #pragma once
+#include "oracle_guide.h"
 #include "oracle_internal.h"
 
 namespace orc {
@@ -60,6 +61,13 @@ struct RenderParams {
   double cutoff_eps;
   int nee;         // 1: light sampling + MIS, 0: lights found by phase sampling only
   int spawn_mode;  // 0: centre of the primitive's clipped interval, 1: x_{t_u}
+  // Learned guide (NULL: plain phase sampling). With a guide, each scattering vertex picks the
+  // guide with probability guide_alpha, else phase sampling, and weights the sample by the
+  // balance heuristic over both (one-sample MIS); the same mixture pdf enters the MIS with
+  // light sampling.
+  const float* guide = nullptr;
+  GuideCfg guide_cfg{};
+  double guide_alpha = 0.5;
 };
 
 // Renders pixels [p_begin, p_end) of the image (row-major), adding per-channel sums of the

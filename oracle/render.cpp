@@ -16,8 +16,17 @@
 //  * MIS (Table 1) is the balance heuristic between light sampling and phase sampling,
 //    with the approximate phase pdf of App. B.
 //  * Random numbers: Philox4x32-10 with key (seed lo, seed hi) and counter
-//    (pixel, sample, 16 * bounce + slot, 0); slot 0 free flight, 1 phase sampling, 3 light
-//    point, 4-5 stochastic phase evaluation; the camera jitter uses bounce 15, slot 0.
+//    (pixel, sample, 16 * bounce + slot, 0); slot 0 free flight, 1 phase sampling, 2 guide
+//    (lobe choice, technique choice, two for the vMF lobe), 3 light point, 4-5 stochastic
+//    phase evaluation of the light sample, 6-7 stochastic phase evaluation of a guide sample;
+//    the camera jitter uses bounce 15, slot 0.
+//  * With a guide, one-sample MIS between the guide (probability alpha) and phase sampling
+//    (1 - alpha), balance heuristic with the approximate phase pdf p~ of App. B:
+//      guide sample:  weight = f(wi) / (alpha q(wi) + (1 - alpha) p~(wi))
+//      phase sample:  weight = (f / p)(wi) * p~(wi) / (alpha q(wi) + (1 - alpha) p~(wi))
+//    The two weights of the balance heuristic sum to one at every direction, so the estimate
+//    stays unbiased for any q and any approximation p~ (Sec. 6). The mixture pdf
+//    alpha q + (1 - alpha) p~ replaces p~ in the MIS with light sampling.
 #include <algorithm>
 #include <cmath>
 
@@ -133,6 +142,19 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
         if (b == P.max_depth) break;
         const V3 x = o + (P.spawn_mode == 1 ? ff.t_u : ff.t_spawn) * d;
         const V3 wo = -d;
+        const bool guided = P.guide != nullptr;
+        const double al = P.guide_alpha;
+        Mixture mix{};
+        if (guided) {
+          double Y[kGOut];
+          guide_forward(P.guide_cfg, P.guide, x, wo, Y, nullptr);
+          mix = guide_mixture(P.guide_cfg, Y);
+        }
+        // Density of the scattering technique (the MIS partner of light sampling).
+        auto p_scatter = [&](V3 w) {
+          const double pt = phase_pdf_approx(m, w, wo);
+          return guided ? al * mixture_pdf(mix, w) + (1 - al) * pt : pt;
+        };
         if (P.nee && L.has_quad && area > 0) {
           rng4(P.seed, uint32_t(p), sample, uint32_t(b), 3, U);
           const V3 y = L.corner + U[0] * L.e1 + U[1] * L.e2;
@@ -152,18 +174,46 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
               const double tr = transmittance(prims, x, wl, 0.0, r, k, ff.prim, nullptr);
               ++shd;
               if (tr > 0) {
-                const double wmis = mis2(pl, phase_pdf_approx(m, wl, wo));
+                const double wmis = mis2(pl, p_scatter(wl));
                 Lr = Lr + (tr * wmis / pl) * (beta * (f * L.Le));
               }
             }
           }
         }
-        rng4(P.seed, uint32_t(p), sample, uint32_t(b), 1, U);
         V3 wi, wgt;
-        if (!phase_sample(m, wo, U, &wi, &wgt)) break;
+        if (!guided) {
+          rng4(P.seed, uint32_t(p), sample, uint32_t(b), 1, U);
+          if (!phase_sample(m, wo, U, &wi, &wgt)) break;
+          pdf_prev = phase_pdf_approx(m, wi, wo);
+        } else {
+          double G[4];
+          rng4(P.seed, uint32_t(p), sample, uint32_t(b), 2, G);
+          if (G[1] < al) {
+            const double Gs[3] = {G[0], G[2], G[3]};
+            wi = mixture_sample(mix, Gs);
+            double Ug[6], U7[4];
+            rng4(P.seed, uint32_t(p), sample, uint32_t(b), 6, Ug);
+            rng4(P.seed, uint32_t(p), sample, uint32_t(b), 7, U7);
+            Ug[4] = U7[0];
+            Ug[5] = U7[1];
+            const V3 f = phase_eval(m, wi, wo, Ug);
+            const double pm = p_scatter(wi);
+            if (!(pm > 0)) break;
+            wgt = (1.0 / pm) * f;
+            pdf_prev = pm;
+          } else {
+            rng4(P.seed, uint32_t(p), sample, uint32_t(b), 1, U);
+            V3 w0;
+            if (!phase_sample(m, wo, U, &wi, &w0)) break;
+            const double pt = phase_pdf_approx(m, wi, wo);
+            const double pm = al * mixture_pdf(mix, wi) + (1 - al) * pt;
+            if (!(pm > 0)) break;
+            wgt = (pt / pm) * w0;
+            pdf_prev = pm;
+          }
+        }
         beta = beta * wgt;
         if (beta.x <= 0 && beta.y <= 0 && beta.z <= 0) break;
-        pdf_prev = phase_pdf_approx(m, wi, wo);
         o = x;
         d = wi;
         excl = ff.prim;

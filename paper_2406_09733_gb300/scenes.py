@@ -357,3 +357,79 @@ def uniforms24(rng_or_seed, shape) -> np.ndarray:
     rng = _rng(rng_or_seed) if isinstance(rng_or_seed, (int, np.integer)) else rng_or_seed
     k = rng.integers(0, 1 << 24, size=shape, dtype=np.int64)
     return _f32(k.astype(np.float64) * (2.0 ** -24))
+
+
+# ------------------------------------------------------------------ learned guide inputs
+GUIDE_LOBES = 8
+GUIDE_WIDTH = 64
+GUIDE_OUT = 5 * GUIDE_LOBES
+GUIDE_LAYERS = 4
+# Flat parameter vector: for l = 0..3, W_l (64 x 64, [out][in]) then b_l (64); then the head
+# W_4 (40 x 64) and b_4 (40).
+GUIDE_SHAPES = [(GUIDE_WIDTH, GUIDE_WIDTH)] * GUIDE_LAYERS + [(GUIDE_OUT, GUIDE_WIDTH)]
+GUIDE_NPARAMS = sum(o * i + o for o, i in GUIDE_SHAPES)
+
+
+@dataclass
+class GuideConfig:
+    """Position box of the guide's input normalisation and the range of the lobe sharpness."""
+    pos_lo: tuple = (0.0, 0.0, 0.0)
+    pos_hi: tuple = (1.0, 1.0, 1.0)
+    kappa_min: float = 0.1
+    kappa_max: float = 1.0e4
+
+
+def guide_param_slices():
+    """[(W slice, b slice)] of the flat parameter vector, per layer."""
+    out, off = [], 0
+    for o, i in GUIDE_SHAPES:
+        w = slice(off, off + o * i)
+        off += o * i
+        b = slice(off, off + o)
+        off += o
+        out.append((w, b))
+    return out
+
+
+def guide_init_params(seed: int = 0, bias_scale: float = 0.0) -> np.ndarray:
+    """Seeded initial weights: He-uniform W (bound sqrt(6 / fan_in)), biases U[-s, s]."""
+    rng = _rng(seed)
+    p = np.zeros(GUIDE_NPARAMS, np.float32)
+    for (o, i), (ws, bs) in zip(GUIDE_SHAPES, guide_param_slices()):
+        lim = np.sqrt(6.0 / i)
+        p[ws] = rng.uniform(-lim, lim, o * i).astype(np.float32)
+        if bias_scale > 0:
+            p[bs] = rng.uniform(-bias_scale, bias_scale, o).astype(np.float32)
+    return p
+
+
+def unit_vectors(rng_or_seed, n: int) -> np.ndarray:
+    rng = rng_or_seed if isinstance(rng_or_seed, np.random.Generator) else _rng(rng_or_seed)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(np.float32)
+
+
+@dataclass
+class GuideBatch:
+    """Logged scattering vertices: position, outgoing and incident directions, loss weight."""
+    x: np.ndarray
+    wo: np.ndarray
+    wi: np.ndarray
+    weight: np.ndarray
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+
+def guide_batch(n: int, seed: int = 0, cfg: GuideConfig | None = None, zero_frac: float = 0.1) -> GuideBatch:
+    """Random vertices in (and slightly outside) the box, weights log-uniform over 4 decades with a
+    fraction of zero weights (vertices whose paths found no light)."""
+    cfg = cfg or GuideConfig()
+    rng = _rng(seed)
+    lo, hi = np.asarray(cfg.pos_lo), np.asarray(cfg.pos_hi)
+    x = lo + (hi - lo) * rng.uniform(-0.05, 1.05, size=(n, 3))
+    w = 10.0 ** rng.uniform(-2, 2, n)
+    w[rng.uniform(size=n) < zero_frac] = 0.0
+    return GuideBatch(_f32(x), unit_vectors(rng, n), unit_vectors(rng, n), _f32(w))
