@@ -242,22 +242,101 @@ typedef struct ugp_lights {
   float bg[3];
 } ugp_lights;
 
+/* ------------------------------------------------------------------ learned guide
+ * A learned proposal for scattering directions. Sec. 6 allows any sampling technique that
+ * is combined by MIS with the approximate phase pdf p~ of App. B; this one is a small MLP
+ * that maps a scattering vertex (position x, outgoing direction wo) to a mixture of
+ * UGP_GUIDE_LOBES von Mises-Fisher lobes q(wi). The paper fixes none of its details; the
+ * network is:
+ *   input   64 features: x normalised to [0,1]^3 over [pos_lo, pos_hi] (clamped), with
+ *           sin/cos(2^l pi x), l = 0..5 (36); the polar angles (theta, phi) of wo in radians,
+ *           with sin/cos(2^l angle), l = 0..3 (16); the raw (x, y, z, theta / pi,
+ *           phi / (2 pi) + 1/2) (5); zeros (7)
+ *   layers  four 64 x 64 ReLU layers and a 64 -> 40 head with biases, on the tensor cores:
+ *           weights and layer inputs rounded to BF16 (nearest even), FP32 sums and biases
+ *   head    lobe j = outputs 5j..5j+4 = (m (3), s, a): mu_j = m / |m|,
+ *           kappa_j = min(kappa_max, kappa_min + softplus(s)), pi = softmax(a)
+ *   q(wi) = sum_j pi_j kappa_j / (2 pi (1 - e^{-2 kappa_j})) e^{kappa_j (mu_j . wi - 1)}
+ * Training minimises the mean over samples of -(L / p) ln q(wi), with L the incident-
+ * radiance estimate along wi and p the pdf wi was drawn with, by Adam on FP32 master weights.
+ * Parameters (FP32, UGP_GUIDE_NPARAMS): for l = 0..3, W_l (64 x 64, row-major [out][in]) then
+ * b_l (64); then the head W_4 (40 x 64) and b_4 (40).
+ * Mixture arrays ("mix") hold 40 floats per row: per lobe mu_x, mu_y, mu_z, kappa, pi. */
+#define UGP_GUIDE_LOBES 8
+#define UGP_GUIDE_WIDTH 64
+#define UGP_GUIDE_OUT 40
+#define UGP_GUIDE_NPARAMS 19240
+
+typedef struct ugp_guide {
+  float* params;   /* device, UGP_GUIDE_NPARAMS FP32 master weights */
+  float* adam_m;   /* device, UGP_GUIDE_NPARAMS Adam first moments (zero before the first step) */
+  float* adam_v;   /* device, UGP_GUIDE_NPARAMS Adam second moments (zero before the first step) */
+  int64_t step;    /* Adam steps taken; ugp_guide_adam_step increments it */
+  float lr, beta1, beta2, eps;   /* Adam hyper-parameters (e.g. 1e-3, 0.9, 0.99, 1e-8) */
+  float pos_lo[3], pos_hi[3];    /* input normalisation box, pos_hi > pos_lo */
+  float kappa_min, kappa_max;    /* lobe sharpness range, 0 < kappa_min <= kappa_max */
+} ugp_guide;
+
+/* Bytes of the scratch every guide call takes (packed BF16 weights, per-block gradient
+ * partials, an error word). The first 256 bytes must be zero before first use
+ * (ugp_guide_reset_workspace); the guide calls never clear them. */
+size_t ugp_guide_workspace_size(void);
+ugp_status ugp_guide_reset_workspace(void* workspace, void* stream);
+/* UGP_OK, or UGP_ERR_TIMEOUT if a bounded tensor-core wait of an earlier guide call on this
+ * workspace gave up (its outputs are then invalid). Synchronises `stream`. */
+ugp_status ugp_guide_check(const void* workspace, void* stream);
+
+/* Forward pass for n vertices (x3, wo3: float3 arrays). Writes, where not NULL, the head
+ * outputs head_out (n x 40) and the mixture mix_out (n x 40). Asynchronous. */
+ugp_status ugp_guide_forward(const ugp_guide* g, int64_t n, const float* x3, const float* wo3, float* head_out,
+                             float* mix_out, void* workspace, size_t workspace_bytes, void* stream);
+/* Mixture density of each row of mix at the unit direction wi3[row]. */
+ugp_status ugp_guide_mixture_pdf(int64_t n, const float* mix, const float* wi3, float* pdf_out, void* stream);
+/* One direction per row from uniforms u3[row] = (lobe choice, u1, u2): the lobe is the first
+ * whose cumulative pi exceeds the lobe choice; 1 - mu.wi = -ln(v + (1 - v) e^{-2 kappa}) / kappa
+ * with v = 1 - u1; azimuth 2 pi u2 about mu. pdf_out (may be NULL) receives q(wi). */
+ugp_status ugp_guide_mixture_sample(int64_t n, const float* mix, const float* u3, float* wi_out, float* pdf_out,
+                                    void* stream);
+/* Gradient of the mean loss over n samples (x3, wo3, wi3: float3 arrays; weight[n] = L / p)
+ * into grad_out (device, UGP_GUIDE_NPARAMS floats) and the mean loss into loss_out (device
+ * float, may be NULL). The sum over samples is in a fixed order (deterministic). Asynchronous. */
+ugp_status ugp_guide_grad(const ugp_guide* g, int64_t n, const float* x3, const float* wo3, const float* wi3,
+                          const float* weight, float* grad_out, float* loss_out, void* workspace,
+                          size_t workspace_bytes, void* stream);
+/* One Adam step with the gradient grad (device): params, adam_m, adam_v in place, bias
+ * corrections 1 - beta^t with t = g->step + 1; then g->step = t (host field). */
+ugp_status ugp_guide_adam_step(ugp_guide* g, const float* grad, void* stream);
+
 /* Render parameters (host struct).
  *   spp, spp_begin  samples [spp_begin, spp_begin + spp) of every pixel (resumable)
  *   max_depth       at most max_depth scattering vertices per path (>= 0)
  *   nee             1: light sampling with balance-heuristic MIS (Table 1), 0: none
  *   seed            Philox key (low, high 32 bits)
  *   spawn_mode      0: scattered rays start at the centre of the chosen primitive's
- *                   clipped interval (Sec. 6), 1: at x_{t_u} */
+ *                   clipped interval (Sec. 6), 1: at x_{t_u}
+ *   guide           NULL: phase sampling. Otherwise each scattering vertex draws its
+ *                   direction from the guide with probability guide_alpha in (0, 1), else by
+ *                   phase sampling, and weights it by the balance heuristic over both
+ *                   techniques with p~ (one-sample MIS; unbiased for any guide). The
+ *                   mixture pdf alpha q + (1 - alpha) p~ is the MIS partner of light sampling.
+ *   guide_log       1: record every scattering vertex of this call for training
+ *                   (ugp_guide_train_from_render); requires spp == 1 and a guide */
 typedef struct ugp_render_params {
   int32_t spp, spp_begin, max_depth, nee;
   uint64_t seed;
-  int32_t spawn_mode, reserved;
+  int32_t spawn_mode, guide_log;
+  const ugp_guide* guide;
+  float guide_alpha;
+  int32_t reserved;
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
  * per-path primitive-slot lists, 704 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
+/* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
+ * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per
+ * pixel and vertex) and the guide's packed weights. */
+size_t ugp_render_guided_workspace_size(int32_t width, int32_t height, int32_t max_depth);
 
 /* Path-traces the image with the volumetric path tracer of Table 1 (right column)
  * as a wavefront: per bounce, an extend pass (free-flight sampling,
@@ -265,7 +344,9 @@ size_t ugp_render_workspace_size(int32_t width, int32_t height);
  * sampling) and a shadow pass (ugp_trace_transmittance), with live paths
  * compacted between bounces.  Random numbers are Philox4x32-10 with counter
  * (pixel, sample, 16 * bounce + slot, 0); slots: 0 free flight, 1 phase
- * sampling, 3 light point, 4-5 stochastic phase evaluation.
+ * sampling, 2 guide (lobe choice, technique choice, two for the lobe), 3 light point,
+ * 4-5 stochastic phase evaluation of the light sample, 6-7 stochastic phase evaluation
+ * of a guide sample.
  *   accum_rgb, accum_sq_rgb  device float arrays (height x width x 3) to which the
  *                per-pixel sums of sample values and of their squares are ADDED
  *   ray_counts   device uint64[3] or NULL: [0] += free-flight queries,
@@ -275,6 +356,19 @@ ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const 
                       const ugp_lights* lights, const ugp_render_params* params, float* accum_rgb,
                       float* accum_sq_rgb, void* workspace, size_t workspace_bytes,
                       unsigned long long* ray_counts, void* stream);
+
+/* Trains the guide on the vertices logged by the last ugp_render call with guide_log = 1 on
+ * `render_ws` (same width, height and max_depth). For every logged vertex the incident
+ * radiance L along its sampled direction is the radiance the path gathered after the vertex
+ * divided by the path throughput after it (per channel, luminance-weighted); vertices with
+ * L > 0 are the training samples, with weight L / p. If there are more than max_samples, a
+ * deterministic hash keeps about max_samples of them. They are visited in minibatches of
+ * `minibatch` rows, one ugp_guide_grad + ugp_guide_adam_step each. Writes the number of
+ * samples used and the mean loss of the last minibatch (host, may be NULL). Synchronises. */
+ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* render_ws, size_t render_ws_bytes, int32_t width,
+                                       int32_t height, int32_t max_depth, int64_t max_samples, int32_t minibatch,
+                                       void* guide_ws, size_t guide_ws_bytes, int64_t* n_samples_out,
+                                       float* mean_loss_out, void* stream);
 
 /* Optional traversal statistics: when `counters` is a device pointer to 12
  * zero-initialised uint64, later tracing calls on any stream add (atomically)
@@ -294,12 +388,13 @@ ugp_status ugp_set_trace_counters(unsigned long long* counters);
  *   0 BVH build (all its kernels, the radix sort included), 1 camera rays,
  *   2 extend (free flight, per thread), 3 shade, 4 shadow (transmittance),
  *   5 accumulate, 6 standalone queries (ugp_trace_transmittance,
- *   ugp_sample_free_flight), 7 free flight of dense rays (warp per ray).
+ *   ugp_sample_free_flight), 7 free flight of dense rays (warp per ray), 8 learned guide
+ *   (packing, forward, gradient, Adam, training-set selection).
  * ugp_profile_end waits for the recorded events, writes the summed milliseconds and
  * launch counts per stage (arrays of UGP_PROFILE_STAGES, host) and stops recording.
  * At most max_records event pairs are kept; later launches are counted but not timed
  * (ugp_profile_end returns UGP_ERR_OVERFLOW then).  Not thread safe. */
-#define UGP_PROFILE_STAGES 8
+#define UGP_PROFILE_STAGES 9
 ugp_status ugp_profile_begin(int32_t max_records);
 ugp_status ugp_profile_end(double* ms_out, int64_t* launches_out);
 

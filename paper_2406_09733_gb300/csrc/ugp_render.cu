@@ -15,12 +15,19 @@
 //    radiance if the ray reaches its front face.
 //  * Scattered and shadow rays start at the centre of the chosen primitive's clipped interval
 //    and skip that primitive (Sec. 6).
+//  * With a learned guide, a vertex draws its direction from the guide with probability alpha,
+//    else by phase sampling, and weights it by the balance heuristic over both techniques with
+//    the approximate phase pdf p~ of App. B (one-sample MIS, unbiased for any guide, Sec. 6);
+//    alpha q + (1 - alpha) p~ is then the MIS partner of light sampling. The guide's mixtures
+//    of a bounce come from one tensor-core pass over the shade queue before k_shade.
 #include <cooperative_groups.h>
 
+#include <cub/cub.cuh>
 #include <math.h>
 
 #include "ugp_dense.cuh"
 #include "ugp_freeflight.cuh"
+#include "ugp_guide_kernels.cuh"
 #include "ugp_phase.cuh"
 #include "ugp_philox.cuh"
 #include "ugp_transmit.cuh"
@@ -67,6 +74,26 @@ struct MatDev {
   const float* albedo3;
   const float* roughness;
   const float* emission3;
+};
+
+// Training log of a guided frame: one entry per (bounce b, path p), e = b * n + p, as columns
+// of E = max_depth * n floats:
+//   0-2 vertex position, 3-5 wo, 6-8 sampled wi, 9 pdf of wi (alpha q + (1 - alpha) p~; 0:
+//   no vertex), 10-12 throughput after the vertex, 13-15 path radiance before anything the
+//   path gathers after the vertex (written at bounce b + 1), 16 training weight L / pdf,
+//   17 selection key (int), 18 selected entry indices (int).
+constexpr int kLogCols = 19;
+struct GuideLog {
+  float* c[kLogCols];
+  int64_t E;
+};
+
+struct GuidedShade {
+  const float* mix;  // n x 40 mixtures, by path
+  float alpha;
+  int log;           // 1: write the training log
+  GuideLog L;
+  int n;             // paths per frame
 };
 
 __device__ __forceinline__ float4 rng(uint2 key, int pixel, int sample, int bounce, int slot) {
@@ -166,16 +193,22 @@ __device__ __forceinline__ Material load_material(const MatDev& m, int k) {
   return M;
 }
 
+template <bool kGuided>
 __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 key, int sample, int bounce, int max_depth,
                                                int nee, PathSoA ps, const int* __restrict__ q, const int* cnt,
                                                int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow,
-                                               int* dense_cnt) {
+                                               int* dense_cnt, GuidedShade gs) {
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0) *dense_cnt = 0;  // the dense pass of this bounce has run
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const int p = q[i];
     float3 beta = f3(ps.br[p], ps.bg[p], ps.bb[p]);
     float3 Lr = f3(ps.lr[p], ps.lg[p], ps.lb[p]);
+    if (kGuided && gs.log && bounce > 0) {
+      // radiance before anything gathered after the previous vertex (its light sample included)
+      const int64_t e = int64_t(bounce - 1) * gs.n + p;
+      gs.L.c[13][e] = Lr.x; gs.L.c[14][e] = Lr.y; gs.L.c[15][e] = Lr.z;
+    }
     const float3 o = f3(ps.ox[p], ps.oy[p], ps.oz[p]), d = f3(ps.dx[p], ps.dy[p], ps.dz[p]);
     const int k = ps.prim[p];
     bool alive = false;
@@ -199,6 +232,15 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
       const Material M = load_material(mats, k);
       const float t = ps.tsp[p];
       const float3 x = o + t * d, wo = -d;
+      float mix[kGuided ? kGOut : 1];
+      if (kGuided) {
+        const float4* m4 = reinterpret_cast<const float4*>(gs.mix + size_t(p) * kGOut);
+#pragma unroll
+        for (int j = 0; j < kGOut / 4; ++j) {
+          const float4 v = m4[j];
+          mix[4 * j] = v.x; mix[4 * j + 1] = v.y; mix[4 * j + 2] = v.z; mix[4 * j + 3] = v.w;
+        }
+      }
       if (nee && L.has_quad && L.area > 0.f) {
         const float4 Uy = rng(key, p, sample, bounce, 3);
         const float3 y = L.corner + Uy.x * L.e1 + Uy.y * L.e2;
@@ -212,7 +254,9 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
           const float Ue[6] = {Ua.x, Ua.y, Ua.z, Ua.w, Ub.x, Ub.y};
           const float3 f = phase_eval(M, wl, wo, Ue);
           if (f.x > 0.f || f.y > 0.f || f.z > 0.f) {
-            const float wm = mis_w(pl, phase_pdf_approx(M, wl, wo));
+            float ps_l = phase_pdf_approx(M, wl, wo);
+            if (kGuided) ps_l = gs.alpha * mixture_pdf(mix, wl) + (1.f - gs.alpha) * ps_l;
+            const float wm = mis_w(pl, ps_l);
             const float3 contrib = (wm / pl) * (beta * (f * L.Le));
             const int j = queue_append(cnt_shadow);
             sh.path[j] = p;
@@ -224,13 +268,50 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
           }
         }
       }
-      const float4 Us = rng(key, p, sample, bounce, 1);
-      const float U4[4] = {Us.x, Us.y, Us.z, Us.w};
       float3 wi, wgt;
-      if (phase_sample(M, wo, U4, wi, wgt)) {
+      float pdf_s = 0.f;
+      bool sampled = false;
+      if (!kGuided) {
+        const float4 Us = rng(key, p, sample, bounce, 1);
+        const float U4[4] = {Us.x, Us.y, Us.z, Us.w};
+        sampled = phase_sample(M, wo, U4, wi, wgt);
+        if (sampled) pdf_s = phase_pdf_approx(M, wi, wo);
+      } else {
+        const float al = gs.alpha;
+        const float4 G = rng(key, p, sample, bounce, 2);
+        if (G.y < al) {
+          wi = mixture_sample(mix, G.x, G.z, G.w);
+          const float4 Ga = rng(key, p, sample, bounce, 6), Gb = rng(key, p, sample, bounce, 7);
+          const float Ug[6] = {Ga.x, Ga.y, Ga.z, Ga.w, Gb.x, Gb.y};
+          const float3 f = phase_eval(M, wi, wo, Ug);
+          pdf_s = al * mixture_pdf(mix, wi) + (1.f - al) * phase_pdf_approx(M, wi, wo);
+          sampled = pdf_s > 0.f;
+          if (sampled) wgt = (1.f / pdf_s) * f;
+        } else {
+          const float4 Us = rng(key, p, sample, bounce, 1);
+          const float U4[4] = {Us.x, Us.y, Us.z, Us.w};
+          float3 w0;
+          if (phase_sample(M, wo, U4, wi, w0)) {
+            const float pt = phase_pdf_approx(M, wi, wo);
+            pdf_s = al * mixture_pdf(mix, wi) + (1.f - al) * pt;
+            sampled = pdf_s > 0.f;
+            if (sampled) wgt = (pt / pdf_s) * w0;
+          }
+        }
+      }
+      if (sampled) {
         beta = beta * wgt;
         if (beta.x > 0.f || beta.y > 0.f || beta.z > 0.f) {
-          ps.pdf_prev[p] = phase_pdf_approx(M, wi, wo);
+          ps.pdf_prev[p] = pdf_s;
+          if (kGuided && gs.log) {
+            const int64_t e = int64_t(bounce) * gs.n + p;
+            float* const* c = gs.L.c;
+            c[0][e] = x.x; c[1][e] = x.y; c[2][e] = x.z;
+            c[3][e] = wo.x; c[4][e] = wo.y; c[5][e] = wo.z;
+            c[6][e] = wi.x; c[7][e] = wi.y; c[8][e] = wi.z;
+            c[9][e] = pdf_s;
+            c[10][e] = beta.x; c[11][e] = beta.y; c[12][e] = beta.z;
+          }
           ps.ox[p] = x.x; ps.oy[p] = x.y; ps.oz[p] = x.z;
           ps.dx[p] = wi.x; ps.dy[p] = wi.y; ps.dz[p] = wi.z;
           ps.br[p] = beta.x; ps.bg[p] = beta.y; ps.bb[p] = beta.z;
@@ -277,12 +358,111 @@ __global__ void __launch_bounds__(256) k_accumulate(int n, PathSoA ps, float* __
   }
 }
 
+// Rows of the guide's forward pass in a bounce: the entries of the shade queue; a row is a
+// vertex when its path scatters here (a non-emissive primitive before the depth limit).
+struct ShadeQueueSrc {
+  PathSoA ps;
+  const int* q;
+  const uint8_t* type;
+  int bounce, max_depth;
+  __device__ bool vertex(int64_t r, float3& x, float3& wo) const {
+    const int p = q[r];
+    const int k = ps.prim[p];
+    if (k < 0 || bounce >= max_depth || type[k] == kMatEmissive) return false;
+    const float3 o = f3(ps.ox[p], ps.oy[p], ps.oz[p]), d = f3(ps.dx[p], ps.dy[p], ps.dz[p]);
+    x = o + ps.tsp[p] * d;
+    wo = -d;
+    return true;
+  }
+  __device__ int path(int64_t r) const { return q[r]; }
+};
+
+struct MixByPathDst {
+  const int* q;
+  float* mix;
+  GuideCfgDev cfg;
+  __device__ void put(int64_t r, const float (&Y)[kGOut]) const {
+    float m[kGOut];
+    mixture_from_head(cfg, Y, m);
+    float4* out = reinterpret_cast<float4*>(mix + size_t(q[r]) * kGOut);
+#pragma unroll
+    for (int j = 0; j < kGOut / 4; ++j) out[j] = make_float4(m[4 * j], m[4 * j + 1], m[4 * j + 2], m[4 * j + 3]);
+  }
+};
+
+// Training rows: selected log entries.
+struct LogSrc {
+  GuideLog L;
+  const int* idx;
+  int64_t offset;
+  __device__ bool sample(int64_t r, float3& x, float3& wo, float3& wi, float& w) const {
+    const int64_t e = idx[offset + r];
+    x = f3(L.c[0][e], L.c[1][e], L.c[2][e]);
+    wo = f3(L.c[3][e], L.c[4][e], L.c[5][e]);
+    wi = f3(L.c[6][e], L.c[7][e], L.c[8][e]);
+    w = L.c[16][e];
+    return true;
+  }
+};
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  // integer finaliser of MurmurHash3 (public domain)
+  x ^= x >> 16;
+  x *= 0x85ebca6bu;
+  x ^= x >> 13;
+  x *= 0xc2b2ae35u;
+  x ^= x >> 16;
+  return x;
+}
+
+// Incident-radiance estimate and training weight of every logged vertex; counts the usable ones.
+__global__ void __launch_bounds__(256) k_log_finalize(GuideLog L, int n, PathSoA ps, int* count) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < L.E; e += int64_t(gridDim.x) * blockDim.x) {
+    const float pdf = L.c[9][e];
+    float w = 0.f;
+    if (pdf > 0.f) {
+      const int p = int(e % n);
+      const float Lf[3] = {ps.lr[p], ps.lg[p], ps.lb[p]};
+      const float lum[3] = {0.2126f, 0.7152f, 0.0722f};
+      float Li = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float b = L.c[10 + c][e];
+        if (b > 0.f) Li += lum[c] * fmaxf(0.f, (Lf[c] - L.c[13 + c][e]) / b);
+      }
+      w = Li / pdf;
+      if (!(w > 0.f) || !isfinite(w)) w = 0.f;
+    }
+    L.c[16][e] = w;
+    if (w > 0.f) atomicAdd(count, 1);
+  }
+}
+
+// Keeps about max_samples of the usable entries (hash thinning): key = e if kept, else -1.
+__global__ void __launch_bounds__(256) k_log_thin(GuideLog L, const int* count, int64_t max_samples) {
+  const int c = *count;
+  const double keep = c > max_samples ? double(max_samples) / double(c) : 1.0;
+  const uint32_t thr = keep >= 1.0 ? 0xffffffffu : uint32_t(keep * 4294967295.0);
+  int* key = reinterpret_cast<int*>(L.c[17]);
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < L.E; e += int64_t(gridDim.x) * blockDim.x) {
+    const bool use = L.c[16][e] > 0.f && (keep >= 1.0 || hash32(uint32_t(e) * 0x9e3779b9u + 0x2406u) <= thr);
+    key[e] = use ? int(e) : -1;
+  }
+}
+
+struct NonNegative {
+  __device__ __forceinline__ bool operator()(const int& v) const { return v >= 0; }
+};
+
 struct RenderLayout {
   size_t total;
   size_t state, queues, shadow, counts, dense, lists;
+  // guided renders only
+  size_t mix, log, img, cub, cub_bytes;
+  int64_t E;
 };
 
-RenderLayout render_layout(int64_t n) {
+RenderLayout render_layout(int64_t n, int max_depth = -1) {
   RenderLayout L;
   size_t off = 0;
   const size_t col = align256(size_t(n) * 4);
@@ -292,8 +472,28 @@ RenderLayout render_layout(int64_t n) {
   L.counts = off;  off += 256;
   L.dense = off;   off += dense_queue_bytes(n);
   L.lists = off;   off += slot_list_bytes(n);
+  L.mix = L.log = L.img = L.cub = L.cub_bytes = 0;
+  L.E = 0;
+  if (max_depth >= 0) {
+    L.E = int64_t(max_depth > 0 ? max_depth : 1) * n;
+    L.mix = off;   off += align256(size_t(n) * kGOut * 4);
+    L.log = off;   off += size_t(kLogCols) * align256(size_t(L.E) * 4);
+    L.img = off;   off += 256 + align256(kImgBytes);
+    size_t cb = 0;
+    cub::DeviceSelect::If(nullptr, cb, (const int*)nullptr, (int*)nullptr, (int*)nullptr, int(L.E), NonNegative());
+    L.cub_bytes = cb;
+    L.cub = off;   off += align256(cb + 256);
+  }
   L.total = off;
   return L;
+}
+
+GuideLog log_at(char* ws, const RenderLayout& RL) {
+  GuideLog g;
+  const size_t col = align256(size_t(RL.E) * 4);
+  for (int c = 0; c < kLogCols; ++c) g.c[c] = reinterpret_cast<float*>(ws + RL.log + c * col);
+  g.E = RL.E;
+  return g;
 }
 
 int grid_for(const void* kernel, int block, int64_t n) {
@@ -322,6 +522,13 @@ extern "C" size_t ugp_render_workspace_size(int32_t width, int32_t height) {
   return render_layout(int64_t(width) * height).total;
 }
 
+extern "C" size_t ugp_render_guided_workspace_size(int32_t width, int32_t height, int32_t max_depth) {
+  if (width <= 0 || height <= 0 || max_depth < 0 || max_depth > 14) return 0;
+  const int64_t n = int64_t(width) * height;
+  if (n * (max_depth > 0 ? max_depth : 1) > (int64_t(1) << 31) - 1) return 0;
+  return render_layout(n, max_depth).total;
+}
+
 extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const ugp_camera* camera,
                                  const ugp_lights* lights, const ugp_render_params* params, float* accum_rgb,
                                  float* accum_sq_rgb, void* workspace, size_t workspace_bytes,
@@ -342,8 +549,22 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
     return fail(UGP_ERR_INVALID_ARG, "ugp_render: vfov_deg must be in (0, 180)");
   if (reinterpret_cast<uintptr_t>(workspace) & 255)
     return fail(UGP_ERR_INVALID_ARG, "ugp_render: workspace must be 256-byte aligned");
+  const ugp_guide* guide = params->guide;
+  if (guide) {
+    if (!(params->guide_alpha > 0.f && params->guide_alpha < 1.f))
+      return fail(UGP_ERR_INVALID_ARG, "ugp_render: guide_alpha must be in (0, 1)");
+    if (!guide->params || !(guide->kappa_min > 0.f) || !(guide->kappa_max >= guide->kappa_min))
+      return fail(UGP_ERR_INVALID_ARG, "ugp_render: bad guide (NULL parameters or kappa range)");
+    for (int a = 0; a < 3; ++a)
+      if (!(guide->pos_hi[a] > guide->pos_lo[a]))
+        return fail(UGP_ERR_INVALID_ARG, "ugp_render: guide pos_hi must exceed pos_lo");
+  }
+  if (params->guide_log && (!guide || params->spp != 1))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_render: guide_log needs a guide and spp == 1");
   const int64_t n = int64_t(W) * H;
-  const RenderLayout RL = render_layout(n);
+  if (guide && n * (params->max_depth > 0 ? params->max_depth : 1) > (int64_t(1) << 31) - 1)
+    return fail(UGP_ERR_INVALID_ARG, "ugp_render: image too large for a guided render");
+  const RenderLayout RL = render_layout(n, guide ? params->max_depth : -1);
   if (workspace_bytes < RL.total)
     return fail(UGP_ERR_WORKSPACE_TOO_SMALL, "ugp_render: need %zu bytes, got %zu", RL.total, workspace_bytes);
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
@@ -406,9 +627,25 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   const uint2 key = make_uint2(uint32_t(params->seed & 0xffffffffu), uint32_t(params->seed >> 32));
   unsigned long long* stats = trace_counters();
 
+  GuidedShade gs{};
+  GuideDev gd{};
+  if (guide) {
+    gs.mix = reinterpret_cast<const float*>(ws + RL.mix);
+    gs.alpha = params->guide_alpha;
+    gs.log = params->guide_log;
+    gs.L = log_at(ws, RL);
+    gs.n = int(n);
+    gd.cfg = guide_cfg_dev(guide);
+    gd.err = reinterpret_cast<int*>(ws + RL.img);
+    gd.img = reinterpret_cast<const uint8_t*>(ws + RL.img + 256);
+    const ugp_status s = launch_guide_pack(guide->params, const_cast<uint8_t*>(gd.img), st);
+    if (s != UGP_OK) return s;
+    if (params->guide_log)  // no vertex yet: every entry's pdf is zero
+      UGP_CUDA_CHECK(cudaMemsetAsync(gs.L.c[9], 0, size_t(RL.E) * 4, st));
+  }
   const int g_cam = grid_for((const void*)k_camera, 256, n);
   const int g_ext = grid_for((const void*)k_extend, kFFBlock, n);
-  const int g_shade = grid_for((const void*)k_shade, 128, n);
+  const int g_shade = guide ? grid_for((const void*)k_shade<true>, 128, n) : grid_for((const void*)k_shade<false>, 128, n);
   const int g_shadow = grid_for((const void*)k_shadow, kTrBlock, n);
   const int g_acc = grid_for((const void*)k_accumulate, 256, n);
   for (int si = 0; si < params->spp; ++si) {
@@ -428,9 +665,22 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
                                            ray_counts ? ray_counts + 2 : nullptr, st);
         if (ds != UGP_OK) return ds;
       }
+      if (guide && b < params->max_depth) {
+        prof_begin(kStGuide, st);
+        const ugp_status gsx = launch_guide_forward(
+            gd, ShadeQueueSrc{ps, queue[cur], md.type, b, params->max_depth},
+            MixByPathDst{queue[cur], const_cast<float*>(gs.mix), gd.cfg}, n, counts + cur, n, st);
+        prof_end(kStGuide, st);
+        if (gsx != UGP_OK) return gsx;
+      }
       prof_begin(kStShade, st);
-      k_shade<<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
-                                        counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count);
+      if (guide)
+        k_shade<true><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
+                                                counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count, gs);
+      else
+        k_shade<false><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps,
+                                                 queue[cur], counts + cur, queue[nxt], counts + nxt, sh, counts + 2,
+                                                 dq.count, gs);
       prof_end(kStShade, st);
       if (params->nee && Ld.has_quad) {
         prof_begin(kStShadow, st);
@@ -443,6 +693,84 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
     k_accumulate<<<g_acc, 256, 0, st>>>(int(n), ps, accum_rgb, accum_sq_rgb);
     prof_end(kStAccum, st);
     UGP_CUDA_CHECK(cudaGetLastError());
+  }
+  return UGP_OK;
+}
+
+extern "C" ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* render_ws, size_t render_ws_bytes,
+                                                  int32_t width, int32_t height, int32_t max_depth,
+                                                  int64_t max_samples, int32_t minibatch, void* guide_ws,
+                                                  size_t guide_ws_bytes, int64_t* n_samples_out,
+                                                  float* mean_loss_out, void* stream_) {
+  clear_error();
+  if (!g || !g->params || !g->adam_m || !g->adam_v)
+    return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: NULL guide, parameters or moments");
+  if (!render_ws || !guide_ws) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: NULL workspace");
+  if (width <= 0 || height <= 0 || max_depth < 1 || max_depth > 14 || max_samples < 1 || minibatch < 1)
+    return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: bad size argument");
+  const int64_t n = int64_t(width) * height;
+  if (n * max_depth > (int64_t(1) << 31) - 1) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: too large");
+  const RenderLayout RL = render_layout(n, max_depth);
+  if (render_ws_bytes < RL.total)
+    return fail(UGP_ERR_WORKSPACE_TOO_SMALL, "ugp_guide_train_from_render: render workspace needs %zu bytes", RL.total);
+  if (guide_ws_bytes < ugp::guide_ws_bytes())
+    return fail(UGP_ERR_WORKSPACE_TOO_SMALL, "ugp_guide_train_from_render: guide workspace needs %zu bytes",
+                ugp::guide_ws_bytes());
+  cudaStream_t st = static_cast<cudaStream_t>(stream_);
+  char* ws = static_cast<char*>(const_cast<void*>(render_ws));
+  const size_t col = align256(size_t(n) * 4);
+  PathSoA ps{};
+  ps.lr = reinterpret_cast<float*>(ws + RL.state + 9 * col);
+  ps.lg = reinterpret_cast<float*>(ws + RL.state + 10 * col);
+  ps.lb = reinterpret_cast<float*>(ws + RL.state + 11 * col);
+  const GuideLog L = log_at(ws, RL);
+  int* cnt = reinterpret_cast<int*>(ws + RL.cub);  // [0] usable entries, [1] selected entries
+  void* cub_tmp = ws + RL.cub + 256;
+  UGP_CUDA_CHECK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+  const int grid = grid_for((const void*)k_log_finalize, 256, RL.E);
+  prof_begin(kStGuide, st);
+  k_log_finalize<<<grid, 256, 0, st>>>(L, int(n), ps, cnt);
+  prof_end(kStGuide, st);
+  prof_begin(kStGuide, st);
+  k_log_thin<<<grid, 256, 0, st>>>(L, cnt, max_samples);
+  prof_end(kStGuide, st);
+  UGP_CUDA_CHECK(cudaGetLastError());
+  int* sel = reinterpret_cast<int*>(L.c[18]);
+  size_t cb = RL.cub_bytes;
+  prof_begin(kStGuide, st);
+  UGP_CUDA_CHECK(cub::DeviceSelect::If(cub_tmp, cb, reinterpret_cast<const int*>(L.c[17]), sel, cnt + 1, int(RL.E),
+                                       NonNegative(), st));
+  prof_end(kStGuide, st, 1);
+  int n_sel = 0;
+  UGP_CUDA_CHECK(cudaMemcpyAsync(&n_sel, cnt + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  UGP_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (n_samples_out) *n_samples_out = n_sel;
+  const GuideWs gw = guide_ws_at(guide_ws);
+  ugp_status s = launch_guide_pack(g->params, gw.img, st);
+  if (s != UGP_OK) return s;
+  // gradient and loss of each minibatch land in the guide workspace's scratch after the partials
+  float* grad = gw.partial + size_t(kGMaxGradBlocks - 1) * UGP_GUIDE_NPARAMS;
+  float* loss = gw.loss_partial + kGMaxGradBlocks - 1;
+  const GuideDev gd{guide_cfg_dev(g), gw.img, gw.err};
+  for (int64_t i0 = 0; i0 < n_sel; i0 += minibatch) {
+    const int64_t m = (n_sel - i0 < minibatch) ? n_sel - i0 : minibatch;
+    if (i0 > 0 && (s = launch_guide_pack(g->params, gw.img, st)) != UGP_OK) return s;
+    int gg = 0;
+    prof_begin(kStGuide, st);
+    s = launch_guide_grad(gd, LogSrc{L, sel, i0}, m, nullptr, m, gw, &gg, st);
+    prof_end(kStGuide, st);
+    if (s != UGP_OK) return s;
+    if (gg >= kGMaxGradBlocks) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: too many blocks");
+    if ((s = launch_guide_reduce(gw, gg, grad, loss, st)) != UGP_OK) return s;
+    if ((s = ugp_guide_adam_step(g, grad, st)) != UGP_OK) return s;
+  }
+  if (mean_loss_out) {
+    float lv = 0.f;
+    if (n_sel > 0) {
+      UGP_CUDA_CHECK(cudaMemcpyAsync(&lv, loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+      UGP_CUDA_CHECK(cudaStreamSynchronize(st));
+    }
+    *mean_loss_out = lv;
   }
   return UGP_OK;
 }

@@ -43,9 +43,16 @@ class UgpLights(C.Structure):
                 ("quad_e2", C.c_float * 3), ("quad_Le", C.c_float * 3), ("bg", C.c_float * 3)]
 
 
+class UgpGuide(C.Structure):
+    _fields_ = [("params", vp), ("adam_m", vp), ("adam_v", vp), ("step", C.c_int64), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("pos_lo", C.c_float * 3),
+                ("pos_hi", C.c_float * 3), ("kappa_min", C.c_float), ("kappa_max", C.c_float)]
+
+
 class UgpRenderParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("nee", C.c_int32), ("seed", C.c_uint64), ("spawn_mode", C.c_int32),
+                ("guide_log", C.c_int32), ("guide", C.POINTER(UgpGuide)), ("guide_alpha", C.c_float),
                 ("reserved", C.c_int32)]
 
 
@@ -299,11 +306,17 @@ class Renderer:
         if nb == 0:
             raise UgpError("bad image size")
         self.workspace = torch.empty(nb, dtype=torch.uint8, device=device)
+        self.guided_depth = None
 
     def render(self, bvh: Bvh, mats: Materials, camera: UgpCamera, lights: UgpLights, spp: int,
                max_depth: int, seed: int = 0, spp_begin: int = 0, nee: bool = True, spawn_mode: int = 0,
-               accum=None, accum_sq=None, ray_counts=None, stream=None):
-        """Adds spp samples per pixel into accum / accum_sq ((H, W, 3) float32, created if None)."""
+               accum=None, accum_sq=None, ray_counts=None, stream=None, guide=None, guide_alpha: float = 0.5,
+               guide_log: bool = False):
+        """Adds spp samples per pixel into accum / accum_sq ((H, W, 3) float32, created if None).
+
+        With ``guide`` (a ``Guide``) the renderer samples directions by one-sample MIS between
+        the guide and phase sampling; ``guide_log`` records the vertices for ``Guide.train_from``.
+        """
         dev = self.workspace.device
         shape = (self.height, self.width, 3)
         if accum is None:
@@ -319,7 +332,13 @@ class Renderer:
         if camera.width != self.width or camera.height != self.height:
             raise ValueError("camera size does not match the renderer")
         prm = UgpRenderParams(int(spp), int(spp_begin), int(max_depth), int(bool(nee)), int(seed),
-                              int(spawn_mode), 0)
+                              int(spawn_mode), int(bool(guide_log)),
+                              C.pointer(guide.c) if guide is not None else None, float(guide_alpha), 0)
+        if guide is not None:
+            need = guided_workspace_size(self.width, self.height, max_depth)
+            if self.workspace.numel() < need:
+                self.workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+            self.guided_depth = int(max_depth)
         _check(lib().ugp_render(C.c_void_p(bvh.handle), C.byref(mats.c), C.byref(camera),
                                 C.byref(lights), C.byref(prm), _p(accum), _p(accum_sq),
                                 _p(self.workspace), self.workspace.numel(), _p(ray_counts),
@@ -336,7 +355,7 @@ def set_trace_counters(counters=None):
     _check(lib().ugp_set_trace_counters(_p(counters)), "ugp_set_trace_counters")
 
 
-PROFILE_STAGES = ("build", "camera", "extend", "shade", "shadow", "accumulate", "query", "dense")
+PROFILE_STAGES = ("build", "camera", "extend", "shade", "shadow", "accumulate", "query", "dense", "guide")
 
 
 def profile_begin(max_records: int = 1 << 16):
@@ -346,8 +365,8 @@ def profile_begin(max_records: int = 1 << 16):
 
 def profile_end():
     """Stops timing; returns {stage: (milliseconds, launches)} (waits for the recorded events)."""
-    ms = (C.c_double * 8)()
-    nl = (C.c_int64 * 8)()
+    ms = (C.c_double * len(PROFILE_STAGES))()
+    nl = (C.c_int64 * len(PROFILE_STAGES))()
     _check(lib().ugp_profile_end(ms, nl), "ugp_profile_end")
     return {name: (ms[i], nl[i]) for i, name in enumerate(PROFILE_STAGES)}
 
@@ -358,3 +377,126 @@ def launch_count() -> int:
 
 def version() -> str:
     return lib().ugp_version().decode()
+
+
+# ------------------------------------------------------------------ learned guide
+GUIDE_NPARAMS = 19240
+
+
+def _register_guide(L):
+    L.ugp_guide_workspace_size.restype = C.c_size_t
+    L.ugp_guide_workspace_size.argtypes = []
+    L.ugp_guide_reset_workspace.restype = C.c_int
+    L.ugp_guide_reset_workspace.argtypes = [vp, vp]
+    L.ugp_guide_check.restype = C.c_int
+    L.ugp_guide_check.argtypes = [vp, vp]
+    L.ugp_guide_forward.restype = C.c_int
+    L.ugp_guide_forward.argtypes = [C.POINTER(UgpGuide), C.c_int64, vp, vp, vp, vp, vp, C.c_size_t, vp]
+    L.ugp_guide_mixture_pdf.restype = C.c_int
+    L.ugp_guide_mixture_pdf.argtypes = [C.c_int64, vp, vp, vp, vp]
+    L.ugp_guide_mixture_sample.restype = C.c_int
+    L.ugp_guide_mixture_sample.argtypes = [C.c_int64, vp, vp, vp, vp, vp]
+    L.ugp_guide_grad.restype = C.c_int
+    L.ugp_guide_grad.argtypes = [C.POINTER(UgpGuide), C.c_int64, vp, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+    L.ugp_guide_adam_step.restype = C.c_int
+    L.ugp_guide_adam_step.argtypes = [C.POINTER(UgpGuide), vp, vp]
+    L.ugp_guide_train_from_render.restype = C.c_int
+    L.ugp_guide_train_from_render.argtypes = [C.POINTER(UgpGuide), vp, C.c_size_t, C.c_int32, C.c_int32, C.c_int32,
+                                              C.c_int64, C.c_int32, vp, C.c_size_t, C.POINTER(C.c_int64),
+                                              C.POINTER(C.c_float), vp]
+    L.ugp_render_guided_workspace_size.restype = C.c_size_t
+    L.ugp_render_guided_workspace_size.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+
+
+_EXTRA.append(_register_guide)
+
+
+def guided_workspace_size(width: int, height: int, max_depth: int) -> int:
+    return int(lib().ugp_render_guided_workspace_size(int(width), int(height), int(max_depth)))
+
+
+class Guide:
+    """The learned vMF-mixture guide: FP32 master weights, Adam moments and a workspace, all on
+    the device; the C struct points at them."""
+
+    def __init__(self, params, pos_lo=(0.0, 0.0, 0.0), pos_hi=(1.0, 1.0, 1.0), kappa_min=0.1, kappa_max=1e4,
+                 lr=1e-3, beta1=0.9, beta2=0.99, eps=1e-8, device="cuda"):
+        p = torch.as_tensor(params, dtype=torch.float32).to(device).contiguous().clone()
+        if p.numel() != GUIDE_NPARAMS:
+            raise ValueError(f"guide needs {GUIDE_NPARAMS} parameters")
+        self.params = p
+        self.adam_m = torch.zeros_like(p)
+        self.adam_v = torch.zeros_like(p)
+        self.workspace = torch.empty(int(lib().ugp_guide_workspace_size()), dtype=torch.uint8, device=device)
+        _check(lib().ugp_guide_reset_workspace(_p(self.workspace), C.c_void_p(_stream())), "ugp_guide_reset_workspace")
+        self.c = UgpGuide(_p(self.params), _p(self.adam_m), _p(self.adam_v), 0, float(lr), float(beta1), float(beta2),
+                          float(eps), (C.c_float * 3)(*pos_lo), (C.c_float * 3)(*pos_hi), float(kappa_min),
+                          float(kappa_max))
+
+    @property
+    def step(self) -> int:
+        return int(self.c.step)
+
+    def check(self, stream=None):
+        _check(lib().ugp_guide_check(_p(self.workspace), C.c_void_p(_stream(stream))), "ugp_guide_check")
+
+    def forward(self, x3, wo3, head=True, mix=True, stream=None):
+        """(head outputs (n, 40), mixtures (n, 40)) for vertices x3, wo3 ((n, 3) float32)."""
+        n = int(x3.shape[0])
+        _dev(x3, torch.float32, "x3", 3)
+        _dev(wo3, torch.float32, "wo3", 3)
+        Y = torch.empty((n, 40), dtype=torch.float32, device=x3.device) if head else None
+        M = torch.empty((n, 40), dtype=torch.float32, device=x3.device) if mix else None
+        _check(lib().ugp_guide_forward(C.byref(self.c), n, _p(x3), _p(wo3), _p(Y), _p(M), _p(self.workspace),
+                                       self.workspace.numel(), C.c_void_p(_stream(stream))), "ugp_guide_forward")
+        return Y, M
+
+    def grad(self, x3, wo3, wi3, weight, stream=None):
+        """(gradient of the mean loss (GUIDE_NPARAMS,), mean loss (1,)) on the device."""
+        n = int(x3.shape[0])
+        for t, nm in ((x3, "x3"), (wo3, "wo3"), (wi3, "wi3")):
+            _dev(t, torch.float32, nm, 3)
+        _dev(weight, torch.float32, "weight")
+        g = torch.empty(GUIDE_NPARAMS, dtype=torch.float32, device=self.params.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.params.device)
+        _check(lib().ugp_guide_grad(C.byref(self.c), n, _p(x3), _p(wo3), _p(wi3), _p(weight), _p(g), _p(loss),
+                                    _p(self.workspace), self.workspace.numel(), C.c_void_p(_stream(stream))),
+               "ugp_guide_grad")
+        return g, loss
+
+    def adam_step(self, grad, stream=None):
+        _dev(grad, torch.float32, "grad")
+        _check(lib().ugp_guide_adam_step(C.byref(self.c), _p(grad), C.c_void_p(_stream(stream))), "ugp_guide_adam_step")
+
+    def train_from(self, renderer: "Renderer", max_samples: int = 1 << 20, minibatch: int = 1 << 16, stream=None):
+        """One pass of Adam over the vertices the renderer's last logged call recorded.
+        Returns (samples used, mean loss of the last minibatch); synchronises."""
+        ns = C.c_int64(0)
+        ml = C.c_float(0)
+        _check(lib().ugp_guide_train_from_render(C.byref(self.c), _p(renderer.workspace), renderer.workspace.numel(),
+                                                 renderer.width, renderer.height, renderer.guided_depth,
+                                                 int(max_samples), int(minibatch), _p(self.workspace),
+                                                 self.workspace.numel(), C.byref(ns), C.byref(ml),
+                                                 C.c_void_p(_stream(stream))), "ugp_guide_train_from_render")
+        return int(ns.value), float(ml.value)
+
+
+def mixture_pdf(mix, wi3, stream=None):
+    n = int(mix.shape[0])
+    _dev(mix, torch.float32, "mix", 40)
+    _dev(wi3, torch.float32, "wi3", 3)
+    out = torch.empty(n, dtype=torch.float32, device=mix.device)
+    _check(lib().ugp_guide_mixture_pdf(n, _p(mix), _p(wi3), _p(out), C.c_void_p(_stream(stream))),
+           "ugp_guide_mixture_pdf")
+    return out
+
+
+def mixture_sample(mix, u3, stream=None):
+    n = int(mix.shape[0])
+    _dev(mix, torch.float32, "mix", 40)
+    _dev(u3, torch.float32, "u3", 3)
+    wi = torch.empty((n, 3), dtype=torch.float32, device=mix.device)
+    pdf = torch.empty(n, dtype=torch.float32, device=mix.device)
+    _check(lib().ugp_guide_mixture_sample(n, _p(mix), _p(u3), _p(wi), _p(pdf), C.c_void_p(_stream(stream))),
+           "ugp_guide_mixture_sample")
+    return wi, pdf

@@ -53,3 +53,30 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(ugp, "_LIB", None)
     with pytest.raises(ugp.UgpError):
         ugp.lib()
+
+
+def test_guide_entry_points_validate_on_host(libugp):
+    libugp.ugp_guide_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_render_guided_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_render_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_last_error.restype = ctypes.c_char_p
+    assert libugp.ugp_guide_workspace_size() > 83200
+    plain = libugp.ugp_render_workspace_size(4, 4)
+    guided = libugp.ugp_render_guided_workspace_size(4, 4, 3)
+    assert guided > plain > 0
+    assert libugp.ugp_render_guided_workspace_size(4, 4, 15) == 0
+    st = libugp.ugp_guide_forward(None, ctypes.c_int64(4), None, None, None, None, None, ctypes.c_size_t(0), None)
+    assert st == 1 and b"NULL guide" in libugp.ugp_last_error()
+    st = libugp.ugp_guide_adam_step(None, None, None)
+    assert st == 1
+    st = libugp.ugp_guide_mixture_pdf(ctypes.c_int64(-1), None, None, None, None)
+    assert st == 1
+
+
+def test_guide_struct_layouts_match_the_header():
+    """The ctypes mirrors have the C layout (offsets follow the header's field order)."""
+    from paper_2406_09733_gb300 import ugp
+    assert ctypes.sizeof(ugp.UgpGuide) == 80
+    assert ugp.UgpGuide.kappa_max.offset == 76
+    assert ctypes.sizeof(ugp.UgpRenderParams) == 48
+    assert ugp.UgpRenderParams.guide.offset == 32 and ugp.UgpRenderParams.guide_alpha.offset == 40

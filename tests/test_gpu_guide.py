@@ -1,0 +1,219 @@
+"""Parity of the tensor-core guide kernels with the BF16-mirrored FP64 oracle.
+
+Tolerances (derived from the arithmetic): the GPU and the oracle round the same layer inputs
+to BF16, but the GPU's FP32 sums can land on the other side of a BF16 rounding boundary
+(about one element in a few thousand); one such flip moves a head output by roughly 5e-4 of
+its norm. So the head outputs must agree to a relative L2 error of 1e-3 for 99% of the rows
+and 1e-2 for every row. The backward pass also rounds dZ to BF16 (the oracle keeps FP64):
+per-tensor gradients must have cosine >= 0.999 and relative L2 error <= 1e-2.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2406_09733_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+CFG = scenes.GuideConfig()
+
+
+@pytest.fixture(scope="module")
+def ugp():
+    from paper_2406_09733_gb300 import ugp as U
+    U.lib()
+    return U
+
+
+def _guide(ugp, seed=0, bias=0.2, cfg=CFG):
+    return ugp.Guide(scenes.guide_init_params(seed=seed, bias_scale=bias), cfg.pos_lo, cfg.pos_hi, cfg.kappa_min,
+                     cfg.kappa_max)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _head_rel_err(Yg, Yr):
+    return np.linalg.norm(Yg - Yr, axis=1) / np.maximum(np.linalg.norm(Yr, axis=1), 1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000])
+def test_forward_parity(ugp, orc, n):
+    g = _guide(ugp, seed=n)
+    b = scenes.guide_batch(n, seed=100 + n)
+    Y, M = g.forward(_t(b.x), _t(b.wo))
+    torch.cuda.synchronize()
+    g.check()
+    Yr, Mr = orc.guide_forward(CFG, g.params.cpu().numpy(), b.x, b.wo)
+    err = _head_rel_err(Y.cpu().numpy().astype(np.float64), Yr)
+    assert np.quantile(err, 0.99) <= 1e-3 and err.max() <= 1e-2, (np.quantile(err, 0.99), err.max())
+    M = M.cpu().numpy().reshape(n, 8, 5).astype(np.float64)
+    ok = err <= 1e-3
+    assert np.abs(M[ok, :, :3] - Mr[ok, :, :3]).max() < 2e-3
+    assert np.abs(M[ok, :, 3] / Mr[ok, :, 3] - 1).max() < 2e-3
+    assert np.abs(M[ok, :, 4] - Mr[ok, :, 4]).max() < 2e-3
+
+
+def test_forward_large_batch_sampled(ugp, orc):
+    n = 300_000
+    g = _guide(ugp, seed=7)
+    b = scenes.guide_batch(n, seed=8)
+    Y, _ = g.forward(_t(b.x), _t(b.wo), mix=False)
+    torch.cuda.synchronize()
+    g.check()
+    rows = np.random.default_rng(0).choice(n, 2000, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    Yr, _ = orc.guide_forward(CFG, g.params.cpu().numpy(), b.x[rows], b.wo[rows])
+    err = _head_rel_err(Y.cpu().numpy()[rows].astype(np.float64), Yr)
+    assert np.quantile(err, 0.99) <= 1e-3 and err.max() <= 1e-2
+
+
+def test_forward_empty_and_errors(ugp):
+    g = _guide(ugp)
+    e = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    Y, M = g.forward(e, e)
+    assert Y.shape == (0, 40)
+    bad = ugp.Guide(scenes.guide_init_params(0), (0, 0, 0), (0, 1, 1))
+    with pytest.raises(ugp.UgpError):
+        bad.forward(_t(np.zeros((4, 3))), _t(np.zeros((4, 3))))
+
+
+def test_mixture_pdf_and_sample_parity(ugp, orc):
+    n = 4096
+    b = scenes.guide_batch(n, seed=21)
+    p = scenes.guide_init_params(seed=22, bias_scale=1.0)
+    _, mix = orc.guide_forward(CFG, p, b.x, b.wo)
+    mix32 = mix.reshape(n, 40).astype(np.float32)
+    rng = np.random.default_rng(3)
+    U = rng.random((n, 3)).astype(np.float32)
+    wi, pdf = ugp.mixture_sample(_t(mix32), _t(U))
+    wi_r, pdf_r = orc.mixture_sample(mix32.astype(np.float64), U.astype(np.float64))
+    wi = wi.cpu().numpy().astype(np.float64)
+    # lobe choices agree except where the lobe uniform sits on a cumulative boundary
+    cum = np.cumsum(mix32[:, 4::5].astype(np.float64), axis=1)
+    near = np.min(np.abs(cum - U[:, :1]), axis=1) < 1e-5
+    ang = np.arccos(np.clip((wi * wi_r).sum(1), -1, 1))
+    assert np.all(ang[~near] < 2e-3), np.sort(ang[~near])[-5:]
+    assert near.mean() < 0.01
+    q = ugp.mixture_pdf(_t(mix32), _t(wi_r.astype(np.float32))).cpu().numpy()
+    q_r = orc.mixture_pdf(mix32.astype(np.float64), wi_r.astype(np.float32).astype(np.float64))
+    assert np.allclose(q, q_r, rtol=2e-3, atol=0)
+    assert np.allclose(pdf.cpu().numpy()[~near], orc.mixture_pdf(mix32.astype(np.float64), wi)[~near], rtol=2e-3)
+
+
+def _per_tensor(g):
+    return [(g[w], g[bb]) for (w, bb) in scenes.guide_param_slices()]
+
+
+@pytest.mark.parametrize("n", [1000, 5000])
+def test_gradient_parity(ugp, orc, n):
+    g = _guide(ugp, seed=31)
+    b = scenes.guide_batch(n, seed=32)
+    grad, loss = g.grad(_t(b.x), _t(b.wo), _t(b.wi), _t(b.weight))
+    torch.cuda.synchronize()
+    g.check()
+    lr, gr = orc.guide_loss_grad(CFG, g.params.cpu().numpy(), b.x, b.wo, b.wi, b.weight)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - lr) <= 2e-3 * abs(lr)
+    for l, ((w, bb), (wr, br)) in enumerate(zip(_per_tensor(gg), _per_tensor(gr))):
+        for name, a, r in (("W", w, wr), ("b", bb, br)):
+            cos = a @ r / (np.linalg.norm(a) * np.linalg.norm(r))
+            rel = np.linalg.norm(a - r) / np.linalg.norm(r)
+            assert cos >= 0.999 and rel <= 1e-2, (l, name, cos, rel)
+    # deterministic: a second call gives the same bits
+    grad2, _ = g.grad(_t(b.x), _t(b.wo), _t(b.wi), _t(b.weight))
+    assert torch.equal(grad, grad2)
+
+
+def test_gradient_zero_batch(ugp):
+    g = _guide(ugp)
+    e = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    grad, loss = g.grad(e, e, e, torch.zeros(0, dtype=torch.float32, device="cuda"))
+    assert torch.count_nonzero(grad).item() == 0 and loss.item() == 0
+
+
+def test_adam_parity(ugp, orc):
+    g = _guide(ugp, seed=41)
+    rng = np.random.default_rng(4)
+    th = g.params.cpu().numpy().astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    for t in range(1, 4):
+        gr = (rng.normal(size=th.size) * 10 ** rng.uniform(-4, 1, th.size)).astype(np.float32)
+        g.adam_step(_t(gr))
+        th, m, v = orc.adam_step(th, m, v, gr.astype(np.float64), t)
+        assert g.step == t
+    got = g.params.cpu().numpy().astype(np.float64)
+    assert np.abs(got - th).max() <= 1e-6 * max(1, np.abs(th).max())
+    assert np.abs(g.adam_v.cpu().numpy() - v).max() <= 1e-5 * np.abs(v).max()
+
+
+def _lit_scene():
+    s = scenes.tiny_scene(n=200, seed=3, width=6, height=6)
+    s.mtype[:] = scenes.MAT_DIFFUSE
+    s.emission[:] = 0.0
+    s.mtype[::3] = scenes.MAT_GGX
+    s.roughness[:] = 0.4
+    s.camera = scenes.Camera((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 35.0, 6, 6)
+    s.lights = scenes.Lights(True, (0.2, 1.2, 0.2), (0.6, 0.0, 0.0), (0.0, 0.0, 0.6), (6.0, 6.0, 6.0),
+                             (0.05, 0.05, 0.05))
+    return s
+
+
+def _z(a1, q1, spp1, a0, q0, spp0):
+    m1, m0 = a1 / spp1, a0 / spp0
+    se1 = np.sqrt(np.maximum(q1 / spp1 - m1 ** 2, 0) / spp1)
+    se0 = np.sqrt(np.maximum(q0 / spp0 - m0 ** 2, 0) / spp0)
+    return np.abs(m1 - m0) / np.maximum(np.sqrt(se1 ** 2 + se0 ** 2), 1e-12), m1, m0, se1, se0
+
+
+def test_guided_render_matches_oracle(ugp, orc):
+    """GPU guided render (fixed guide) vs the oracle's guided render: per-pixel 3.5 SE."""
+    s = _lit_scene()
+    p = scenes.guide_init_params(seed=21, bias_scale=1.0)
+    g = ugp.Guide(p, CFG.pos_lo, CFG.pos_hi, CFG.kappa_min, CFG.kappa_max)
+    bvh, mats, cam, lights = ugp.scene_to_device(s)
+    r = ugp.Renderer(6, 6)
+    spp = 16384
+    acc, acc2 = r.render(bvh, mats, cam, lights, spp=spp, max_depth=3, seed=5, guide=g, guide_alpha=0.5)
+    torch.cuda.synchronize()
+    g.check()
+    a1, q1 = acc.cpu().numpy().astype(np.float64), acc2.cpu().numpy().astype(np.float64)
+    a0, q0, _ = orc.render(s, spp=4096, max_depth=3, seed=6, guide=(p, CFG), guide_alpha=0.5)
+    z, m1, m0, se1, se0 = _z(a1, q1, spp, a0, q0, 4096)
+    assert (z > 3.5).mean() <= 0.03, np.sort(z.ravel())[-5:]
+    zi = abs(m1.sum() - m0.sum()) / math.sqrt((se1 ** 2).sum() + (se0 ** 2).sum())
+    assert zi < 4, zi
+
+
+def test_trained_guide_stays_unbiased(ugp, orc):
+    """Train on the GPU for a few samples per pixel, then a guided render keeps the plain mean."""
+    s = _lit_scene()
+    s.camera = scenes.Camera((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), 35.0, 16, 16)
+    bvh, mats, cam, lights = ugp.scene_to_device(s)
+    g = _guide(ugp, seed=51, bias=0.2)
+    r = ugp.Renderer(16, 16)
+    acc = torch.zeros((16, 16, 3), dtype=torch.float32, device="cuda")
+    acc2 = torch.zeros_like(acc)
+    p0 = g.params.clone()
+    used = []
+    for k in range(8):
+        r.render(bvh, mats, cam, lights, spp=1, max_depth=3, seed=9, spp_begin=k, guide=g, guide_log=True,
+                 accum=acc, accum_sq=acc2)
+        n_used, loss = g.train_from(r, minibatch=256)
+        used.append(n_used)
+        assert math.isfinite(loss)
+    g.check()
+    assert min(used) > 0 and g.step > 0
+    assert not torch.equal(p0, g.params)
+    spp = 2048
+    a1, q1 = r.render(bvh, mats, cam, lights, spp=spp, max_depth=3, seed=10, spp_begin=100, guide=g)
+    a0, q0 = r.render(bvh, mats, cam, lights, spp=spp, max_depth=3, seed=11, spp_begin=100)
+    z, m1, m0, se1, se0 = _z(*(t.cpu().numpy().astype(np.float64) for t in (a1, q1)), spp,
+                             *(t.cpu().numpy().astype(np.float64) for t in (a0, q0)), spp)
+    assert (z > 3.5).mean() <= 0.03, np.sort(z.ravel())[-5:]
+    zi = abs(m1.sum() - m0.sum()) / math.sqrt((se1 ** 2).sum() + (se0 ** 2).sum())
+    assert zi < 4, zi
