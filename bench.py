@@ -9,7 +9,12 @@ the primitives + one sample per pixel of the wavefront path tracer (camera, free
 extend, shading with light sampling + MIS, shadow transmittance, accumulation); 64 steps
 are the full 64-spp frame.  Inputs are synthetic (seeded generator).
 
-Metric: Mrays/s = (free-flight queries + shadow queries) / time.
+Metric: Mrays/s = (free-flight queries + shadow queries) / time, plus the equal-time MSE of
+the learned-guide renderer against plain phase sampling: on the same scene and BVH at a
+reduced image size, a converged plain reference is rendered first; then the plain renderer
+runs for a budget of spp and the guided renderer (trained online during its first spp, the
+training time counted) runs for the same wall time; both MSEs are taken against the reference
+with the reference's own variance subtracted.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ugp|reference]
 For N > 1 run under torch.distributed.run: every rank renders its own replica of the
@@ -47,8 +52,17 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-pixels", type=int, default=1024, help="pixels of the CPU-baseline sample")
-    p.add_argument("--kernel-case", choices=["ff_camera512"], default=None,
+    p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
+    p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
+    p.add_argument("--mse-res", type=int, default=384, help="image side of the MSE study")
+    p.add_argument("--mse-ref-spp", type=int, default=512, help="spp of the plain reference")
+    p.add_argument("--mse-budget-spp", type=int, default=64, help="plain spp that set the time budget")
+    p.add_argument("--mse-train-spp", type=int, default=32, help="guided spp that also train the guide")
+    p.add_argument("--mse-minibatch", type=int, default=1 << 14)
+    p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
+    p.add_argument("--guide-alpha", type=float, default=0.5)
+    p.add_argument("--guide-lr", type=float, default=1e-3)
     return p.parse_args(argv)
 
 
@@ -61,6 +75,129 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "of measured"
     except Exception:
         return 6800.0, "of fallback"
+
+
+def measured_bf16_peak():
+    """Burst dense BF16 tensor throughput (TFLOP/s) for kernels timed alone."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "of measured"
+    except Exception:
+        return 1900.0, "of fallback"
+
+
+# Algorithmic FLOP per row of the guide network (4 x 64x64 layers and a 64 -> 40 head):
+# forward 2 (4*64*64 + 40*64); training adds dW of every layer (same count) and dX of layers 1..4.
+GUIDE_FWD_FLOP = 2 * (4 * 64 * 64 + 40 * 64)
+GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
+
+
+def guide_kernel_timing(dev, rows=1 << 20, reps=10):
+    """CUDA-event time of the guide's forward and gradient calls on `rows` random vertices."""
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    t = lambda a: torch.from_numpy(a).to(dev)
+    g = ugp.Guide(scenes.guide_init_params(seed=0, bias_scale=0.2), device=dev)
+    b = scenes.guide_batch(rows, seed=1)
+    x, wo, wi, w = t(b.x), t(b.wo), t(b.wi), t(b.weight)
+    out = {}
+    peak, note = measured_bf16_peak()
+    for name, fn, flop in (("forward", lambda: g.forward(x, wo, head=False), GUIDE_FWD_FLOP),
+                           ("grad", lambda: g.grad(x, wo, wi, w), GUIDE_GRAD_FLOP)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        ugp.profile_begin(4096)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        prof = ugp.profile_end()
+        ms = e0.elapsed_time(e1) / reps
+        tf = rows * flop / (ms / 1e3) / 1e12
+        out[name] = {"rows": rows, "ms_per_call": ms, "algorithmic_flop_per_row": flop, "achieved_tflops": tf,
+                     "peak_tflops": peak, "frac": tf / peak, "peak_note": note,
+                     "launches_per_call": prof["guide"][1] / reps}
+    g.check()
+    return out
+
+
+def equal_time_mse(args, d, mats, scene, dev):
+    """Equal-time MSE of guided vs plain rendering against a converged plain reference."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    R = args.mse_res
+    cam = scene.camera
+    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, R, R)
+    li = scene.lights
+    lights = ugp.lights_struct(li.has_quad, li.quad_corner, li.quad_e1, li.quad_e2, li.quad_Le, li.bg)
+    bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
+    info = bvh.info()
+    r = ugp.Renderer(R, R, device=dev)
+    z = lambda: torch.zeros((R, R, 3), dtype=torch.float32, device=dev)
+    depth = args.depth
+
+    # converged plain reference (different seed), in chunks of 64 spp
+    ref, ref2 = z(), z()
+    for s0 in range(0, args.mse_ref_spp, 64):
+        r.render(bvh, mats, camera, lights, spp=min(64, args.mse_ref_spp - s0), max_depth=depth, seed=777,
+                 spp_begin=s0, accum=ref, accum_sq=ref2)
+    torch.cuda.synchronize(dev)
+    ref_mean = (ref / args.mse_ref_spp).double()
+    ref_var = ((ref2 / args.mse_ref_spp).double() - ref_mean ** 2).clamp(min=0) / args.mse_ref_spp
+    ref_var_mean = float(ref_var.mean())
+
+    def mse(acc, spp):
+        return float(((acc.double() / spp - ref_mean) ** 2).mean()) - ref_var_mean
+
+    checkpoints = sorted({8, 16, 32, args.mse_budget_spp})
+    # plain: one spp per call, timed on the host around synchronised calls
+    acc, acc2 = z(), z()
+    torch.cuda.synchronize(dev)
+    t_plain, curve_p = 0.0, []
+    for k in range(args.mse_budget_spp):
+        t0 = time.perf_counter()
+        r.render(bvh, mats, camera, lights, spp=1, max_depth=depth, seed=1, spp_begin=k, accum=acc, accum_sq=acc2)
+        torch.cuda.synchronize(dev)
+        t_plain += time.perf_counter() - t0
+        if k + 1 in checkpoints:
+            curve_p.append([1e3 * t_plain, mse(acc, k + 1)])
+    mse_plain = mse(acc, args.mse_budget_spp)
+
+    # guided: trained during its first mse_train_spp samples, then frozen, until the same time
+    g = ugp.Guide(scenes.guide_init_params(seed=0, bias_scale=0.0), info["bounds_lo"], info["bounds_hi"],
+                  lr=args.guide_lr, device=dev)
+    gacc, gacc2 = z(), z()
+    t_g, k, curve_g, n_train, losses = 0.0, 0, [], 0, []
+    while t_g < t_plain and k < 64 * args.mse_budget_spp:
+        train = k < args.mse_train_spp
+        t0 = time.perf_counter()
+        r.render(bvh, mats, camera, lights, spp=1, max_depth=depth, seed=2, spp_begin=k, accum=gacc,
+                 accum_sq=gacc2, guide=g, guide_alpha=args.guide_alpha, guide_log=train)
+        if train:
+            ns, loss = g.train_from(r, max_samples=1 << 20, minibatch=args.mse_minibatch,
+                                    min_steps=args.mse_min_steps)
+            n_train += ns
+            losses.append(loss)
+        torch.cuda.synchronize(dev)
+        t_g += time.perf_counter() - t0
+        k += 1
+        if k in checkpoints or t_g >= t_plain:
+            curve_g.append([1e3 * t_g, mse(gacc, k)])
+    g.check()
+    mse_guided = mse(gacc, k)
+    return {"plain": mse_plain, "guided": mse_guided, "ratio_guided_over_plain": mse_guided / mse_plain,
+            "budget_ms": 1e3 * t_plain, "plain_spp": args.mse_budget_spp, "guided_spp": k, "guided_ms": 1e3 * t_g,
+            "train_spp": min(args.mse_train_spp, k), "train_samples": n_train, "adam_steps": g.step,
+            "loss_first_last": [losses[0], losses[-1]] if losses else None,
+            "reference_spp": args.mse_ref_spp, "reference_var_subtracted": ref_var_mean,
+            "image": f"{R}x{R}", "max_depth": depth, "guide_alpha": args.guide_alpha,
+            "curve_ms_mse": {"plain": curve_p, "guided": curve_g},
+            "note": "MSE over linear RGB, no clamping; times include the guide's training"}
 
 
 class ClockSampler:
@@ -304,6 +441,12 @@ def run_ugp(args):
                "sample": f"{args.cpu_pixels} pixels x 1 spp of the middle row, {r} queries in {dt:.1f} s, "
                          f"brute force over all primitives, FP64"}
 
+    guide_perf = None
+    mse = None
+    if rank == 0 and world == 1 and not args.no_mse:
+        guide_perf = guide_kernel_timing(dev)
+        mse = equal_time_mse(args, d, mats, scene, dev)
+
     if rank == 0:
         clk = clocks.summary()
         line = {
@@ -321,7 +464,7 @@ def run_ugp(args):
                          "nodes_per_query": nodes_per_query, "prims_per_query": prims_per_query,
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "wall_s_timed_region": wall, "equal_time_mse": None,
+            "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -361,8 +504,27 @@ def run_kernel_case(args):
     return 0
 
 
+def run_guide_case(args):
+    """One forward and one gradient call of the guide on 2^18 random vertices (ncu case)."""
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    dev = torch.device("cuda")
+    t = lambda a: torch.from_numpy(a).to(dev)
+    g = ugp.Guide(scenes.guide_init_params(seed=0, bias_scale=0.2), device=dev)
+    b = scenes.guide_batch(1 << 18, seed=1)
+    _, mix = g.forward(t(b.x), t(b.wo), head=False)
+    grad, loss = g.grad(t(b.x), t(b.wo), t(b.wi), t(b.weight))
+    torch.cuda.synchronize()
+    g.check()
+    print(json.dumps({"kernel_case": args.kernel_case, "rows": b.n, "loss": float(loss.item()),
+                      "grad_norm": float(grad.norm().item())}))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.kernel_case == "guide_rows256k":
+        return run_guide_case(args)
     if args.kernel_case:
         return run_kernel_case(args)
     if args.impl == "reference":

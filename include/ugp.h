@@ -363,12 +363,13 @@ ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materials, const 
  * divided by the path throughput after it (per channel, luminance-weighted); vertices with
  * L > 0 are the training samples, with weight L / p. If there are more than max_samples, a
  * deterministic hash keeps about max_samples of them. They are visited in minibatches of
- * `minibatch` rows, one ugp_guide_grad + ugp_guide_adam_step each. Writes the number of
- * samples used and the mean loss of the last minibatch (host, may be NULL). Synchronises. */
+ * `minibatch` rows, one ugp_guide_grad + ugp_guide_adam_step each: one pass over the samples,
+ * or min_steps minibatches taken cyclically when that is more. Writes the number of samples
+ * used and the mean loss of the last minibatch (host, may be NULL). Synchronises. */
 ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* render_ws, size_t render_ws_bytes, int32_t width,
                                        int32_t height, int32_t max_depth, int64_t max_samples, int32_t minibatch,
-                                       void* guide_ws, size_t guide_ws_bytes, int64_t* n_samples_out,
-                                       float* mean_loss_out, void* stream);
+                                       int32_t min_steps, void* guide_ws, size_t guide_ws_bytes,
+                                       int64_t* n_samples_out, float* mean_loss_out, void* stream);
 
 /* Optional traversal statistics: when `counters` is a device pointer to 12
  * zero-initialised uint64, later tracing calls on any stream add (atomically)

@@ -390,13 +390,13 @@ struct MixByPathDst {
   }
 };
 
-// Training rows: selected log entries.
+// Training rows: selected log entries, taken cyclically from `offset` (n_sel entries).
 struct LogSrc {
   GuideLog L;
   const int* idx;
-  int64_t offset;
+  int64_t offset, n_sel;
   __device__ bool sample(int64_t r, float3& x, float3& wo, float3& wi, float& w) const {
-    const int64_t e = idx[offset + r];
+    const int64_t e = idx[(offset + r) % n_sel];
     x = f3(L.c[0][e], L.c[1][e], L.c[2][e]);
     wo = f3(L.c[3][e], L.c[4][e], L.c[5][e]);
     wi = f3(L.c[6][e], L.c[7][e], L.c[8][e]);
@@ -699,14 +699,16 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
 
 extern "C" ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* render_ws, size_t render_ws_bytes,
                                                   int32_t width, int32_t height, int32_t max_depth,
-                                                  int64_t max_samples, int32_t minibatch, void* guide_ws,
+                                                  int64_t max_samples, int32_t minibatch, int32_t min_steps,
+                                                  void* guide_ws,
                                                   size_t guide_ws_bytes, int64_t* n_samples_out,
                                                   float* mean_loss_out, void* stream_) {
   clear_error();
   if (!g || !g->params || !g->adam_m || !g->adam_v)
     return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: NULL guide, parameters or moments");
   if (!render_ws || !guide_ws) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: NULL workspace");
-  if (width <= 0 || height <= 0 || max_depth < 1 || max_depth > 14 || max_samples < 1 || minibatch < 1)
+  if (width <= 0 || height <= 0 || max_depth < 1 || max_depth > 14 || max_samples < 1 || minibatch < 1 ||
+      min_steps < 0)
     return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: bad size argument");
   const int64_t n = int64_t(width) * height;
   if (n * max_depth > (int64_t(1) << 31) - 1) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: too large");
@@ -752,12 +754,17 @@ extern "C" ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* rend
   float* grad = gw.partial + size_t(kGMaxGradBlocks - 1) * UGP_GUIDE_NPARAMS;
   float* loss = gw.loss_partial + kGMaxGradBlocks - 1;
   const GuideDev gd{guide_cfg_dev(g), gw.img, gw.err};
-  for (int64_t i0 = 0; i0 < n_sel; i0 += minibatch) {
-    const int64_t m = (n_sel - i0 < minibatch) ? n_sel - i0 : minibatch;
-    if (i0 > 0 && (s = launch_guide_pack(g->params, gw.img, st)) != UGP_OK) return s;
+  // one pass over the samples, or min_steps minibatches taken cyclically if that is more
+  const int64_t m = n_sel < minibatch ? n_sel : minibatch;
+  const int64_t pass = n_sel > 0 ? (n_sel + minibatch - 1) / minibatch : 0;
+  const int64_t steps = n_sel > 0 ? (pass > min_steps ? pass : min_steps) : 0;
+  for (int64_t k = 0; k < steps; ++k) {
+    const int64_t i0 = (k * m) % n_sel;
+    const int64_t rows = (k < pass && n_sel - i0 < m) ? n_sel - i0 : m;
+    if (k > 0 && (s = launch_guide_pack(g->params, gw.img, st)) != UGP_OK) return s;
     int gg = 0;
     prof_begin(kStGuide, st);
-    s = launch_guide_grad(gd, LogSrc{L, sel, i0}, m, nullptr, m, gw, &gg, st);
+    s = launch_guide_grad(gd, LogSrc{L, sel, i0, n_sel}, rows, nullptr, rows, gw, &gg, st);
     prof_end(kStGuide, st);
     if (s != UGP_OK) return s;
     if (gg >= kGMaxGradBlocks) return fail(UGP_ERR_INVALID_ARG, "ugp_guide_train_from_render: too many blocks");

@@ -402,7 +402,7 @@ def _register_guide(L):
     L.ugp_guide_adam_step.argtypes = [C.POINTER(UgpGuide), vp, vp]
     L.ugp_guide_train_from_render.restype = C.c_int
     L.ugp_guide_train_from_render.argtypes = [C.POINTER(UgpGuide), vp, C.c_size_t, C.c_int32, C.c_int32, C.c_int32,
-                                              C.c_int64, C.c_int32, vp, C.c_size_t, C.POINTER(C.c_int64),
+                                              C.c_int64, C.c_int32, C.c_int32, vp, C.c_size_t, C.POINTER(C.c_int64),
                                               C.POINTER(C.c_float), vp]
     L.ugp_render_guided_workspace_size.restype = C.c_size_t
     L.ugp_render_guided_workspace_size.argtypes = [C.c_int32, C.c_int32, C.c_int32]
@@ -468,14 +468,16 @@ class Guide:
         _dev(grad, torch.float32, "grad")
         _check(lib().ugp_guide_adam_step(C.byref(self.c), _p(grad), C.c_void_p(_stream(stream))), "ugp_guide_adam_step")
 
-    def train_from(self, renderer: "Renderer", max_samples: int = 1 << 20, minibatch: int = 1 << 16, stream=None):
-        """One pass of Adam over the vertices the renderer's last logged call recorded.
-        Returns (samples used, mean loss of the last minibatch); synchronises."""
+    def train_from(self, renderer: "Renderer", max_samples: int = 1 << 20, minibatch: int = 1 << 16,
+                   min_steps: int = 0, stream=None):
+        """Adam over the vertices the renderer's last logged call recorded: one pass in minibatches,
+        or min_steps minibatches (cycling) if that is more. Returns (samples used, mean loss of the
+        last minibatch); synchronises."""
         ns = C.c_int64(0)
         ml = C.c_float(0)
         _check(lib().ugp_guide_train_from_render(C.byref(self.c), _p(renderer.workspace), renderer.workspace.numel(),
                                                  renderer.width, renderer.height, renderer.guided_depth,
-                                                 int(max_samples), int(minibatch), _p(self.workspace),
+                                                 int(max_samples), int(minibatch), int(min_steps), _p(self.workspace),
                                                  self.workspace.numel(), C.byref(ns), C.byref(ml),
                                                  C.c_void_p(_stream(stream))), "ugp_guide_train_from_render")
         return int(ns.value), float(ml.value)
