@@ -62,6 +62,10 @@ def parse_args(argv=None):
     p.add_argument("--mse-minibatch", type=int, default=1 << 14)
     p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
     p.add_argument("--guide-alpha", type=float, default=0.5)
+    p.add_argument("--no-serving", action="store_true", help="skip the batched-serving study")
+    p.add_argument("--serve-requests", type=int, default=64)
+    p.add_argument("--serve-spp-max", type=int, default=4,
+                   help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
     p.add_argument("--guide-lr", type=float, default=1e-3)
     return p.parse_args(argv)
 
@@ -123,6 +127,77 @@ def guide_kernel_timing(dev, rows=1 << 20, reps=10):
                      "launches_per_call": prof["guide"][1] / reps}
     g.check()
     return out
+
+
+def serving_study(args, dev):
+    """Batched serving: the same requests served one by one (ugp_render, sequentially) and as one
+    batch (ugp_render_batch: one CUDA graph launch, autotuned tile and pool, shortest first)."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    ns, specs = scenes.serving_batch(args.serve_requests, 8, seed=0, spp_range=(1, args.serve_spp_max))
+    sd = []
+    for i, n in enumerate(ns):
+        sc = scenes.serving_scene(n, seed=i)
+        sd.append((sc, ugp.scene_to_device(sc, device=dev)))
+
+    def make_reqs():
+        out = []
+        for q in specs:
+            sc, (bvh, mats, _, lights) = sd[q.scene]
+            c = sc.camera
+            cam = ugp.camera_struct(c.eye, c.look, c.up, c.vfov_deg, q.width, q.height)
+            out.append(ugp.Request(bvh, mats, cam, lights, q.spp, q.max_depth, seed=q.seed, device=dev))
+        return out
+
+    paths = int(sum(q.width * q.height * q.spp for q in specs))
+    # one by one, in the given order (latency = time until the request's image is done)
+    reqs = make_reqs()
+    rends = {}
+    for q in specs:   # workspaces allocated before timing
+        rends.setdefault((q.width, q.height), ugp.Renderer(q.width, q.height, device=dev))
+    rc = torch.zeros(3, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lat_seq = []
+    for q, spec in zip(reqs, specs):
+        sc, (bvh, mats, _, lights) = sd[spec.scene]
+        rends[(spec.width, spec.height)].render(bvh, mats, q.c.camera, lights, spp=spec.spp, max_depth=spec.max_depth,
+                                                seed=spec.seed, accum=q.accum, accum_sq=q.accum_sq, ray_counts=rc)
+        torch.cuda.synchronize(dev)
+        lat_seq.append(1e3 * (time.perf_counter() - t0))
+    t_seq = time.perf_counter() - t0
+    rays_seq = int(rc[0] + rc[1])
+    ref = [q.accum for q in reqs]
+
+    br = ugp.BatchRenderer(len(specs), pool_log2=20, tile=16, use_graph=True, shortest_first=True, device=dev)
+    t0 = time.perf_counter()
+    (tile, lg), table = br.autotune(make_reqs()[:16], probe_spp=1, pool_log2_range=(20, 22))
+    t_tune = time.perf_counter() - t0
+    br.render(make_reqs())   # builds the graph of the chosen pool once
+    reqs = make_reqs()
+    rc = torch.zeros(3, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    lat = br.render(reqs, ray_counts=rc)
+    torch.cuda.synchronize(dev)
+    t_b = time.perf_counter() - t0
+    rays_b = int(rc[0] + rc[1])
+    rel = max(float(((a - b).abs().max() / (b.abs().max() + 1e-6)).item()) for a, b in zip([q.accum for q in reqs], ref))
+    return {
+        "workload": (f"{len(specs)} requests over 8 room scenes of {min(ns)}-{max(ns)} primitives, "
+                     f"images 256^2/512^2/1024^2, spp log-uniform 1..{args.serve_spp_max}, depth 4..8, all at t=0"),
+        "paths": paths, "rays": rays_b,
+        "batch": {"makespan_ms": 1e3 * t_b, "Mrays_per_s": rays_b / t_b / 1e6,
+                  "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+                  "config": {"tile": tile, "pool": 1 << lg, "graph": True, "order": "shortest first"}},
+        "one_by_one": {"makespan_ms": 1e3 * t_seq, "Mrays_per_s": rays_seq / t_seq / 1e6,
+                       "latency_p50_ms": float(np.percentile(lat_seq, 50)),
+                       "latency_p99_ms": float(np.percentile(lat_seq, 99))},
+        "same_rays": rays_b == rays_seq, "max_rel_diff_images": rel,
+        "autotune": {"seconds": t_tune, "probe": "first 16 requests at 1 spp",
+                     "ms": {f"tile{k[0]}_pool2^{k[1]}": v for k, v in table.items()}},
+    }
 
 
 def equal_time_mse(args, d, mats, scene, dev):
@@ -443,9 +518,12 @@ def run_ugp(args):
 
     guide_perf = None
     mse = None
+    serving = None
     if rank == 0 and world == 1 and not args.no_mse:
         guide_perf = guide_kernel_timing(dev)
         mse = equal_time_mse(args, d, mats, scene, dev)
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_study(args, dev)
 
     if rank == 0:
         clk = clocks.summary()
@@ -464,7 +542,7 @@ def run_ugp(args):
                          "nodes_per_query": nodes_per_query, "prims_per_query": prims_per_query,
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-            "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf,
+            "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -166,7 +166,7 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
 /* Scratch bytes ugp_sample_free_flight needs for n_rays rays: a queue of the rays whose
  * bracketed root has more overlapping intervals than one thread buffers (they are
  * finished by a warp-per-ray pass), and per ray a list of up to 128 primitive slots met
- * by the first pass (576 bytes per ray in all).  The workspace must be 256-byte aligned
+ * by the first pass (580 bytes per ray in all).  The workspace must be 256-byte aligned
  * and is only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
@@ -175,7 +175,7 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  * call cudaMalloc or hand the library a workspace -- for example code that runs while a
  * host application owns every device allocation, or a real-time loop that must not
  * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
- * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.2 MB); every GPU that
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.5 MB); every GPU that
  * loads the library holds it until the process exits.  Without the per-ray slot lists of
  * the regular entry point, its warp pass finds dense intervals by traversal; the results
  * are the same.
@@ -331,7 +331,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 704 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 708 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per
@@ -371,6 +371,66 @@ ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* render_ws, size
                                        int32_t min_steps, void* guide_ws, size_t guide_ws_bytes,
                                        int64_t* n_samples_out, float* mean_loss_out, void* stream);
 
+/* ------------------------------------------------------------------ batched serving
+ * Many independent render requests (own scene, camera, lights, image size, spp and depth)
+ * served together. The paper has no counterpart: it is the serving form of ugp_render.
+ * Work items are (request, sample, square tile of `tile` x `tile` pixels), taken in request
+ * order from one atomic counter into a shared pool of 2^pool_log2 paths: every wave fills the
+ * free pool slots with camera paths of new items, then extends, finishes, shades and
+ * shadow-traces every live path in its own request's scene, and retires the paths that
+ * ended into their request's image. A path draws exactly the Philox numbers ugp_render
+ * draws for that request (counter (pixel, sample, 16 * bounce + slot, 0), key = the
+ * request's seed), so each image equals ugp_render's up to the order of the per-pixel sums.
+ * With use_graph = 1 the waves run inside one CUDA graph launch (a conditional while-node
+ * whose body is one wave; the graph is instantiated once per workspace and pool size and
+ * reused); with use_graph = 0 the host launches the waves and polls a device flag. */
+typedef struct ugp_request {
+  const ugp_bvh* bvh;              /* built scene of the request */
+  const ugp_materials* materials;  /* host struct of device arrays, as for ugp_render */
+  ugp_camera camera;               /* image of camera.width x camera.height pixels */
+  ugp_lights lights;
+  int32_t spp;                     /* samples 0 .. spp-1 of every pixel */
+  int32_t max_depth;               /* scattering vertices per path, 0..14 */
+  int32_t nee, spawn_mode;         /* as in ugp_render_params */
+  uint64_t seed;                   /* Philox key */
+  float* accum_rgb;                /* device, height x width x 3: per-pixel sums ADDED */
+  float* accum_sq_rgb;             /* device, same layout: sums of squares ADDED */
+} ugp_request;
+
+typedef struct ugp_batch_config {
+  int32_t tile;       /* side of a work item's pixel tile: 8, 16 or 32 */
+  int32_t pool_log2;  /* paths in flight: 2^pool_log2, 10..24 */
+  int32_t use_graph;  /* 1: one CUDA graph launch with a device-side loop; 0: host loop */
+  int32_t order;      /* service order: 0 as given, 1 shortest first (pixels x spp x (depth + 1)) */
+} ugp_batch_config;
+
+/* Workspace bytes for batches of up to max_requests requests with this config (path pool,
+ * queues, request table); 0 for a bad argument. */
+size_t ugp_render_batch_workspace_size(int32_t max_requests, const ugp_batch_config* cfg);
+/* Renders the n_req requests (host array) with a workspace sized for max_requests. Waits for
+ * the batch to finish. latency_ms_out (host, n_req doubles, may be NULL) receives each
+ * request's completion time after the batch started (device %globaltimer; 0 for a request
+ * with no paths). ray_counts as for ugp_render. UGP_ERR_ITER_LIMIT if the device-side wave
+ * bound was reached with work left (never expected). A graph built for a workspace must not
+ * be launched concurrently from two streams. */
+ugp_status ugp_render_batch(int32_t n_req, const ugp_request* reqs, const ugp_batch_config* cfg,
+                            int32_t max_requests, void* workspace, size_t workspace_bytes, double* latency_ms_out,
+                            unsigned long long* ray_counts, void* stream);
+
+/* Autotuner of the batch configuration: renders a probe of the batch (every request at
+ * min(spp, probe_spp) samples, accumulating into `scratch`, which must hold
+ * 6 x (largest width x height) floats) with every candidate tile in {8, 16, 32} and pool in
+ * 2^[pool_log2_min, pool_log2_max] whose workspace fits `workspace_bytes`, each once to build
+ * its graph and once timed (CUDA events), and returns the fastest in best_out. ms_out (host,
+ * 3 x (pool_log2_max - pool_log2_min + 1) doubles, pool-major, -1 for skipped candidates,
+ * may be NULL) receives the probe times. Results are cached per device and batch shape
+ * (request count, deepest request, probe paths) and reused when ms_out is NULL.
+ * Synchronises. */
+ugp_status ugp_render_batch_autotune(int32_t n_req, const ugp_request* reqs, int32_t probe_spp, int32_t pool_log2_min,
+                                     int32_t pool_log2_max, int32_t use_graph, void* workspace,
+                                     size_t workspace_bytes, float* scratch, size_t scratch_floats,
+                                     ugp_batch_config* best_out, double* ms_out, void* stream);
+
 /* Optional traversal statistics: when `counters` is a device pointer to 12
  * zero-initialised uint64, later tracing calls on any stream add (atomically)
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
@@ -390,12 +450,14 @@ ugp_status ugp_set_trace_counters(unsigned long long* counters);
  *   2 extend (free flight, per thread), 3 shade, 4 shadow (transmittance),
  *   5 accumulate, 6 standalone queries (ugp_trace_transmittance,
  *   ugp_sample_free_flight), 7 free flight of dense rays (warp per ray), 8 learned guide
- *   (packing, forward, gradient, Adam, training-set selection).
+ *   (packing, forward, gradient, Adam, training-set selection), 9 batched serving (one pair
+ *   around each batch's graph launch or wave loop; graph launches add their kernels to the
+ *   counts after the batch).
  * ugp_profile_end waits for the recorded events, writes the summed milliseconds and
  * launch counts per stage (arrays of UGP_PROFILE_STAGES, host) and stops recording.
  * At most max_records event pairs are kept; later launches are counted but not timed
  * (ugp_profile_end returns UGP_ERR_OVERFLOW then).  Not thread safe. */
-#define UGP_PROFILE_STAGES 9
+#define UGP_PROFILE_STAGES 10
 ugp_status ugp_profile_begin(int32_t max_records);
 ugp_status ugp_profile_end(double* ms_out, int64_t* launches_out);
 

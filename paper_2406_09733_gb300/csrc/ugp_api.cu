@@ -42,9 +42,18 @@ struct Prof {
 };
 static Prof g_prof;
 
+static bool g_prof_suspended = false;
+
+void prof_suspend(bool on) { g_prof_suspended = on; }
+
+void add_launches(int stage, int64_t n) {
+  g_launches += (unsigned long long)n;
+  if (g_prof.on && stage >= 0 && stage < UGP_PROFILE_STAGES) g_prof.launches[stage] += n;
+}
+
 void prof_begin(int stage, cudaStream_t s) {
   (void)stage;
-  if (!g_prof.on) return;
+  if (g_prof_suspended || !g_prof.on) return;
   if (g_prof.used >= g_prof.max_records) {
     g_prof.overflow = true;
     g_prof.open_slot = -1;
@@ -61,6 +70,7 @@ void prof_begin(int stage, cudaStream_t s) {
 }
 
 void prof_end(int stage, cudaStream_t s, int n_kernels) {
+  if (g_prof_suspended) return;
   g_launches += (unsigned long long)n_kernels;
   if (!g_prof.on) return;
   g_prof.launches[stage] += n_kernels;

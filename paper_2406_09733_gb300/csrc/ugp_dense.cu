@@ -113,7 +113,7 @@ __device__ void for_each_candidate(WarpSmem& W, const TraceScene& sc, const Ray&
   warp_traverse(W, sc, ray, lo, hi, lane, st, nn, leaf);
 }
 
-__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueue q, int* __restrict__ prim_out,
+__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQueue q, int* __restrict__ prim_out,
                                                         float* __restrict__ tu_out, float* __restrict__ tsp_out,
                                                         uint8_t* __restrict__ st_out, int spawn_mode,
                                                         unsigned long long* stats, unsigned long long* rays_err) {
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueu
   const int count = *reinterpret_cast<const volatile int*>(q.count);
   const int nwarps = gridDim.x * kDWarps;
   for (int j = blockIdx.x * kDWarps + (threadIdx.x >> 5); j < count; j += nwarps) {
+    const TraceScene sc = q.scenes ? q.scenes[q.scene[j]] : sc0;
     const int idx = q.idx[j];
     float lo = q.lo[j], hi = q.hi[j], Flo = q.Flo[j];
     const float u = q.u[j], u2 = q.u2[j], t0 = q.t0[j], t1 = q.t1[j];
@@ -300,19 +301,27 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc, DenseQueu
 
 }  // namespace
 
+static int g_dense_grid = 0;
+
+ugp_status dense_prepare() {
+  if (g_dense_grid != 0) return UGP_OK;
+  const size_t smem = sizeof(WarpSmem) * kDWarps;
+  UGP_CUDA_CHECK(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int dev = 0, sms = 0, per_sm = 0;
+  UGP_CUDA_CHECK(cudaGetDevice(&dev));
+  UGP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  UGP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, 32 * kDWarps, smem));
+  g_dense_grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  return UGP_OK;
+}
+
 ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
                         float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
                         unsigned long long* rays_err, cudaStream_t stream) {
-  static int grid = 0;
+  const ugp_status ps = dense_prepare();
+  if (ps != UGP_OK) return ps;
+  const int grid = g_dense_grid;
   const size_t smem = sizeof(WarpSmem) * kDWarps;
-  if (grid == 0) {
-    UGP_CUDA_CHECK(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    int dev = 0, sms = 0, per_sm = 0;
-    UGP_CUDA_CHECK(cudaGetDevice(&dev));
-    UGP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    UGP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, 32 * kDWarps, smem));
-    grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-  }
   prof_begin(kStDense, stream);
   k_dense<<<grid, 32 * kDWarps, smem, stream>>>(sc, q, prim_out, t_u_out, t_spawn_out, status_out, spawn_mode, stats,
                                                rays_err);

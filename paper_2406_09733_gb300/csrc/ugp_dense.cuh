@@ -16,10 +16,12 @@ struct DenseQueue {
   float *ox, *oy, *oz, *dx, *dy, *dz, *t0, *t1;
   int* excl;
   int* nlist;    // primitive slots the scan recorded for the ray (> kListCap: list incomplete)
+  int* scene;    // index of the ray's scene in `scenes` (batched rendering)
   const int* list;  // per-ray slot lists, kListCap ints at list + idx * kListCap (NULL: none)
+  const TraceScene* scenes;  // device table of scenes (NULL: every ray uses the launch's scene)
 };
 
-constexpr int kDenseCols = 16;
+constexpr int kDenseCols = 17;
 // Slots of the primitives the scan met before its window end, kept per ray so the dense pass
 // can rebuild the window's intervals without another traversal.
 constexpr int kListCap = 128;
@@ -41,13 +43,16 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   q.t0 = F(12); q.t1 = F(13);
   q.excl = reinterpret_cast<int*>(F(14));
   q.nlist = reinterpret_cast<int*>(F(15));
+  q.scene = reinterpret_cast<int*>(F(16));
   q.list = nullptr;
+  q.scenes = nullptr;
   return q;
 }
 
 // Appends one ray (threads of a warp that call together share one atomic).
 __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float lo, float hi, float Flo, float u,
-                                           float u2, float3 o, float3 d, float t0, float t1, int excl, int nlist) {
+                                           float u2, float3 o, float3 d, float t0, float t1, int excl, int nlist,
+                                           int scene = 0) {
   namespace cg = cooperative_groups;
   cg::coalesced_group g = cg::coalesced_threads();
   int base = 0;
@@ -60,12 +65,16 @@ __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float l
   q.t0[j] = t0; q.t1[j] = t1;
   q.excl[j] = excl;
   q.nlist[j] = nlist;
+  if (q.scenes) q.scene[j] = scene;
 }
 
 // Finishes every queued ray: prim_out[idx], t_spawn_out[idx] (the spawn distance, or t_u when
 // spawn_mode == 1) and, when not NULL, t_u_out[idx] and status_out[idx].  `stats` as for the
 // trace counters (nodes, primitives of the warp pass are added to [0], [1]), `rays_err` (may be
 // NULL) counts rays that ended with a non-zero status.
+// One-time setup of the finish kernel (shared-memory attribute, grid size); launch_dense calls it,
+// and callers that capture launches into a graph call it before capturing.
+ugp_status dense_prepare();
 ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
                         float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
                         unsigned long long* rays_err, cudaStream_t stream);

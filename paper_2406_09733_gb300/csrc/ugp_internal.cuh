@@ -61,9 +61,14 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Launch accounting and optional event timing (defined in ugp_api.cu).  Wrap each launch:
 //   prof_begin(stage, stream); kernel<<<...>>>(...); prof_end(stage, stream, n_kernels);
 enum ProfStage { kStBuild = 0, kStCamera = 1, kStExtend = 2, kStShade = 3, kStShadow = 4, kStAccum = 5, kStQuery = 6,
-                 kStDense = 7, kStGuide = 8 };
+                 kStDense = 7, kStGuide = 8, kStBatch = 9 };
 void prof_begin(int stage, cudaStream_t s);
 void prof_end(int stage, cudaStream_t s, int n_kernels = 1);
+// While suspended, prof_begin / prof_end neither record events nor count launches (used while
+// launches are captured into a graph, whose bodies cannot hold event records).
+void prof_suspend(bool on);
+// Adds launches that ran inside a graph to the counts.
+void add_launches(int stage, int64_t n);
 
 bool valid_bvh(const ugp_bvh* b);
 

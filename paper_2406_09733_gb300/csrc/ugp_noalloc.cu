@@ -13,10 +13,10 @@
 namespace ugp {
 namespace {
 
-// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header and 16 columns of
+// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header and kDenseCols columns of
 // 4-byte entries, each padded to 256 bytes (the layout of dense_queue_at).
 constexpr int64_t kNoallocMaxRays = UGP_NOALLOC_MAX_RAYS;
-constexpr size_t kNoallocBytes = 256 + 16 * ((size_t(kNoallocMaxRays) * 4 + 255) & ~size_t(255));
+constexpr size_t kNoallocBytes = 256 + kDenseCols * ((size_t(kNoallocMaxRays) * 4 + 255) & ~size_t(255));
 
 static __device__ __align__(256) unsigned char g_ff_scratch[kNoallocBytes];
 

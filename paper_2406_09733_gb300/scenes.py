@@ -433,3 +433,40 @@ def guide_batch(n: int, seed: int = 0, cfg: GuideConfig | None = None, zero_frac
     w = 10.0 ** rng.uniform(-2, 2, n)
     w[rng.uniform(size=n) < zero_frac] = 0.0
     return GuideBatch(_f32(x), unit_vectors(rng, n), unit_vectors(rng, n), _f32(w))
+
+
+# ------------------------------------------------------------------ batched serving inputs
+@dataclass
+class RequestSpec:
+    """One render request of a serving batch: which scene, image size, samples, depth, seed."""
+    scene: int
+    width: int
+    height: int
+    spp: int
+    max_depth: int
+    seed: int
+    nee: bool = True
+
+
+def serving_batch(n_requests: int = 64, n_scenes: int = 8, seed: int = 0, n_range=(1e4, 1e6),
+                  sizes=(256, 512, 1024), spp_range=(1, 64), depth_range=(4, 8)):
+    """Requests of a serving batch: scenes from the room generator with primitive counts
+    log-uniform over n_range (cluster count scaled with n), requests with a size drawn from
+    `sizes` (square images), spp log-uniform over spp_range (integers) and depth uniform over
+    depth_range; every request names one of the scenes. Returns (scene sizes, requests)."""
+    rng = _rng(seed)
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    ns = [int(round(np.exp(rng.uniform(lo, hi)))) for _ in range(n_scenes)]
+    reqs = []
+    for i in range(n_requests):
+        size = int(rng.choice(sizes))
+        spp = int(np.floor(np.exp(rng.uniform(np.log(spp_range[0]), np.log(spp_range[1] + 1)))))
+        spp = min(max(spp, spp_range[0]), spp_range[1])
+        depth = int(rng.integers(depth_range[0], depth_range[1] + 1))
+        reqs.append(RequestSpec(int(rng.integers(0, n_scenes)), size, size, spp, depth, 1000 + i))
+    return ns, reqs
+
+
+def serving_scene(n: int, seed: int, width: int = 256, height: int = 256) -> Scene:
+    """A room scene of n primitives for serving (aggregate clusters scaled with n)."""
+    return room_scene(n, seed=seed, width=width, height=height, n_clusters=max(1, int(round(300 * n / 1e6))))

@@ -502,3 +502,115 @@ def mixture_sample(mix, u3, stream=None):
     _check(lib().ugp_guide_mixture_sample(n, _p(mix), _p(u3), _p(wi), _p(pdf), C.c_void_p(_stream(stream))),
            "ugp_guide_mixture_sample")
     return wi, pdf
+
+
+# ------------------------------------------------------------------ batched serving
+class UgpRequest(C.Structure):
+    _fields_ = [("bvh", vp), ("materials", C.POINTER(UgpMaterials)), ("camera", UgpCamera), ("lights", UgpLights),
+                ("spp", C.c_int32), ("max_depth", C.c_int32), ("nee", C.c_int32), ("spawn_mode", C.c_int32),
+                ("seed", C.c_uint64), ("accum_rgb", vp), ("accum_sq_rgb", vp)]
+
+
+class UgpBatchConfig(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("pool_log2", C.c_int32), ("use_graph", C.c_int32), ("order", C.c_int32)]
+
+
+def _register_batch(L):
+    L.ugp_render_batch_workspace_size.restype = C.c_size_t
+    L.ugp_render_batch_workspace_size.argtypes = [C.c_int32, C.POINTER(UgpBatchConfig)]
+    L.ugp_render_batch.restype = C.c_int
+    L.ugp_render_batch.argtypes = [C.c_int32, C.POINTER(UgpRequest), C.POINTER(UgpBatchConfig), C.c_int32, vp,
+                                   C.c_size_t, C.POINTER(C.c_double), vp, vp]
+    L.ugp_render_batch_autotune.restype = C.c_int
+    L.ugp_render_batch_autotune.argtypes = [C.c_int32, C.POINTER(UgpRequest), C.c_int32, C.c_int32, C.c_int32,
+                                            C.c_int32, vp, C.c_size_t, vp, C.c_size_t, C.POINTER(UgpBatchConfig),
+                                            C.POINTER(C.c_double), vp]
+
+
+_EXTRA.append(_register_batch)
+
+
+class Request:
+    """One render request of a batch; accumulators are created if not given."""
+
+    def __init__(self, bvh: Bvh, mats: Materials, camera: UgpCamera, lights: UgpLights, spp: int, max_depth: int,
+                 seed: int = 0, nee: bool = True, spawn_mode: int = 0, accum=None, accum_sq=None, device="cuda"):
+        shape = (camera.height, camera.width, 3)
+        self.accum = accum if accum is not None else torch.zeros(shape, dtype=torch.float32, device=device)
+        self.accum_sq = accum_sq if accum_sq is not None else torch.zeros(shape, dtype=torch.float32, device=device)
+        for t, nm in ((self.accum, "accum"), (self.accum_sq, "accum_sq")):
+            _dev(t, torch.float32, nm)
+            if tuple(t.shape) != shape:
+                raise ValueError(f"{nm} must have shape {shape}")
+        self.bvh, self.mats = bvh, mats
+        self.c = UgpRequest(C.c_void_p(bvh.handle).value, C.pointer(mats.c), camera, lights, int(spp), int(max_depth),
+                            int(bool(nee)), int(spawn_mode), int(seed), _p(self.accum).value,
+                            _p(self.accum_sq).value)
+
+
+def batch_workspace_size(max_requests: int, tile: int, pool_log2: int) -> int:
+    cfg = UgpBatchConfig(int(tile), int(pool_log2), 1, 1)
+    return int(lib().ugp_render_batch_workspace_size(int(max_requests), C.byref(cfg)))
+
+
+class BatchRenderer:
+    """Serves batches of render requests in one wavefront over a shared path pool (one CUDA graph
+    launch per batch). The workspace is sized for `max_requests` and the largest pool used."""
+
+    def __init__(self, max_requests: int, pool_log2: int = 20, tile: int = 16, use_graph: bool = True,
+                 shortest_first: bool = True, device="cuda"):
+        self.max_requests = int(max_requests)
+        self.cfg = UgpBatchConfig(int(tile), int(pool_log2), int(bool(use_graph)), int(bool(shortest_first)))
+        self.device = device
+        self.workspace = None
+        self._ensure(int(pool_log2))
+
+    def _ensure(self, pool_log2):
+        nb = batch_workspace_size(self.max_requests, self.cfg.tile, pool_log2)
+        if nb == 0:
+            raise UgpError("bad batch configuration")
+        if self.workspace is None or self.workspace.numel() < nb:
+            self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
+
+    def render(self, requests, ray_counts=None, stream=None):
+        """Renders all requests; returns the per-request completion times in ms (numpy array)."""
+        import numpy as np
+        n = len(requests)
+        if n > self.max_requests:
+            raise ValueError("more requests than the workspace was sized for")
+        arr = (UgpRequest * max(n, 1))(*[r.c for r in requests])
+        lat = (C.c_double * max(n, 1))()
+        if ray_counts is not None:
+            _dev(ray_counts, torch.int64, "ray_counts")
+        self._ensure(self.cfg.pool_log2)
+        _check(lib().ugp_render_batch(n, arr, C.byref(self.cfg), self.max_requests, _p(self.workspace),
+                                      self.workspace.numel(), lat, _p(ray_counts), C.c_void_p(_stream(stream))),
+               "ugp_render_batch")
+        return np.array(lat[:n])
+
+    def autotune(self, requests, probe_spp: int = 1, pool_log2_range=(18, 22), stream=None):
+        """Picks tile and pool size on a probe of `requests`; sets and returns the config and the
+        table of probe times {(tile, pool_log2): ms}."""
+        lo, hi = pool_log2_range
+        n = len(requests)
+        for lg in range(lo, hi + 1):
+            nb = batch_workspace_size(max(n, self.max_requests), 8, lg)
+            if self.workspace is None or self.workspace.numel() < nb:
+                self.workspace = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        px = max(r.c.camera.width * r.c.camera.height for r in requests)
+        scratch = torch.zeros(6 * px, dtype=torch.float32, device=self.device)
+        arr = (UgpRequest * n)(*[r.c for r in requests])
+        best = UgpBatchConfig()
+        ms = (C.c_double * (3 * (hi - lo + 1)))()
+        _check(lib().ugp_render_batch_autotune(n, arr, int(probe_spp), int(lo), int(hi), self.cfg.use_graph,
+                                               _p(self.workspace), self.workspace.numel(), _p(scratch),
+                                               scratch.numel(), C.byref(best), ms, C.c_void_p(_stream(stream))),
+               "ugp_render_batch_autotune")
+        table = {}
+        k = 0
+        for lg in range(lo, hi + 1):
+            for t in (8, 16, 32):
+                table[(t, lg)] = ms[k]
+                k += 1
+        self.cfg = UgpBatchConfig(best.tile, best.pool_log2, best.use_graph, self.cfg.order)
+        return (best.tile, best.pool_log2), table

@@ -80,3 +80,14 @@ def test_guide_struct_layouts_match_the_header():
     assert ugp.UgpGuide.kappa_max.offset == 76
     assert ctypes.sizeof(ugp.UgpRenderParams) == 48
     assert ugp.UgpRenderParams.guide.offset == 32 and ugp.UgpRenderParams.guide_alpha.offset == 40
+
+
+def test_batch_entry_points_validate_on_host(libugp):
+    from paper_2406_09733_gb300 import ugp
+    libugp.ugp_render_batch_workspace_size.restype = ctypes.c_size_t
+    cfg = ugp.UgpBatchConfig(16, 12, 1, 0)
+    assert libugp.ugp_render_batch_workspace_size(4, ctypes.byref(cfg)) > (1 << 12) * 24 * 4
+    bad = ugp.UgpBatchConfig(12, 12, 1, 0)
+    st = libugp.ugp_render_batch(0, None, ctypes.byref(bad), 4, None, ctypes.c_size_t(0), None, None, None)
+    assert st == 1
+    assert ctypes.sizeof(ugp.UgpRequest) == 168 and ugp.UgpRequest.seed.offset == 144

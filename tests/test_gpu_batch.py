@@ -1,0 +1,136 @@
+"""Batched serving: every request of a batch equals its single-request render.
+
+A batched path draws the same Philox numbers as ugp_render does for that request (counter
+(pixel, sample, 16 bounce + slot), key = the request's seed), so the per-pixel sums agree up to
+the order of the floating-point additions across samples, and the extend and shadow query
+counts agree exactly.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2406_09733_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ugp():
+    from paper_2406_09733_gb300 import ugp as U
+    U.lib()
+    return U
+
+
+def _scene_dev(ugp, n, seed, lighting="A"):
+    s = scenes.room_scene(n, seed=seed, lighting=lighting, width=8, height=8, n_clusters=max(1, n // 3000))
+    return s, ugp.scene_to_device(s)
+
+
+def _requests(ugp, scenes_dev, specs):
+    out = []
+    for sc_i, W, H, spp, depth, seed, nee, spawn in specs:
+        s, (bvh, mats, cam, lights) = scenes_dev[sc_i]
+        c = s.camera
+        camera = ugp.camera_struct(c.eye, c.look, c.up, c.vfov_deg, W, H)
+        out.append(ugp.Request(bvh, mats, camera, lights, spp, depth, seed=seed, nee=nee, spawn_mode=spawn))
+    return out
+
+
+SPECS = [  # scene, width, height, spp, depth, seed, nee, spawn_mode
+    (0, 40, 30, 3, 4, 11, True, 0),    # image not a multiple of the tile
+    (1, 64, 64, 2, 6, 12, True, 0),
+    (2, 96, 80, 1, 3, 13, False, 0),
+    (0, 33, 17, 4, 8, 14, True, 1),    # spawn at x_{t_u}
+    (1, 16, 16, 0, 4, 15, True, 0),    # no samples
+    (2, 128, 72, 2, 0, 16, True, 0),   # depth 0: emission and escape only
+]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("tile,pool_log2", [(16, 12), (8, 14), (32, 16)])
+def test_batch_equals_single_renders(ugp, use_graph, tile, pool_log2):
+    sd = [_scene_dev(ugp, 20_000, 1), _scene_dev(ugp, 50_000, 2, "B"), _scene_dev(ugp, 8_000, 3)]
+    reqs = _requests(ugp, sd, SPECS)
+    br = ugp.BatchRenderer(max_requests=8, pool_log2=pool_log2, tile=tile, use_graph=use_graph)
+    rc = torch.zeros(3, dtype=torch.int64, device="cuda")
+    lat = br.render(reqs, ray_counts=rc)
+    torch.cuda.synchronize()
+    rc1 = torch.zeros(3, dtype=torch.int64, device="cuda")
+    for (sc_i, W, H, spp, depth, seed, nee, spawn), q in zip(SPECS, reqs):
+        s, (bvh, mats, cam, lights) = sd[sc_i]
+        c = s.camera
+        camera = ugp.camera_struct(c.eye, c.look, c.up, c.vfov_deg, W, H)
+        r = ugp.Renderer(W, H)
+        a, a2 = r.render(bvh, mats, camera, lights, spp=spp, max_depth=depth, seed=seed, nee=nee, spawn_mode=spawn,
+                         ray_counts=rc1)
+        torch.cuda.synchronize()
+        tol = 2e-6 * max(spp, 1)
+        assert torch.allclose(q.accum, a, rtol=tol, atol=1e-6), (sc_i, W, H, (q.accum - a).abs().max().item())
+        assert torch.allclose(q.accum_sq, a2, rtol=tol, atol=1e-6)
+    assert rc[0].item() == rc1[0].item() and rc[1].item() == rc1[1].item(), (rc.tolist(), rc1.tolist())
+    assert rc[2].item() == 0
+    # latencies: positive for requests with paths, zero for the empty one, ordered loosely by request
+    assert lat[4] == 0.0
+    assert np.all(lat[[0, 1, 2, 3, 5]] > 0)
+
+
+def test_batch_reuses_graph_and_accumulates(ugp):
+    sd = [_scene_dev(ugp, 10_000, 4)]
+    specs = [(0, 48, 48, 2, 4, 21, True, 0), (0, 32, 32, 1, 5, 22, True, 0)]
+    reqs = _requests(ugp, sd, specs)
+    br = ugp.BatchRenderer(max_requests=4, pool_log2=13, tile=16, use_graph=True)
+    br.render(reqs)
+    first = [q.accum.clone() for q in reqs]
+    br.render(reqs)            # the cached graph, same seeds: every sum doubles
+    torch.cuda.synchronize()
+    for q, f in zip(reqs, first):
+        assert torch.allclose(q.accum, 2 * f, rtol=1e-6, atol=1e-6)
+
+
+def test_batch_many_requests_small_pool(ugp):
+    """More work than the pool holds at once: many claim rounds, regeneration every wave."""
+    sd = [_scene_dev(ugp, 15_000, 5), _scene_dev(ugp, 5_000, 6)]
+    specs = [(i % 2, 24 + 8 * (i % 3), 16 + 8 * (i % 2), 1 + i % 3, 2 + i % 5, 100 + i, True, 0) for i in range(20)]
+    reqs = _requests(ugp, sd, specs)
+    br = ugp.BatchRenderer(max_requests=32, pool_log2=10, tile=8, use_graph=True)
+    lat = br.render(reqs)
+    torch.cuda.synchronize()
+    for (sc_i, W, H, spp, depth, seed, nee, spawn), q in zip(specs, reqs):
+        s, (bvh, mats, cam, lights) = sd[sc_i]
+        c = s.camera
+        a, _ = ugp.Renderer(W, H).render(bvh, mats, ugp.camera_struct(c.eye, c.look, c.up, c.vfov_deg, W, H), lights,
+                                         spp=spp, max_depth=depth, seed=seed)
+        assert torch.allclose(q.accum, a, rtol=2e-6 * spp, atol=1e-6)
+    assert np.all(lat > 0)
+
+
+def test_autotune_picks_a_valid_config(ugp):
+    sd = [_scene_dev(ugp, 20_000, 7)]
+    specs = [(0, 64, 64, 2, 4, 31 + i, True, 0) for i in range(4)]
+    reqs = _requests(ugp, sd, specs)
+    br = ugp.BatchRenderer(max_requests=4, pool_log2=12, tile=16)
+    (tile, lg), table = br.autotune(reqs, probe_spp=1, pool_log2_range=(12, 14))
+    assert tile in (8, 16, 32) and 12 <= lg <= 14
+    assert table[(tile, lg)] == min(v for v in table.values() if v >= 0)
+    # the probe wrote only to scratch: the requests' images are untouched
+    assert all(torch.count_nonzero(q.accum).item() == 0 for q in reqs)
+    lat = br.render(reqs)
+    assert np.all(lat > 0)
+
+
+def test_shortest_first_serves_small_requests_first(ugp):
+    sd = [_scene_dev(ugp, 20_000, 8)]
+    # large request first in the given order; shortest-first must finish the small ones earlier
+    specs = [(0, 256, 256, 4, 6, 41, True, 0), (0, 16, 16, 1, 2, 42, True, 0), (0, 32, 32, 1, 3, 43, True, 0)]
+    reqs = _requests(ugp, sd, specs)
+    br = ugp.BatchRenderer(max_requests=4, pool_log2=14, tile=16, shortest_first=True)
+    lat = br.render(reqs)
+    assert lat[1] < lat[0] and lat[2] < lat[0]
+    reqs2 = _requests(ugp, sd, specs)
+    br2 = ugp.BatchRenderer(max_requests=4, pool_log2=14, tile=16, shortest_first=False)
+    br2.render(reqs2)
+    torch.cuda.synchronize()
+    for a, b in zip(reqs, reqs2):
+        assert torch.allclose(a.accum, b.accum, rtol=1e-5, atol=1e-6)
