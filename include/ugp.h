@@ -331,7 +331,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 708 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 716 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per

@@ -54,6 +54,8 @@ struct BCtl {
   int n_req, tile, tile_px, pool, max_waves, status, more;
   unsigned long long* rays;        // caller's ray counters of this batch (may be NULL)
   unsigned long long dense_err;    // rays of the warp finish that ended with a non-zero status
+  int scan_next;                   // ray counter of the persistent scan of this wave
+  int dense_slots;                 // slots of this wave's finish table (the live paths)
 };
 static_assert(sizeof(BCtl) <= 256, "control block");
 
@@ -64,6 +66,7 @@ struct BPaths {
 };
 
 struct BState {
+  int64_t pool;
   BCtl* ctl;
   const BReq* reqs;
   const TraceScene* scenes;
@@ -78,7 +81,7 @@ struct BState {
 // Kernel parameters hold only workspace addresses (fixed for a cached graph); per-call values
 // such as the caller's ray counters live in the control block.
 
-constexpr int kPathCols = 24;  // PathSoA (18) + tu, req, pix, smp, bounce (+1 spare)
+constexpr int kPathCols = 25;  // PathSoA (20) + tu, req, pix, smp, bounce
 
 __device__ __forceinline__ int find_request(const BReq* reqs, int n, long long item) {
   int lo = 0, hi = n - 1;
@@ -117,6 +120,7 @@ __global__ void k_b_init(BState S, int n_req, unsigned long long items_total, in
     c.more = items_total > 0 ? 1 : 0;
     c.rays = rays;
     c.dense_err = 0ull;
+    c.scan_next = 0;
     *S.dq.count = 0;
     c.start_ns = umma::global_timer_ns();
   }
@@ -138,6 +142,7 @@ __global__ void k_b_claim(BState S) {
   c.free_top -= c.claim_n;
   c.work_next += n;
   c.live[cur] += c.claim_n;
+  c.dense_slots = c.live[cur];
 }
 
 // New camera paths for the claimed items (tile pixels outside the image become empty paths,
@@ -171,45 +176,66 @@ __global__ void __launch_bounds__(256) k_b_regen(BState S) {
       P.ps.lr[slot] = 0.f; P.ps.lg[slot] = 0.f; P.ps.lb[slot] = 0.f;
       P.ps.pdf_prev[slot] = -1.f;
       P.ps.excl[slot] = -1;
+      prepare_extend(P.ps, slot, R.L, R.key, p, sample, 0, R.cam.eye, d);
     }
     S.live[cur][c.claim_base + k] = slot;
   }
 }
 
+// Rays of a wave: the live paths, each in its own request's scene.
+struct BatchScanSrc {
+  BState S;
+  int cur, count_;
+  int i_, p, r, qf;
+  float tq, u, u2;
+  TraceScene sc;
+  __device__ int count() const { return count_; }
+  __device__ TraceScene scene() const { return sc; }
+  __device__ bool begin(int i, ScanState& s, float& uo) {
+    i_ = i;
+    p = S.live[cur][i];
+    const int pix = S.P.pix[p];
+    if (pix < 0) {  // empty path of a partial tile
+      dense_none(S.dq, i);
+      return false;
+    }
+    r = S.P.req[p];
+    const BReq& R = S.reqs[r];
+    sc = S.scenes[r];
+    const PathSoA& ps = S.P.ps;
+    const float3 o = f3(ps.ox[p], ps.oy[p], ps.oz[p]), d = f3(ps.dx[p], ps.dy[p], ps.dz[p]);
+    tq = ps.tq[p];
+    qf = ps.qflag[p];
+    s.ray = make_ray(o, d);
+    s.t0 = 0.f;
+    s.t1 = qf ? tq : 1e30f;
+    s.ex = ps.excl[p];
+    s.list = S.dq.list ? const_cast<int*>(S.dq.list) + size_t(p) * kListCap : nullptr;
+    u = ps.fu[p];
+    u2 = ps.fu2[p];
+    uo = u;
+    return true;
+  }
+  __device__ void finish(const ScanState& s, const FFResult& fr) {
+    if (fr.pending) dense_push(S.dq, i_, p, fr.lo, fr.hi, fr.Flo, u, u2, s.ray.o, s.ray.d, 0.f, s.t1, s.ex, fr.nlist, r);
+    else dense_none(S.dq, i_);
+    S.P.ps.prim[p] = fr.prim;
+    S.P.ps.tsp[p] = fr.t_spawn;
+    S.P.tu[p] = fr.t_u;
+    unsigned long long* rays = S.ctl->rays;
+    if (rays) {
+      atomicAdd(rays, 1ull);
+      if (s.st != UGP_RAY_OK) atomicAdd(rays + 2, 1ull);
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kFFBlock) k_b_extend(BState S) {
   __shared__ FFSmem sm;
   const BCtl& c = *S.ctl;
   const int cur = c.wave & 1;
-  const int count = c.live[cur];
-  const BPaths& P = S.P;
-  for (int i = int(blockIdx.x * blockDim.x + threadIdx.x); i < count; i += int(gridDim.x * blockDim.x)) {
-    const int p = S.live[cur][i];
-    const int pix = P.pix[p];
-    if (pix < 0) continue;
-    const int r = P.req[p];
-    const BReq& R = S.reqs[r];
-    const TraceScene sc = S.scenes[r];
-    const float3 o = f3(P.ps.ox[p], P.ps.oy[p], P.ps.oz[p]), d = f3(P.ps.dx[p], P.ps.dy[p], P.ps.dz[p]);
-    float tq = 1e30f;
-    const int qf = quad_hit(R.L, o, d, tq);
-    const float t1 = qf ? tq : 1e30f;
-    const int bounce = P.bounce[p];
-    const float4 U = rng(R.key, pix, P.smp[p], bounce, 0);
-    Ctx cx{sm, int(threadIdx.x), sc, make_ray(o, d), 0.f, t1, P.ps.excl[p], 0u, 0u, UGP_RAY_OK,
-           S.dq.list ? const_cast<int*>(S.dq.list) + size_t(p) * kListCap : nullptr, 0};
-    const FFResult fr = ff_sample(cx, U.x, U.y);
-    if (fr.pending) dense_push(S.dq, p, fr.lo, fr.hi, fr.Flo, U.x, U.y, o, d, 0.f, t1, cx.ex, fr.nlist, r);
-    P.ps.prim[p] = fr.prim;
-    P.ps.tsp[p] = fr.t_spawn;
-    P.tu[p] = fr.t_u;
-    P.ps.tq[p] = tq;
-    P.ps.qflag[p] = qf;
-    unsigned long long* rays = c.rays;
-    if (rays) {
-      atomicAdd(rays, 1ull);
-      if (cx.st != UGP_RAY_OK) atomicAdd(rays + 2, 1ull);
-    }
-  }
+  BatchScanSrc src{S, cur, c.live[cur], 0, 0, 0, 0, 0.f, 0.f, 0.f, TraceScene{}};
+  scan_persistent(sm, src, &S.ctl->scan_next);
 }
 
 __global__ void __launch_bounds__(128) k_b_shade(BState S) {
@@ -288,6 +314,7 @@ __global__ void __launch_bounds__(128) k_b_shade(BState S) {
             P.ps.br[p] = beta.x; P.ps.bg[p] = beta.y; P.ps.bb[p] = beta.z;
             P.ps.excl[p] = k;
             P.bounce[p] = bounce + 1;
+            prepare_extend(P.ps, p, L, R.key, pix, sample, bounce + 1, x, wi);
             alive = true;
           }
         }
@@ -354,6 +381,7 @@ __global__ void k_b_cond(BState S, cudaGraphConditionalHandle handle, int use_gr
   c.live[cur] = 0;
   c.shadow = 0;
   c.retire = 0;
+  c.scan_next = 0;
   *S.dq.count = 0;
   c.wave += 1;
   int more = (c.live[nxt] > 0 || c.work_next < c.items_total) ? 1 : 0;
@@ -397,6 +425,7 @@ BatchLayout batch_layout(int max_req, int64_t pool) {
 
 BState batch_state(char* ws, const BatchLayout& L, int64_t pool) {
   BState S;
+  S.pool = pool;
   const size_t col = align256(size_t(pool) * 4);
   auto F = [&](size_t base, int k) { return reinterpret_cast<float*>(ws + base + k * col); };
   auto I = [&](size_t base, int k) { return reinterpret_cast<int*>(ws + base + k * col); };
@@ -408,12 +437,13 @@ BState batch_state(char* ws, const BatchLayout& L, int64_t pool) {
   PathSoA& ps = S.P.ps;
   ps = PathSoA{F(L.paths, 0), F(L.paths, 1), F(L.paths, 2), F(L.paths, 3), F(L.paths, 4), F(L.paths, 5),
                F(L.paths, 6), F(L.paths, 7), F(L.paths, 8), F(L.paths, 9), F(L.paths, 10), F(L.paths, 11),
-               F(L.paths, 12), I(L.paths, 13), I(L.paths, 14), F(L.paths, 15), F(L.paths, 16), I(L.paths, 17)};
-  S.P.tu = F(L.paths, 18);
-  S.P.req = I(L.paths, 19);
-  S.P.pix = I(L.paths, 20);
-  S.P.smp = I(L.paths, 21);
-  S.P.bounce = I(L.paths, 22);
+               F(L.paths, 12), I(L.paths, 13), I(L.paths, 14), F(L.paths, 15), F(L.paths, 16), I(L.paths, 17),
+               F(L.paths, 18), F(L.paths, 19)};
+  S.P.tu = F(L.paths, 20);
+  S.P.req = I(L.paths, 21);
+  S.P.pix = I(L.paths, 22);
+  S.P.smp = I(L.paths, 23);
+  S.P.bounce = I(L.paths, 24);
   S.live[0] = I(L.live0, 0);
   S.live[1] = I(L.live1, 0);
   S.retire = I(L.retire, 0);
@@ -446,7 +476,8 @@ struct WaveGrids {
   int regen, ext, shade, shadow, retire;
 };
 WaveGrids wave_grids(int64_t pool) {
-  return WaveGrids{grid_of((const void*)k_b_regen, 256, pool), grid_of((const void*)k_b_extend, kFFBlock, pool),
+  const int ext_need = int((pool + kFFBlock - 1) / kFFBlock), ext_cap = scan_grid((const void*)k_b_extend);
+  return WaveGrids{grid_of((const void*)k_b_regen, 256, pool), ext_need < ext_cap ? ext_need : ext_cap,
                    grid_of((const void*)k_b_shade, 128, pool), grid_of((const void*)k_b_shadow, kTrBlock, pool),
                    grid_of((const void*)k_b_retire, 256, pool)};
 }
@@ -458,8 +489,8 @@ ugp_status launch_wave(const BState& S, const WaveGrids& g, cudaGraphConditional
   k_b_regen<<<g.regen, 256, 0, st>>>(S);
   k_b_extend<<<g.ext, kFFBlock, 0, st>>>(S);
   // every queued ray names its scene (S.dq.scenes), so the launch's own scene is unused
-  ugp_status s = launch_dense(TraceScene{}, S.dq, S.P.ps.prim, S.P.tu, S.P.ps.tsp, nullptr, 0, nullptr,
-                              &S.ctl->dense_err, st);
+  ugp_status s = launch_dense(TraceScene{}, S.dq, 0, &S.ctl->dense_slots, S.pool, S.P.ps.prim, S.P.tu, S.P.ps.tsp,
+                              nullptr, 0, nullptr, &S.ctl->dense_err, st);
   if (s != UGP_OK) return s;
   k_b_shade<<<g.shade, 128, 0, st>>>(S);
   k_b_shadow<<<g.shadow, kTrBlock, 0, st>>>(S);

@@ -113,16 +113,21 @@ __device__ void for_each_candidate(WarpSmem& W, const TraceScene& sc, const Ray&
   warp_traverse(W, sc, ray, lo, hi, lane, st, nn, leaf);
 }
 
-__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQueue q, int* __restrict__ prim_out,
+__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQueue q, int64_t n_host,
+                                                        const int* n_dev, int* __restrict__ prim_out,
                                                         float* __restrict__ tu_out, float* __restrict__ tsp_out,
                                                         uint8_t* __restrict__ st_out, int spawn_mode,
                                                         unsigned long long* stats, unsigned long long* rays_err) {
   extern __shared__ __align__(16) unsigned char dsm[];
   WarpSmem& W = reinterpret_cast<WarpSmem*>(dsm)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int count = *reinterpret_cast<const volatile int*>(q.count);
+  const int count = n_dev ? *reinterpret_cast<const volatile int*>(n_dev) : int(n_host);
   const int nwarps = gridDim.x * kDWarps;
+  // slot j to warp j mod (warps), so the rays in flight together are neighbours in the table;
+  // empty slots are skipped by the whole warp
   for (int j = blockIdx.x * kDWarps + (threadIdx.x >> 5); j < count; j += nwarps) {
+  if (__ldg(q.idx + j) < 0) continue;
+  {
     const TraceScene sc = q.scenes ? q.scenes[q.scene[j]] : sc0;
     const int idx = q.idx[j];
     float lo = q.lo[j], hi = q.hi[j], Flo = q.Flo[j];
@@ -297,6 +302,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
     }
     __syncwarp();
   }
+  }
 }
 
 }  // namespace
@@ -315,16 +321,17 @@ ugp_status dense_prepare() {
   return UGP_OK;
 }
 
-ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
-                        float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
-                        unsigned long long* rays_err, cudaStream_t stream) {
+ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int64_t n_host, const int* n_dev,
+                        int64_t max_slots, int* prim_out, float* t_u_out, float* t_spawn_out, uint8_t* status_out,
+                        int spawn_mode, unsigned long long* stats, unsigned long long* rays_err, cudaStream_t stream) {
   const ugp_status ps = dense_prepare();
   if (ps != UGP_OK) return ps;
-  const int grid = g_dense_grid;
+  const int64_t need = (max_slots + 32 * kDWarps - 1) / (32 * kDWarps);
+  const int grid = int(need < g_dense_grid ? (need > 0 ? need : 1) : g_dense_grid);
   const size_t smem = sizeof(WarpSmem) * kDWarps;
   prof_begin(kStDense, stream);
-  k_dense<<<grid, 32 * kDWarps, smem, stream>>>(sc, q, prim_out, t_u_out, t_spawn_out, status_out, spawn_mode, stats,
-                                               rays_err);
+  k_dense<<<grid, 32 * kDWarps, smem, stream>>>(sc, q, n_host, n_dev, prim_out, t_u_out, t_spawn_out, status_out,
+                                               spawn_mode, stats, rays_err);
   prof_end(kStDense, stream);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;

@@ -1,5 +1,7 @@
-// Queue of free-flight rays whose t_u is bracketed but whose bracket holds more intervals than a
-// thread's buffer: the per-thread pass appends them, a warp-per-ray pass finishes them.
+// Rays whose t_u the scan has bracketed, for the warp-per-ray finish. The table has one slot per
+// scanned ray (its index in the scan's launch): the scan writes the ray's record there, or marks
+// the slot empty (idx = -1), so no counter is shared between lanes; the finish pass walks the
+// slots 32 at a time and takes the filled ones.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -8,10 +10,10 @@
 
 namespace ugp {
 
-// Structure of arrays in caller-provided scratch memory; `count` is a device int.
+// Structure of arrays in caller-provided scratch memory (a 256-byte header, then the columns).
 struct DenseQueue {
-  int* count;
-  int* idx;      // output slot of the ray
+  int* count;    // header ints: [0] unused, [1] ray counter of the persistent scan
+  int* idx;      // output index of the ray (-1: empty slot)
   float *lo, *hi, *Flo, *u, *u2;
   float *ox, *oy, *oz, *dx, *dy, *dz, *t0, *t1;
   int* excl;
@@ -49,15 +51,10 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   return q;
 }
 
-// Appends one ray (threads of a warp that call together share one atomic).
-__device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float lo, float hi, float Flo, float u,
+// Fills slot j with a bracketed ray whose results go to output index idx.
+__device__ __forceinline__ void dense_push(const DenseQueue& q, int j, int idx, float lo, float hi, float Flo, float u,
                                            float u2, float3 o, float3 d, float t0, float t1, int excl, int nlist,
                                            int scene = 0) {
-  namespace cg = cooperative_groups;
-  cg::coalesced_group g = cg::coalesced_threads();
-  int base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(q.count, int(g.size()));
-  const int j = g.shfl(base, 0) + int(g.thread_rank());
   q.idx[j] = idx;
   q.lo[j] = lo; q.hi[j] = hi; q.Flo[j] = Flo; q.u[j] = u; q.u2[j] = u2;
   q.ox[j] = o.x; q.oy[j] = o.y; q.oz[j] = o.z;
@@ -67,6 +64,8 @@ __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float l
   q.nlist[j] = nlist;
   if (q.scenes) q.scene[j] = scene;
 }
+// Marks slot j empty (the ray escaped or ended in the scan).
+__device__ __forceinline__ void dense_none(const DenseQueue& q, int j) { q.idx[j] = -1; }
 
 // Finishes every queued ray: prim_out[idx], t_spawn_out[idx] (the spawn distance, or t_u when
 // spawn_mode == 1) and, when not NULL, t_u_out[idx] and status_out[idx].  `stats` as for the
@@ -75,8 +74,10 @@ __device__ __forceinline__ void dense_push(const DenseQueue& q, int idx, float l
 // One-time setup of the finish kernel (shared-memory attribute, grid size); launch_dense calls it,
 // and callers that capture launches into a graph call it before capturing.
 ugp_status dense_prepare();
-ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int* prim_out, float* t_u_out,
-                        float* t_spawn_out, uint8_t* status_out, int spawn_mode, unsigned long long* stats,
-                        unsigned long long* rays_err, cudaStream_t stream);
+// Slots 0 .. n-1 are walked, n = *n_dev when n_dev is not NULL, else n_host; max_slots bounds n
+// (grid size).
+ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int64_t n_host, const int* n_dev,
+                        int64_t max_slots, int* prim_out, float* t_u_out, float* t_spawn_out, uint8_t* status_out,
+                        int spawn_mode, unsigned long long* stats, unsigned long long* rays_err, cudaStream_t stream);
 
 }  // namespace ugp

@@ -56,8 +56,8 @@ struct GuidedShade {
   int n;             // paths per frame
 };
 
-__global__ void __launch_bounds__(256) k_camera(CameraDev cam, int n, uint2 key, int sample, PathSoA ps, int* q,
-                                                int* cnt, int* dense_cnt) {
+__global__ void __launch_bounds__(256) k_camera(CameraDev cam, LightsDev L, int n, uint2 key, int sample, PathSoA ps,
+                                                int* q, int* cnt, int* dense_cnt, int* scan_next) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const float3 d = camera_dir(cam, key, p, sample);
     ps.ox[p] = cam.eye.x; ps.oy[p] = cam.eye.y; ps.oz[p] = cam.eye.z;
@@ -66,19 +66,59 @@ __global__ void __launch_bounds__(256) k_camera(CameraDev cam, int n, uint2 key,
     ps.lr[p] = 0.f; ps.lg[p] = 0.f; ps.lb[p] = 0.f;
     ps.pdf_prev[p] = -1.f;
     ps.excl[p] = -1;
+    prepare_extend(ps, p, L, key, p, sample, 0, cam.eye, d);
     q[p] = p;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *cnt = n;
     *dense_cnt = 0;
+    *scan_next = 0;
   }
 }
+
+// Rays of a bounce: the live paths in the queue.
+struct PathScanSrc {
+  TraceScene sc;
+  int spawn_mode, count_;
+  PathSoA ps;
+  const int* q;
+  DenseQueue dq;
+  unsigned long long *rays, *stats;
+  int i_, p, qf;
+  float tq, u, u2;
+  __device__ int count() const { return count_; }
+  __device__ TraceScene scene() const { return sc; }
+  __device__ bool begin(int i, ScanState& s, float& uo) {
+    i_ = i;
+    p = q[i];
+    const float3 o = f3(ps.ox[p], ps.oy[p], ps.oz[p]), d = f3(ps.dx[p], ps.dy[p], ps.dz[p]);
+    tq = ps.tq[p];
+    qf = ps.qflag[p];
+    s.ray = make_ray(o, d);
+    s.t0 = 0.f;
+    s.t1 = qf ? tq : 1e30f;
+    s.ex = ps.excl[p];
+    s.list = dq.list ? const_cast<int*>(dq.list) + size_t(p) * kListCap : nullptr;
+    u = ps.fu[p];
+    u2 = ps.fu2[p];
+    uo = u;
+    return true;
+  }
+  __device__ void finish(const ScanState& s, const FFResult& r) {
+    if (r.pending) dense_push(dq, i_, p, r.lo, r.hi, r.Flo, u, u2, s.ray.o, s.ray.d, 0.f, s.t1, s.ex, r.nlist);
+    else dense_none(dq, i_);
+    ps.prim[p] = r.prim;
+    ps.tsp[p] = spawn_mode == 1 ? r.t_u : r.t_spawn;
+    if (s.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
+    if (stats) add_counters(stats, s.n_nodes, s.n_prims, 1u, 1u, r.pending ? 1u : 0u);
+  }
+};
 
 __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
                                                      int spawn_mode, PathSoA ps, const int* __restrict__ q,
                                                      const int* cnt, int* reset_next, int* reset_shadow,
                                                      unsigned long long* rays, unsigned long long* stats,
-                                                     DenseQueue dq) {
+                                                     DenseQueue dq, int* scan_next) {
   __shared__ FFSmem sm;
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -86,33 +126,20 @@ __global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L,
     *reset_shadow = 0;
     if (rays) atomicAdd(rays, (unsigned long long)count);
   }
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    const int p = q[i];
-    const float3 o = f3(ps.ox[p], ps.oy[p], ps.oz[p]), d = f3(ps.dx[p], ps.dy[p], ps.dz[p]);
-    float tq = 1e30f;
-    const int qf = quad_hit(L, o, d, tq);
-    const float t1 = qf ? tq : 1e30f;
-    const float4 U = rng(key, p, sample, bounce, 0);
-    Ctx c{sm, int(threadIdx.x), sc, make_ray(o, d), 0.f, t1, ps.excl[p], 0u, 0u, UGP_RAY_OK,
-          dq.list ? const_cast<int*>(dq.list) + size_t(p) * kListCap : nullptr, 0};
-    const FFResult r = ff_sample(c, U.x, U.y);
-    if (r.pending) dense_push(dq, p, r.lo, r.hi, r.Flo, U.x, U.y, o, d, 0.f, t1, c.ex, r.nlist);
-    ps.prim[p] = r.prim;
-    ps.tsp[p] = spawn_mode == 1 ? r.t_u : r.t_spawn;
-    ps.tq[p] = tq;
-    ps.qflag[p] = qf;
-    if (c.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
-    if (stats) add_counters(stats, c.n_nodes, c.n_prims, 1u, 1u, r.pending ? 1u : 0u);
-  }
+  PathScanSrc src{sc, spawn_mode, count, ps, q, dq, rays, stats, 0, 0, 0, 0.f, 0.f, 0.f};
+  scan_persistent(sm, src, scan_next);
 }
 
 template <bool kGuided>
 __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 key, int sample, int bounce, int max_depth,
                                                int nee, PathSoA ps, const int* __restrict__ q, const int* cnt,
                                                int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow,
-                                               int* dense_cnt, GuidedShade gs) {
+                                               int* dense_cnt, int* scan_next, GuidedShade gs) {
   const int count = load_count(cnt);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *dense_cnt = 0;  // the dense pass of this bounce has run
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the extend and dense passes of this bounce have run
+    *dense_cnt = 0;
+    *scan_next = 0;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
     const int p = q[i];
     float3 beta = f3(ps.br[p], ps.bg[p], ps.bb[p]);
@@ -216,6 +243,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
         beta = beta * wgt;
         if (beta.x > 0.f || beta.y > 0.f || beta.z > 0.f) {
           ps.pdf_prev[p] = pdf_s;
+          prepare_extend(ps, p, L, key, p, sample, bounce + 1, x, wi);
           if (kGuided && gs.log) {
             const int64_t e = int64_t(bounce) * gs.n + p;
             float* const* c = gs.L.c;
@@ -378,7 +406,7 @@ RenderLayout render_layout(int64_t n, int max_depth = -1) {
   RenderLayout L;
   size_t off = 0;
   const size_t col = align256(size_t(n) * 4);
-  L.state = off;   off += 18 * col;
+  L.state = off;   off += 20 * col;
   L.queues = off;  off += 2 * col;
   L.shadow = off;  off += 12 * col;
   L.counts = off;  off += 256;
@@ -485,12 +513,14 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   auto I = [&](size_t base, int k) { return reinterpret_cast<int*>(ws + base + k * col); };
   PathSoA ps{F(RL.state, 0), F(RL.state, 1), F(RL.state, 2), F(RL.state, 3), F(RL.state, 4), F(RL.state, 5),
              F(RL.state, 6), F(RL.state, 7), F(RL.state, 8), F(RL.state, 9), F(RL.state, 10), F(RL.state, 11),
-             F(RL.state, 12), I(RL.state, 13), I(RL.state, 14), F(RL.state, 15), F(RL.state, 16), I(RL.state, 17)};
+             F(RL.state, 12), I(RL.state, 13), I(RL.state, 14), F(RL.state, 15), F(RL.state, 16), I(RL.state, 17),
+             F(RL.state, 18), F(RL.state, 19)};
   ShadowSoA sh{I(RL.shadow, 0), F(RL.shadow, 1), F(RL.shadow, 2), F(RL.shadow, 3), F(RL.shadow, 4),
                F(RL.shadow, 5), F(RL.shadow, 6), F(RL.shadow, 7), I(RL.shadow, 8), F(RL.shadow, 9),
                F(RL.shadow, 10), F(RL.shadow, 11)};
   int* queue[2] = {I(RL.queues, 0), I(RL.queues, 1)};
-  int* counts = reinterpret_cast<int*>(ws + RL.counts);  // [0], [1] queue lengths, [2] shadow
+  int* counts = reinterpret_cast<int*>(ws + RL.counts);  // [0], [1] queue lengths, [2] shadow, [3] scan rays
+  int* scan_next = counts + 3;
   DenseQueue dq = dense_queue_at(ws + RL.dense, n);
   dq.list = reinterpret_cast<const int*>(ws + RL.lists);
 
@@ -529,18 +559,18 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   for (int si = 0; si < params->spp; ++si) {
     const int sample = params->spp_begin + si;
     prof_begin(kStCamera, st);
-    k_camera<<<g_cam, 256, 0, st>>>(cd, int(n), key, sample, ps, queue[0], counts + 0, dq.count);
+    k_camera<<<g_cam, 256, 0, st>>>(cd, Ld, int(n), key, sample, ps, queue[0], counts + 0, dq.count, scan_next);
     prof_end(kStCamera, st);
     int cur = 0;
     for (int b = 0; b <= params->max_depth; ++b) {
       const int nxt = 1 - cur;
       prof_begin(kStExtend, st);
       k_extend<<<g_ext, kFFBlock, 0, st>>>(sc, Ld, key, sample, b, params->spawn_mode, ps, queue[cur], counts + cur,
-                                            counts + nxt, counts + 2, ray_counts, stats, dq);
+                                            counts + nxt, counts + 2, ray_counts, stats, dq, scan_next);
       prof_end(kStExtend, st);
       {
-        const ugp_status ds = launch_dense(sc, dq, ps.prim, nullptr, ps.tsp, nullptr, params->spawn_mode, stats,
-                                           ray_counts ? ray_counts + 2 : nullptr, st);
+        const ugp_status ds = launch_dense(sc, dq, 0, counts + cur, n, ps.prim, nullptr, ps.tsp, nullptr,
+                                           params->spawn_mode, stats, ray_counts ? ray_counts + 2 : nullptr, st);
         if (ds != UGP_OK) return ds;
       }
       if (guide && b < params->max_depth) {
@@ -554,11 +584,12 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
       prof_begin(kStShade, st);
       if (guide)
         k_shade<true><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
-                                                counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count, gs);
+                                                counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count,
+                                                scan_next, gs);
       else
         k_shade<false><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps,
                                                  queue[cur], counts + cur, queue[nxt], counts + nxt, sh, counts + 2,
-                                                 dq.count, gs);
+                                                 dq.count, scan_next, gs);
       prof_end(kStShade, st);
       if (params->nee && Ld.has_quad) {
         prof_begin(kStShadow, st);

@@ -22,6 +22,7 @@ struct PathSoA {
   float* tsp;            // spawn distance along the current ray
   float* tq;             // distance to the area light along the current ray
   int* qflag;            // 0 no light hit, 1 front face, 2 back face
+  float *fu, *fu2;       // free-flight uniforms of the current ray (u, u2)
 };
 
 struct ShadowSoA {
@@ -149,6 +150,20 @@ inline ugp_status camera_dev(const ugp_camera* camera, const char* fn, CameraDev
   cd.height = H;
   *out = cd;
   return UGP_OK;
+}
+
+// Inputs of the next free flight of path slot `slot` (ray o + t d at `bounce`): the light-hit
+// distance and face, and the free-flight uniforms (Philox slot 0). Computed where the ray is made
+// (camera or shading), so the scan only loads them.
+__device__ __forceinline__ void prepare_extend(const PathSoA& ps, int slot, const LightsDev& L, uint2 key, int pixel,
+                                               int sample, int bounce, float3 o, float3 d) {
+  float tq = 1e30f;
+  const int qf = quad_hit(L, o, d, tq);
+  const float4 U = rng(key, pixel, sample, bounce, 0);
+  ps.tq[slot] = tq;
+  ps.qflag[slot] = qf;
+  ps.fu[slot] = U.x;
+  ps.fu2[slot] = U.y;
 }
 
 // Pinhole camera ray through pixel p of the image at the Philox jitter of (sample, bounce 15).
