@@ -330,23 +330,24 @@ __global__ void __launch_bounds__(kTrBlock) k_b_shadow(BState S) {
   __shared__ int stk[kTrStack * kTrBlock];
   const int count = S.ctl->shadow;
   const BPaths& P = S.P;
-  for (int j = int(blockIdx.x * blockDim.x + threadIdx.x); j < count; j += int(gridDim.x * blockDim.x)) {
-    const int p = S.sh.path[j];
-    const TraceScene sc = S.scenes[P.req[p]];
-    const Ray ray = make_ray(f3(S.sh.ox[j], S.sh.oy[j], S.sh.oz[j]), f3(S.sh.dx[j], S.sh.dy[j], S.sh.dz[j]));
-    TrStats ts{0u, 0u, UGP_RAY_OK};
-    const float tau = tr_optical_depth(sc, ray, 0.f, S.sh.dist[j], S.sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
-    const float T = fmaxf(0.f, 1.f - tau);
-    if (T > 0.f) {
-      P.ps.lr[p] += T * S.sh.cr[j];
-      P.ps.lg[p] += T * S.sh.cg[j];
-      P.ps.lb[p] += T * S.sh.cb[j];
-    }
-    unsigned long long* rays = S.ctl->rays;
-    if (rays) {
-      atomicAdd(rays + 1, 1ull);
-      if (ts.st != UGP_RAY_OK) atomicAdd(rays + 2, 1ull);
-    }
+  // one ray per thread over a grid sized for the pool: the hardware spreads the blocks
+  const int j = int(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= count) return;
+  const int p = S.sh.path[j];
+  const TraceScene sc = S.scenes[P.req[p]];
+  const Ray ray = make_ray(f3(S.sh.ox[j], S.sh.oy[j], S.sh.oz[j]), f3(S.sh.dx[j], S.sh.dy[j], S.sh.dz[j]));
+  TrStats ts{0u, 0u, UGP_RAY_OK};
+  const float tau = tr_optical_depth(sc, ray, 0.f, S.sh.dist[j], S.sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
+  const float T = fmaxf(0.f, 1.f - tau);
+  if (T > 0.f) {
+    P.ps.lr[p] += T * S.sh.cr[j];
+    P.ps.lg[p] += T * S.sh.cg[j];
+    P.ps.lb[p] += T * S.sh.cb[j];
+  }
+  unsigned long long* rays = S.ctl->rays;
+  if (rays) {
+    atomicAdd(rays + 1, 1ull);
+    if (ts.st != UGP_RAY_OK) atomicAdd(rays + 2, 1ull);
   }
 }
 
@@ -478,7 +479,7 @@ struct WaveGrids {
 WaveGrids wave_grids(int64_t pool) {
   const int ext_need = int((pool + kFFBlock - 1) / kFFBlock), ext_cap = scan_grid((const void*)k_b_extend);
   return WaveGrids{grid_of((const void*)k_b_regen, 256, pool), ext_need < ext_cap ? ext_need : ext_cap,
-                   grid_of((const void*)k_b_shade, 128, pool), grid_of((const void*)k_b_shadow, kTrBlock, pool),
+                   grid_of((const void*)k_b_shade, 128, pool), int((pool + kTrBlock - 1) / kTrBlock),
                    grid_of((const void*)k_b_retire, 256, pool)};
 }
 

@@ -271,20 +271,21 @@ __global__ void __launch_bounds__(kTrBlock) k_shadow(TraceScene sc, ShadowSoA sh
   __shared__ int stk[kTrStack * kTrBlock];
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0 && rays) atomicAdd(rays + 1, (unsigned long long)count);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
-    const Ray ray = make_ray(f3(sh.ox[j], sh.oy[j], sh.oz[j]), f3(sh.dx[j], sh.dy[j], sh.dz[j]));
-    TrStats ts{0u, 0u, UGP_RAY_OK};
-    const float tau = tr_optical_depth(sc, ray, 0.f, sh.dist[j], sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
-    const float T = fmaxf(0.f, 1.f - tau);
-    if (T > 0.f) {
-      const int p = sh.path[j];
-      ps.lr[p] += T * sh.cr[j];
-      ps.lg[p] += T * sh.cg[j];
-      ps.lb[p] += T * sh.cb[j];
-    }
-    if (ts.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
-    if (stats) add_counters(stats + 6, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);
+  // one ray per thread over a grid sized for the longest queue: the hardware spreads the blocks
+  const int j = int(blockIdx.x * blockDim.x + threadIdx.x);
+  if (j >= count) return;
+  const Ray ray = make_ray(f3(sh.ox[j], sh.oy[j], sh.oz[j]), f3(sh.dx[j], sh.dy[j], sh.dz[j]));
+  TrStats ts{0u, 0u, UGP_RAY_OK};
+  const float tau = tr_optical_depth(sc, ray, 0.f, sh.dist[j], sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
+  const float T = fmaxf(0.f, 1.f - tau);
+  if (T > 0.f) {
+    const int p = sh.path[j];
+    ps.lr[p] += T * sh.cr[j];
+    ps.lg[p] += T * sh.cg[j];
+    ps.lb[p] += T * sh.cb[j];
   }
+  if (ts.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
+  if (stats) add_counters(stats + 6, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);
 }
 
 __global__ void __launch_bounds__(256) k_accumulate(int n, PathSoA ps, float* __restrict__ acc, float* __restrict__ acc2) {
@@ -519,7 +520,8 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
                F(RL.shadow, 5), F(RL.shadow, 6), F(RL.shadow, 7), I(RL.shadow, 8), F(RL.shadow, 9),
                F(RL.shadow, 10), F(RL.shadow, 11)};
   int* queue[2] = {I(RL.queues, 0), I(RL.queues, 1)};
-  int* counts = reinterpret_cast<int*>(ws + RL.counts);  // [0], [1] queue lengths, [2] shadow, [3] scan rays
+  // [0], [1] queue lengths, [2] shadow rays, [3] scan ray counter
+  int* counts = reinterpret_cast<int*>(ws + RL.counts);
   int* scan_next = counts + 3;
   DenseQueue dq = dense_queue_at(ws + RL.dense, n);
   dq.list = reinterpret_cast<const int*>(ws + RL.lists);
@@ -554,7 +556,7 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   const int g_cam = grid_for((const void*)k_camera, 256, n);
   const int g_ext = grid_for((const void*)k_extend, kFFBlock, n);
   const int g_shade = guide ? grid_for((const void*)k_shade<true>, 128, n) : grid_for((const void*)k_shade<false>, 128, n);
-  const int g_shadow = grid_for((const void*)k_shadow, kTrBlock, n);
+  const int g_shadow = int((n + kTrBlock - 1) / kTrBlock);
   const int g_acc = grid_for((const void*)k_accumulate, 256, n);
   for (int si = 0; si < params->spp; ++si) {
     const int sample = params->spp_begin + si;
