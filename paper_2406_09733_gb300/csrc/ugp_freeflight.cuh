@@ -27,11 +27,16 @@
 //    solve F(t_u) = u by a safeguarded Newton iteration with warp-reduced F and F' = 1/2 sum G
 //    (Eq. 9), and run the race as a warp argmin.
 //
-// The scan runs one BVH node per loop step on persistent lanes: a lane whose ray is done takes
-// a new one, and the idle lanes of a warp fetch together (one atomic) once kRefill of them are
-// idle, so a warp does not wait for its slowest ray before starting new ones (per-ray work
-// varies several-fold; on camera rays of a 1M-primitive room the mean over a warp is 0.58 of
-// its maximum).
+// The scan runs on persistent lanes: a lane whose ray is done takes a new one, and the idle
+// lanes of a warp fetch together (one atomic) once kRefill of them are idle, so a warp does not
+// wait for its slowest ray before starting new ones (per-ray work varies several-fold; on camera
+// rays of a 1M-primitive room the mean over a warp is 0.58 of its maximum). Each loop step is
+// either a node step (every lane with nodes left visits one) or a leaf step (every lane with
+// held-back primitives tests one and bins it): primitives met in node steps are held back
+// until kLeafBatch lanes have some (or a lane's queue is nearly full or its traversal is over),
+// so the expensive primitive test and binning run with most lanes together instead of inside a
+// node step that most lanes skip. Holding a primitive back can only delay a lowering of the
+// pruning limit, never skip a node that matters.
 #include "ugp_dense.cuh"
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
@@ -39,9 +44,26 @@
 
 namespace ugp {
 
+constexpr int kLeafQ = 4;      // primitives a lane may hold back before testing them
+constexpr int kLeafBatch = 16;  // lanes with held-back primitives that start a joint leaf phase
+
+// Bins hold 1/2 I in fixed point, units of 2^-30, with saturating adds: integer sums do not depend
+// on the order the contributions arrive in, so a ray's result does not depend on which rays share
+// its warp. Bins before the crossing bin sum to less than u <= 1; a bin that saturates (>= 2) lies
+// at or after it, where only "exceeds u" matters. Contributions below 2^-31 are dropped.
+constexpr float kBinScale = 1073741824.f;         // 2^30
+constexpr float kBinUnit = 9.313225746154785e-10f;  // 2^-30
+
+__device__ __forceinline__ int bin_add(int b, float v) {
+  const float f = fminf(fmaxf(v, 0.f) * kBinScale, 2147483520.f);
+  const long long t = (long long)b + (long long)__float2int_rn(f);
+  return t > 2147483647ll ? 2147483647 : int(t);
+}
+
 struct FFSmem {
-  float bin[kB][kFFBlock];
+  int bin[kB][kFFBlock];     // fixed-point bins
   int stk[kFFStack][kFFBlock];
+  int lq[kLeafQ][kFFBlock];  // held-back primitive slots
 };
 
 // A ray as handed to and returned from the scan (Src::begin fills the ray fields, the driver
@@ -90,8 +112,9 @@ struct FFResult {
 static __device__ FFResult scan_result(FFSmem& sm, int tid, const ScanState& s, bool traversed) {
   FFResult r{-1, s.t1, s.t1, false, 0.f, 0.f, 0.f, 0};
   if (!traversed || s.st != UGP_RAY_OK || s.jc == kB) return r;  // F(end) <= u: escape
-  float Flo = 0.f;
-  for (int k = 0; k < s.jc; ++k) Flo += FB(bin, k);
+  long long acc = 0;
+  for (int k = 0; k < s.jc; ++k) acc += FB(bin, k);
+  const float Flo = float(acc) * kBinUnit;
   r.pending = true;
   r.lo = s.lo + s.w * float(s.jc);
   r.hi = s.jc + 1 >= kB ? s.hi : s.lo + s.w * float(s.jc + 1);
@@ -138,12 +161,15 @@ struct ScanBins {
     const int kend = jc < kB ? jc + 1 : kB;
     for (int k = j; k < kend && edge(k) < y; ++k) {
       const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
-      if (xa < ya) c.sm.bin[k][c.tid] += seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th);
+      if (xa < ya)
+        c.sm.bin[k][c.tid] = bin_add(c.sm.bin[k][c.tid], seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn,
+                                                                             h.ts, h.s, h.e0, h.th));
     }
-    float acc = 0.f;
+    const long long tgt = (long long)(target * kBinScale);  // u is a multiple of 2^-24: exact
+    long long acc = 0;
     for (int k = 0; k < jc; ++k) {
       acc += c.sm.bin[k][c.tid];
-      if (acc > target) {
+      if (acc > tgt) {
         jc = k;
         limit = edge(jc + 1);
         break;
@@ -174,8 +200,8 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
   ScanCtx c{sm, int(threadIdx.x), src.scene(), make_ray(make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 1.f)), 0.f,
             0.f, -1, 0u, 0u, UGP_RAY_OK, nullptr, 0};
   ScanState s;
-  bool busy = false, exhausted = false;
-  int node = 0, sp = 0, jc = kB;
+  bool busy = false, exhausted = false, tdone = false;
+  int node = 0, sp = 0, jc = kB, nq = 0;
   float lo = 0.f, hi = 0.f, w = 0.f, target = 0.f, limit = 0.f;
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !busy && !exhausted);
@@ -211,11 +237,13 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
               src.finish(s, scan_result(sm, c.tid, s, false));
             } else {
               w = (hi - lo) / float(kB);
-              for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0.f;
+              for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0;
               jc = kB;
               limit = hi;
               node = 0;
               sp = 0;
+              nq = 0;
+              tdone = false;
               busy = true;
             }
           }
@@ -226,11 +254,18 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       if (__all_sync(kFull, exhausted)) break;
       continue;
     }
-    if (!busy) continue;
-    // ---- one node of the nearest-first traversal
-    bool finished = false;
-    {
-      ScanBins v{c, lo, hi, w, target, jc};
+    const unsigned pend = __ballot_sync(kFull, busy && nq > 0);
+    const bool urgent = __any_sync(kFull, busy && (nq >= kLeafQ - 1 || (tdone && nq > 0)));
+    if (pend && (__popc(pend) >= kLeafBatch || urgent)) {
+      // ---- leaf step: one held-back primitive per lane
+      if (busy && nq > 0) {
+        --nq;
+        ScanBins v{c, lo, hi, w, target, jc};
+        v.leaf(sm.lq[nq][c.tid], limit);
+        jc = v.jc;
+      }
+    } else if (busy && !tdone) {
+      // ---- node step: one node of the nearest-first traversal
       if (unsigned(node) >= unsigned(c.sc.n_nodes)) {
         c.st = UGP_RAY_BAD_NODE;
         node = 0;
@@ -257,16 +292,18 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
         if (ch[k] >= 0) continue;
         hc[k] = false;
         ++c.n_prims;
-        v.leaf(~ch[k], limit);
+        sm.lq[nq][c.tid] = ~ch[k];  // nq <= kLeafQ - 2 here: a node adds at most two
+        ++nq;
       }
-      jc = v.jc;
       if (c.st != UGP_RAY_OK) {
-        finished = true;
+        tdone = true;
+        nq = 0;
       } else if (hc[0] && hc[1]) {
         const bool first0 = en[0] <= en[1];
         if (sp == kFFStack) {
           c.st = UGP_RAY_STACK_OVERFLOW;
-          finished = true;
+          tdone = true;
+          nq = 0;
         } else {
           sm.stk[sp][c.tid] = first0 ? ch[1] : ch[0];
           ++sp;
@@ -277,13 +314,13 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       } else if (hc[1]) {
         node = ch[1];
       } else if (sp == 0) {
-        finished = true;
+        tdone = true;
       } else {
         --sp;
         node = sm.stk[sp][c.tid];
       }
     }
-    if (finished) {
+    if (busy && tdone && nq == 0) {
       s.lo = lo;
       s.hi = hi;
       s.w = w;
