@@ -22,7 +22,7 @@ namespace ugp {
 namespace {
 
 constexpr int kDWarps = 4;    // rays in flight per block
-constexpr int kDCap = 512;    // intervals one warp holds
+constexpr int kDCap = 256;    // intervals one warp holds
 constexpr int kDStack = 512;  // shared traversal stack of one warp
 constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
