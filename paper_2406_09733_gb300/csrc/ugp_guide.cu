@@ -40,9 +40,7 @@ __global__ void __launch_bounds__(256) k_guide_pack(const float* __restrict__ pa
     const int l = t / (kGWidth * kGWidth), o = (t / kGWidth) % kGWidth, i = t % kGWidth;
     const float w = o < guide_out_dim(l) ? params[guide_w_off(l) + o * kGWidth + i] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(w);
-    // W_l: B operand of X W_l^T (rows = outputs); W_l^T: B operand of dZ W_l (rows = inputs)
-    *reinterpret_cast<__nv_bfloat16*>(img + kImgW + l * kImgTile + umma::canon_off(o, i, 64)) = h;
-    *reinterpret_cast<__nv_bfloat16*>(img + kImgWT + l * kImgTile + umma::canon_off(i, o, 64)) = h;
+    *reinterpret_cast<__nv_bfloat16*>(img + kImgW + l * kImgTile + umma::tile_off(o, i, 64)) = h;
   } else if (t < 5 * kGWidth * kGWidth + 5 * kGWidth) {
     const int u = t - 5 * kGWidth * kGWidth, l = u / kGWidth, o = u % kGWidth;
     reinterpret_cast<float*>(img + kImgBias)[u] = o < guide_out_dim(l) ? params[guide_b_off(l) + o] : 0.f;

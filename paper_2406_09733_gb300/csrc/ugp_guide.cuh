@@ -38,14 +38,13 @@ __host__ __device__ constexpr int guide_b_off(int l) { return guide_w_off(l) + g
 static_assert(guide_b_off(kGLayers) + kGOut == UGP_GUIDE_NPARAMS, "guide parameter count");
 
 // Shared-memory image of the network (the guide kernels bulk-copy it from the workspace):
-//   [0, 40960)       W_l for l = 0..4 as the B operand of X W_l^T (rows = out, padded to 64)
+//   [0, 40960)       W_l for l = 0..4, 64 x 64 tiles (rows = outputs, head padded with zero rows),
+//                    the K-major B operand of X W_l^T and the MN-major B operand of dZ W_l
 //   [40960, 42240)   biases, FP32, 64 per layer (head padded with zeros)
-//   [42240, 83200)   W_l^T for l = 0..4 as the B operand of dZ W_l (rows = in, K = out)
 constexpr uint32_t kImgW = 0;
 constexpr uint32_t kImgTile = kGWidth * kGWidth * 2;  // 8192
 constexpr uint32_t kImgBias = 5 * kImgTile;           // 40960
-constexpr uint32_t kImgWT = kImgBias + 5 * kGWidth * 4;  // 42240
-constexpr uint32_t kImgBytes = kImgWT + 5 * kImgTile;    // 83200
+constexpr uint32_t kImgBytes = kImgBias + 5 * kGWidth * 4;  // 42240
 
 struct GuideCfgDev {
   float3 lo, inv_ext;  // position box: xn = (x - lo) * inv_ext

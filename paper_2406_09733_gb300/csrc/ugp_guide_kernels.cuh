@@ -11,11 +11,13 @@
 // Training (k_guide_grad) runs the forward pass of a tile, the loss gradient of the head in
 // the epilogue, and the backward pass layer by layer:
 //   dW_l += dZ_l^T X_l   M = 128 (64 output rows + 64 unused), N = 80 (64 inputs, a ones
-//                        column that yields the bias gradient, 15 zero columns), K = 128 rows
-//   dX_l  = dZ_l W_l     M = 128, N = 64, K = 64
-// The five dW accumulators stay in tensor memory across all tiles of the block (5 x 80
-// columns) and are written once per block as a partial sum; a second kernel adds the partials
-// in a fixed order, so the gradient is deterministic.
+//                        column that yields the bias gradient, 15 unused), K = 128 rows;
+//                        both operands MN-major views of the row-major tiles dZ_l and X_l
+//   dX_l  = dZ_l W_l     M = 128, N = 64, K = 64; W_l as an MN-major view of its tile
+// so no operand is ever transposed in shared memory. The five dW accumulators stay in tensor
+// memory across all tiles of the block (5 x 80 columns) and are written once per block as a
+// partial sum; a second kernel adds the partials in a fixed order, so the gradient is
+// deterministic.
 #pragma once
 #include "ugp_guide.cuh"
 #include "ugp_internal.cuh"
@@ -67,8 +69,9 @@ namespace gk {
 
 using namespace umma;
 
-constexpr uint32_t kIdesc64 = idesc_bf16_f32(128, 64);
-constexpr uint32_t kIdesc80 = idesc_bf16_f32(128, 80);
+constexpr uint32_t kIdescFwd = idesc_bf16_f32(128, 64);        // X W^T: both K-major
+constexpr uint32_t kIdescDX = idesc_bf16_f32(128, 64, 0, 1);    // dZ W: B MN-major
+constexpr uint32_t kIdescDW = idesc_bf16_f32(128, 80, 1, 1);    // dZ^T X: both MN-major
 constexpr uint32_t kXTile = 128 * kGWidth * 2;  // 16384: one 128 x 64 BF16 activation tile
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -76,7 +79,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Writes row r (64 values) of a K-major 128-row tile as BF16.
+// Writes row r (64 values) of a 128-row tile as BF16.
 __device__ __forceinline__ void store_row(uint8_t* tile, int r, const float (&v)[kGWidth]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -85,15 +88,15 @@ __device__ __forceinline__ void store_row(uint8_t* tile, int r, const float (&v)
     q.y = pack_bf16x2(v[8 * c + 2], v[8 * c + 3]);
     q.z = pack_bf16x2(v[8 * c + 4], v[8 * c + 5]);
     q.w = pack_bf16x2(v[8 * c + 6], v[8 * c + 7]);
-    *reinterpret_cast<uint4*>(tile + canon_off(uint32_t(r), uint32_t(8 * c), 128u)) = q;
+    *reinterpret_cast<uint4*>(tile + tile_off(uint32_t(r), uint32_t(8 * c), 128u)) = q;
   }
 }
 
-// Reads row r of a K-major 128-row BF16 tile as raw 16-bit values.
+// Reads row r of a 128-row BF16 tile as raw 16-bit values.
 __device__ __forceinline__ void load_row_bits(const uint8_t* tile, int r, uint16_t (&h)[kGWidth]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const uint4 q = *reinterpret_cast<const uint4*>(tile + canon_off(uint32_t(r), uint32_t(8 * c), 128u));
+    const uint4 q = *reinterpret_cast<const uint4*>(tile + tile_off(uint32_t(r), uint32_t(8 * c), 128u));
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -118,13 +121,26 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, float (&v)[kCols]) {
   }
 }
 
-// Issues one layer: D = A B^T over `ksteps` K = 16 slices (A slices a_stride bytes apart, B
-// slices b_stride apart), then commits to the mbarrier. Called by one thread.
-__device__ __forceinline__ void issue(uint32_t d, uint32_t a, uint32_t a_stride, uint32_t b, uint32_t b_stride,
-                                      int ksteps, uint32_t idesc, bool accumulate) {
+// An operand view of an R-row tile (layout in ugp_umma.cuh): start address, the descriptor's
+// leading- and stride-dimension byte offsets, and the distance between K = 16 slices.
+struct Operand {
+  uint32_t addr, lbo, sbo, kstep;
+};
+// Rows are M or N, columns are K (X W^T reads X and W this way).
+__device__ __forceinline__ Operand kmajor(const uint8_t* tile, uint32_t R) {
+  return {smem_u32(tile), R * 16u, 128u, R * 32u};
+}
+// Rows are K, columns are M or N (dZ^T X reads dZ and X this way, dZ W reads W this way).
+__device__ __forceinline__ Operand mnmajor(const uint8_t* tile, uint32_t R) {
+  return {smem_u32(tile), 128u, R * 16u, 256u};
+}
+
+// Issues D = A B^T (+ D) over `ksteps` K = 16 slices. Called by one thread.
+__device__ __forceinline__ void issue(uint32_t d, const Operand& a, const Operand& b, int ksteps, uint32_t idesc,
+                                      bool accumulate) {
   for (int ks = 0; ks < ksteps; ++ks)
-    mma_bf16(d, desc_kmajor(a + uint32_t(ks) * a_stride), desc_kmajor(b + uint32_t(ks) * b_stride), idesc,
-             (accumulate || ks > 0) ? 1u : 0u);
+    mma_bf16(d, desc_smem(a.addr + uint32_t(ks) * a.kstep, a.lbo, a.sbo),
+             desc_smem(b.addr + uint32_t(ks) * b.kstep, b.lbo, b.sbo), idesc, (accumulate || ks > 0) ? 1u : 0u);
 }
 
 __device__ __forceinline__ int64_t row_count(int64_t n_host, const int* n_dev) {
@@ -132,7 +148,7 @@ __device__ __forceinline__ int64_t row_count(int64_t n_host, const int* n_dev) {
 }
 
 // ------------------------------------------------------------------ forward
-constexpr uint32_t kFwdX = kImgWT;                 // after W and biases
+constexpr uint32_t kFwdX = kImgBytes;              // after W and biases
 constexpr uint32_t kFwdBar = kFwdX + kXTile;       // 58624
 constexpr uint32_t kFwdTmemSlot = kFwdBar + 8;
 constexpr uint32_t kFwdSmem = kFwdBar + 128;
@@ -166,8 +182,8 @@ __global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Ds
   uint32_t phase = 0;
   bool failed = false;
   if (tid == 0) {
-    mbar_expect_tx(bar, kImgWT);
-    bulk_g2s(smem_u32(sm), g.img, kImgWT, bar);
+    mbar_expect_tx(bar, kImgBytes);
+    bulk_g2s(smem_u32(sm), g.img, kImgBytes, bar);
   }
   failed = __syncthreads_or(!mbar_wait(bar, phase, kGWaitNs));
   phase ^= 1u;
@@ -193,7 +209,7 @@ __global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Ds
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        issue(tmem, smem_u32(X), 4096u, smem_u32(sm + kImgW + l * kImgTile), 2048u, 4, kIdesc64, false);
+        issue(tmem, kmajor(X, 128), kmajor(sm + kImgW + l * kImgTile, 64), 4, kIdescFwd, false);
         mma_commit(bar);
       }
       const bool ok = mbar_wait(bar, phase, kGWaitNs);
@@ -229,19 +245,20 @@ __global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Ds
 }
 
 // ------------------------------------------------------------------ training
-constexpr uint32_t kGrX = kImgBytes;                    // 83200: X_0 .. X_4
-constexpr uint32_t kGrDZ = kGrX + 5 * kXTile;           // 165120: dZ, K-major over outputs
-constexpr uint32_t kGrDZT = kGrDZ + kXTile;             // 181504: dZ^T, K-major over rows
-constexpr uint32_t kGrXT = kGrDZT + kXTile;             // 197888: X^T (+ ones row), 80 rows
-constexpr uint32_t kGrXTBytes = 80 * 128 * 2;           // 20480
-constexpr uint32_t kGrBar = kGrXT + kGrXTBytes;         // 218368
+// X_l tiles carry 80 columns: 64 activations, a ones column (64) and 15 zeros, so the dW MMA's
+// N = 80 view of X_l yields the bias gradient in column 64.
+constexpr uint32_t kGrXCols = 80;
+constexpr uint32_t kGrXTile = 128 * kGrXCols * 2;       // 20480
+constexpr uint32_t kGrDZ = kImgBytes;                   // 42240: dZ, 128 rows x 64 outputs
+constexpr uint32_t kGrX = kGrDZ + kXTile;               // 58624: X_0 .. X_4
+constexpr uint32_t kGrBar = kGrX + 5 * kGrXTile;        // 161024
 constexpr uint32_t kGrTmemSlot = kGrBar + 8;
 constexpr uint32_t kGrRed = kGrBar + 16;                // 4 floats of loss reduction
-constexpr uint32_t kGrSmem = kGrBar + 128;              // 218496
+constexpr uint32_t kGrSmem = kGrBar + 128;              // 161152
 static_assert(kGrSmem <= 227 * 1024, "guide training block exceeds shared memory");
-// The dW MMA reads rows 64..127 of its A operand (unused accumulator lanes) up to 2 KB past dZ^T;
-// that range is X^T, inside the block's shared memory.
-static_assert(kGrXT == kGrDZT + kXTile && kGrXTBytes >= 2048, "dZ^T must be followed by readable shared memory");
+// The dW MMA's M = 128 view of dZ reads 16 column chunks, the upper 8 (unused accumulator lanes)
+// up to 16 KB past the dZ tile; that range is X_0, inside the block's shared memory.
+static_assert(kGrX == kGrDZ + kXTile && 5 * kGrXTile >= kXTile, "dZ must be followed by readable shared memory");
 
 constexpr uint32_t kTmScratch = 0;   // 64 columns: layer output / dX
 constexpr uint32_t kTmDW = 64;       // 5 x 80 columns: dW_l and db_l
@@ -265,8 +282,6 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
   const float inv_n = 1.f / float(n);
   uint8_t* X = sm + kGrX;
   uint8_t* DZ = sm + kGrDZ;
-  uint8_t* DZT = sm + kGrDZT;
-  uint8_t* XT = sm + kGrXT;
   const uint32_t bar = smem_u32(sm + kGrBar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kGrTmemSlot);
   float* red = reinterpret_cast<float*>(sm + kGrRed);
@@ -278,11 +293,14 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
     tmem_alloc(smem_u32(tslot), kTmCols);
     tmem_relinquish();
   }
-  // Rows 64..79 of X^T: a ones row (bias gradient) and zeros; written once.
+  // Columns 64..79 of every X_l: a ones column (bias gradient) and zeros; written once.
   {
-    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
-    for (int i = 64; i < 80; ++i)
-      *reinterpret_cast<__nv_bfloat16*>(XT + canon_off(uint32_t(i), uint32_t(tid), 80u)) = i == 64 ? one : zero;
+    const uint4 ones = make_uint4(pack_bf16x2(1.f, 0.f), 0u, 0u, 0u), zeros = make_uint4(0u, 0u, 0u, 0u);
+    for (int l = 0; l <= kGLayers; ++l) {
+      uint8_t* t = X + l * kGrXTile;
+      *reinterpret_cast<uint4*>(t + tile_off(uint32_t(tid), 64u, 128u)) = ones;
+      *reinterpret_cast<uint4*>(t + tile_off(uint32_t(tid), 72u, 128u)) = zeros;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -321,8 +339,8 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        issue(tmem + kTmScratch, smem_u32(X + l * kXTile), 4096u, smem_u32(sm + kImgW + l * kImgTile), 2048u, 4,
-              kIdesc64, false);
+        issue(tmem + kTmScratch, kmajor(X + l * kGrXTile, 128), kmajor(sm + kImgW + l * kImgTile, 64), 4, kIdescFwd,
+              false);
         mma_commit(bar);
       }
       const bool ok = mbar_wait(bar, phase, kGWaitNs);
@@ -337,7 +355,7 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
         tmem_row<kGWidth>(lane_addr + kTmScratch, v);
 #pragma unroll
         for (int i = 0; i < kGWidth; ++i) v[i] = fmaxf(v[i] + bias[l * kGWidth + i], 0.f);
-        store_row(X + (l + 1) * kXTile, tid, v);
+        store_row(X + (l + 1) * kGrXTile, tid, v);
       } else {
         float v[48];
         tmem_row<48>(lane_addr + kTmScratch, v);
@@ -354,30 +372,19 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
 #pragma unroll
         for (int i = 0; i < kGWidth; ++i) d64[i] = i < kGOut ? dY[i] : 0.f;
         store_row(DZ, tid, d64);
-#pragma unroll
-        for (int o = 0; o < kGWidth; ++o)
-          *reinterpret_cast<__nv_bfloat16*>(DZT + canon_off(uint32_t(o), uint32_t(tid), 64u)) =
-              __float2bfloat16_rn(d64[o]);
       }
     }
     // backward, head first
     for (int l = kGLayers; l >= 0 && !failed; --l) {
-      {
-        uint16_t h[kGWidth];
-        load_row_bits(X + l * kXTile, tid, h);
-#pragma unroll
-        for (int i = 0; i < kGWidth; ++i)
-          *reinterpret_cast<uint16_t*>(XT + canon_off(uint32_t(i), uint32_t(tid), 80u)) = h[i];
-      }
       fence_async_smem();
       tc_fence_before();
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        issue(tmem + kTmDW + 80u * uint32_t(l), smem_u32(DZT), 2048u, smem_u32(XT), 2560u, 8, kIdesc80, !first);
+        issue(tmem + kTmDW + 80u * uint32_t(l), mnmajor(DZ, 128), mnmajor(X + l * kGrXTile, 128), 8, kIdescDW,
+              !first);
         if (l > 0)
-          issue(tmem + kTmScratch, smem_u32(DZ), 4096u, smem_u32(sm + kImgWT + l * kImgTile), 2048u, 4, kIdesc64,
-                false);
+          issue(tmem + kTmScratch, kmajor(DZ, 128), mnmajor(sm + kImgW + l * kImgTile, 64), 4, kIdescDX, false);
         mma_commit(bar);
       }
       const bool ok = mbar_wait(bar, phase, kGWaitNs);
@@ -391,14 +398,10 @@ __global__ void __launch_bounds__(kGThreads, 1) k_guide_grad(GuideDev g, Src src
         float v[kGWidth];
         tmem_row<kGWidth>(lane_addr + kTmScratch, v);
         uint16_t h[kGWidth];
-        load_row_bits(X + l * kXTile, tid, h);  // X_l = relu(Z_{l-1}) rounded: > 0 iff Z_{l-1} > 0
+        load_row_bits(X + l * kGrXTile, tid, h);  // X_l = relu(Z_{l-1}) rounded: > 0 iff Z_{l-1} > 0
 #pragma unroll
         for (int i = 0; i < kGWidth; ++i) v[i] = (h[i] != 0 && !(h[i] & 0x8000u)) ? v[i] : 0.f;
         store_row(DZ, tid, v);
-#pragma unroll
-        for (int o = 0; o < kGWidth; ++o)
-          *reinterpret_cast<__nv_bfloat16*>(DZT + canon_off(uint32_t(o), uint32_t(tid), 64u)) =
-              __float2bfloat16_rn(v[o]);
       }
     }
     first = false;

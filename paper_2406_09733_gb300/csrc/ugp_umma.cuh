@@ -2,13 +2,16 @@
 // tensor-memory allocation, tcgen05.mma with shared-memory operand descriptors, and
 // tcgen05.ld of the accumulator.
 //
-// Operand layout used throughout (no swizzle, K-major): a tile of R rows x K columns of 16-bit
-// elements is cut into 8 x 8 "core matrices" of 128 contiguous bytes (8 rows of 16 bytes).
-// Element (r, k) sits at
-//     (k / 16) * (R * 32) + (r / 8) * 256 + ((k / 8) % 2) * 128 + (r % 8) * 16 + (k % 8) * 2,
-// so each K = 16 slice of the tile is R * 32 contiguous bytes, the two core matrices of a row
-// group along K are 128 bytes apart (leading-dimension offset) and consecutive row groups are
-// 256 bytes apart (stride-dimension offset). One tcgen05.mma consumes one K = 16 slice.
+// Operand layout used throughout (no swizzle): a tile of R rows x C columns of 16-bit elements is
+// cut into 8 x 8 "core matrices" of 128 contiguous bytes (8 rows of 16 bytes), stored chunk-major:
+// element (r, c) sits at
+//     (c / 8) * (R * 16) + (r / 8) * 128 + (r % 8) * 16 + (c % 8) * 2,
+// i.e. all rows of an 8-column chunk are consecutive core matrices. Both directions then have a
+// uniform stride (row groups 128 bytes apart, column chunks R * 16 apart), so one tile serves
+// as a K-major operand (rows = M or N, columns = K: leading-dimension offset R * 16 between K
+// chunks, stride-dimension offset 128 between row groups) and as an MN-major operand (rows = K,
+// columns = M or N: 128 between K groups, R * 16 between M/N chunks). One tcgen05.mma consumes
+// K = 16, two K chunks or two K groups.
 #pragma once
 #include <cstdint>
 
@@ -17,9 +20,9 @@ namespace umma {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
-// Byte offset of element (r, k) in an R-row tile of the layout above.
-__host__ __device__ __forceinline__ uint32_t canon_off(uint32_t r, uint32_t k, uint32_t R) {
-  return (k >> 4) * (R * 32u) + (r >> 3) * 256u + ((k >> 3) & 1u) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+// Byte offset of element (r, c) in an R-row tile of the layout above.
+__host__ __device__ __forceinline__ uint32_t tile_off(uint32_t r, uint32_t c, uint32_t R) {
+  return (c >> 3) * (R * 16u) + (r >> 3) * 128u + (r & 7u) * 16u + (c & 7u) * 2u;
 }
 
 // ------------------------------------------------------------------ mbarrier
@@ -86,14 +89,17 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ------------------------------------------------------------------ MMA
-// Shared-memory descriptor of a K-major, unswizzled operand slice (layout in the file header).
-__device__ __forceinline__ uint64_t desc_kmajor(uint32_t saddr) {
-  constexpr uint64_t kLBO = 128, kSBO = 256;
-  return uint64_t((saddr & 0x3FFFFu) >> 4) | ((kLBO >> 4) << 16) | ((kSBO >> 4) << 32) | (uint64_t(1) << 46);
+// Shared-memory descriptor of an unswizzled operand slice starting at saddr: lbo = leading-
+// dimension byte offset, sbo = stride-dimension byte offset (meaning per major-ness as in the file
+// header), version 1 (tcgen05), no swizzle.
+__device__ __forceinline__ uint64_t desc_smem(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t(lbo >> 4) << 16) | (uint64_t(sbo >> 4) << 32) |
+         (uint64_t(1) << 46);
 }
-// Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 accumulator, M x N, A and B K-major
+// (0) or MN-major (1).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(uint32_t M, uint32_t N, uint32_t a_mn = 0, uint32_t b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (b_mn << 16) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 // D (tensor memory) = A * B^T (+ D if accumulate), issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,

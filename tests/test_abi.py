@@ -60,7 +60,7 @@ def test_guide_entry_points_validate_on_host(libugp):
     libugp.ugp_render_guided_workspace_size.restype = ctypes.c_size_t
     libugp.ugp_render_workspace_size.restype = ctypes.c_size_t
     libugp.ugp_last_error.restype = ctypes.c_char_p
-    assert libugp.ugp_guide_workspace_size() > 83200
+    assert libugp.ugp_guide_workspace_size() > 42240
     plain = libugp.ugp_render_workspace_size(4, 4)
     guided = libugp.ugp_render_guided_workspace_size(4, 4, 3)
     assert guided > plain > 0
