@@ -14,6 +14,9 @@
 //   3. otherwise adds every interval's contribution to 32 sub-bins of the bracket (shared-memory
 //      atomics), moves the bracket to the crossing sub-bin and repeats.
 // The result is the same function of (u, u2) as the per-thread paths: the same F, root and race.
+// It is also bit-for-bit independent of the order in which the intervals were collected (the
+// scan's slot list follows its warp's schedule): the solve sums the intervals in primitive-id
+// order, and the sub-bins are fixed-point integers.
 #include "ugp_dense.cuh"
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
@@ -26,14 +29,46 @@ constexpr int kDCap = 256;    // intervals one warp holds
 constexpr int kDStack = 512;  // shared traversal stack of one warp
 constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
+constexpr float kNewtonStep = 1e-6f;   // relative Newton step that ends the iteration
+constexpr float kNewtonFloor = 1e-3f;  // distance scale below which the step is taken absolute
 constexpr unsigned kFull = 0xffffffffu;
 
 struct WarpSmem {
   float a[kDCap], b[kDCap], tn[kDCap], ts[kDCap], s[kDCap], e0[kDCap], th[kDCap];
   int id[kDCap];  // index with the end-point flags (pack_id)
-  int stk[kDStack];
-  float bin[32];
+  int stk[kDStack];  // traversal stack; after a collection, keys and the id order (stk + kDCap)
+  unsigned long long bin[32];  // sub-bins of step 3, units of 2^-40
 };
+static_assert(kDStack >= 2 * kDCap, "the ordering reuses the traversal stack");
+constexpr float kSubScale = 1099511627776.f;           // 2^40
+constexpr float kSubUnit = 9.094947017729282e-13f;     // 2^-40
+
+// Orders the n <= kDCap collected intervals by primitive id (ids along one ray are distinct):
+// each interval's rank is the number of smaller ids, counted with shuffles when the intervals
+// fit one per lane and with broadcast shared-memory reads otherwise. On return ord[r] (the
+// second half of the traversal stack) is the interval of rank r.
+__device__ void order_by_id(WarpSmem& W, int n, int lane) {
+  int* key = W.stk;
+  int* ord = W.stk + kDCap;
+  if (n <= 32) {
+    const int k = lane < n ? unpack_id(W.id[lane]) : INT32_MAX;
+    int r = 0;
+#pragma unroll 4
+    for (int m = 0; m < n; ++m) r += __shfl_sync(kFull, k, m) < k ? 1 : 0;
+    if (lane < n) ord[r] = lane;
+  } else {
+    for (int i = lane; i < n; i += 32) key[i] = unpack_id(W.id[i]);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const int k = key[i];
+      int r = 0;
+#pragma unroll 4
+      for (int m = 0; m < n; ++m) r += key[m] < k ? 1 : 0;
+      ord[r] = i;
+    }
+  }
+  __syncwarp();
+}
 
 __device__ __forceinline__ float warp_sum(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
@@ -165,6 +200,8 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
       if (st != UGP_RAY_OK) break;
       if (n <= kDCap) {
         // ---- 2. root of F = u on [lo, min(hi, last interval end)], then the race at t_u
+        order_by_id(W, n, lane);
+        const int* ord = W.stk + kDCap;
         float bmax = lo;
         for (int e = lane; e < n; e += 32) bmax = fmaxf(bmax, W.b[e]);
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
@@ -172,7 +209,8 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
         const float w_lo = lo;
         auto evalF = [&](float t, float& f, float& fp) {
           float fl = 0.f, fpl = 0.f;
-          for (int e = lane; e < n; e += 32) {
+          for (int r = lane; r < n; r += 32) {
+            const int e = ord[r];
             const float x0 = fmaxf(W.a[e], w_lo), x1 = fminf(W.b[e], t);
             const int p = W.id[e];
             if (x0 < x1)
@@ -206,6 +244,13 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
               dx_old = dx;
               dx = f / fp;
               tnew = tn;
+              // a Newton step below 1e-6 of the distance scale: its own error is of the order of
+              // its square (or of itself across a kink of F'), far below the 1e-5 accuracy asked
+              if (fabsf(dx) <= kNewtonStep * fmaxf(fabsf(tnew), kNewtonFloor)) {
+                t = tnew;
+                conv = true;
+                break;
+              }
             } else {
               dx_old = dx;
               dx = 0.5f * (b0 - a0);
@@ -247,7 +292,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
         done = true;
       } else {
         // ---- 3. too many intervals: shrink the bracket to the crossing sub-bin
-        W.bin[lane] = 0.f;
+        W.bin[lane] = 0ull;
         __syncwarp();
         const float w = (hi - lo) / 32.f;
         auto edge = [&](int k) { return k >= 32 ? hi : lo + w * float(k); };
@@ -263,25 +308,27 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
           while (k < 31 && x >= edge(k + 1)) ++k;
           for (; k < 32 && edge(k) < y; ++k) {
             const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
-            if (xa < ya)
-              atomicAdd(&W.bin[k], seg_half_integral(xa, ya, hh.a, hh.b, hh.a_end, hh.b_end, hh.tn, hh.ts, hh.s,
-                                                     hh.e0, hh.th));
+            if (xa < ya) {
+              const float v = seg_half_integral(xa, ya, hh.a, hh.b, hh.a_end, hh.b_end, hh.tn, hh.ts, hh.s, hh.e0,
+                                                hh.th);
+              atomicAdd(&W.bin[k], (unsigned long long)__float2ll_rn(fminf(fmaxf(v, 0.f), 4.f) * kSubScale));
+            }
           }
         });
         __syncwarp();
         if (st != UGP_RAY_OK) break;
-        float acc = 0.f;
+        unsigned long long acc = 0ull;
         int jx = 31;
         for (int k = 0; k < 32; ++k) {
-          const float nxt = acc + W.bin[k];
-          if (nxt > u - Flo) {
+          const unsigned long long nxt = acc + W.bin[k];
+          if (float(nxt) * kSubUnit > u - Flo) {
             jx = k;
             break;
           }
           if (k < 31) acc = nxt;
         }
         const float nlo = edge(jx), nhi = edge(jx + 1);
-        Flo += acc;
+        Flo += float(acc) * kSubUnit;
         lo = nlo;
         hi = nhi;
         __syncwarp();

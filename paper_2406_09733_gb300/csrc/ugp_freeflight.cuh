@@ -145,7 +145,8 @@ struct ScanCtx {
 struct ScanBins {
   ScanCtx& c;
   float lo, hi, w, target;
-  int jc;  // crossing bin (kB: none yet)
+  int jc;           // crossing bin (kB: none yet)
+  long long below;  // sum of the bins before the crossing bin (of all bins while there is none)
   __device__ float edge(int j) const { return j >= kB ? hi : lo + w * float(j); }
   // The interval's contribution goes to the bins up to the crossing bin; the crossing bin (and
   // the pruning limit) may move earlier; primitives met before its end go into the slot list.
@@ -161,18 +162,27 @@ struct ScanBins {
     const int kend = jc < kB ? jc + 1 : kB;
     for (int k = j; k < kend && edge(k) < y; ++k) {
       const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
-      if (xa < ya)
-        c.sm.bin[k][c.tid] = bin_add(c.sm.bin[k][c.tid], seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn,
-                                                                             h.ts, h.s, h.e0, h.th));
+      if (xa < ya) {
+        const int old = c.sm.bin[k][c.tid];
+        const int nb = bin_add(old, seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th));
+        c.sm.bin[k][c.tid] = nb;
+        if (k < jc) below += nb - old;
+      }
     }
+    // Bins are non-negative, so while the bins before the crossing bin sum to at most u no
+    // prefix passes u earlier, and the crossing bin stands; otherwise find the new one.
     const long long tgt = (long long)(target * kBinScale);  // u is a multiple of 2^-24: exact
-    long long acc = 0;
-    for (int k = 0; k < jc; ++k) {
-      acc += c.sm.bin[k][c.tid];
-      if (acc > tgt) {
-        jc = k;
-        limit = edge(jc + 1);
-        break;
+    if (below > tgt) {
+      long long acc = 0;
+      for (int k = 0; k < jc; ++k) {
+        const long long before = acc;
+        acc += c.sm.bin[k][c.tid];
+        if (acc > tgt) {
+          jc = k;
+          limit = edge(jc + 1);
+          below = before;
+          break;
+        }
       }
     }
     if (x < edge(jc + 1) && c.list) {
@@ -202,6 +212,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
   ScanState s;
   bool busy = false, exhausted = false, tdone = false;
   int node = 0, sp = 0, jc = kB, nq = 0;
+  long long below = 0;
   float lo = 0.f, hi = 0.f, w = 0.f, target = 0.f, limit = 0.f;
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !busy && !exhausted);
@@ -239,6 +250,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
               w = (hi - lo) / float(kB);
               for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0;
               jc = kB;
+              below = 0;
               limit = hi;
               node = 0;
               sp = 0;
@@ -260,9 +272,10 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       // ---- leaf step: one held-back primitive per lane
       if (busy && nq > 0) {
         --nq;
-        ScanBins v{c, lo, hi, w, target, jc};
+        ScanBins v{c, lo, hi, w, target, jc, below};
         v.leaf(sm.lq[nq][c.tid], limit);
         jc = v.jc;
+        below = v.below;
       }
     } else if (busy && !tdone) {
       // ---- node step: one node of the nearest-first traversal
