@@ -207,28 +207,50 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
         float hi_e = fminf(hi, bmax);
         const float w_lo = lo;
+        // full[r]: the term of the interval of rank r at t = hi_e, which for an interval ending at
+        // or before hi_e is its whole contribution; later evaluations reuse it for every interval
+        // that ends before t, so only the intervals containing t need the erf.
+        float* full = reinterpret_cast<float*>(W.stk);
+        auto term = [&](int e, float t) {
+          const float x0 = fmaxf(W.a[e], w_lo), x1 = fminf(W.b[e], t);
+          const int p = W.id[e];
+          return x0 < x1 ? seg_half_integral(x0, x1, W.a[e], W.b[e], packed_a_end(p), packed_b_end(p), W.tn[e],
+                                             W.ts[e], W.s[e], W.e0[e], W.th[e])
+                         : 0.f;
+        };
         auto evalF = [&](float t, float& f, float& fp) {
           float fl = 0.f, fpl = 0.f;
           for (int r = lane; r < n; r += 32) {
             const int e = ord[r];
-            const float x0 = fmaxf(W.a[e], w_lo), x1 = fminf(W.b[e], t);
-            const int p = W.id[e];
-            if (x0 < x1)
-              fl += seg_half_integral(x0, x1, W.a[e], W.b[e], packed_a_end(p), packed_b_end(p), W.tn[e], W.ts[e],
-                                      W.s[e], W.e0[e], W.th[e]);
-            if (W.a[e] <= t && t <= W.b[e]) fpl += 0.5f * gauss_at(t, W.tn[e], W.ts[e], W.s[e], W.e0[e]);
+            const float a = W.a[e], b = W.b[e];
+            fl += b <= t ? full[r] : term(e, t);
+            if (a <= t && t <= b) fpl += 0.5f * gauss_at(t, W.tn[e], W.ts[e], W.s[e], W.e0[e]);
           }
           f = Flo - u + warp_sum(fl);
           fp = warp_sum(fpl);
         };
-        float fh, fph;
-        evalF(hi_e, fh, fph);
+        float fh;
+        {
+          float fl = 0.f;
+          for (int r = lane; r < n; r += 32) {
+            const float v = term(ord[r], hi_e);
+            full[r] = v;
+            fl += v;
+          }
+          fh = Flo - u + warp_sum(fl);
+          __syncwarp();
+        }
         float t;
         if (!(fh > 0.f)) {
           t = hi_e;  // rounding placed the crossing at the end of the bracket
         } else {
-          float a0 = lo, b0 = hi_e;
-          t = a0 + (u - Flo) / (fh + u - Flo) * (b0 - a0);
+          // Newton's method safeguarded by a bracket [a0, b0] with f(a0) < 0 < f(b0); a step that
+          // leaves the bracket or does not shrink fast enough is replaced by a false-position step
+          // with the Illinois rule (F is monotone and S-shaped across thin primitives, where plain
+          // Newton overshoots and bisection would crawl)
+          float a0 = lo, b0 = hi_e, fa = Flo - u, fb = fh;
+          int moved = 0;  // -1: a0 moved last, +1: b0 moved last
+          t = a0 - fa * (b0 - a0) / (fb - fa);
           if (!(t > a0 && t < b0)) t = 0.5f * (a0 + b0);
           float dx_old = b0 - a0, dx = dx_old;
           bool conv = false;
@@ -236,7 +258,17 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
             float f, fp;
             evalF(t, f, fp);
             if (f == 0.f) { conv = true; break; }
-            if (f < 0.f) a0 = t; else b0 = t;
+            if (f < 0.f) {
+              a0 = t;
+              fa = f;
+              if (moved < 0) fb *= 0.5f;
+              moved = -1;
+            } else {
+              b0 = t;
+              fb = f;
+              if (moved > 0) fa *= 0.5f;
+              moved = 1;
+            }
             if (!(nextafterf(a0, INFINITY) < b0)) { conv = true; break; }
             const float tn = fp > 0.f ? t - f / fp : a0;
             float tnew;
@@ -252,9 +284,10 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
                 break;
               }
             } else {
+              tnew = a0 - fa * (b0 - a0) / (fb - fa);
+              if (!(tnew > a0 && tnew < b0)) tnew = 0.5f * (a0 + b0);
               dx_old = dx;
-              dx = 0.5f * (b0 - a0);
-              tnew = a0 + dx;
+              dx = tnew - t;
             }
             if (tnew == t) { conv = true; break; }
             t = tnew;
