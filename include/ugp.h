@@ -175,7 +175,7 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  * call cudaMalloc or hand the library a workspace -- for example code that runs while a
  * host application owns every device allocation, or a real-time loop that must not
  * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
- * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.5 MB); every GPU that
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.7 MB); every GPU that
  * loads the library holds it until the process exits.  Without the per-ray slot lists of
  * the regular entry point, its warp pass finds dense intervals by traversal; the results
  * are the same.
@@ -331,7 +331,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 716 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 720 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per

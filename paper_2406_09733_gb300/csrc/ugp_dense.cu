@@ -11,8 +11,11 @@
 //   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method safeguarded
 //      with bisection, F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive
 //      with the exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
-//   3. otherwise adds every interval's contribution to 32 sub-bins of the bracket (shared-memory
-//      atomics), moves the bracket to the crossing sub-bin and repeats.
+//   3. otherwise hands the ray to a second kernel in which one warp per block holds up to 2048
+//      intervals (rays through the cores of dense clusters, where hundreds of ellipsoids contain
+//      the root itself, so no narrower bracket would hold fewer); beyond that, it adds every
+//      interval's contribution to 32 sub-bins of the bracket (shared-memory atomics), moves the
+//      bracket to the crossing sub-bin and repeats.
 // The result is the same function of (u, u2) as the per-thread paths: the same F, root and race.
 // It is also bit-for-bit independent of the order in which the intervals were collected (the
 // scan's slot list follows its warp's schedule): the solve sums the intervals in primitive-id
@@ -24,22 +27,26 @@
 namespace ugp {
 namespace {
 
-constexpr int kDWarps = 4;    // rays in flight per block
-constexpr int kDCap = 256;    // intervals one warp holds
-constexpr int kDStack = 512;  // shared traversal stack of one warp
+constexpr int kDWarps = 4;     // rays in flight per block
+constexpr int kDCap = 256;     // intervals one warp holds
+constexpr int kDCapH = 2048;   // intervals the warp of the heavy-ray kernel holds
 constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
 constexpr float kNewtonStep = 1e-6f;   // relative Newton step that ends the iteration
 constexpr float kNewtonFloor = 1e-3f;  // distance scale below which the step is taken absolute
 constexpr unsigned kFull = 0xffffffffu;
 
-struct WarpSmem {
-  float a[kDCap], b[kDCap], tn[kDCap], ts[kDCap], s[kDCap], e0[kDCap], th[kDCap];
-  int id[kDCap];  // index with the end-point flags (pack_id)
-  int stk[kDStack];  // traversal stack; after a collection, keys and the id order (stk + kDCap)
+template <int kCapacity>
+struct WarpSmemT {
+  static constexpr int kCap = kCapacity;
+  static constexpr int kStack = 2 * kCap > 512 ? 2 * kCap : 512;  // shared traversal stack
+  float a[kCap], b[kCap], tn[kCap], ts[kCap], s[kCap], e0[kCap], th[kCap];
+  int id[kCap];  // index with the end-point flags (pack_id)
+  int stk[kStack];  // traversal stack; after a collection, keys and the id order (stk + kCap)
   unsigned long long bin[32];  // sub-bins of step 3, units of 2^-40
 };
-static_assert(kDStack >= 2 * kDCap, "the ordering reuses the traversal stack");
+using WarpSmem = WarpSmemT<kDCap>;
+using WarpSmemH = WarpSmemT<kDCapH>;
 constexpr float kSubScale = 1099511627776.f;           // 2^40
 constexpr float kSubUnit = 9.094947017729282e-13f;     // 2^-40
 
@@ -47,9 +54,10 @@ constexpr float kSubUnit = 9.094947017729282e-13f;     // 2^-40
 // each interval's rank is the number of smaller ids, counted with shuffles when the intervals
 // fit one per lane and with broadcast shared-memory reads otherwise. On return ord[r] (the
 // second half of the traversal stack) is the interval of rank r.
-__device__ void order_by_id(WarpSmem& W, int n, int lane) {
+template <class WS>
+__device__ void order_by_id(WS& W, int n, int lane) {
   int* key = W.stk;
-  int* ord = W.stk + kDCap;
+  int* ord = W.stk + WS::kCap;
   if (n <= 32) {
     const int k = lane < n ? unpack_id(W.id[lane]) : INT32_MAX;
     int r = 0;
@@ -77,8 +85,8 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // Warp-parallel traversal of the leaves whose boxes meet [lo, hi]; `leaf(slot)` is called by all
 // lanes together (slot < 0 for lanes without a leaf), twice per step.
-template <class LeafFn>
-__device__ void warp_traverse(WarpSmem& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
+template <class WS, class LeafFn>
+__device__ void warp_traverse(WS& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
                               uint8_t& st, unsigned& nn, LeafFn&& leaf) {
   int size = 1;
   if (lane == 0) W.stk[0] = 0;
@@ -117,11 +125,11 @@ __device__ void warp_traverse(WarpSmem& W, const TraceScene& sc, const Ray& ray,
       const unsigned mask = __ballot_sync(kFull, push);
       if (push) {
         const int off = size + __popc(mask & ((1u << lane) - 1u));
-        if (off < kDStack) W.stk[off] = ch[c];
+        if (off < WS::kStack) W.stk[off] = ch[c];
       }
       size += __popc(mask);
     }
-    if (size > kDStack) {
+    if (size > WS::kStack) {
       st = UGP_RAY_STACK_OVERFLOW;
       return;
     }
@@ -134,8 +142,8 @@ __device__ void warp_traverse(WarpSmem& W, const TraceScene& sc, const Ray& ray,
 
 // Calls `leaf(slot)` on all lanes for every candidate primitive of [lo, hi]: from the ray's
 // recorded slot list when it is complete (32 slots per step), else by a warp traversal.
-template <class LeafFn>
-__device__ void for_each_candidate(WarpSmem& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
+template <class WS, class LeafFn>
+__device__ void for_each_candidate(WS& W, const TraceScene& sc, const Ray& ray, float lo, float hi, int lane,
                                    uint8_t& st, unsigned& nn, const int* list, int nlist, LeafFn&& leaf) {
   if (list) {
     for (int base = 0; base < nlist; base += 32) {
@@ -148,20 +156,14 @@ __device__ void for_each_candidate(WarpSmem& W, const TraceScene& sc, const Ray&
   warp_traverse(W, sc, ray, lo, hi, lane, st, nn, leaf);
 }
 
-__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQueue q, int64_t n_host,
-                                                        const int* n_dev, int* __restrict__ prim_out,
-                                                        float* __restrict__ tu_out, float* __restrict__ tsp_out,
-                                                        uint8_t* __restrict__ st_out, int spawn_mode,
-                                                        unsigned long long* stats, unsigned long long* rays_err) {
-  extern __shared__ __align__(16) unsigned char dsm[];
-  WarpSmem& W = reinterpret_cast<WarpSmem*>(dsm)[threadIdx.x >> 5];
-  const int lane = threadIdx.x & 31;
-  const int count = n_dev ? *reinterpret_cast<const volatile int*>(n_dev) : int(n_host);
-  const int nwarps = gridDim.x * kDWarps;
-  // slot j to warp j mod (warps), so the rays in flight together are neighbours in the table;
-  // empty slots are skipped by the whole warp
-  for (int j = blockIdx.x * kDWarps + (threadIdx.x >> 5); j < count; j += nwarps) {
-  if (__ldg(q.idx + j) < 0) continue;
+// Finishes the ray in slot j of the table with the warp's interval buffer W. In the main pass
+// (kHeavy false) a ray with more intervals than W holds is appended to the heavy-ray list (when
+// the queue has one) and left to the heavy-ray kernel, which writes its results.
+template <bool kHeavy, class WS>
+__device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, int j, int lane, int* __restrict__ prim_out,
+                           float* __restrict__ tu_out, float* __restrict__ tsp_out, uint8_t* __restrict__ st_out,
+                           int spawn_mode, unsigned long long* stats, unsigned long long* rays_err) {
+  constexpr int kCap = WS::kCap;
   {
     const TraceScene sc = q.scenes ? q.scenes[q.scene[j]] : sc0;
     const int idx = q.idx[j];
@@ -175,7 +177,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
     unsigned nn = 0, np = 0;
     int out_prim = -1;
     float out_tu = t1, out_tsp = t1;
-    bool done = false;
+    bool done = false, deferred = false;
     for (int level = 0; level < kDLevels && !done && st == UGP_RAY_OK; ++level) {
       // ---- 1. collect the intervals meeting [lo, hi]
       int n = 0;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
         const unsigned mask = __ballot_sync(kFull, ok);
         if (ok) {
           const int i = n + __popc(mask & ((1u << lane) - 1u));
-          if (i < kDCap) {
+          if (i < kCap) {
             W.a[i] = hh.a; W.b[i] = hh.b; W.tn[i] = hh.tn; W.ts[i] = hh.ts;
             W.s[i] = hh.s; W.e0[i] = hh.e0; W.th[i] = hh.th; W.id[i] = pack_id(hh);
           }
@@ -198,10 +200,10 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
       });
       __syncwarp();
       if (st != UGP_RAY_OK) break;
-      if (n <= kDCap) {
+      if (n <= kCap) {
         // ---- 2. root of F = u on [lo, min(hi, last interval end)], then the race at t_u
         order_by_id(W, n, lane);
-        const int* ord = W.stk + kDCap;
+        const int* ord = W.stk + kCap;
         float bmax = lo;
         for (int e = lane; e < n; e += 32) bmax = fmaxf(bmax, W.b[e]);
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
@@ -323,6 +325,9 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
           out_tsp = spawn_mode == 1 ? t : 0.5f * (W.a[best_e] + W.b[best_e]);
         }
         done = true;
+      } else if (!kHeavy && q.heavy) {
+        deferred = true;  // the heavy-ray kernel holds more intervals
+        break;
       } else {
         // ---- 3. too many intervals: shrink the bracket to the crossing sub-bin
         W.bin[lane] = 0ull;
@@ -367,8 +372,19 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
         __syncwarp();
       }
     }
-    if (!done && st == UGP_RAY_OK) st = UGP_RAY_ITER_LIMIT;
     const unsigned tn_nodes = __reduce_add_sync(kFull, nn), tn_prims = __reduce_add_sync(kFull, np);
+    if (deferred) {
+      if (lane == 0) {
+        q.heavy[atomicAdd(q.count + 2, 1)] = j;
+        if (stats) {
+          atomicAdd(stats + 0, (unsigned long long)tn_nodes);
+          atomicAdd(stats + 1, (unsigned long long)tn_prims);
+        }
+      }
+      __syncwarp();
+      return;
+    }
+    if (!done && st == UGP_RAY_OK) st = UGP_RAY_ITER_LIMIT;
     if (lane == 0) {
       prim_out[idx] = out_prim;
       tsp_out[idx] = out_tsp;
@@ -382,22 +398,56 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
     }
     __syncwarp();
   }
+}
+
+__global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQueue q, int64_t n_host,
+                                                        const int* n_dev, int* __restrict__ prim_out,
+                                                        float* __restrict__ tu_out, float* __restrict__ tsp_out,
+                                                        uint8_t* __restrict__ st_out, int spawn_mode,
+                                                        unsigned long long* stats, unsigned long long* rays_err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  WarpSmem& W = reinterpret_cast<WarpSmem*>(dsm)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const int count = n_dev ? *reinterpret_cast<const volatile int*>(n_dev) : int(n_host);
+  const int nwarps = gridDim.x * kDWarps;
+  // slot j to warp j mod (warps), so the rays in flight together are neighbours in the table;
+  // empty slots are skipped by the whole warp
+  for (int j = blockIdx.x * kDWarps + (threadIdx.x >> 5); j < count; j += nwarps) {
+    if (__ldg(q.idx + j) < 0) continue;
+    finish_ray<false>(W, sc0, q, j, lane, prim_out, tu_out, tsp_out, st_out, spawn_mode, stats, rays_err);
   }
+}
+
+// The rays the main pass handed on, one warp per block; q.count[2] of them, in q.heavy.
+__global__ void __launch_bounds__(32) k_dense_heavy(TraceScene sc0, DenseQueue q, int* __restrict__ prim_out,
+                                                    float* __restrict__ tu_out, float* __restrict__ tsp_out,
+                                                    uint8_t* __restrict__ st_out, int spawn_mode,
+                                                    unsigned long long* stats, unsigned long long* rays_err) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  WarpSmemH& W = *reinterpret_cast<WarpSmemH*>(dsm);
+  const int lane = threadIdx.x & 31;
+  const int count = *reinterpret_cast<const volatile int*>(q.count + 2);
+  for (int h = blockIdx.x; h < count; h += gridDim.x)
+    finish_ray<true>(W, sc0, q, q.heavy[h], lane, prim_out, tu_out, tsp_out, st_out, spawn_mode, stats, rays_err);
 }
 
 }  // namespace
 
-static int g_dense_grid = 0;
+static int g_dense_grid = 0, g_heavy_grid = 0;
 
 ugp_status dense_prepare() {
   if (g_dense_grid != 0) return UGP_OK;
-  const size_t smem = sizeof(WarpSmem) * kDWarps;
+  const size_t smem = sizeof(WarpSmem) * kDWarps, smem_h = sizeof(WarpSmemH);
   UGP_CUDA_CHECK(cudaFuncSetAttribute(k_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  int dev = 0, sms = 0, per_sm = 0;
+  UGP_CUDA_CHECK(cudaFuncSetAttribute(k_dense_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_h)));
+  int dev = 0, sms = 0, per_sm = 0, per_sm_h = 0;
   UGP_CUDA_CHECK(cudaGetDevice(&dev));
   UGP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   UGP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense, 32 * kDWarps, smem));
-  g_dense_grid = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  UGP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_h, k_dense_heavy, 32, smem_h));
+  if (sms <= 0) sms = 1;
+  g_heavy_grid = sms * (per_sm_h > 0 ? per_sm_h : 1);
+  g_dense_grid = sms * (per_sm > 0 ? per_sm : 1);
   return UGP_OK;
 }
 
@@ -409,10 +459,14 @@ ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int64_t n_hos
   const int64_t need = (max_slots + 32 * kDWarps - 1) / (32 * kDWarps);
   const int grid = int(need < g_dense_grid ? (need > 0 ? need : 1) : g_dense_grid);
   const size_t smem = sizeof(WarpSmem) * kDWarps;
+  const int64_t need_h = max_slots < g_heavy_grid ? (max_slots > 0 ? max_slots : 1) : g_heavy_grid;
+  UGP_CUDA_CHECK(cudaMemsetAsync(q.count + 2, 0, sizeof(int), stream));
   prof_begin(kStDense, stream);
   k_dense<<<grid, 32 * kDWarps, smem, stream>>>(sc, q, n_host, n_dev, prim_out, t_u_out, t_spawn_out, status_out,
                                                spawn_mode, stats, rays_err);
-  prof_end(kStDense, stream);
+  k_dense_heavy<<<unsigned(need_h), 32, sizeof(WarpSmemH), stream>>>(sc, q, prim_out, t_u_out, t_spawn_out,
+                                                                     status_out, spawn_mode, stats, rays_err);
+  prof_end(kStDense, stream, 2);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }

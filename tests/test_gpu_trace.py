@@ -345,6 +345,67 @@ def test_free_flight_room_scene_binned_mode(gpu, orc):
                 tsp.cpu().numpy().astype(np.float64))
 
 
+def _cluster_scene(n, seed, sigma, smin, smax, rho):
+    """n Gaussians around (0.5, 0.5, 0.5) whose ellipsoids are much larger than the cluster, so
+    that almost all of them contain every point of its core."""
+    s = scenes.tiny_scene(n=n, seed=seed)
+    rng = np.random.default_rng(seed)
+    s.mean[:] = 0.5 + rng.normal(scale=sigma, size=(n, 3))
+    s.scale[:] = np.exp(rng.uniform(np.log(smin), np.log(smax), size=(n, 3)))
+    s.magnitude[:] = rho * (2 * np.pi) ** 1.5 * s.scale.astype(np.float64).prod(axis=1)
+    return s
+
+
+def _rays_at_centre(n, seed, radius, jitter):
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = 0.5 - radius * d
+    tgt = 0.5 + rng.normal(scale=jitter, size=(n, 3))
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return scenes.Rays(o.astype(np.float32), d.astype(np.float32), np.zeros(n, np.float32),
+                       np.full(n, 2 * radius, np.float32))
+
+
+def test_free_flight_hundreds_of_overlaps(gpu, orc):
+    """A cluster core inside about a thousand ellipsoids: every sampled point lies in hundreds of
+    intervals, more than the finish pass holds per warp, so these rays go to its heavy-ray kernel
+    (up to 2048 intervals)."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = _cluster_scene(1200, 51, 0.01, 0.02, 0.04, 0.3)
+    r = _rays_at_centre(1024, 52, 0.4, 0.005)
+    u, u2 = scenes.uniforms24(53, r.n), scenes.uniforms24(54, r.n)
+    prim, tu, tsp, st = ugp.sample_free_flight(build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                               dev(torch, r.t0), dev(torch, r.t1), dev(torch, u), dev(torch, u2))
+    stn = st.cpu().numpy()
+    assert stn.max() == 0, np.bincount(stn)
+    ref = _ff_compare(orc, s, r, u, u2, prim.cpu().numpy(), tu.cpu().numpy().astype(np.float64),
+                      tsp.cpu().numpy().astype(np.float64))
+    assert (ref["n_active"] > 256).mean() > 0.5, np.percentile(ref["n_active"], [10, 50, 90])
+
+
+def test_free_flight_overlap_limit_is_reported(gpu):
+    """More ellipsoids containing the sampled point than the heavy-ray kernel holds (2048): the
+    bracket cannot be narrowed below them, and such a ray ends with UGP_RAY_ITER_LIMIT (a status,
+    not a silent escape); rays that miss the core are unaffected."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    s = _cluster_scene(2600, 55, 0.005, 0.03, 0.05, 0.05)
+    r = _rays_at_centre(64, 56, 0.4, 0.002)
+    far = _rays_at_centre(64, 57, 0.4, 0.002)
+    far.o[:] += np.float32(1.0)             # parallel rays 1.0 away: they miss every ellipsoid
+    o = np.concatenate([r.o, far.o]); d = np.concatenate([r.d, far.d])
+    t0 = np.concatenate([r.t0, far.t0]); t1 = np.concatenate([r.t1, far.t1])
+    u = np.full(o.shape[0], 0.5, np.float32)
+    prim, tu, tsp, st = ugp.sample_free_flight(build_scene(torch, s), dev(torch, o), dev(torch, d),
+                                               dev(torch, t0), dev(torch, t1), dev(torch, u), dev(torch, u))
+    stn, pn = st.cpu().numpy(), prim.cpu().numpy()
+    assert (stn[:64] == 3).mean() > 0.5, np.bincount(stn[:64])   # UGP_RAY_ITER_LIMIT
+    assert np.all(stn[64:] == 0) and np.all(pn[64:] == -1)
+
+
 def test_free_flight_independent_of_ray_order(gpu):
     """A ray's sample does not depend on which rays share its warp. The scan's slot list follows
     the warp's schedule of node and leaf steps, so the same rays in another order reach the finish
