@@ -533,6 +533,7 @@ def run_ugp(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded generator)",
             "config": workload_config(args, "flushed between steps (256 MB write)"),
             "rays_per_step": rays_local / args.steps, "extend_queries_per_step": queries_per_step,
+            "queries_with_error_status": int(c[2]),
             "stage_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
             "roofline": {"bound": "hbm", "kernel": "k_extend (free-flight sampling)",
                          "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",

@@ -163,11 +163,11 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
                                   uint8_t* status_out, void* workspace, size_t workspace_bytes,
                                   void* stream);
 
-/* Scratch bytes ugp_sample_free_flight needs for n_rays rays: a queue of the rays whose
- * bracketed root has more overlapping intervals than one thread buffers (they are
- * finished by a warp-per-ray pass), and per ray a list of up to 128 primitive slots met
- * by the first pass (580 bytes per ray in all).  The workspace must be 256-byte aligned
- * and is only used during the call's device work. */
+/* Scratch bytes ugp_sample_free_flight needs for n_rays rays: the table of rays whose root
+ * the first pass has bracketed (they are finished by a warp-per-ray pass), the list of rays
+ * that pass hands to its heavy-ray kernel, and per ray a list of up to 256 primitive slots
+ * met by the first pass (1096 bytes per ray in all).  The workspace must be 256-byte
+ * aligned and is only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
 /* Free-flight sampling without any device allocation (no counterpart in the paper).
@@ -331,7 +331,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 720 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 1232 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per

@@ -11,7 +11,7 @@
 //   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method safeguarded
 //      with bisection, F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive
 //      with the exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
-//   3. otherwise hands the ray to a second kernel in which one warp per block holds up to 2048
+//   3. otherwise hands the ray to a second kernel in which one warp per block holds up to 1024
 //      intervals (rays through the cores of dense clusters, where hundreds of ellipsoids contain
 //      the root itself, so no narrower bracket would hold fewer); beyond that, it adds every
 //      interval's contribution to 32 sub-bins of the bracket (shared-memory atomics), moves the
@@ -29,9 +29,10 @@ namespace {
 
 constexpr int kDWarps = 4;     // rays in flight per block
 constexpr int kDCap = 256;     // intervals one warp holds
-constexpr int kDCapH = 2048;   // intervals the warp of the heavy-ray kernel holds
+constexpr int kDCapH = 1024;   // intervals the warp of the heavy-ray kernel holds
 constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
+constexpr int kDBisectAfter = 24;  // Newton / false-position steps before plain bisection
 constexpr float kNewtonStep = 1e-6f;   // relative Newton step that ends the iteration
 constexpr float kNewtonFloor = 1e-3f;  // distance scale below which the step is taken absolute
 constexpr unsigned kFull = 0xffffffffu;
@@ -47,13 +48,14 @@ struct WarpSmemT {
 };
 using WarpSmem = WarpSmemT<kDCap>;
 using WarpSmemH = WarpSmemT<kDCapH>;
+static_assert(kDCap >= kListCap, "a ray with more intervals than the main pass holds has overflowed its list");
 constexpr float kSubScale = 1099511627776.f;           // 2^40
 constexpr float kSubUnit = 9.094947017729282e-13f;     // 2^-40
 
 // Orders the n <= kDCap collected intervals by primitive id (ids along one ray are distinct):
 // each interval's rank is the number of smaller ids, counted with shuffles when the intervals
-// fit one per lane and with broadcast shared-memory reads otherwise. On return ord[r] (the
-// second half of the traversal stack) is the interval of rank r.
+// fit one or two per lane and with broadcast shared-memory reads otherwise. On return ord[r]
+// (the second half of the traversal stack) is the interval of rank r.
 template <class WS>
 __device__ void order_by_id(WS& W, int n, int lane) {
   int* key = W.stk;
@@ -64,6 +66,18 @@ __device__ void order_by_id(WS& W, int n, int lane) {
 #pragma unroll 4
     for (int m = 0; m < n; ++m) r += __shfl_sync(kFull, k, m) < k ? 1 : 0;
     if (lane < n) ord[r] = lane;
+  } else if (n <= 64) {
+    const int k0 = unpack_id(W.id[lane]);
+    const int k1 = lane + 32 < n ? unpack_id(W.id[lane + 32]) : INT32_MAX;
+    int r0 = 0, r1 = 0;
+#pragma unroll 4
+    for (int m = 0; m < 32; ++m) {
+      const int a = __shfl_sync(kFull, k0, m), b = __shfl_sync(kFull, k1, m);
+      r0 += (a < k0 ? 1 : 0) + (b < k0 ? 1 : 0);
+      r1 += (a < k1 ? 1 : 0) + (b < k1 ? 1 : 0);
+    }
+    ord[r0] = lane;
+    if (lane + 32 < n) ord[r1] = lane + 32;
   } else {
     for (int i = lane; i < n; i += 32) key[i] = unpack_id(W.id[i]);
     __syncwarp();
@@ -202,8 +216,17 @@ __device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, in
       if (st != UGP_RAY_OK) break;
       if (n <= kCap) {
         // ---- 2. root of F = u on [lo, min(hi, last interval end)], then the race at t_u
-        order_by_id(W, n, lane);
-        const int* ord = W.stk + kCap;
+        // The main pass orders the intervals by id: whether a ray's list overflowed (list or
+        // traversal) follows its warp's schedule. A heavy ray always overflowed its list (it
+        // has more intervals than the list holds), so its traversal order is already a
+        // function of the ray alone.
+        int* ord = W.stk + kCap;
+        if (kHeavy) {
+          for (int i = lane; i < n; i += 32) ord[i] = i;
+          __syncwarp();
+        } else {
+          order_by_id(W, n, lane);
+        }
         float bmax = lo;
         for (int e = lane; e < n; e += 32) bmax = fmaxf(bmax, W.b[e]);
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
@@ -274,7 +297,10 @@ __device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, in
             if (!(nextafterf(a0, INFINITY) < b0)) { conv = true; break; }
             const float tn = fp > 0.f ? t - f / fp : a0;
             float tnew;
-            if (fp > 0.f && tn > a0 && tn < b0 && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
+            // past kDBisectAfter steps only bisection: the bracket then collapses to adjacent
+            // floats within the iteration bound, whatever F looks like
+            const bool bisect = it >= kDBisectAfter;
+            if (!bisect && fp > 0.f && tn > a0 && tn < b0 && fabsf(2.f * f) <= fabsf(dx_old * fp)) {
               dx_old = dx;
               dx = f / fp;
               tnew = tn;
@@ -286,7 +312,7 @@ __device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, in
                 break;
               }
             } else {
-              tnew = a0 - fa * (b0 - a0) / (fb - fa);
+              tnew = bisect ? 0.5f * (a0 + b0) : a0 - fa * (b0 - a0) / (fb - fa);
               if (!(tnew > a0 && tnew < b0)) tnew = 0.5f * (a0 + b0);
               dx_old = dx;
               dx = tnew - t;

@@ -27,7 +27,7 @@ struct DenseQueue {
 constexpr int kDenseCols = 18;
 // Slots of the primitives the scan met before its window end, kept per ray so the dense pass
 // can rebuild the window's intervals without another traversal.
-constexpr int kListCap = 128;
+constexpr int kListCap = 256;
 inline size_t slot_list_bytes(int64_t n) { return align256(size_t(n) * kListCap * 4); }
 
 // Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header); the slot
