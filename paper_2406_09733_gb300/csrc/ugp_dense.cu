@@ -1,6 +1,5 @@
-// Warp-per-ray finish of free-flight sampling for rays whose bracket [lo, hi] (with F(lo) = Flo)
-// holds more intervals than one thread can buffer -- in practice rays inside dense aggregate
-// clusters, where over a hundred bounding ellipsoids can overlap at one point.
+// Warp-per-ray finish of free-flight sampling: every ray whose root the scan has bracketed in
+// [lo, hi] (with F(lo) = Flo) is finished here.
 //
 // For each queued ray one warp
 //   1. collects every clipped interval meeting [lo, hi] into a per-warp shared-memory list: from
@@ -8,9 +7,10 @@
 //      (32 re-tests per step), else by a warp-parallel traversal that pops up to 32 nodes from a
 //      shared stack per step, one per lane, pushing the hit internal children and appending hit
 //      leaves with ballot-ranked slots;
-//   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method safeguarded
-//      with bisection, F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive
-//      with the exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
+//   2. if the list fits, solves F(t_u) = u (Eq. 10) on the bracket by Newton's method, kept in a
+//      shrinking bracket by false-position steps (Illinois rule) and finally by bisection, with
+//      F and F' = 1/2 sum G (Eq. 9) summed across lanes, and draws the primitive with the
+//      exponential race (smallest E_k / G_k(x_{t_u})) as a warp argmin;
 //   3. otherwise hands the ray to a second kernel in which one warp per block holds up to 1024
 //      intervals (rays through the cores of dense clusters, where hundreds of ellipsoids contain
 //      the root itself, so no narrower bracket would hold fewer); beyond that, it adds every
@@ -30,7 +30,7 @@ namespace {
 constexpr int kDWarps = 4;     // rays in flight per block
 constexpr int kDCap = 256;     // intervals one warp holds
 constexpr int kDCapH = 1024;   // intervals the warp of the heavy-ray kernel holds
-constexpr int kDLevels = 8;   // bracket refinements when the intervals do not fit
+constexpr int kDLevels = 8;    // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
 constexpr int kDBisectAfter = 24;  // Newton / false-position steps before plain bisection
 constexpr float kNewtonStep = 1e-6f;   // relative Newton step that ends the iteration
