@@ -182,9 +182,10 @@ __global__ void __launch_bounds__(256) k_b_regen(BState S) {
   }
 }
 
-// Rays of a wave: the live paths, each in its own request's scene.
+// Rays of a wave: the live paths, each in its own request's scene. S refers to the kernel's
+// parameter (read through the constant bank, not copied into local memory).
 struct BatchScanSrc {
-  BState S;
+  const BState& S;
   int cur, count_;
   int i_, p, r, qf;
   float tq, u, u2;
@@ -230,7 +231,7 @@ struct BatchScanSrc {
   }
 };
 
-__global__ void __launch_bounds__(kFFBlock) k_b_extend(BState S) {
+__global__ void __launch_bounds__(kFFBlock, kFFBlocksPerSM) k_b_extend(BState S) {
   __shared__ FFSmem sm;
   const BCtl& c = *S.ctl;
   const int cur = c.wave & 1;
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(128) k_b_shade(BState S) {
   }
 }
 
-__global__ void __launch_bounds__(kTrBlock) k_b_shadow(BState S) {
+__global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_b_shadow(BState S) {
   __shared__ int stk[kTrStack * kTrBlock];
   const int count = S.ctl->shadow;
   const BPaths& P = S.P;

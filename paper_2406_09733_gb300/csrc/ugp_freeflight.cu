@@ -45,7 +45,7 @@ struct ArrayScanSrc {
 };
 
 template <bool STATS>
-__global__ void __launch_bounds__(kFFBlock)
+__global__ void __launch_bounds__(kFFBlock, kFFBlocksPerSM)
 k_free_flight(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const float* __restrict__ d3,
               const float* __restrict__ t0a, const float* __restrict__ t1a, const float* __restrict__ ua,
               const float* __restrict__ u2a, const int32_t* __restrict__ excl,

@@ -114,7 +114,7 @@ struct PathScanSrc {
   }
 };
 
-__global__ void __launch_bounds__(kFFBlock) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
+__global__ void __launch_bounds__(kFFBlock, kFFBlocksPerSM) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
                                                      int spawn_mode, PathSoA ps, const int* __restrict__ q,
                                                      const int* cnt, int* reset_next, int* reset_shadow,
                                                      unsigned long long* rays, unsigned long long* stats,
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
   }
 }
 
-__global__ void __launch_bounds__(kTrBlock) k_shadow(TraceScene sc, ShadowSoA sh, const int* cnt, PathSoA ps,
+__global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene sc, ShadowSoA sh, const int* cnt, PathSoA ps,
                                                      unsigned long long* rays, unsigned long long* stats) {
   __shared__ int stk[kTrStack * kTrBlock];
   const int count = load_count(cnt);

@@ -12,7 +12,7 @@ namespace ugp {
 // Transmittance: T = max(0, 1 - 1/2 sum_k I_k(clip_k)).  Any traversal order gives the same
 // sum; nearest-child-first only makes the early exit at sum >= 1 come sooner.
 template <bool STATS>
-__global__ void __launch_bounds__(kTrBlock)
+__global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM)
 k_transmittance(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, const float* __restrict__ d3,
                 const float* __restrict__ t0a, const float* __restrict__ t1a,
                 const int32_t* __restrict__ excl, float* __restrict__ T_out, uint8_t* __restrict__ st_out,
