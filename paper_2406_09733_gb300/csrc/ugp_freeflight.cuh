@@ -125,7 +125,7 @@ static __device__ FFResult scan_result(FFSmem& sm, int tid, const ScanState& s, 
 
 #undef FB
 
-constexpr int kRefill = 8;  // idle lanes of a warp that trigger a joint fetch of new rays
+constexpr int kRefill = 2;  // idle lanes of a warp that trigger a joint fetch of new rays
 
 // Traversal context of one lane (the scene, the ray and its counters) and the bin visitor of a
 // primitive met by the traversal, as used by the persistent driver below.
