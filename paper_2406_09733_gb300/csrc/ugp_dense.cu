@@ -295,6 +295,16 @@ __device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, in
               moved = 1;
             }
             if (!(nextafterf(a0, INFINITY) < b0)) { conv = true; break; }
+            // a Newton correction below 1e-6 of the distance scale ends the iteration: its own
+            // error is of the order of its square (or of itself across a kink of F'), far below
+            // the 1e-5 accuracy asked (taken even where the shrink safeguard below would refuse
+            // the step, which near the root only reflects the rounding noise of f)
+            if (fp > 0.f && fabsf(f) <= kNewtonStep * fmaxf(fabsf(t), kNewtonFloor) * fp) {
+              const float tn = t - f / fp;
+              if (tn > a0 && tn < b0) t = tn;
+              conv = true;
+              break;
+            }
             const float tn = fp > 0.f ? t - f / fp : a0;
             float tnew;
             // past kDBisectAfter steps only bisection: the bracket then collapses to adjacent
@@ -304,13 +314,6 @@ __device__ void finish_ray(WS& W, const TraceScene& sc0, const DenseQueue& q, in
               dx_old = dx;
               dx = f / fp;
               tnew = tn;
-              // a Newton step below 1e-6 of the distance scale: its own error is of the order of
-              // its square (or of itself across a kink of F'), far below the 1e-5 accuracy asked
-              if (fabsf(dx) <= kNewtonStep * fmaxf(fabsf(tnew), kNewtonFloor)) {
-                t = tnew;
-                conv = true;
-                break;
-              }
             } else {
               tnew = bisect ? 0.5f * (a0 + b0) : a0 - fa * (b0 - a0) / (fb - fa);
               if (!(tnew > a0 && tnew < b0)) tnew = 0.5f * (a0 + b0);
