@@ -164,10 +164,10 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
                                   void* stream);
 
 /* Scratch bytes ugp_sample_free_flight needs for n_rays rays: the table of rays whose root
- * the first pass has bracketed (they are finished by a warp-per-ray pass), the list of rays
- * that pass hands to its heavy-ray kernel, and per ray a list of up to 256 primitive slots
- * met by the first pass (1096 bytes per ray in all).  The workspace must be 256-byte
- * aligned and is only used during the call's device work. */
+ * the first pass has bracketed (they are finished by the passes that follow it), the lists of
+ * rays handed between those passes, and per ray a list of up to 256 primitive slots met by
+ * the first pass (1100 bytes per ray in all).  The workspace must be 256-byte aligned and is
+ * only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
 /* Free-flight sampling without any device allocation (no counterpart in the paper).
@@ -175,7 +175,7 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  * call cudaMalloc or hand the library a workspace -- for example code that runs while a
  * host application owns every device allocation, or a real-time loop that must not
  * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
- * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 4.7 MB); every GPU that
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 5.0 MB); every GPU that
  * loads the library holds it until the process exits.  Without the per-ray slot lists of
  * the regular entry point, its warp pass finds dense intervals by traversal; the results
  * are the same.
@@ -331,7 +331,7 @@ typedef struct ugp_render_params {
 } ugp_render_params;
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 1232 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 1236 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per

@@ -12,19 +12,21 @@ namespace ugp {
 
 // Structure of arrays in caller-provided scratch memory (a 256-byte header, then the columns).
 struct DenseQueue {
-  int* count;    // header ints: [0] unused, [1] ray counter of the persistent scan, [2] heavy rays
+  int* count;    // header ints: [0] unused, [1] ray counter of the persistent scan, [2] and [3]
+                 // rays handed to the finish's second and third passes
   int* idx;      // output index of the ray (-1: empty slot)
   float *lo, *hi, *Flo, *u, *u2;
   float *ox, *oy, *oz, *dx, *dy, *dz, *t0, *t1;
   int* excl;
   int* nlist;    // primitive slots the scan recorded for the ray (> kListCap: list incomplete)
   int* scene;    // index of the ray's scene in `scenes` (batched rendering)
-  int* heavy;    // slots the finish pass handed to its heavy-ray kernel (count[2] of them)
+  int* wide;     // slots the finish's first pass handed to its second (count[2] of them)
+  int* heavy;    // slots its second pass handed to its third (count[3] of them)
   const int* list;  // per-ray slot lists, kListCap ints at list + idx * kListCap (NULL: none)
   const TraceScene* scenes;  // device table of scenes (NULL: every ray uses the launch's scene)
 };
 
-constexpr int kDenseCols = 18;
+constexpr int kDenseCols = 19;
 // Slots of the primitives the scan met before its window end, kept per ray so the dense pass
 // can rebuild the window's intervals without another traversal.
 constexpr int kListCap = 256;
@@ -47,7 +49,8 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   q.excl = reinterpret_cast<int*>(F(14));
   q.nlist = reinterpret_cast<int*>(F(15));
   q.scene = reinterpret_cast<int*>(F(16));
-  q.heavy = reinterpret_cast<int*>(F(17));
+  q.wide = reinterpret_cast<int*>(F(17));
+  q.heavy = reinterpret_cast<int*>(F(18));
   q.list = nullptr;
   q.scenes = nullptr;
   return q;
