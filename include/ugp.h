@@ -434,8 +434,8 @@ ugp_status ugp_render_batch_autotune(int32_t n_req, const ugp_request* reqs, int
 /* Optional traversal statistics: when `counters` is a device pointer to 12
  * zero-initialised uint64, later tracing calls on any stream add (atomically)
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
- *   [3] per-thread traversal passes, [4] free-flight rays handed to the warp-per-ray
- *   dense pass (whose node and record loads are added to [0] and [1])
+ *   [3] per-thread traversal passes, [4] free-flight rays handed to the finish passes
+ *   (whose node and record loads are added to [0] and [1])
  * for free-flight and transmittance queries (standalone, and the renderer's extend
  * pass), and the same five quantities at [6..10] for the renderer's shadow rays;
  * [5] and [11] are reserved.  NULL turns counting off (the default).  Host-side
@@ -449,7 +449,7 @@ ugp_status ugp_set_trace_counters(unsigned long long* counters);
  *   0 BVH build (all its kernels, the radix sort included), 1 camera rays,
  *   2 extend (free flight, per thread), 3 shade, 4 shadow (transmittance),
  *   5 accumulate, 6 standalone queries (ugp_trace_transmittance,
- *   ugp_sample_free_flight), 7 free flight of dense rays (warp per ray), 8 learned guide
+ *   ugp_sample_free_flight), 7 finish of free flight (the bracketed rays), 8 learned guide
  *   (packing, forward, gradient, Adam, training-set selection), 9 batched serving (one pair
  *   around each batch's graph launch or wave loop; graph launches add their kernels to the
  *   counts after the batch).

@@ -6,7 +6,7 @@
 //   1. claims as many items as the free pool slots hold (one thread) and turns every tile
 //      pixel into a camera path in a free slot, appended to the live queue;
 //   2. extends every live path (free-flight sampling in its request's scene), finishes the
-//      bracketed ones warp per ray, shades them (emission, light sampling with MIS, phase
+//      bracketed ones (16 lanes per ray), shades them (emission, light sampling with MIS, phase
 //      sampling with the request's materials and lights), and traces the shadow rays;
 //   3. retires the paths that ended: adds their radiance to the request's image, counts them,
 //      stamps the request's completion time (%globaltimer) when its last path lands, and

@@ -1,4 +1,4 @@
-// Rays whose t_u the scan has bracketed, for the warp-per-ray finish. The table has one slot per
+// Rays whose t_u the scan has bracketed, for the finish passes (ugp_dense.cu). The table has one slot per
 // scanned ray (its index in the scan's launch): the scan writes the ray's record there, or marks
 // the slot empty (idx = -1), so no counter is shared between lanes; the finish pass walks the
 // slots 32 at a time and takes the filled ones.

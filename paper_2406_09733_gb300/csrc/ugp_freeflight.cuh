@@ -23,9 +23,10 @@
 //    the primitives met before its end are recorded in the ray's slot list.  Afterwards F(e_j)
 //    is exact from the bins, t_u lies in [e_j, e_j+1], and the list holds every primitive whose
 //    interval meets that bin.
-//  * finish (ugp_dense.cu, one warp per ray): 32 lanes rebuild the bin's intervals from the list,
-//    solve F(t_u) = u by a safeguarded Newton iteration with warp-reduced F and F' = 1/2 sum G
-//    (Eq. 9), and run the race as a warp argmin.
+//  * finish (ugp_dense.cu, 16 lanes per ray, more for rays with many intervals): the lanes
+//    rebuild the bin's intervals from the list, solve F(t_u) = u by a safeguarded Newton
+//    iteration with F and F' = 1/2 sum G (Eq. 9) summed across them, and run the race as an
+//    argmin across them.
 //
 // The scan runs on persistent lanes: a lane whose ray is done takes a new one, and the idle
 // lanes of a warp fetch together (one atomic) once kRefill of them are idle, so a warp does not

@@ -370,8 +370,8 @@ def _rays_at_centre(n, seed, radius, jitter):
 
 def test_free_flight_hundreds_of_overlaps(gpu, orc):
     """A cluster core inside several hundred ellipsoids: most sampled points lie in hundreds of
-    intervals, more than the finish pass holds per warp, so these rays go to its heavy-ray kernel
-    (up to 1024 intervals)."""
+    intervals, more than the finish's first two passes hold (128 and 256), so these rays go to
+    its third (up to 1024 intervals)."""
     from paper_2406_09733_gb300 import ugp
     torch = gpu
     s = _cluster_scene(800, 51, 0.01, 0.02, 0.04, 0.3)
@@ -387,7 +387,7 @@ def test_free_flight_hundreds_of_overlaps(gpu, orc):
 
 
 def test_free_flight_overlap_limit_is_reported(gpu):
-    """More ellipsoids containing the sampled point than the heavy-ray kernel holds (1024): the
+    """More ellipsoids containing the sampled point than the finish's third pass holds (1024): the
     bracket cannot be narrowed below them, and such a ray ends with UGP_RAY_ITER_LIMIT (a status,
     not a silent escape); rays that miss the core are unaffected."""
     from paper_2406_09733_gb300 import ugp
