@@ -97,6 +97,16 @@ GUIDE_FWD_FLOP = 2 * (4 * 64 * 64 + 40 * 64)
 GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 
 
+# DRAM bytes (read + write) per k_extend launch of the default workload, averaged over the nine
+# launches of one step, from one ncu capture of the current kernel
+# (profiles/k_extend_dram_room1M_1024.md); None for any other workload.
+EXTEND_TRAFFIC_BYTES = {(1_000_000, 1024, 1024, 8): 472.27e6}
+
+
+def extend_traffic(args):
+    return EXTEND_TRAFFIC_BYTES.get((args.n_prims, args.width, args.height, args.depth))
+
+
 def guide_kernel_timing(dev, rows=1 << 20, reps=10):
     """CUDA-event time of the guide's forward and gradient calls on `rows` random vertices."""
     import torch
@@ -538,7 +548,7 @@ def run_ugp(args):
             "roofline": {"bound": "hbm", "kernel": "k_extend (free-flight sampling)",
                          "achieved": achieved_gbs, "peak": peak, "unit": "GB/s",
                          "frac": (achieved_gbs / peak) if achieved_gbs else None, "peak_note": peak_note,
-                         "traffic": None,
+                         "traffic": extend_traffic(args),
                          "algorithmic_bytes_per_launch": alg_bytes_per_launch,
                          "nodes_per_query": nodes_per_query, "prims_per_query": prims_per_query,
                          "avg_launch_ms": avg_ext_ms},
