@@ -1,11 +1,13 @@
 """The allocation-free free-flight entry point against the regular one.
 
 ugp_sample_free_flight_noalloc serves callers that cannot allocate device memory: its scratch
-lives in a fixed device array inside the library.  Through the C ABI it must give the same
-samples as ugp_sample_free_flight (identical primitives, t_u and t_spawn within the parity
-tolerance), on two calls in a row (the second reuses the array the first left behind), and
-reject more rays than the array holds.  This file runs last so a failure here leaves every
-other test already run.
+lives in a fixed device array inside the library, without per-ray slot lists, so every bracketed
+ray is finished by a warp that rebuilds its intervals by traversal, where the regular entry
+point finishes most rays on 16 lanes from the slot list.  Through the C ABI it must give the
+same samples bit for bit (the finish sums in fixed point, so neither the collection path nor
+the lane count may change a result), on two calls in a row (the second reuses the array the
+first left behind), and reject more rays than the array holds.  This file runs last so a
+failure here leaves every other test already run.
 """
 import ctypes as C
 
@@ -16,7 +18,6 @@ from paper_2406_09733_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
 
-REL = 1e-5
 MAX_RAYS = 65536
 
 
@@ -66,11 +67,9 @@ def test_noalloc_matches_regular_entry_point_twice(env):
             bvh, dev(r.o), dev(r.d), dev(r.t0), dev(r.t1), dev(u), dev(u2)))
         assert np.array_equal(st, ref_st) and st.max() == 0
         assert np.array_equal(prim, ref_p)
-        hit = prim >= 0
-        span = (r.t1 - r.t0).astype(np.float64)
-        assert hit.mean() > 0.3
-        assert np.max(np.abs(tu[hit] - ref_tu[hit]) / span[hit]) <= REL
-        assert np.max(np.abs(tsp[hit] - ref_tsp[hit]) / span[hit]) <= REL
+        assert (prim >= 0).mean() > 0.3
+        assert np.array_equal(tu, ref_tu)
+        assert np.array_equal(tsp, ref_tsp)
 
 
 def test_noalloc_rejects_more_rays_than_its_array(env):
