@@ -63,6 +63,7 @@ def parse_args(argv=None):
     p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
     p.add_argument("--guide-alpha", type=float, default=0.5)
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving study")
+    p.add_argument("--no-rf", action="store_true", help="skip the radiance-field render study")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-spp-max", type=int, default=4,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
@@ -534,6 +535,9 @@ def run_ugp(args):
         mse = equal_time_mse(args, d, mats, scene, dev)
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_study(args, dev)
+    rf = None
+    if rank == 0 and world == 1 and not args.no_rf:
+        rf = radiance_field_study(args, d, scene, dev)
 
     if rank == 0:
         clk = clocks.summary()
@@ -554,11 +558,55 @@ def run_ugp(args):
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf, "serving": serving,
+            "radiance_field": rf,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def pinhole_rays(cam, W, H):
+    """Unit directions of W x H pixel-centre pinhole rays of a scene camera (row-major)."""
+    import numpy as np
+    f = np.array(cam.look, float) - cam.eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, cam.up); r /= np.linalg.norm(r)
+    up = np.cross(r, f)
+    th = np.tan(np.radians(cam.vfov_deg) / 2)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    d = f + ((W / H) * (2 * px / W - 1) * th)[..., None] * r + ((1 - 2 * py / H) * th)[..., None] * up
+    return (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3).astype(np.float32)
+
+
+def radiance_field_study(args, d, scene, dev, reps=10):
+    """Radiance-field forward render (Sec. 7, Eq. rf) of the bench scene's camera view, every
+    primitive emitting its albedo, background 0.2: one camera ray per pixel, CUDA-event time per
+    frame after 3 warm-up frames."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import ugp
+    W, H = args.width, args.height
+    dirs = torch.from_numpy(pinhole_rays(scene.camera, W, H)).to(dev)
+    n = dirs.shape[0]
+    O = torch.tensor(np.array(scene.camera.eye, np.float32), device=dev).expand(n, 3).contiguous()
+    T0, T1 = torch.zeros(n, device=dev), torch.full((n,), 1e30, device=dev)
+    em = torch.from_numpy(np.ascontiguousarray(scene.albedo, dtype=np.float32)).to(dev)
+    bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
+    ws = torch.empty(int(ugp.lib().ugp_render_radiance_field_workspace_size(n)), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        rgb, st = ugp.render_radiance_field(bvh, O, dirs, T0, T1, em, (0.2, 0.2, 0.2), workspace=ws)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        rgb, st = ugp.render_radiance_field(bvh, O, dirs, T0, T1, em, (0.2, 0.2, 0.2), workspace=ws)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    return {"image": f"{W}x{H}", "rays": n, "ms_per_frame": ms, "Mrays_per_s": n / (ms / 1e3) / 1e6,
+            "queries_with_error_status": int((st != 0).sum().item()), "mean_rgb": rgb.mean(0).tolist(),
+            "emission": "per-primitive albedo, background 0.2"}
 
 
 def run_kernel_case(args):
@@ -571,16 +619,8 @@ def run_kernel_case(args):
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     s = scenes.room_scene(args.n_prims)
     bvh = ugp.build_bvh(t(s.mean), t(s.quat), t(s.scale), t(s.magnitude))
-    W = H = 512
     cam = s.camera
-    f = np.array(cam.look, float) - cam.eye
-    f /= np.linalg.norm(f)
-    r = np.cross(f, cam.up); r /= np.linalg.norm(r)
-    up = np.cross(r, f)
-    th = np.tan(np.radians(cam.vfov_deg) / 2)
-    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
-    d = f + ((2 * px / W - 1) * th)[..., None] * r + ((1 - 2 * py / H) * th)[..., None] * up
-    d = (d / np.linalg.norm(d, axis=-1, keepdims=True)).reshape(-1, 3).astype(np.float32)
+    d = pinhole_rays(cam, 512, 512)
     n = d.shape[0]
     O, D = t(np.tile(np.array(cam.eye, np.float32), (n, 1))), t(d)
     T0, T1 = torch.zeros(n, device=dev), torch.full((n,), 4.0, device=dev)

@@ -210,6 +210,31 @@ ugp_status ugp_collect_hits(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
                             int32_t cap, int32_t* ids_out, float* a_out, float* b_out,
                             int32_t* count_out, uint8_t* status_out, void* stream);
 
+/* Radiance-field forward render (Sec. 7, Eq. rf): the primitives as an emitting,
+ * non-scattering medium, rendered deterministically.  For ray r, with F the free-flight CDF
+ * of Eq. 8 over [t0, t1] and t_sat its root at 1 (the saturating distance; t_sat = t1 when
+ * F(t1) <= 1):
+ *   rgb_out[3r + c] = sum_k 1/2 I_k(a_k, min(b_k, t_sat)) emission3[3k + c]
+ *                     + (F(t1) <= 1 ? 1 - F(t1) : 0) background3[c]
+ * summed over the primitives whose clipped interval [a_k, b_k] meets [t0, t_sat].
+ *   emission3    device float array (n_prims x 3), indexed by the caller's primitive index
+ *   background3  HOST pointer to 3 floats, or NULL for black
+ *   rgb_out      device float array (n_rays x 3)
+ *   status_out   device uint8 array (n_rays) or NULL: the free-flight pass's status, else
+ *                the traversal's (UGP_RAY_*)
+ *   workspace    device scratch of ugp_render_radiance_field_workspace_size(n_rays) bytes,
+ *                256-byte aligned
+ *   other arguments as for ugp_trace_transmittance (rays are not clipped at an excluded
+ *   primitive here).
+ * Asynchronous on `stream`.  Errors: UGP_ERR_NOT_BUILT for an invalid handle;
+ * UGP_ERR_INVALID_ARG for a NULL array, a misaligned workspace or n_rays outside
+ * [0, 2^31 - 1]; UGP_ERR_WORKSPACE_TOO_SMALL. */
+size_t ugp_render_radiance_field_workspace_size(int64_t n_rays);
+ugp_status ugp_render_radiance_field(const ugp_bvh* bvh, int64_t n_rays, const float* o3, const float* d3,
+                                     const float* t0, const float* t1, const float* emission3,
+                                     const float* background3, float* rgb_out, uint8_t* status_out,
+                                     void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------ rendering
  * Per-primitive appearance (Sec. 6), device arrays in the caller's order:
  *   sggx6      SGGX matrix S (Sxx, Syy, Szz, Sxy, Sxz, Syz), positive definite (n x 6)

@@ -52,6 +52,8 @@ def lib():
                                              f32p, f32p, f32p, i32p, f32p, f32p, i32p, f64p,
                                              f64p, f64p, i32p, f64p]
         L.orc_race_exponential.argtypes = [C.c_double, C.c_int32]
+        L.orc_radiance_field.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p,
+                                         f32p, f64p, C.c_double, f64p, f64p, f64p]
         L.orc_race_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
         L.orc_erfinv.argtypes = [C.c_double]
@@ -180,6 +182,25 @@ def sample_free_flight(scene, rays, u, u2, exclude=None, eps=0.01):
                                  _ptr(prim, i32p), _ptr(tu, f64p), _ptr(ts, f64p), _ptr(fe, f64p),
                                  _ptr(na, i32p), _ptr(mg, f64p))
     return dict(prim=prim, t_u=tu, t_spawn=ts, F_end=fe, n_active=na, race_margin=mg)
+
+
+def radiance_field(scene, rays, emission, background=(0.0, 0.0, 0.0), eps=0.01, t_shift_ulps=0.0):
+    """Radiance-field render of Sec. 7 (Eq. rf): per ray the RGB sum of 1/2 I_k clipped at the
+    saturating distance times primitive k's emission (indexed by primitive), plus the
+    unsaturated remainder times the background. t_shift_ulps moves the saturating distance by
+    that many float32 ulps of itself (for tolerance bounds). Returns (rgb (n, 3), t_sat (n,),
+    F_end (n,))."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    em = _c(emission, np.float32)
+    bg = _c(np.asarray(background, np.float64), np.float64)
+    rgb, ts, fe = np.zeros((n, 3)), np.zeros(n), np.zeros(n)
+    lib().orc_radiance_field(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p), _ptr(t1, f32p),
+                             _ptr(em, f32p), _ptr(bg, f64p), float(t_shift_ulps), _ptr(rgb, f64p), _ptr(ts, f64p),
+                             _ptr(fe, f64p))
+    return rgb, ts, fe
 
 
 def race_exponential(u2: float, k: int) -> float:

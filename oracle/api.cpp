@@ -143,6 +143,19 @@ void orc_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, c
   }
 }
 
+// Batched radiance-field render (Sec. 7, Eq. rf) by brute force.
+void orc_radiance_field(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3, const float* d3,
+                        const float* t0, const float* t1, const float* emission3, const double* background3,
+                        double t_shift_ulps, double* rgb_out, double* t_sat_out, double* F_end_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r)
+    radiance_field(prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r], t1[r], k, emission3, background3,
+                   t_shift_ulps, rgb_out + 3 * r, t_sat_out ? t_sat_out + r : nullptr,
+                   F_end_out ? F_end_out + r : nullptr);
+}
+
 // App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.
 void orc_prim_quadratic(const orc_scene* s, int64_t i, const float* o3, const float* d3, double* out3) {
   const Prim p = make_prim(s->mean3 + 3 * i, s->quat4 + 4 * i, s->scale3 + 3 * i, s->magnitude[i]);

@@ -267,6 +267,34 @@ FreeFlight sample_free_flight(const std::vector<Prim>& prims, V3 o, V3 d, double
   return sample_free_flight_hits(all_hits(prims, o, d, t0, t1, k, exclude), t0, t1, u, u2);
 }
 
+// Sec. 7, Eq. rf. The saturating distance is where F reaches 1, i.e. the free-flight root for
+// u = 1 (the paper's "u = 1" disambiguation); every primitive then counts with its probability
+// mass up to t_sat, 1/2 I_k(a_k, min(b_k, t_sat)), which needs no disambiguation at all.
+void radiance_field(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1, double k,
+                    const float* emission3, const double* background3, double t_shift_ulps, double* rgb_out,
+                    double* t_sat_out, double* F_end_out) {
+  const std::vector<Hit> hits = all_hits(prims, o, d, t0, t1, k, -1);
+  const FreeFlight f = sample_free_flight_hits(hits, t0, t1, 1.0, 0.0);
+  const bool saturated = f.prim >= 0;
+  double t_sat = saturated ? f.t_u : t1;
+  if (saturated && t_shift_ulps != 0.0) {
+    const float tf = float(t_sat);
+    t_sat += t_shift_ulps * double(std::nextafter(tf, INFINITY) - tf);
+  }
+  double rgb[3] = {0.0, 0.0, 0.0}, mass = 0.0;
+  for (const Hit& h : hits) {
+    const double y = std::min(h.b, t_sat);
+    if (!(h.a < y)) continue;
+    const double w = 0.5 * ray_integral(h, h.a, y);
+    mass += w;
+    for (int c = 0; c < 3; ++c) rgb[c] += w * double(emission3[3 * size_t(h.id) + c]);
+  }
+  const double rest = saturated ? 0.0 : std::max(0.0, 1.0 - mass);
+  for (int c = 0; c < 3; ++c) rgb_out[c] = rgb[c] + rest * (background3 ? background3[c] : 0.0);
+  if (t_sat_out) *t_sat_out = t_sat;
+  if (F_end_out) *F_end_out = f.F_end;
+}
+
 // Philox4x32-10: ten rounds of two 32x32->64 multiplications with the key bumped by the
 // Weyl constants between rounds (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 4).
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

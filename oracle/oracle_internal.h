@@ -99,6 +99,16 @@ FreeFlight sample_free_flight(const std::vector<Prim>& prims, V3 o, V3 d, double
 FreeFlight sample_free_flight_hits(const std::vector<Hit>& hits, double t0, double t1, double u,
                                    double u2);
 
+// Radiance-field render of Sec. 7 (Eq. rf): L = sum_k 1/2 I_k(a_k, min(b_k, t_sat)) L_e,k, with
+// t_sat the root of F(t_sat) = 1 (free flight at u = 1); when F(t1) <= 1 the ray is not
+// saturated, t_sat = t1 and the remaining 1 - F(t1) sees the background. emission3 is indexed
+// by primitive id. Returns F(t1) in *F_end (unclamped).
+// t_shift_ulps moves the saturating distance by that many float32 ulps of itself (0: none), so a
+// test can bound how much the float32 resolution of t changes the result.
+void radiance_field(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1, double k,
+                    const float* emission3, const double* background3, double t_shift_ulps, double* rgb_out,
+                    double* t_sat_out, double* F_end_out);
+
 double erfinv(double y);
 double race_exponential(double u2, int32_t k);
 

@@ -105,6 +105,11 @@ def lib():
         L.ugp_profile_end.restype = C.c_int
         L.ugp_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.ugp_launch_count.restype = C.c_int64
+        L.ugp_render_radiance_field_workspace_size.restype = C.c_size_t
+        L.ugp_render_radiance_field_workspace_size.argtypes = [C.c_int64]
+        L.ugp_render_radiance_field.restype = C.c_int
+        L.ugp_render_radiance_field.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.POINTER(C.c_float), vp, vp, vp,
+                                                C.c_size_t, vp]
         L.ugp_set_trace_counters.restype = C.c_int
         L.ugp_set_trace_counters.argtypes = [vp]
         for fn in _EXTRA:
@@ -237,6 +242,29 @@ def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None,
                                         C.c_void_p(_stream(stream))),
            "ugp_sample_free_flight")
     return prim, tu, tsp, st
+
+
+def render_radiance_field(bvh: Bvh, o, d, t0, t1, emission, background=None, stream=None, workspace=None):
+    """Radiance-field forward render (Sec. 7, Eq. rf): per ray the emission-weighted 1/2 I of
+    every primitive clipped at the saturating distance, plus the unsaturated remainder times
+    the background. Returns (rgb (n, 3), status (n,))."""
+    n = int(o.shape[0])
+    nb = int(lib().ugp_render_radiance_field_workspace_size(n))
+    if workspace is None or workspace.numel() < nb:
+        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=o.device)
+    for t, nm in ((t0, "t0"), (t1, "t1")):
+        _dev(t, torch.float32, nm)
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    _dev(emission, torch.float32, "emission", 3)
+    rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    bg = None if background is None else (C.c_float * 3)(*[float(x) for x in background])
+    _check(lib().ugp_render_radiance_field(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1), _p(emission),
+                                           bg, _p(rgb), _p(st), _p(workspace), workspace.numel(),
+                                           C.c_void_p(_stream(stream))),
+           "ugp_render_radiance_field")
+    return rgb, st
 
 
 def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):

@@ -55,6 +55,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         ugp.lib()
 
 
+def test_radiance_field_entry_point_validates_on_host(libugp):
+    libugp.ugp_render_radiance_field_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_render_radiance_field_workspace_size.argtypes = [ctypes.c_int64]
+    libugp.ugp_last_error.restype = ctypes.c_char_p
+    ff = libugp.ugp_sample_free_flight_workspace_size
+    ff.restype = ctypes.c_size_t
+    ff.argtypes = [ctypes.c_int64]
+    # the free-flight pass's scratch plus six per-ray columns
+    assert libugp.ugp_render_radiance_field_workspace_size(1000) >= ff(1000) + 6 * 1000
+    assert libugp.ugp_render_radiance_field_workspace_size(-1) == 0
+    st = libugp.ugp_render_radiance_field(None, ctypes.c_int64(4), None, None, None, None, None, None, None, None,
+                                          None, ctypes.c_size_t(0), None)
+    assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()   # UGP_ERR_NOT_BUILT
+
+
 def test_guide_entry_points_validate_on_host(libugp):
     libugp.ugp_guide_workspace_size.restype = ctypes.c_size_t
     libugp.ugp_render_guided_workspace_size.restype = ctypes.c_size_t

@@ -436,6 +436,44 @@ def test_free_flight_independent_of_ray_order(gpu):
         assert np.array_equal(x[perm], y)
 
 
+def test_radiance_field_parity(gpu, orc):
+    """Radiance-field render (Sec. 7, Eq. rf) against the FP64 oracle: random rays through a
+    tiny scene (mostly unsaturated: the background shows through), the same with saturating
+    clusters, and camera and interior rays of a room with surface splats and dense clusters."""
+    from paper_2406_09733_gb300 import ugp
+    torch = gpu
+    rng = np.random.default_rng(80)
+    s1 = scenes.tiny_scene(n=2000, seed=81)
+    s2 = scenes.tiny_scene(n=2000, seed=82)
+    s2.magnitude[:] *= 6.0
+    s3 = scenes.room_scene(100_000, seed=3, n_clusters=30)
+    n3 = 2000
+    o3 = np.tile(np.array(s3.camera.eye), (n3, 1))
+    o3[n3 // 2:] = rng.uniform(0.05, 0.95, (n3 - n3 // 2, 3))
+    d3 = rng.uniform(0.02, 0.98, (n3, 3)) - o3
+    d3 /= np.linalg.norm(d3, axis=1, keepdims=True)
+    r3 = scenes.Rays(o3.astype(np.float32), d3.astype(np.float32), np.zeros(n3, np.float32),
+                     np.full(n3, 4.0, np.float32))
+    bg = (0.2, 0.5, 0.9)
+    for s, r in ((s1, scenes.random_rays(4000, seed=83)), (s2, scenes.random_rays(4000, seed=84)), (s3, r3)):
+        em = rng.uniform(0.0, 2.0, (s.n, 3)).astype(np.float32)
+        rgb, st = ugp.render_radiance_field(build_scene(torch, s), dev(torch, r.o), dev(torch, r.d),
+                                            dev(torch, r.t0), dev(torch, r.t1), dev(torch, em), bg)
+        ref, _, F_end = orc.radiance_field(s, r, em, bg)
+        # float32 t resolves the saturating distance to an ulp of itself; through a splat 1e-5
+        # thick that is a visible share of its mass, so the bound includes how much L moves
+        # when t_sat moves by 4 ulps (the weights' split among the primitives straddling it)
+        lo = orc.radiance_field(s, r, em, bg, t_shift_ulps=-4.0)[0]
+        hi = orc.radiance_field(s, r, em, bg, t_shift_ulps=4.0)[0]
+        assert st.cpu().numpy().max() == 0
+        got = rgb.cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref)
+        tol = (np.maximum(np.abs(lo - ref), np.abs(hi - ref)) + 5e-5 * max(float(em.max()), max(bg))
+               + 1e-5 * np.abs(ref))
+        assert np.all(err <= tol), (err.max(), np.unravel_index(np.argmax(err / tol), err.shape))
+    assert (F_end > 1).mean() > 0.2   # the room's rays saturate
+
+
 def test_edge_cases(gpu, orc):
     from paper_2406_09733_gb300 import ugp
     torch = gpu

@@ -408,3 +408,78 @@ def test_escape_probability_equals_transmittance(orc):
 def test_erfinv(orc):
     for y in np.linspace(-0.999999, 0.999999, 41):
         assert abs(orc.erfinv(y) - special.erfinv(y)) < 1e-12 * max(1, abs(special.erfinv(y)))
+
+
+# ---------------------------------------------------------------------------- f3: radiance field
+def _rf_reference(s, o, d, t1, em, bg):
+    """Eq. rf by quadrature: the saturating distance is the root of the quadrature F at 1, and
+    each primitive weighs its emission by 1/2 the quadrature integral of G up to it."""
+    od, dd = o.astype(np.float64), d.astype(np.float64)
+    from oracle import hits as _h
+    F_end = _F_quad(s, od, dd, 0.0, t1)
+    h = _h(s, o, d, 0.0, t1)
+    t_sat = t1
+    if F_end > 1.0:
+        t_sat = optimize.brentq(lambda t: _F_quad(s, od, dd, 0.0, t) - 1.0, h["a"].min(), h["b"].max(),
+                                xtol=1e-13)
+    rgb = np.zeros(3)
+    mass = 0.0
+    for k, i in enumerate(h["ids"]):
+        a, b = h["a"][k], min(h["b"][k], t_sat)
+        if b <= a:
+            continue
+        w = 0.5 * integrate.quad(lambda t: density(s, i, od + t * dd), a, b, epsabs=0, epsrel=1e-13)[0]
+        mass += w
+        rgb += w * em[i].astype(np.float64)
+    if F_end <= 1.0:
+        rgb += max(0.0, 1.0 - mass) * np.asarray(bg, np.float64)
+    return rgb, t_sat
+
+
+@pytest.mark.parametrize("boost", [0.2, 5.0])
+def test_radiance_field_matches_quadrature(orc, boost):
+    """Sec. 7, Eq. rf against quadrature: an unsaturated ray (background seen through) and a
+    saturated one (emission summed up to t_sat, where several ellipsoids straddle t_sat)."""
+    s = _dense_cluster(n=8, seed=60, boost=boost)
+    rng = np.random.default_rng(70)
+    em = rng.uniform(0.0, 2.0, (s.n, 3)).astype(np.float32)
+    bg = (0.3, 0.1, 0.7)
+    o = np.array([0.5, 0.5, 0.0], np.float32)
+    d = np.array([0.002, -0.001, 1.0]); d = (d / np.linalg.norm(d)).astype(np.float32)
+    r = scenes.Rays(o[None], d[None], np.zeros(1, np.float32), np.full(1, 2.0, np.float32))
+    rgb, t_sat, F_end = orc.radiance_field(s, r, em, bg)
+    ref, ref_t = _rf_reference(s, o, d, 2.0, em, bg)
+    assert (F_end[0] > 1.0) == (boost > 1.0)
+    assert abs(t_sat[0] - ref_t) < 1e-10
+    np.testing.assert_allclose(rgb[0], ref, rtol=1e-9, atol=1e-12)
+
+
+def test_radiance_field_partition_of_unity(orc):
+    """With one emission for every primitive and the background, the weights of Eq. rf sum to 1:
+    every ray sees exactly that radiance, saturated or not."""
+    s = _dense_cluster(n=60, seed=71, boost=3.0)
+    r = scenes.random_rays(400, seed=72, centre=(0.5, 0.5, 0.5), radius=0.3)
+    c = np.array([0.25, 1.5, 3.0])
+    rgb, _, F_end = orc.radiance_field(s, r, np.tile(c.astype(np.float32), (s.n, 1)), c)
+    assert (F_end > 1).mean() > 0.2 and (F_end < 1).mean() > 0.2
+    np.testing.assert_allclose(rgb, np.tile(c, (r.n, 1)), rtol=1e-12)
+
+
+def test_radiance_field_is_the_mean_of_free_flight_samples(orc):
+    """The render is the expectation of the path tracer's one-sample estimator for an emitting,
+    non-scattering medium: the emission of the free-flight sample (the background when it
+    escapes), Sec. 7. Checked against 200,000 samples of the oracle's sampler."""
+    s = _dense_cluster(n=8, seed=60, boost=1.1)
+    rng = np.random.default_rng(73)
+    em = rng.uniform(0.0, 1.0, (s.n, 3)).astype(np.float32)
+    bg = np.array([0.9, 0.2, 0.4])
+    o = np.array([0.5, 0.5, 0.0], np.float32)
+    d = np.array([0.002, -0.001, 1.0]); d = (d / np.linalg.norm(d)).astype(np.float32)
+    r1 = scenes.Rays(o[None], d[None], np.zeros(1, np.float32), np.full(1, 2.0, np.float32))
+    rgb, _, _ = orc.radiance_field(s, r1, em, bg)
+    n = 200000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    f = orc.sample_free_flight(s, r, scenes.uniforms24(74, n), scenes.uniforms24(75, n))
+    val = np.where(f["prim"][:, None] >= 0, em[np.maximum(f["prim"], 0)].astype(np.float64), bg[None])
+    mean, se = val.mean(0), val.std(0) / math.sqrt(n)
+    assert np.all(np.abs(mean - rgb[0]) <= 5 * se + 1e-12), (mean, rgb[0], se)
