@@ -55,6 +55,13 @@ def lib():
         L.orc_radiance_field.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p,
                                          f32p, f64p, C.c_double, f64p, f64p, f64p]
         L.orc_race_exponential.restype = C.c_double
+        L.orc_sample_free_flight_exponential.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
+                                                         f32p, f32p, i32p, f32p, i32p, f64p, f64p, f64p, f64p,
+                                                         f64p, f64p]
+        L.orc_transmittance_exponential.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
+                                                    f32p, f32p, i32p, f64p, f64p]
+        L.orc_decomposition_exponential.argtypes = [C.c_double, C.c_int32]
+        L.orc_decomposition_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
         L.orc_erfinv.argtypes = [C.c_double]
         L.orc_erfinv.restype = C.c_double
@@ -201,6 +208,45 @@ def radiance_field(scene, rays, emission, background=(0.0, 0.0, 0.0), eps=0.01, 
                              _ptr(em, f32p), _ptr(bg, f64p), float(t_shift_ulps), _ptr(rgb, f64p), _ptr(ts, f64p),
                              _ptr(fe, f64p))
     return rgb, ts, fe
+
+
+def sample_free_flight_exponential(scene, rays, u, exclude=None, eps=0.01):
+    """Analog decomposition tracking of the exponential variant (sigma_t = sum_k G_k): per ray
+    the nearest per-primitive exponential collision, keyed by the uniform u. Returns a dict of
+    prim (-1: escape), t (t1 on escape), t_second (next-nearest collision, inf if none), margin
+    (min relative gap between a primitive's variate and its optical depth), amp and G_t of the
+    chosen primitive (I = amp [erf(tau_t) - erf(tau_a)], G at t) and depth (sum_k I_k)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    u = _c(u, np.float32)
+    ex = None if exclude is None else _c(exclude, np.int32)
+    prim = np.zeros(n, np.int32)
+    t, t2, mg, amp, G, depth = (np.zeros(n) for _ in range(6))
+    lib().orc_sample_free_flight_exponential(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
+                                             _ptr(t1, f32p), _ptr(ex, i32p), _ptr(u, f32p), _ptr(prim, i32p),
+                                             _ptr(t, f64p), _ptr(t2, f64p), _ptr(mg, f64p), _ptr(amp, f64p),
+                                             _ptr(G, f64p), _ptr(depth, f64p))
+    return dict(prim=prim, t=t, t_second=t2, margin=mg, amp=amp, G_t=G, depth=depth)
+
+
+def transmittance_exponential(scene, rays, exclude=None, eps=0.01):
+    """exp(-sum_k I_k) over each ray's [t0, t1]; returns (T, optical depth)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    ex = None if exclude is None else _c(exclude, np.int32)
+    T, depth = np.zeros(n), np.zeros(n)
+    lib().orc_transmittance_exponential(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
+                                        _ptr(t1, f32p), _ptr(ex, i32p), _ptr(T, f64p), _ptr(depth, f64p))
+    return T, depth
+
+
+def decomposition_exponential(u: float, k: int) -> float:
+    """The collision depth E_k = -ln U_k of primitive k for the ray uniform u."""
+    return float(lib().orc_decomposition_exponential(float(np.float32(u)), int(k)))
 
 
 def race_exponential(u2: float, k: int) -> float:

@@ -156,6 +156,43 @@ void orc_radiance_field(const orc_scene* s, double cutoff_eps, int64_t nr, const
                    F_end_out ? F_end_out + r : nullptr);
 }
 
+// Batched analog decomposition tracking of the exponential variant, one uniform u per ray
+// (the key of the per-primitive variates).
+void orc_sample_free_flight_exponential(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3,
+                                        const float* d3, const float* t0, const float* t1,
+                                        const int32_t* exclude, const float* u, int32_t* prim_out,
+                                        double* t_out, double* t_second_out, double* margin_out, double* amp_out,
+                                        double* G_out, double* depth_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r) {
+    const ExpFreeFlight f = sample_free_flight_exponential(prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r],
+                                                           t1[r], k, exclude ? exclude[r] : -1, u[r]);
+    prim_out[r] = f.prim;
+    t_out[r] = f.t;
+    t_second_out[r] = f.t_second;
+    margin_out[r] = f.margin;
+    amp_out[r] = f.amp;
+    G_out[r] = f.G_t;
+    depth_out[r] = f.depth;
+  }
+}
+
+// Batched exponential transmittance exp(-sum_k I_k).
+void orc_transmittance_exponential(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3,
+                                   const float* d3, const float* t0, const float* t1, const int32_t* exclude,
+                                   double* T_out, double* depth_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r)
+    T_out[r] = transmittance_exponential(prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r], t1[r], k,
+                                         exclude ? exclude[r] : -1, depth_out ? depth_out + r : nullptr);
+}
+
+double orc_decomposition_exponential(double u, int32_t k) { return decomposition_exponential(u, k); }
+
 // App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.
 void orc_prim_quadratic(const orc_scene* s, int64_t i, const float* o3, const float* d3, double* out3) {
   const Prim p = make_prim(s->mean3 + 3 * i, s->quat4 + 4 * i, s->scale3 + 3 * i, s->magnitude[i]);

@@ -295,6 +295,89 @@ void radiance_field(const std::vector<Prim>& prims, V3 o, V3 d, double t0, doubl
   if (F_end_out) *F_end_out = f.F_end;
 }
 
+// Appendix "Sampling Exponential Transmittance Gaussians via Analog Decomposition Tracking".
+// The same Gaussians read as an extinction coefficient sigma_t(x) = sum_k G_k(x) of the
+// exponential model (Eq. exp_ff): T(t0, t) = exp(-sum_k I_k), every contribution clipped to the
+// primitive's ellipsoid as in Sec. 4.1.
+
+// Optical depth E_k at which component k collides: Philox4x32-10 with key (bits of u,
+// 0x2406DEC0) and counter (k, 0, 0, 0), U = ((x0 >> 8) + 1) / 2^24 in (0, 1], E_k = -ln U (the
+// appendix's -ln(1 - u') with u' = 1 - U).
+double decomposition_exponential(double u, int32_t k) {
+  const float f = float(u);
+  uint32_t bits;
+  std::memcpy(&bits, &f, 4);
+  const uint32_t ctr[4] = {uint32_t(k), 0u, 0u, 0u};
+  const uint32_t key[2] = {bits, 0x2406DEC0u};
+  uint32_t x[4];
+  philox4x32_10(ctr, key, x);
+  return -std::log(double((x[0] >> 8) + 1u) * (1.0 / 16777216.0));
+}
+
+// The distance t in [a, b] of a hit with I(a, t) = E, for 0 < E < I(a, b): the erf^-1 closed
+// form of App. A as the first guess, then Newton's method on I(a, t) - E with I' = G, kept
+// inside a shrinking bracket.
+double invert_integral(const Hit& h, double E) {
+  const double s = std::sqrt(0.5 * h.A);
+  const double amp = h.g0 * std::exp(-0.5 * h.d2) * std::sqrt(kPi / (2.0 * h.A));
+  double lo = h.a, hi = h.b;
+  double t = h.tstar + erfinv(std::erf(s * (h.a - h.tstar)) + E / amp) / s;
+  if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    const double f = ray_integral(h, h.a, t) - E;
+    if (f == 0.0) return t;
+    if (f < 0) lo = t; else hi = t;
+    const double fp = gauss_at(h, t);
+    double tn = fp > 0 ? t - f / fp : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) || hi - lo <= 1e-16 * std::max(1.0, std::fabs(t)))
+      return tn;
+    t = tn;
+  }
+  return t;
+}
+
+// Analog decomposition tracking: every primitive on the ray samples its own exponential
+// free flight by inverting 1 - exp(-I_k(a_k, t)) (a collision only when E_k < I_k(a_k, b_k)),
+// and the nearest collision is the sample of the summed medium (equal distances: the lower id).
+ExpFreeFlight sample_free_flight_exponential(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
+                                             double k, int32_t exclude, double u) {
+  const double inf = std::numeric_limits<double>::infinity();
+  ExpFreeFlight r{-1, t1, inf, inf, 0.0, 0.0, 0.0};
+  const std::vector<Hit> hits = all_hits(prims, o, d, t0, t1, k, exclude);
+  const Hit* pick = nullptr;
+  for (const Hit& h : hits) {
+    const double E = decomposition_exponential(u, h.id);
+    const double I = ray_integral(h, h.a, h.b);
+    r.depth += I;
+    r.margin = std::min(r.margin, std::fabs(E - I) / std::max(E, I));
+    if (!(E < I)) continue;
+    const double t = invert_integral(h, E);
+    if (!pick || t < r.t) {
+      if (pick) r.t_second = r.t;
+      r.t = t;
+      pick = &h;
+    } else if (t < r.t_second) {
+      r.t_second = t;
+    }
+  }
+  if (pick) {
+    r.prim = pick->id;
+    r.amp = pick->g0 * std::exp(-0.5 * pick->d2) * std::sqrt(kPi / (2.0 * pick->A));
+    r.G_t = gauss_at(*pick, r.t);
+  }
+  return r;
+}
+
+// Exponential transmittance over [t0, t1] (Eq. exp_ff with the ellipsoid cut-off).
+double transmittance_exponential(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1, double k,
+                                 int32_t exclude, double* depth_out) {
+  double depth = 0.0;
+  for (const Hit& h : all_hits(prims, o, d, t0, t1, k, exclude)) depth += ray_integral(h, h.a, h.b);
+  if (depth_out) *depth_out = depth;
+  return std::exp(-depth);
+}
+
 // Philox4x32-10: ten rounds of two 32x32->64 multiplications with the key bumped by the
 // Weyl constants between rounds (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 4).
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

@@ -109,6 +109,24 @@ void radiance_field(const std::vector<Prim>& prims, V3 o, V3 d, double t0, doubl
                     const float* emission3, const double* background3, double t_shift_ulps, double* rgb_out,
                     double* t_sat_out, double* F_end_out);
 
+// Exponential-transmittance variant (appendix on analog decomposition tracking): sigma_t(x) =
+// sum_k G_k(x) and T = exp(-sum_k I_k) with the ellipsoid cut-off.
+struct ExpFreeFlight {
+  int32_t prim;     // nearest colliding primitive, -1: escape
+  double t;         // its collision distance (t1 on escape)
+  double t_second;  // second-nearest collision distance (inf if none)
+  double margin;    // min over the ray's primitives of |E_k - I_k(a_k, b_k)| / max(E_k, I_k)
+  double amp;       // g0 e^{-d2/2} sqrt(pi / 2A) of the chosen primitive: I = amp [erf(tau_t) - erf(tau_a)]
+  double G_t;       // G of the chosen primitive at t
+  double depth;     // sum_k I_k(a_k, b_k): optical depth of [t0, t1]
+};
+double decomposition_exponential(double u, int32_t k);
+double invert_integral(const Hit& h, double E);
+ExpFreeFlight sample_free_flight_exponential(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
+                                             double k, int32_t exclude, double u);
+double transmittance_exponential(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1, double k,
+                                 int32_t exclude, double* depth_out);
+
 double erfinv(double y);
 double race_exponential(double u2, int32_t k);
 

@@ -483,3 +483,162 @@ def test_radiance_field_is_the_mean_of_free_flight_samples(orc):
     val = np.where(f["prim"][:, None] >= 0, em[np.maximum(f["prim"], 0)].astype(np.float64), bg[None])
     mean, se = val.mean(0), val.std(0) / math.sqrt(n)
     assert np.all(np.abs(mean - rgb[0]) <= 5 * se + 1e-12), (mean, rgb[0], se)
+
+
+# ---------------------------------------------------------------------------- f3: exponential variant
+def _exp_ray():
+    o = np.array([0.5, 0.5, 0.0], np.float32)
+    d = np.array([0.002, -0.001, 1.0]); d = (d / np.linalg.norm(d)).astype(np.float32)
+    return o, d
+
+
+def test_decomposition_variates_are_unit_exponential(orc):
+    """The per-primitive collision depths E_k are independent unit exponentials (KS over the ray
+    uniform for one primitive, and across primitives for one uniform)."""
+    from scipy import stats
+    us = np.arange(1, 40001, dtype=np.float64) / 40001.0
+    e1 = np.array([orc.decomposition_exponential(u, 7) for u in us])
+    e2 = np.array([orc.decomposition_exponential(0.375, k) for k in range(40000)])
+    assert stats.kstest(e1, "expon").pvalue > 1e-3
+    assert stats.kstest(e2, "expon").pvalue > 1e-3
+    assert abs(np.corrcoef(e1[:-1], e1[1:])[0, 1]) < 0.03
+
+
+def test_exponential_collision_is_the_nearest_component_sample(orc):
+    """Appendix on analog decomposition tracking: the chosen primitive's optical depth from its
+    entry to t equals its variate E_k (quadrature of Eq. 1), and no other primitive on the ray
+    reaches its own E_j before t; an escaping ray has E_j above every primitive's depth."""
+    s = _dense_cluster(n=8, seed=60, boost=0.6)
+    n = 60
+    rng = np.random.default_rng(90)
+    o = np.tile(np.array([0.5, 0.5, 0.0], np.float32), (n, 1))
+    d = np.tile(np.array([0, 0, 1.0]), (n, 1)) + rng.normal(scale=0.01, size=(n, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    r = scenes.Rays(o, d, np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    u = scenes.uniforms24(91, n)
+    f = orc.sample_free_flight_exponential(s, r, u)
+    assert 10 < (f["prim"] >= 0).sum() < n - 10
+    for j in range(n):
+        od, dd = o[j].astype(np.float64), d[j].astype(np.float64)
+        h = orc.hits(s, o[j], d[j], 0.0, 2.0)
+        for m, i in enumerate(h["ids"]):
+            E = orc.decomposition_exponential(u[j], i)
+            upto = h["b"][m] if f["prim"][j] < 0 else min(h["b"][m], f["t"][j])
+            depth = 0.0 if upto <= h["a"][m] else integrate.quad(
+                lambda t: density(s, i, od + t * dd), h["a"][m], upto, epsabs=0, epsrel=1e-13)[0]
+            if i == f["prim"][j]:
+                assert abs(depth - E) <= 1e-10 * E, (j, i, depth, E)
+            else:
+                assert depth <= E * (1 + 1e-10), (j, i, depth, E)
+
+
+def test_exponential_single_component_closed_form(orc):
+    """One primitive inverts 1 - exp(-I(a, t)) = u' in closed form through erf^-1 (App. A), in
+    40-digit arithmetic from Eq. 1 written out with mpmath."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    s = scenes.tiny_scene(n=1, seed=50)
+    s.magnitude[0] *= 50
+    d = np.array([0.2, 0.1, 0.97]); d = (d / np.linalg.norm(d)).astype(np.float32)
+    o = (s.mean[0] - 1.0 * d + np.array([0.003, -0.002, 0.0])).astype(np.float32)
+    n = 200
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32),
+                    np.full(n, 3.0, np.float32))
+    u = scenes.uniforms24(92, n)
+    f = orc.sample_free_flight_exponential(s, r, u)
+    w, x, y, z = [mp.mpf(float(v)) for v in s.quat[0]]
+    qn = mp.sqrt(w * w + x * x + y * y + z * z)
+    w, x, y, z = w / qn, x / qn, y / qn, z / qn
+    R = mp.matrix([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                   [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                   [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    S = mp.diag([mp.mpf(float(v)) for v in s.scale[0]])
+    Si = (R * S * S * R.T) ** -1
+    xx = mp.matrix([mp.mpf(float(v)) for v in o]) - mp.matrix([mp.mpf(float(v)) for v in s.mean[0]])
+    dm = mp.matrix([mp.mpf(float(v)) for v in d])
+    A = (dm.T * Si * dm)[0]
+    B = 2 * (dm.T * Si * xx)[0]
+    C = (xx.T * Si * xx)[0]
+    g0 = mp.mpf(float(s.magnitude[0])) / ((2 * mp.pi) ** 1.5 * mp.sqrt(mp.det(R * S * S * R.T)))
+    amp = g0 * mp.exp(B * B / (8 * A) - C / 2) * mp.sqrt(mp.pi / (2 * A))
+    tau = lambda t: mp.sqrt(A / 2) * t + B / (2 * mp.sqrt(2 * A))
+    kk = mp.sqrt(-2 * mp.log(mp.mpf("0.01")))
+    t_a = -B / (2 * A) - mp.sqrt((kk * kk - (C - B * B / (4 * A))) / A)
+    t_b = -B / (2 * A) + mp.sqrt((kk * kk - (C - B * B / (4 * A))) / A)
+    I_ab = amp * (mp.erf(tau(t_b)) - mp.erf(tau(t_a)))
+    assert 1.5 < float(I_ab) < 4.0
+    hits = 0
+    for j in range(n):
+        E = mp.mpf(orc.decomposition_exponential(u[j], 0))
+        if E >= I_ab:
+            assert f["prim"][j] == -1 and f["t"][j] == 3.0
+            continue
+        hits += 1
+        ref = (mp.erfinv(mp.erf(tau(t_a)) + E / amp) - B / (2 * mp.sqrt(2 * A))) / mp.sqrt(A / 2)
+        assert f["prim"][j] == 0 and abs(f["t"][j] - float(ref)) < 1e-11
+    assert 0.5 * n < hits < n
+
+
+def test_exponential_distribution_is_exact(orc):
+    """chi^2 over 200,000 samples along one ray through a cluster: the collision distance has the
+    CDF 1 - exp(-int sigma_t) of Eq. exp_ff, the chosen primitive has probability
+    int G_k(t) exp(-int_0^t sigma_t) dt, and escape has exp(-sum_k I_k). The references come from
+    the densities of Eq. 1 on a fine grid (trapezoid rule), inside the oracle's clipped intervals."""
+    from scipy.stats import chi2 as chi2d
+    s = _dense_cluster(n=8, seed=60, boost=1.0)
+    o, d = _exp_ray()
+    od, dd = o.astype(np.float64), d.astype(np.float64)
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    assert len(h["ids"]) >= 6
+    tg = np.linspace(0.0, 2.0, 400001)
+    G = np.zeros((len(h["ids"]), tg.size))
+    for m, i in enumerate(h["ids"]):
+        inside = (tg >= h["a"][m]) & (tg <= h["b"][m])
+        G[m, inside] = density(s, i, od + tg[inside, None] * dd)
+    sig = G.sum(0)
+    dt = tg[1] - tg[0]
+    tau = np.concatenate([[0.0], np.cumsum(0.5 * (sig[1:] + sig[:-1]) * dt)])
+    T = np.exp(-tau)
+    p_k = np.array([np.sum(0.5 * (G[m, 1:] * T[1:] + G[m, :-1] * T[:-1]) * dt) for m in range(len(h["ids"]))])
+    p_esc = T[-1]
+    assert abs(p_k.sum() + p_esc - 1.0) < 1e-6 and 0.05 < p_esc < 0.6
+    n = 200000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    f = orc.sample_free_flight_exponential(s, r, scenes.uniforms24(93, n))
+    counts = np.array([(f["prim"] == i).sum() for i in h["ids"]] + [(f["prim"] < 0).sum()], np.float64)
+    exp = np.concatenate([p_k, [p_esc]]) * n
+    m = exp > 5
+    chi2 = (((counts - exp) ** 2)[m] / exp[m]).sum()
+    assert chi2 < chi2d.ppf(0.999, int(m.sum()) - 1), (chi2, counts, exp)
+    # the distance: 40 bins of equal probability under the grid CDF
+    cdf = 1.0 - T
+    edges = np.interp(np.linspace(0, cdf[-1], 41), cdf, tg)
+    tc = f["t"][f["prim"] >= 0]
+    cnt, _ = np.histogram(tc, edges)
+    e = np.full(40, tc.size / 40.0)
+    assert (((cnt - e) ** 2) / e).sum() < chi2d.ppf(0.999, 39)
+    np.testing.assert_allclose(f["depth"][0], tau[-1], rtol=1e-7)
+
+
+def test_exponential_transmittance(orc):
+    """exp(-sum_k I_k) against quadrature, and the product rule T(t0, t2) = T(t0, t1) T(t1, t2)
+    that holds for the exponential model (and not for the linear one of Eq. 7)."""
+    s = _dense_cluster(n=8, seed=60, boost=0.4)
+    o, d = _exp_ray()
+    od, dd = o.astype(np.float64), d.astype(np.float64)
+    r = scenes.Rays(o[None], d[None], np.zeros(1, np.float32), np.full(1, 2.0, np.float32))
+    T, depth = orc.transmittance_exponential(s, r)
+    q = 2.0 * _F_quad(s, od, dd, 0.0, 2.0)
+    assert abs(depth[0] - q) < 1e-11 * q and abs(T[0] - math.exp(-q)) < 1e-12
+    s2 = scenes.tiny_scene(n=300, seed=94)
+    s2.magnitude[:] *= 6.0
+    rr = scenes.random_rays(300, seed=95)
+    tm = (rr.t0 + 0.37 * (rr.t1 - rr.t0)).astype(np.float32)
+    Ta, _ = orc.transmittance_exponential(s2, rr)
+    T1, _ = orc.transmittance_exponential(s2, scenes.Rays(rr.o, rr.d, rr.t0, tm))
+    T2, _ = orc.transmittance_exponential(s2, scenes.Rays(rr.o, rr.d, tm, rr.t1))
+    np.testing.assert_allclose(Ta, T1 * T2, rtol=1e-12)
+    assert (Ta < 0.5).mean() > 0.1
+    TL, _, _ = orc.transmittance(s2, rr)
+    assert np.abs(TL - orc.transmittance(s2, scenes.Rays(rr.o, rr.d, rr.t0, tm))[0]
+                  * orc.transmittance(s2, scenes.Rays(rr.o, rr.d, tm, rr.t1))[0]).max() > 1e-3
