@@ -64,6 +64,7 @@ def parse_args(argv=None):
     p.add_argument("--guide-alpha", type=float, default=0.5)
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving study")
     p.add_argument("--no-rf", action="store_true", help="skip the radiance-field render study")
+    p.add_argument("--no-exp", action="store_true", help="skip the exponential-variant query study")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-spp-max", type=int, default=4,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
@@ -538,6 +539,9 @@ def run_ugp(args):
     rf = None
     if rank == 0 and world == 1 and not args.no_rf:
         rf = radiance_field_study(args, d, scene, dev)
+    expo = None
+    if rank == 0 and world == 1 and not args.no_exp:
+        expo = exponential_study(args, d, scene, dev)
 
     if rank == 0:
         clk = clocks.summary()
@@ -558,6 +562,7 @@ def run_ugp(args):
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf, "serving": serving,
+            "exponential_variant": expo,
             "radiance_field": rf,
         }
         print(json.dumps(line), flush=True)
@@ -607,6 +612,42 @@ def radiance_field_study(args, d, scene, dev, reps=10):
     return {"image": f"{W}x{H}", "rays": n, "ms_per_frame": ms, "Mrays_per_s": n / (ms / 1e3) / 1e6,
             "queries_with_error_status": int((st != 0).sum().item()), "mean_rgb": rgb.mean(0).tolist(),
             "emission": "per-primitive albedo, background 0.2"}
+
+
+def exponential_study(args, d, scene, dev, reps=10):
+    """The exponential-transmittance variant's two queries (appendix on analog decomposition
+    tracking) on the bench scene's camera view: one camera ray per pixel, unbounded; CUDA-event
+    time per launch after 3 warm-up launches of each."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    W, H = args.width, args.height
+    dirs = torch.from_numpy(pinhole_rays(scene.camera, W, H)).to(dev)
+    n = dirs.shape[0]
+    O = torch.tensor(np.array(scene.camera.eye, np.float32), device=dev).expand(n, 3).contiguous()
+    T0, T1 = torch.zeros(n, device=dev), torch.full((n,), 1e30, device=dev)
+    U = torch.from_numpy(scenes.uniforms24(5, n)).to(dev)
+    bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
+    out = {"image": f"{W}x{H}", "rays": n}
+    for name, fn in (("free_flight", lambda: ugp.sample_free_flight_exponential(bvh, O, dirs, T0, T1, U)),
+                     ("transmittance", lambda: ugp.trace_transmittance_exponential(bvh, O, dirs, T0, T1))):
+        for _ in range(3):
+            res = fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            res = fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "Mrays_per_s": n / (ms / 1e3) / 1e6,
+                     "queries_with_error_status": int((res[-1] != 0).sum().item())}
+        if name == "free_flight":
+            out[name]["collided"] = float((res[0] >= 0).float().mean().item())
+        else:
+            out[name]["mean_T"] = float(res[0].mean().item())
+    return out
 
 
 def run_kernel_case(args):

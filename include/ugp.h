@@ -235,6 +235,40 @@ ugp_status ugp_render_radiance_field(const ugp_bvh* bvh, int64_t n_rays, const f
                                      const float* background3, float* rgb_out, uint8_t* status_out,
                                      void* workspace, size_t workspace_bytes, void* stream);
 
+/* Exponential-transmittance variant (appendix "Sampling Exponential Transmittance Gaussians
+ * via Analog Decomposition Tracking").  The primitives are read as the extinction coefficient
+ * sigma_t(x) = sum_k G_k(x) of the classical exponential model (Eq. exp_ff) instead of the
+ * linear model of Eq. 7, each contribution clipped to its k-ellipsoid as in Sec. 4.1.
+ *
+ * ugp_sample_free_flight_exponential: analog decomposition tracking.  Every primitive k whose
+ * clipped interval [a_k, b_k] meets [t0, t1] draws a collision depth E_k = -ln U_k, with U_k =
+ * ((x0 >> 8) + 1) / 2^24 and x0 the first word of Philox4x32-10 under key (bits of u[r],
+ * 0x2406DEC0) and counter (k, 0, 0, 0).  If E_k < I_k(a_k, b_k) it collides at t_k with
+ * I_k(a_k, t_k) = E_k; the nearest collision is the sample (equal distances: the lower index).
+ *   u          device float array (n_rays): the ray's uniform in [0, 1) (keys the E_k)
+ *   prim_out   device int32 array (n_rays): the colliding primitive, -1 if none collides
+ *   t_out      device float array (n_rays): its collision distance, t1 on escape
+ *   status_out device uint8 array (n_rays) or NULL: UGP_RAY_OK, UGP_RAY_STACK_OVERFLOW or
+ *              UGP_RAY_BAD_NODE
+ *   other arguments as for ugp_trace_transmittance.  Escape has probability
+ *   exp(-sum_k I_k(a_k, b_k)).
+ *
+ * ugp_trace_transmittance_exponential: T_out[r] = exp(-sum_k I_k(a_k, b_k)) over [t0, t1]
+ * (0 once the sum passes 112, where float32 exp underflows); arguments as for
+ * ugp_trace_transmittance.
+ *
+ * Both: one thread per ray, no workspace, asynchronous on `stream`.  Errors: UGP_ERR_NOT_BUILT
+ * for an invalid handle; UGP_ERR_INVALID_ARG for a NULL array or n_rays outside
+ * [0, (2^31 - 1) * 128]. */
+ugp_status ugp_sample_free_flight_exponential(const ugp_bvh* bvh, int64_t n_rays, const float* o3, const float* d3,
+                                              const float* t0, const float* t1, const float* u,
+                                              const int32_t* exclude_prim, int32_t* prim_out, float* t_out,
+                                              uint8_t* status_out, void* stream);
+ugp_status ugp_trace_transmittance_exponential(const ugp_bvh* bvh, int64_t n_rays, const float* o3,
+                                               const float* d3, const float* t0, const float* t1,
+                                               const int32_t* exclude_prim, float* T_out, uint8_t* status_out,
+                                               void* stream);
+
 /* ------------------------------------------------------------------ rendering
  * Per-primitive appearance (Sec. 6), device arrays in the caller's order:
  *   sggx6      SGGX matrix S (Sxx, Syy, Szz, Sxy, Sxz, Syz), positive definite (n x 6)

@@ -60,6 +60,8 @@ def lib():
                                                          f64p, f64p]
         L.orc_transmittance_exponential.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
                                                     f32p, f32p, i32p, f64p, f64p]
+        L.orc_band_rays.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p, C.c_double,
+                                    i32p]
         L.orc_decomposition_exponential.argtypes = [C.c_double, C.c_int32]
         L.orc_decomposition_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
@@ -242,6 +244,20 @@ def transmittance_exponential(scene, rays, exclude=None, eps=0.01):
     lib().orc_transmittance_exponential(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
                                         _ptr(t1, f32p), _ptr(ex, i32p), _ptr(T, f64p), _ptr(depth, f64p))
     return T, depth
+
+
+def band_rays(scene, rays, rel=1e-5, eps=0.01):
+    """Boolean per ray: its hit set is decided at rounding level (a primitive whose whitened
+    closest approach is within rel of the cut-off k inside [t0, t1], or an ellipsoid end point
+    within rel (t1 - t0) of t0 or t1)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    flag = np.zeros(n, np.int32)
+    lib().orc_band_rays(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p), _ptr(t1, f32p), float(rel),
+                        _ptr(flag, i32p))
+    return flag.astype(bool)
 
 
 def decomposition_exponential(u: float, k: int) -> float:

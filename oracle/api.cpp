@@ -191,6 +191,33 @@ void orc_transmittance_exponential(const orc_scene* s, double cutoff_eps, int64_
                                          exclude ? exclude[r] : -1, depth_out ? depth_out + r : nullptr);
 }
 
+// Rays whose hit set is decided at rounding level (the epsilon band of the parity contract):
+// some primitive with |sqrt(d2) - k| < rel k whose closest approach lies in [t0, t1], or an
+// ellipsoid end point within rel (t1 - t0) of t0 or t1. flag_out[r] = 1 for such a ray.
+void orc_band_rays(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3, const float* d3,
+                   const float* t0, const float* t1, double rel, int32_t* flag_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r) {
+    const V3 o = load3(o3 + 3 * r), d = load3(d3 + 3 * r);
+    const double a = t0[r], b = t1[r], tol = rel * (b - a);
+    int32_t flag = 0;
+    for (size_t i = 0; i < prims.size() && !flag; ++i) {
+      double A, ts, d2;
+      ray_prim_quadratic(prims[i], o, d, &A, &ts, &d2);
+      const double dist = std::sqrt(std::max(d2, 0.0));
+      if (std::fabs(dist - k) < rel * k && ts >= a && ts <= b) flag = 1;
+      if (d2 < k * k) {
+        const double half = std::sqrt((k * k - d2) / A);
+        for (double e : {ts - half, ts + half})
+          if (std::fabs(e - a) <= tol || std::fabs(e - b) <= tol) flag = 1;
+      }
+    }
+    flag_out[r] = flag;
+  }
+}
+
 double orc_decomposition_exponential(double u, int32_t k) { return decomposition_exponential(u, k); }
 
 // App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.

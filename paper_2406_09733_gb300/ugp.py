@@ -110,6 +110,10 @@ def lib():
         L.ugp_render_radiance_field.restype = C.c_int
         L.ugp_render_radiance_field.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.POINTER(C.c_float), vp, vp, vp,
                                                 C.c_size_t, vp]
+        L.ugp_sample_free_flight_exponential.restype = C.c_int
+        L.ugp_sample_free_flight_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ugp_trace_transmittance_exponential.restype = C.c_int
+        L.ugp_trace_transmittance_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_set_trace_counters.restype = C.c_int
         L.ugp_set_trace_counters.argtypes = [vp]
         for fn in _EXTRA:
@@ -265,6 +269,42 @@ def render_radiance_field(bvh: Bvh, o, d, t0, t1, emission, background=None, str
                                            C.c_void_p(_stream(stream))),
            "ugp_render_radiance_field")
     return rgb, st
+
+
+def sample_free_flight_exponential(bvh: Bvh, o, d, t0, t1, u, exclude=None, stream=None):
+    """Exponential variant by analog decomposition tracking (sigma_t = sum_k G_k): per ray the
+    nearest per-primitive exponential collision keyed by the uniform u. Returns (prim (-1:
+    escape), t (t1 on escape), status)."""
+    n = int(o.shape[0])
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    for t, nm in ((t0, "t0"), (t1, "t1"), (u, "u")):
+        _dev(t, torch.float32, nm)
+    _dev(exclude, torch.int32, "exclude")
+    prim = torch.empty(n, dtype=torch.int32, device=o.device)
+    t = torch.empty(n, dtype=torch.float32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    _check(lib().ugp_sample_free_flight_exponential(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1), _p(u),
+                                                    _p(exclude), _p(prim), _p(t), _p(st),
+                                                    C.c_void_p(_stream(stream))),
+           "ugp_sample_free_flight_exponential")
+    return prim, t, st
+
+
+def trace_transmittance_exponential(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
+    """exp(-sum_k I_k) over each ray's [t0, t1] (exponential variant). Returns (T, status)."""
+    n = int(o.shape[0])
+    _dev(o, torch.float32, "o", 3)
+    _dev(d, torch.float32, "d", 3)
+    _dev(t0, torch.float32, "t0")
+    _dev(t1, torch.float32, "t1")
+    _dev(exclude, torch.int32, "exclude")
+    T = torch.empty(n, dtype=torch.float32, device=o.device)
+    st = torch.empty(n, dtype=torch.uint8, device=o.device)
+    _check(lib().ugp_trace_transmittance_exponential(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
+                                                     _p(exclude), _p(T), _p(st), C.c_void_p(_stream(stream))),
+           "ugp_trace_transmittance_exponential")
+    return T, st
 
 
 def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):

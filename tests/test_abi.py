@@ -70,6 +70,16 @@ def test_radiance_field_entry_point_validates_on_host(libugp):
     assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()   # UGP_ERR_NOT_BUILT
 
 
+def test_exponential_entry_points_validate_on_host(libugp):
+    libugp.ugp_last_error.restype = ctypes.c_char_p
+    st = libugp.ugp_sample_free_flight_exponential(None, ctypes.c_int64(4), None, None, None, None, None, None,
+                                                   None, None, None, None)
+    assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()
+    st = libugp.ugp_trace_transmittance_exponential(None, ctypes.c_int64(4), None, None, None, None, None, None,
+                                                    None, None)
+    assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()
+
+
 def test_guide_entry_points_validate_on_host(libugp):
     libugp.ugp_guide_workspace_size.restype = ctypes.c_size_t
     libugp.ugp_render_guided_workspace_size.restype = ctypes.c_size_t
