@@ -62,6 +62,8 @@ def lib():
                                                     f32p, f32p, i32p, f64p, f64p]
         L.orc_band_rays.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p, C.c_double,
                                     i32p]
+        L.orc_sample_free_flight_paper_rule.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
+                                                        f32p, f32p, f32p, f32p, i32p]
         L.orc_decomposition_exponential.argtypes = [C.c_double, C.c_int32]
         L.orc_decomposition_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
@@ -244,6 +246,21 @@ def transmittance_exponential(scene, rays, exclude=None, eps=0.01):
     lib().orc_transmittance_exponential(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
                                         _ptr(t1, f32p), _ptr(ex, i32p), _ptr(T, f64p), _ptr(depth, f64p))
     return T, depth
+
+
+def sample_free_flight_paper_rule(scene, rays, u, u2, eps=0.01):
+    """Free-flight sampling with the paper's own disambiguation rule (pick proportional to
+    I_k(s0, t_u) in the segment where F reaches 1): a diagnostic of that rule's bias, not a
+    parity target. Returns the primitive per ray (-1: escape)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    u, u2 = _c(u, np.float32), _c(u2, np.float32)
+    prim = np.zeros(n, np.int32)
+    lib().orc_sample_free_flight_paper_rule(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
+                                            _ptr(t1, f32p), _ptr(u, f32p), _ptr(u2, f32p), _ptr(prim, i32p))
+    return prim
 
 
 def band_rays(scene, rays, rel=1e-5, eps=0.01):

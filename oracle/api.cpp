@@ -218,6 +218,19 @@ void orc_band_rays(const orc_scene* s, double cutoff_eps, int64_t nr, const floa
   }
 }
 
+// Batched free-flight sampling by the paper's own disambiguation rule (a bias diagnostic).
+void orc_sample_free_flight_paper_rule(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3,
+                                       const float* d3, const float* t0, const float* t1, const float* u,
+                                       const float* u2, int32_t* prim_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r)
+    prim_out[r] = sample_free_flight_paper_rule(all_hits(prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r], t1[r],
+                                                         k, -1),
+                                                t0[r], t1[r], u[r], u2[r]);
+}
+
 double orc_decomposition_exponential(double u, int32_t k) { return decomposition_exponential(u, k); }
 
 // App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.

@@ -267,6 +267,72 @@ FreeFlight sample_free_flight(const std::vector<Prim>& prims, V3 o, V3 d, double
   return sample_free_flight_hits(all_hits(prims, o, d, t0, t1, k, exclude), t0, t1, u, u2);
 }
 
+// The paper's own disambiguation rule (Sec. 5.2, Eq. 10 and the free-flight listing), kept as a
+// diagnostic of its bias; the sampler above is the parity target. Segments as above, primitives
+// in ascending id within a segment (the traversal order of a leaf):
+//  * a segment with one active primitive, or one that does not reach F = 1, accumulates
+//    1/2 I_k over the whole segment primitive by primitive and returns the first primitive
+//    whose running sum passes u;
+//  * the segment in which F reaches 1 (the ambiguous one) solves F(t_u) = u and then picks
+//    among its active primitives proportionally to I_k(s0, t_u), with the uniform
+//    u_seg = F(s0) + u2 (u - F(s0)).
+// Exact where the active primitives' densities keep constant ratios over that segment, biased
+// otherwise (the pick should follow G_k at t_u).
+int32_t sample_free_flight_paper_rule(const std::vector<Hit>& hits, double t0, double t1, double u, double u2) {
+  (void)t0;
+  (void)t1;
+  std::vector<double> ev;
+  for (const Hit& h : hits) {
+    ev.push_back(h.a);
+    ev.push_back(h.b);
+  }
+  std::sort(ev.begin(), ev.end());
+  ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
+  double F = 0.0;
+  std::vector<const Hit*> act;
+  for (size_t j = 0; j + 1 < ev.size(); ++j) {
+    const double s0 = ev[j], s1 = ev[j + 1];
+    act.clear();
+    for (const Hit& h : hits)
+      if (h.a <= s0 && h.b >= s1) act.push_back(&h);
+    if (act.empty()) continue;
+    double dF = 0.0;
+    for (const Hit* h : act) dF += 0.5 * ray_integral(*h, s0, s1);
+    if (act.size() == 1 || F + dF < 1.0) {
+      for (const Hit* h : act) {
+        F += 0.5 * ray_integral(*h, s0, s1);
+        if (u < F) return h->id;
+      }
+      continue;
+    }
+    // ambiguous segment: F reaches 1 inside it, so u < 1 <= F + dF
+    double lo = s0, hi = s1, t = 0.5 * (s0 + s1);
+    for (int it = 0; it < 400; ++it) {
+      double f = F - u, fp = 0.0;
+      for (const Hit* h : act) {
+        f += 0.5 * ray_integral(*h, s0, t);
+        fp += 0.5 * gauss_at(*h, t);
+      }
+      if (f == 0.0) break;
+      if (f < 0) lo = t; else hi = t;
+      double tn = fp > 0 ? t - f / fp : 0.5 * (lo + hi);
+      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+      if (std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) || hi - lo <= 1e-16 * std::max(1.0, std::fabs(t))) {
+        t = tn;
+        break;
+      }
+      t = tn;
+    }
+    const double u_seg = F + u2 * (u - F);
+    for (const Hit* h : act) {
+      F += 0.5 * ray_integral(*h, s0, t);
+      if (u_seg < F) return h->id;
+    }
+    return act.back()->id;  // rounding: the running sum ends a hair below u
+  }
+  return -1;
+}
+
 // Sec. 7, Eq. rf. The saturating distance is where F reaches 1, i.e. the free-flight root for
 // u = 1 (the paper's "u = 1" disambiguation); every primitive then counts with its probability
 // mass up to t_sat, 1/2 I_k(a_k, min(b_k, t_sat)), which needs no disambiguation at all.

@@ -99,6 +99,10 @@ FreeFlight sample_free_flight(const std::vector<Prim>& prims, V3 o, V3 d, double
 FreeFlight sample_free_flight_hits(const std::vector<Hit>& hits, double t0, double t1, double u,
                                    double u2);
 
+// The paper's disambiguation rule (pick proportional to I_k(s0, t_u) in the segment where F
+// reaches 1), kept to measure its bias. Returns the primitive id, or -1 for escape.
+int32_t sample_free_flight_paper_rule(const std::vector<Hit>& hits, double t0, double t1, double u, double u2);
+
 // Radiance-field render of Sec. 7 (Eq. rf): L = sum_k 1/2 I_k(a_k, min(b_k, t_sat)) L_e,k, with
 // t_sat the root of F(t_sat) = 1 (free flight at u = 1); when F(t1) <= 1 the ray is not
 // saturated, t_sat = t1 and the remaining 1 - F(t1) sees the background. emission3 is indexed

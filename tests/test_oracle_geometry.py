@@ -642,3 +642,81 @@ def test_exponential_transmittance(orc):
     TL, _, _ = orc.transmittance(s2, rr)
     assert np.abs(TL - orc.transmittance(s2, scenes.Rays(rr.o, rr.d, rr.t0, tm))[0]
                   * orc.transmittance(s2, scenes.Rays(rr.o, rr.d, tm, rr.t1))[0]).max() > 1e-3
+
+
+# ---------------------------------------------------------------------------- the paper's own rule
+def _grid_profiles(s, o, d, h, lo, hi, m=200001):
+    """Densities of Eq. 1 of the ray's primitives on a uniform grid of [lo, hi], zero outside
+    each primitive's clipped interval."""
+    od, dd = o.astype(np.float64), d.astype(np.float64)
+    tg = np.linspace(lo, hi, m)
+    G = np.zeros((len(h["ids"]), m))
+    for j, i in enumerate(h["ids"]):
+        inside = (tg >= h["a"][j]) & (tg <= h["b"][j])
+        G[j, inside] = density(s, i, od + tg[inside, None] * dd)
+    return tg, G
+
+
+def test_paper_rule_is_exact_away_from_saturation(orc):
+    """On a ray that never saturates no segment is ambiguous, and the paper's rule (Sec. 5.2)
+    samples P(k) = 1/2 I_k exactly (chi^2 against quadrature)."""
+    from scipy.stats import chi2 as chi2d
+    s = _dense_cluster(n=8, seed=60, boost=0.15)
+    o, d = _exp_ray()
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    p = np.array([0.5 * integrate.quad(lambda t: density(s, i, o.astype(np.float64) + t * d.astype(np.float64)),
+                                       h["a"][j], h["b"][j], epsabs=0, epsrel=1e-12)[0]
+                  for j, i in enumerate(h["ids"])])
+    assert p.sum() < 0.9
+    n = 200000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    k = orc.sample_free_flight_paper_rule(s, r, scenes.uniforms24(110, n), scenes.uniforms24(111, n))
+    counts = np.array([(k == i).sum() for i in h["ids"]] + [(k < 0).sum()], np.float64)
+    exp = np.concatenate([p, [1 - p.sum()]]) * n
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < chi2d.ppf(0.999, len(exp) - 1), (chi2, counts, exp)
+
+
+def test_paper_rule_bias_at_the_saturating_distance(orc):
+    """Where several primitives straddle t_sat the paper's rule picks proportionally to
+    I_k(s0, t_u) in the ambiguous segment [s0, s1]. Its own law is then
+    P(k) = 1/2 I_k(a_k, min(b_k, s0)) + int_s0^t_sat I_k(s0, t) / sum_A I_j(s0, t) dF(t),
+    which the samples follow (chi^2, densities of Eq. 1 on a fine grid), while the exact law
+    1/2 I_k(a_k, min(b_k, t_sat)) is rejected by orders of magnitude: the rule's bias."""
+    from scipy.stats import chi2 as chi2d
+    s = _dense_cluster(n=8, seed=60, boost=5.0)
+    o, d = _exp_ray()
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    tg, G = _grid_profiles(s, o, d, h, 0.0, 2.0, 400001)
+    dt = tg[1] - tg[0]
+    Ik = np.concatenate([np.zeros((G.shape[0], 1)), np.cumsum(0.5 * (G[:, 1:] + G[:, :-1]) * dt, 1)], 1)
+    F = 0.5 * Ik.sum(0)
+    t_sat = np.interp(1.0, F, tg)
+    ev = np.unique(np.concatenate([h["a"], h["b"]]))
+    s0 = ev[ev <= t_sat].max()
+    act = (h["a"] <= s0) & (h["b"] > s0)
+    assert act.sum() >= 2
+    # exact law and the rule's law, both from the grid
+    at = lambda row, x: np.interp(x, tg, row)
+    p_exact = np.array([0.5 * at(Ik[j], t_sat) for j in range(len(h["ids"]))])
+    p_rule = np.array([0.5 * at(Ik[j], s0) for j in range(len(h["ids"]))])
+    sel = (tg > s0) & (tg <= t_sat)
+    Iseg = Ik[:, sel] - np.array([at(Ik[j], s0) for j in range(len(h["ids"]))])[:, None]
+    wsum = Iseg[act].sum(0)
+    dF = 0.5 * G[:, sel].sum(0) * dt
+    for j in np.nonzero(act)[0]:
+        p_rule[j] += np.sum(Iseg[j] / wsum * dF)
+    assert abs(p_exact.sum() - 1) < 1e-5 and abs(p_rule.sum() - 1) < 1e-3, (p_exact.sum(), p_rule.sum())
+    n = 400000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    k = orc.sample_free_flight_paper_rule(s, r, scenes.uniforms24(112, n), scenes.uniforms24(113, n))
+    assert np.all(k >= 0)
+    counts = np.array([(k == i).sum() for i in h["ids"]], np.float64)
+    dof = len(counts) - 1
+    chi_rule = ((counts - p_rule * n) ** 2 / (p_rule * n)).sum()
+    chi_exact = ((counts - p_exact * n) ** 2 / (p_exact * n)).sum()
+    assert chi_rule < chi2d.ppf(0.999, dof), (chi_rule, counts / n, p_rule)
+    assert chi_exact > 100 * chi2d.ppf(0.999, dof), chi_exact
+    bias = np.abs(p_rule - p_exact).max()
+    print(f"paper rule: max |P_rule - P_exact| = {bias:.4f} over {act.sum()} ambiguous primitives")
+    assert bias > 0.01
