@@ -317,6 +317,11 @@ def _register_phase(L):
     L.orc_render.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.POINTER(OrcLights),
                              C.POINTER(OrcParams), C.c_int64, C.c_int64, d, d,
                              C.POINTER(C.c_int64)]
+    L.orc_sample_in_ellipsoid.argtypes = [C.POINTER(OrcScene), C.c_int64, C.c_double, C.c_int64, d, d]
+    L.orc_emitter_nee.argtypes = [C.POINTER(OrcScene), C.c_double, d, d, C.c_int32, C.c_int32, d, C.c_double, d,
+                                  C.c_int64, C.c_uint64, d, d]
+    L.orc_chi3_cdf.argtypes = [C.c_double]
+    L.orc_chi3_cdf.restype = C.c_double
 
 
 _REGISTRY.append(_register_phase)
@@ -341,7 +346,7 @@ class OrcParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("seed", C.c_uint64), ("cutoff_eps", C.c_double), ("nee", C.c_int32),
                 ("spawn_mode", C.c_int32), ("guide", f32p), ("guide_cfg", OrcGuideCfg),
-                ("guide_alpha", C.c_double)]
+                ("guide_alpha", C.c_double), ("nee_emitters", C.c_int32)]
 
 
 def _d(a):
@@ -429,11 +434,12 @@ def phase_pdf_approx(mtype, albedo, alpha, S6, wo, wi):
 
 
 def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1, spawn_mode=0,
-           pixels=None, threads=None, guide=None, guide_alpha=0.5):
+           pixels=None, threads=None, guide=None, guide_alpha=0.5, nee_emitters=0):
     """Per-pixel sums of sample values and squares, shape (H, W, 3) each, plus query counts.
 
     ``pixels`` = (p_begin, p_end) renders only that row-major pixel range (others stay zero).
     ``guide`` = (params, GuideConfig) renders with the learned guide by one-sample MIS.
+    ``nee_emitters`` = 1 adds next-event estimation toward emissive primitives (with MIS).
     """
     cam, li = scene.camera, scene.lights
     W, H = cam.width, cam.height
@@ -447,7 +453,7 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
         gp = _c(guide[0], np.float32)
         gcfg = _guide_cfg(guide[1])
     p = OrcParams(int(spp), int(spp_begin), int(max_depth), int(seed), float(cutoff_eps), int(nee),
-                  int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha))
+                  int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha), int(nee_emitters))
     acc = np.zeros((H, W, 3))
     acc2 = np.zeros((H, W, 3))
     counts = (C.c_int64 * 2)(0, 0)
@@ -458,6 +464,29 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
     lib().orc_render(sr.ref, C.byref(c), C.byref(l), C.byref(p), int(pb), int(pe), _ptr(acc, f64p),
                      _ptr(acc2, f64p), counts)
     return acc, acc2, (int(counts[0]), int(counts[1]))
+
+
+def sample_in_ellipsoid(scene, i, U3, eps=0.01):
+    """Points of primitive i drawn from its Gaussian restricted to the k-ellipsoid (n x 3 uniforms)."""
+    U = _d(U3).reshape(-1, 3)
+    y = np.zeros_like(U)
+    lib().orc_sample_in_ellipsoid(_SceneRef(scene).ref, int(i), float(eps), U.shape[0], _ptr(U, f64p), _ptr(y, f64p))
+    return y
+
+
+def emitter_nee(scene, x, wo, mtype, albedo, alpha, S6, n, seed=0, exclude=-1, eps=0.01):
+    """Mean and standard error (per RGB channel) of n one-sample light estimates toward the
+    scene's emissive primitives at vertex x (outgoing wo, the given material), without MIS."""
+    sm, sq = np.zeros(3), np.zeros(3)
+    lib().orc_emitter_nee(_SceneRef(scene).ref, float(eps), _ptr(_d(x), f64p), _ptr(_d(wo), f64p), int(exclude),
+                          int(mtype), _ptr(_d(albedo), f64p), float(alpha), _ptr(_d(S6), f64p), int(n), int(seed),
+                          _ptr(sm, f64p), _ptr(sq, f64p))
+    mean = sm / n
+    return mean, np.sqrt(np.maximum(sq / n - mean ** 2, 0.0) / n)
+
+
+def chi3_cdf(r: float) -> float:
+    return float(lib().orc_chi3_cdf(float(r)))
 
 
 # ------------------------------------------------------------------ learned guide

@@ -345,6 +345,7 @@ typedef struct {
   const float* guide;  // flat guide parameters (NULL: plain phase sampling)
   orc_guide_cfg guide_cfg;
   double guide_alpha;
+  int32_t nee_emitters;  // 1: next-event estimation toward emissive primitives as well
 } orc_params;
 
 static GuideCfg guide_cfg_of(const orc_guide_cfg* g) {
@@ -370,6 +371,7 @@ void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, co
   P.guide = p->guide;
   P.guide_cfg = guide_cfg_of(&p->guide_cfg);
   P.guide_alpha = p->guide_alpha;
+  P.nee_emitters = p->nee_emitters;
   int64_t ne = 0, ns = 0;
   render_pixels(scene_in(s), cam, L, P, p_begin, p_end, accum, accum_sq, &ne, &ns);
   if (counts) {
@@ -377,6 +379,25 @@ void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, co
     counts[1] += ns;
   }
 }
+
+// Points of primitive i from its Gaussian restricted to the k-ellipsoid (three uniforms each).
+void orc_sample_in_ellipsoid(const orc_scene* s, int64_t i, double cutoff_eps, int64_t n, const double* U3,
+                             double* y3) {
+  const Prim p = make_prim(s->mean3 + 3 * i, s->quat4 + 4 * i, s->scale3 + 3 * i, s->magnitude[i]);
+  const double k = cutoff_k(cutoff_eps);
+  for (int64_t r = 0; r < n; ++r) put3(y3 + 3 * r, sample_in_ellipsoid(p, k, U3 + 3 * r));
+}
+
+// Sum and sum of squares of n light estimates toward the scene's emitters (no MIS weight) at the
+// vertex x3 with outgoing direction wo3 and the given material.
+void orc_emitter_nee(const orc_scene* s, double cutoff_eps, const double* x3, const double* wo3, int32_t exclude,
+                     int32_t mtype, const double* albedo3, double alpha, const double* S6, int64_t n, uint64_t seed,
+                     double* sum3, double* sq3) {
+  emitter_nee_sums(scene_in(s), cutoff_eps, mat_of(mtype, albedo3, alpha, S6), d3v(x3), d3v(wo3), exclude, n, seed,
+                   sum3, sq3);
+}
+
+double orc_chi3_cdf(double r) { return chi3_cdf(r); }
 
 // ------------------------------------------------------------------ learned guide
 int64_t orc_guide_nparams() { return kGNParams; }

@@ -68,7 +68,35 @@ struct RenderParams {
   const float* guide = nullptr;
   GuideCfg guide_cfg{};
   double guide_alpha = 0.5;
+  int nee_emitters = 0;  // 1: also next-event estimation toward emissive primitives, with MIS
 };
+
+// Next-event estimation toward emissive primitives (not specified by the paper): emitter j is
+// chosen with probability pi_j proportional to c_j mean(L_e,j), and a point of it from its
+// Gaussian restricted to the k-ellipsoid.
+struct EmitterTable {
+  std::vector<int32_t> ids;
+  std::vector<double> cdf;  // running sums of c_j mean(L_e,j)
+  double total = 0.0;
+  double mass = 0.0;        // P(|z| <= k), z ~ N(0, I_3): the Gaussian mass inside the ellipsoid
+};
+EmitterTable emitter_table(const SceneIn& s, double k);
+// CDF of the chi distribution with 3 degrees of freedom (radius of a standard 3D normal).
+double chi3_cdf(double r);
+// A point of primitive p from its Gaussian restricted to the k-ellipsoid (three uniforms).
+V3 sample_in_ellipsoid(const Prim& p, double k, const double U[3]);
+// One light sample from vertex x (material m, outgoing wo, the vertex's primitive excluded).
+// Returns false when it adds nothing; else *contrib = f_p * L_e * c_j m / (2 r^2 pi_j) (the
+// estimate without beta and MIS weight), *dir the direction, and the two balance-heuristic terms
+// in a common scale: *p_light = 2 r^2 pi_j, *p_scatter_scale = c_j m (times the scattering pdf).
+bool emitter_nee(const SceneIn& s, const std::vector<Prim>& prims, const EmitterTable& E, double k,
+                 const Material& m, V3 x, V3 wo, int32_t exclude, const double U4[4], const double Uf[6],
+                 V3* contrib, V3* dir, double* p_light, double* p_scatter_scale, int64_t* shadow_rays);
+
+// Sum and sum of squares of n one-sample light estimates of emitter_nee (no MIS weight) at the
+// vertex x; uniforms from Philox with key seed and counters (0, sample, 8 | 9 | 10, 0).
+void emitter_nee_sums(const SceneIn& s, double cutoff_eps, const Material& m, V3 x, V3 wo, int32_t exclude,
+                      int64_t n, uint64_t seed, double sum[3], double sq[3]);
 
 // Renders pixels [p_begin, p_end) of the image (row-major), adding per-channel sums of the
 // sample values and of their squares; also counts queries.

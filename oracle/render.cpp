@@ -27,6 +27,9 @@
 //    The two weights of the balance heuristic sum to one at every direction, so the estimate
 //    stays unbiased for any q and any approximation p~ (Sec. 6). The mixture pdf
 //    alpha q + (1 - alpha) p~ replaces p~ in the MIS with light sampling.
+//  * Optionally (nee_emitters), next-event estimation toward emissive primitives as well
+//    (slot 8: emitter choice and point, slots 9-10: stochastic phase evaluation), balanced
+//    against phase sampling; see emitter_nee below.
 #include <algorithm>
 #include <cmath>
 
@@ -88,6 +91,121 @@ static bool quad_hit(const Lights& L, V3 o, V3 d, double tmax, double* t, bool* 
 
 static double mis2(double a, double b) { return a + b > 0 ? a / (a + b) : 0.0; }
 
+// ---- next-event estimation toward emissive primitives ------------------------------------
+// The free flight from x along w picks primitive j at a distance in [t, t + dt] with
+// probability 1/2 G_j(x + t w) dt for t below the saturating distance (Eq. 8 and the exact
+// choice of Sec. 5.2). Its direct emission is therefore
+//   int f_p(w) P_j(w) L_e,j dw = 1/2 L_e,j int f_p(w(y)) G_j(y) 1[|y - x| < t_sat] / |y - x|^2 dy,
+// and with y drawn from G_j / (c_j m) inside the ellipsoid (m its Gaussian mass) and j with
+// probability pi_j, one sample estimates it by 1/2 c_j m L_e,j f_p 1[T(x, y) > 0] / (r^2 pi_j):
+// the linear model needs only that y lies before saturation, not a transmittance factor.
+// The balance heuristic against phase sampling compares the two densities of (j, y) in volume
+// measure: pi_j G_j(y) / (c_j m) and p(w) 1/2 G_j(y) / r^2. G_j(y) cancels, leaving 2 r^2 pi_j
+// against c_j m p(w).
+double chi3_cdf(double r) {
+  return std::erf(r / std::sqrt(2.0)) - std::sqrt(2.0 / kPi) * r * std::exp(-0.5 * r * r);
+}
+
+EmitterTable emitter_table(const SceneIn& s, double k) {
+  EmitterTable E;
+  E.mass = chi3_cdf(k);
+  for (int64_t i = 0; i < s.n; ++i) {
+    if (s.type[i] != kMatEmissive) continue;
+    const double w = double(s.magnitude[i]) *
+                     (double(s.emission3[3 * i]) + s.emission3[3 * i + 1] + s.emission3[3 * i + 2]) / 3.0;
+    if (!(w > 0)) continue;
+    E.total += w;
+    E.ids.push_back(int32_t(i));
+    E.cdf.push_back(E.total);
+  }
+  return E;
+}
+
+V3 sample_in_ellipsoid(const Prim& p, double k, const double U[3]) {
+  // radius: invert the chi-3 CDF on [0, k] by bracketed Newton (pdf sqrt(2/pi) r^2 e^{-r^2/2})
+  const double target = U[0] * chi3_cdf(k);
+  double lo = 0.0, hi = k, r = 0.5 * k;
+  for (int it = 0; it < 200; ++it) {
+    const double f = chi3_cdf(r) - target;
+    if (f == 0.0) break;
+    if (f < 0) lo = r; else hi = r;
+    const double fp = std::sqrt(2.0 / kPi) * r * r * std::exp(-0.5 * r * r);
+    double rn = fp > 0 ? r - f / fp : 0.5 * (lo + hi);
+    if (!(rn > lo && rn < hi)) rn = 0.5 * (lo + hi);
+    if (std::fabs(rn - r) <= 1e-15 * std::max(1.0, r) || hi - lo <= 1e-15) {
+      r = rn;
+      break;
+    }
+    r = rn;
+  }
+  const double cz = 1.0 - 2.0 * U[1], sz = std::sqrt(std::max(0.0, 1.0 - cz * cz)), ph = 2.0 * kPi * U[2];
+  const double z[3] = {r * sz * std::cos(ph) * p.s[0], r * sz * std::sin(ph) * p.s[1], r * cz * p.s[2]};
+  return p.mu + v3(p.R[0] * z[0] + p.R[1] * z[1] + p.R[2] * z[2], p.R[3] * z[0] + p.R[4] * z[1] + p.R[5] * z[2],
+                   p.R[6] * z[0] + p.R[7] * z[1] + p.R[8] * z[2]);
+}
+
+bool emitter_nee(const SceneIn& s, const std::vector<Prim>& prims, const EmitterTable& E, double k,
+                 const Material& m, V3 x, V3 wo, int32_t exclude, const double U4[4], const double Uf[6],
+                 V3* contrib, V3* dir, double* p_light, double* p_scatter_scale, int64_t* shadow_rays) {
+  if (E.ids.empty()) return false;
+  size_t q = size_t(std::upper_bound(E.cdf.begin(), E.cdf.end(), U4[0] * E.total) - E.cdf.begin());
+  if (q >= E.ids.size()) q = E.ids.size() - 1;
+  const int32_t j = E.ids[q];
+  const double pj = (E.cdf[q] - (q ? E.cdf[q - 1] : 0.0)) / E.total;
+  const V3 y = sample_in_ellipsoid(prims[size_t(j)], k, U4 + 1);
+  const V3 w = y - x;
+  const double r2 = dot(w, w);
+  if (!(r2 > 0)) return false;
+  const V3 wl = (1.0 / std::sqrt(r2)) * w;
+  const V3 f = phase_eval(m, wl, wo, Uf);
+  if (!(f.x > 0 || f.y > 0 || f.z > 0)) return false;
+  ++*shadow_rays;
+  if (!(transmittance(prims, x, wl, 0.0, std::sqrt(r2), k, exclude, nullptr) > 0)) return false;
+  const double cm = double(s.magnitude[j]) * E.mass;
+  *contrib = (0.5 * cm / (r2 * pj)) * (f * load3(s.emission3 + 3 * size_t(j)));
+  *dir = wl;
+  *p_light = 2.0 * r2 * pj;
+  *p_scatter_scale = cm;
+  return true;
+}
+
+// Balance weight of an emitter reached by phase sampling (distance r from the previous vertex,
+// scattering pdf p there): the complement of the light-sampling weight above.
+static double emitter_hit_weight(const SceneIn& s, const EmitterTable& E, int32_t j, double r, double p) {
+  const auto it = std::lower_bound(E.ids.begin(), E.ids.end(), j);
+  if (it == E.ids.end() || *it != j) return 1.0;
+  const size_t q = size_t(it - E.ids.begin());
+  const double pj = (E.cdf[q] - (q ? E.cdf[q - 1] : 0.0)) / E.total;
+  return mis2(double(s.magnitude[j]) * E.mass * p, 2.0 * r * r * pj);
+}
+
+void emitter_nee_sums(const SceneIn& s, double cutoff_eps, const Material& m, V3 x, V3 wo, int32_t exclude,
+                      int64_t n, uint64_t seed, double sum[3], double sq[3]) {
+  const std::vector<Prim> prims = make_prims(s);
+  const double k = cutoff_k(cutoff_eps);
+  const EmitterTable E = emitter_table(s, k);
+  double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+#pragma omp parallel for schedule(static) reduction(+ : a[:3], b[:3])
+  for (int64_t i = 0; i < n; ++i) {
+    double Ue[4], Uf[6], U10[4];
+    rng4(seed, 0u, uint32_t(i), 0u, 8, Ue);
+    rng4(seed, 0u, uint32_t(i), 0u, 9, Uf);
+    rng4(seed, 0u, uint32_t(i), 0u, 10, U10);
+    Uf[4] = U10[0];
+    Uf[5] = U10[1];
+    V3 c{0, 0, 0}, wl;
+    double pl, cm;
+    int64_t shd = 0;
+    if (!emitter_nee(s, prims, E, k, m, x, wo, exclude, Ue, Uf, &c, &wl, &pl, &cm, &shd)) c = v3(0, 0, 0);
+    a[0] += c.x; a[1] += c.y; a[2] += c.z;
+    b[0] += c.x * c.x; b[1] += c.y * c.y; b[2] += c.z * c.z;
+  }
+  for (int c = 0; c < 3; ++c) {
+    sum[c] = a[c];
+    sq[c] = b[c];
+  }
+}
+
 void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const RenderParams& P,
                    int64_t p_begin, int64_t p_end, double* accum, double* accum_sq, int64_t* n_extend,
                    int64_t* n_shadow) {
@@ -96,6 +214,7 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
   const V3 ln = cross(L.e1, L.e2);
   const double area = length(ln);
   const V3 lnh = area > 0 ? (1.0 / area) * ln : v3(0, 0, 1);
+  const EmitterTable E = P.nee_emitters ? emitter_table(s, k) : EmitterTable{};
   int64_t ext = 0, shd = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : ext, shd)
   for (int64_t p = p_begin; p < p_end; ++p) {
@@ -136,7 +255,8 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
         }
         const Material m = material_of(s, ff.prim);
         if (m.type == kMatEmissive) {
-          Lr = Lr + beta * m.emission;
+          const double w = (P.nee_emitters && pdf_prev >= 0) ? emitter_hit_weight(s, E, ff.prim, ff.t_u, pdf_prev) : 1.0;
+          Lr = Lr + w * (beta * m.emission);
           break;
         }
         if (b == P.max_depth) break;
@@ -179,6 +299,18 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
               }
             }
           }
+        }
+        if (P.nee_emitters && !E.ids.empty()) {
+          double Ue[4], Uf[6], U10[4];
+          rng4(P.seed, uint32_t(p), sample, uint32_t(b), 8, Ue);
+          rng4(P.seed, uint32_t(p), sample, uint32_t(b), 9, Uf);
+          rng4(P.seed, uint32_t(p), sample, uint32_t(b), 10, U10);
+          Uf[4] = U10[0];
+          Uf[5] = U10[1];
+          V3 c, wl;
+          double pl, cm;
+          if (emitter_nee(s, prims, E, k, m, x, wo, ff.prim, Ue, Uf, &c, &wl, &pl, &cm, &shd))
+            Lr = Lr + mis2(pl, cm * p_scatter(wl)) * (beta * c);
         }
         V3 wi, wgt;
         if (!guided) {

@@ -128,3 +128,119 @@ def test_light_sampling_mis_matches_phase_sampling(orc):
     assert m1.mean() > 0.01   # the light contributes
     # MIS reduces variance relative to phase sampling alone
     assert np.median(se1) < np.median(se0)
+
+
+# ---------------------------------------------------------------------------- f1: light sampling of emitters
+def _emitter_scene():
+    """Three isotropic emitters in well separated directions from the vertex at (0.5, 0.5, 0.5),
+    of different power, the first one dense enough to saturate along its centre line."""
+    s = scenes.tiny_scene(n=3, seed=7)
+    s.quat[:] = [1.0, 0.0, 0.0, 0.0]
+    s.mean[:] = [[0.5, 0.5, 0.95], [0.85, 0.55, 0.5], [0.45, 0.15, 0.55]]
+    sig = np.array([0.04, 0.03, 0.05])
+    s.scale[:] = sig[:, None]
+    half_I_centre = np.array([3.0, 0.4, 0.25])  # 1/2 I through the centre, unclipped: c / (4 pi sigma^2)
+    s.magnitude[:] = (half_I_centre * 4 * math.pi * sig ** 2).astype(np.float32)
+    s.mtype[:] = scenes.MAT_EMISSIVE
+    s.emission[:] = [[4.0, 2.0, 1.0], [0.5, 3.0, 0.5], [6.0, 6.0, 6.0]]
+    return s, sig
+
+
+def test_ellipsoid_points_follow_the_truncated_gaussian(orc):
+    """Light-sampling points: whitened radius follows the chi-3 law truncated at k (KS against
+    scipy), whitened directions are isotropic, every point lies inside the ellipsoid."""
+    from scipy import stats
+    k = math.sqrt(-2 * math.log(0.01))
+    assert abs(orc.chi3_cdf(k) - stats.chi(3).cdf(k)) < 1e-14
+    s = scenes.tiny_scene(n=5, seed=8)
+    i = 3
+    U = np.random.default_rng(120).random((100000, 3))
+    y = orc.sample_in_ellipsoid(s, i, U)
+    w, x_, y_, z = s.quat[i].astype(np.float64)
+    R = Rotation.from_quat([x_, y_, z, w]).as_matrix()
+    zc = (y - s.mean[i].astype(np.float64)) @ R / s.scale[i].astype(np.float64)
+    r = np.linalg.norm(zc, axis=1)
+    assert r.max() <= k * (1 + 1e-12)
+    cdf = lambda x: stats.chi(3).cdf(x) / stats.chi(3).cdf(k)
+    assert stats.kstest(r, cdf).pvalue > 1e-3
+    u = zc / r[:, None]
+    assert np.abs(u.mean(0)).max() < 4 / math.sqrt(len(u))
+    np.testing.assert_allclose(u.T @ u / len(u), np.eye(3) / 3, atol=0.01)
+
+
+def test_emitter_light_sampling_matches_quadrature(orc):
+    """One-sample light estimates toward emissive primitives (no MIS) average to the direct
+    emission int f_p(w) sum_j P_j(w) L_e,j dw, where P_j(w) = min(1, 1/2 I_j) is the free-flight
+    probability of choosing emitter j along w (Eq. 8 with the saturation clamp), and f_p the
+    closed-form phase function of a Lambertian base with S = I (Sec. 6). For an isotropic
+    emitter of scale sigma and magnitude c at distance D, a direction at angle theta from its
+    centre passes at whitened distance d = D sin(theta) / sigma, and App. A over the clipped
+    chord gives 1/2 I = c / (4 pi sigma^2) e^{-d^2/2} erf(sqrt((k^2 - d^2) / 2)). The emitters
+    lie in separate directions, so their cones do not overlap."""
+    from scipy.optimize import brentq
+    s, sig = _emitter_scene()
+    k = math.sqrt(-2 * math.log(0.01))
+    x = np.array([0.5, 0.5, 0.5])
+    wo = np.array([0.3, -0.2, 0.93]); wo /= np.linalg.norm(wo)
+    albedo = np.array([0.8, 0.6, 0.4])
+    S6 = np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    ref = np.zeros(3)
+    for j in range(3):
+        c = s.mean[j].astype(np.float64) - x
+        D = np.linalg.norm(c)
+        ax = c / D
+        e1 = np.cross(ax, [1.0, 0, 0] if abs(ax[0]) < 0.9 else [0, 1.0, 0]); e1 /= np.linalg.norm(e1)
+        e2 = np.cross(ax, e1)
+        th_max = math.asin(k * float(sig[j]) / D)
+        amp = float(s.magnitude[j]) / (4 * math.pi * float(sig[j]) ** 2)
+
+        def P(th, j=j, D=D, amp=amp):
+            d = D * math.sin(th) / float(sig[j])
+            return 0.0 if d >= k else min(1.0, amp * math.exp(-0.5 * d * d) * math.erf(math.sqrt(0.5 * (k * k - d * d))))
+
+        def integrand(ph, th, ax=ax, e1=e1, e2=e2, P=P):
+            w = math.cos(th) * ax + math.sin(th) * (math.cos(ph) * e1 + math.sin(ph) * e2)
+            f = orc.phase_eval(scenes.MAT_DIFFUSE, albedo, 0.5, S6, wo, w)[0, 0] / albedo[0]
+            return f * P(th) * math.sin(th)
+
+        kinks = [brentq(lambda th: P(th) - 1.0 + 1e-300, 0.0, th_max, xtol=1e-15)] if P(0.0) >= 1.0 else []
+        v, _ = integrate.nquad(integrand, [[0.0, 2 * math.pi], [0.0, th_max]],
+                               opts=[{"epsabs": 1e-12, "epsrel": 1e-10, "limit": 200},
+                                     {"epsabs": 1e-11, "epsrel": 1e-9, "limit": 200, "points": kinks}])
+        ref += v * albedo * s.emission[j].astype(np.float64)
+    mean, se = orc.emitter_nee(s, x, wo, scenes.MAT_DIFFUSE, albedo, 0.5, S6, n=2_000_000, seed=121)
+    assert np.all(se < 0.01 * ref), (se, ref)
+    assert np.all(np.abs(mean - ref) <= 4 * se), (mean, ref, se)
+
+
+def test_emitter_light_sampling_render_is_unbiased(orc):
+    """A scene lit only by emissive primitives renders the same with light sampling toward them
+    plus MIS (nee_emitters=1) as with emitters found by phase sampling alone: the balance weights
+    of the two techniques sum to one. Pixels where phase sampling never met an emitter (zero
+    sample variance) have no usable error estimate and are left out of the per-pixel test."""
+    s = scenes.tiny_scene(n=300, seed=9, width=12, height=12)
+    rng = np.random.default_rng(122)
+    s.mtype[:] = scenes.MAT_DIFFUSE
+    s.mtype[rng.random(s.n) < 0.3] = scenes.MAT_GGX
+    s.roughness[:] = 0.3
+    em = rng.random(s.n) < 0.1
+    s.mtype[em] = scenes.MAT_EMISSIVE
+    s.scale[em] *= 3.0
+    s.magnitude[em] *= 9.0
+    s.emission[:] = 0.0
+    s.emission[em] = (rng.uniform(0.5, 2.0, (em.sum(), 1)) * rng.uniform(0.3, 1.0, (em.sum(), 3))).astype(np.float32)
+    s.lights = scenes.Lights(False, (0, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0.0, 0.0, 0.0))
+    spp = 16384
+    a1, q1, (e1, sh1) = orc.render(s, spp=spp, max_depth=3, nee_emitters=1, seed=13)
+    a0, q0, (e0, sh0) = orc.render(s, spp=spp, max_depth=3, nee_emitters=0, seed=14)
+    assert sh1 > 0 and sh0 == 0
+    m1, m0 = a1 / spp, a0 / spp
+    se1 = np.sqrt(np.maximum(q1 / spp - m1 ** 2, 0) / spp)
+    se0 = np.sqrt(np.maximum(q0 / spp - m0 ** 2, 0) / spp)
+    seen = se0 > 0
+    assert seen.mean() > 0.9
+    z = np.abs(m1 - m0)[seen] / np.sqrt(se1 ** 2 + se0 ** 2)[seen]
+    assert (z > 3.5).mean() <= 0.03, np.sort(z)[-5:]
+    zi = abs(m1.mean() - m0.mean()) / math.sqrt((se1 ** 2).sum() + (se0 ** 2).sum()) * m1.size
+    assert zi < 4, zi
+    assert m1.mean() > 0.01
