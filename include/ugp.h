@@ -379,7 +379,13 @@ ugp_status ugp_guide_adam_step(ugp_guide* g, const float* grad, void* stream);
  *                   techniques with p~ (one-sample MIS; unbiased for any guide). The
  *                   mixture pdf alpha q + (1 - alpha) p~ is the MIS partner of light sampling.
  *   guide_log       1: record every scattering vertex of this call for training
- *                   (ugp_guide_train_from_render); requires spp == 1 and a guide */
+ *                   (ugp_guide_train_from_render); requires spp == 1 and a guide
+ *   emitters        NULL, or a device table from ugp_build_emitter_table for this BVH and
+ *                   these materials: each scattering vertex then also samples a point of an
+ *                   emissive primitive (light sampling, balanced against phase sampling). A
+ *                   table built for another primitive count is ignored. Not combined with
+ *                   nee = 1 and an area light (UGP_ERR_INVALID_ARG): one light sample per
+ *                   vertex. */
 typedef struct ugp_render_params {
   int32_t spp, spp_begin, max_depth, nee;
   uint64_t seed;
@@ -387,7 +393,28 @@ typedef struct ugp_render_params {
   const ugp_guide* guide;
   float guide_alpha;
   int32_t reserved;
+  const void* emitters;
 } ugp_render_params;
+
+/* Light sampling toward emissive primitives (the paper finds its emitters by phase sampling
+ * only). Emitter j is chosen with probability pi_j proportional to its power c_j mean(L_e,j),
+ * and a point y from its Gaussian restricted to the k-ellipsoid. The free flight from a vertex
+ * x picks j at distance t with density 1/2 G_j(x + t w) below the saturating distance (Eq. 8),
+ * so one sample estimates the emitter's direct contribution by
+ *   1/2 c_j m L_e,j f_p(w) 1[T(x, y) > 0] / (|y - x|^2 pi_j),  m = P(chi_3 <= k),
+ * weighted by the balance heuristic 2 r_c^2 pi_j / (2 r_c^2 pi_j + c_j m p(w)) against phase
+ * sampling (r_c: distance from x to the emitter's mean; a path that reaches the emitter by
+ * phase sampling takes the complement). Philox slots 8 (choice, radius, direction) and 9-10
+ * (stochastic phase evaluation).
+ * ugp_emitter_table_size: bytes of the table for n_prims primitives (76 per primitive plus
+ *   alignment), 0 for n_prims outside [0, 2^31 - 1].
+ * ugp_build_emitter_table: fills `table` (device, 256-byte aligned, caller-owned) from the BVH
+ *   and the materials' type and emission3 arrays; asynchronous on `stream`; rebuild after
+ *   changing either. Errors: UGP_ERR_NOT_BUILT for an invalid handle, UGP_ERR_INVALID_ARG for
+ *   a NULL or misaligned argument, UGP_ERR_WORKSPACE_TOO_SMALL. */
+size_t ugp_emitter_table_size(int64_t n_prims);
+ugp_status ugp_build_emitter_table(const ugp_bvh* bvh, const ugp_materials* materials, void* table,
+                                   size_t table_bytes, void* stream);
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
  * per-path primitive-slot lists, 1236 bytes per pixel plus alignment). */

@@ -88,7 +88,8 @@ V3 sample_in_ellipsoid(const Prim& p, double k, const double U[3]);
 // One light sample from vertex x (material m, outgoing wo, the vertex's primitive excluded).
 // Returns false when it adds nothing; else *contrib = f_p * L_e * c_j m / (2 r^2 pi_j) (the
 // estimate without beta and MIS weight), *dir the direction, and the two balance-heuristic terms
-// in a common scale: *p_light = 2 r^2 pi_j, *p_scatter_scale = c_j m (times the scattering pdf).
+// in a common scale: *p_light = 2 r_c^2 pi_j with r_c the distance from x to the emitter's mean,
+// *p_scatter_scale = c_j m (times the scattering pdf).
 bool emitter_nee(const SceneIn& s, const std::vector<Prim>& prims, const EmitterTable& E, double k,
                  const Material& m, V3 x, V3 wo, int32_t exclude, const double U4[4], const double Uf[6],
                  V3* contrib, V3* dir, double* p_light, double* p_scatter_scale, int64_t* shadow_rays);

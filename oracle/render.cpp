@@ -100,8 +100,11 @@ static double mis2(double a, double b) { return a + b > 0 ? a / (a + b) : 0.0; }
 // probability pi_j, one sample estimates it by 1/2 c_j m L_e,j f_p 1[T(x, y) > 0] / (r^2 pi_j):
 // the linear model needs only that y lies before saturation, not a transmittance factor.
 // The balance heuristic against phase sampling compares the two densities of (j, y) in volume
-// measure: pi_j G_j(y) / (c_j m) and p(w) 1/2 G_j(y) / r^2. G_j(y) cancels, leaving 2 r^2 pi_j
-// against c_j m p(w).
+// measure, pi_j G_j(y) / (c_j m) and p(w) 1/2 G_j(y) / r^2, in which G_j(y) cancels: 2 r^2 pi_j
+// against c_j m p(w). The weights use r_c, the distance from x to the emitter's mean, in place of
+// r: a weight that depends on (j, x, w) only is available to a path that reaches the emitter by
+// phase sampling without knowing where inside it the free flight stopped, and any weights that
+// sum to one over the two techniques keep the estimate unbiased.
 double chi3_cdf(double r) {
   return std::erf(r / std::sqrt(2.0)) - std::sqrt(2.0 / kPi) * r * std::exp(-0.5 * r * r);
 }
@@ -164,19 +167,22 @@ bool emitter_nee(const SceneIn& s, const std::vector<Prim>& prims, const Emitter
   const double cm = double(s.magnitude[j]) * E.mass;
   *contrib = (0.5 * cm / (r2 * pj)) * (f * load3(s.emission3 + 3 * size_t(j)));
   *dir = wl;
-  *p_light = 2.0 * r2 * pj;
+  const V3 c = prims[size_t(j)].mu - x;
+  *p_light = 2.0 * dot(c, c) * pj;
   *p_scatter_scale = cm;
   return true;
 }
 
-// Balance weight of an emitter reached by phase sampling (distance r from the previous vertex,
-// scattering pdf p there): the complement of the light-sampling weight above.
-static double emitter_hit_weight(const SceneIn& s, const EmitterTable& E, int32_t j, double r, double p) {
+// Balance weight of emitter j reached by phase sampling from the vertex x (scattering pdf p
+// there): the complement of the light-sampling weight above.
+static double emitter_hit_weight(const SceneIn& s, const std::vector<Prim>& prims, const EmitterTable& E, int32_t j,
+                                 V3 x, double p) {
   const auto it = std::lower_bound(E.ids.begin(), E.ids.end(), j);
   if (it == E.ids.end() || *it != j) return 1.0;
   const size_t q = size_t(it - E.ids.begin());
   const double pj = (E.cdf[q] - (q ? E.cdf[q - 1] : 0.0)) / E.total;
-  return mis2(double(s.magnitude[j]) * E.mass * p, 2.0 * r * r * pj);
+  const V3 c = prims[size_t(j)].mu - x;
+  return mis2(double(s.magnitude[j]) * E.mass * p, 2.0 * dot(c, c) * pj);
 }
 
 void emitter_nee_sums(const SceneIn& s, double cutoff_eps, const Material& m, V3 x, V3 wo, int32_t exclude,
@@ -255,7 +261,7 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
         }
         const Material m = material_of(s, ff.prim);
         if (m.type == kMatEmissive) {
-          const double w = (P.nee_emitters && pdf_prev >= 0) ? emitter_hit_weight(s, E, ff.prim, ff.t_u, pdf_prev) : 1.0;
+          const double w = (P.nee_emitters && pdf_prev >= 0) ? emitter_hit_weight(s, prims, E, ff.prim, o, pdf_prev) : 1.0;
           Lr = Lr + w * (beta * m.emission);
           break;
         }

@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "ugp_dense.cuh"
+#include "ugp_emitters.cuh"
 #include "ugp_freeflight.cuh"
 #include "ugp_guide_kernels.cuh"
 #include "ugp_phase.cuh"
@@ -134,7 +135,8 @@ template <bool kGuided>
 __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 key, int sample, int bounce, int max_depth,
                                                int nee, PathSoA ps, const int* __restrict__ q, const int* cnt,
                                                int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow,
-                                               int* dense_cnt, int* scan_next, GuidedShade gs) {
+                                               int* dense_cnt, int* scan_next, GuidedShade gs, EmitterDev E) {
+  const bool em_on = emitters_on(E);
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // the extend and dense passes of this bounce have run
     *dense_cnt = 0;
@@ -167,7 +169,15 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
         Lr = Lr + beta * L.bg;
       }
     } else if (mats.type[k] == kMatEmissive) {
-      Lr = Lr + beta * f3(mats.emission3[3 * k], mats.emission3[3 * k + 1], mats.emission3[3 * k + 2]);
+      float w = 1.f;
+      const float pdf_prev = ps.pdf_prev[p];
+      const int e = em_on && pdf_prev >= 0.f ? E.map[k] : -1;
+      if (e >= 0) {  // reached by phase sampling: the complement of the light-sampling weight
+        const float4 m0 = E.rec[4 * e], m1 = E.rec[4 * e + 1], m2 = E.rec[4 * e + 2], m3 = E.rec[4 * e + 3];
+        const float3 c = f3(m0.w, m1.w, m2.w) - o;
+        w = mis_w(m3.x * pdf_prev, 2.f * dot3(c, c) * emitter_prob(E, e));
+      }
+      Lr = Lr + w * (beta * f3(mats.emission3[3 * k], mats.emission3[3 * k + 1], mats.emission3[3 * k + 2]));
     } else if (bounce < max_depth) {
       const Material M = load_material(mats, k);
       const float t = ps.tsp[p];
@@ -203,6 +213,44 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
             sh.ox[j] = x.x; sh.oy[j] = x.y; sh.oz[j] = x.z;
             sh.dx[j] = wl.x; sh.dy[j] = wl.y; sh.dz[j] = wl.z;
             sh.dist[j] = r;
+            sh.excl[j] = k;
+            sh.cr[j] = contrib.x; sh.cg[j] = contrib.y; sh.cb[j] = contrib.z;
+          }
+        }
+      }
+      if (em_on) {
+        // light sampling of the emitters: emitter by power, point from its Gaussian inside the
+        // ellipsoid (radius from the truncated chi-3 law, direction uniform), Philox slots 8-10
+        const float4 Ua = rng(key, p, sample, bounce, 8);
+        const long long e = emitter_pick(E, Ua.x);
+        const float pj = emitter_prob(E, e);
+        const float4 m0 = E.rec[4 * e], m1 = E.rec[4 * e + 1], m2 = E.rec[4 * e + 2], m3 = E.rec[4 * e + 3];
+        const float rr = chi3_radius(Ua.y * E.mass, E.k);
+        const float cz = 1.f - 2.f * Ua.z, sz = sqrtf(fmaxf(0.f, 1.f - cz * cz));
+        float sp, cp;
+        sincospif(2.f * Ua.w, &sp, &cp);
+        const float zx = rr * sz * cp, zy = rr * sz * sp, zz = rr * cz;
+        const float3 y = f3(m0.w + m0.x * zx + m0.y * zy + m0.z * zz, m1.w + m1.x * zx + m1.y * zy + m1.z * zz,
+                            m2.w + m2.x * zx + m2.y * zy + m2.z * zz);
+        const float3 w = y - x;
+        const float r2 = dot3(w, w);
+        if (r2 > 0.f && pj > 0.f) {
+          const float r = sqrtf(r2);
+          const float3 wl = (1.f / r) * w;
+          const float4 Ub = rng(key, p, sample, bounce, 9), Uc = rng(key, p, sample, bounce, 10);
+          const float Ue[6] = {Ub.x, Ub.y, Ub.z, Ub.w, Uc.x, Uc.y};
+          const float3 f = phase_eval(M, wl, wo, Ue);
+          if (f.x > 0.f || f.y > 0.f || f.z > 0.f) {
+            float ps_l = phase_pdf_approx(M, wl, wo);
+            if (kGuided) ps_l = gs.alpha * mixture_pdf(mix, wl) + (1.f - gs.alpha) * ps_l;
+            const float3 c = f3(m0.w, m1.w, m2.w) - x;
+            const float wm = mis_w(2.f * dot3(c, c) * pj, m3.x * ps_l);
+            const float3 contrib = (wm * 0.5f * m3.x / (r2 * pj)) * (beta * (f * f3(m3.y, m3.z, m3.w)));
+            const int j = queue_append(cnt_shadow);
+            sh.path[j] = p;
+            sh.ox[j] = x.x; sh.oy[j] = x.y; sh.oz[j] = x.z;
+            sh.dx[j] = wl.x; sh.dy[j] = wl.y; sh.dz[j] = wl.z;
+            sh.dist[j] = -r;  // negative: the contribution counts when T > 0, unscaled
             sh.excl[j] = k;
             sh.cr[j] = contrib.x; sh.cg[j] = contrib.y; sh.cb[j] = contrib.z;
           }
@@ -276,13 +324,17 @@ __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene 
   if (j >= count) return;
   const Ray ray = make_ray(f3(sh.ox[j], sh.oy[j], sh.oz[j]), f3(sh.dx[j], sh.dy[j], sh.dz[j]));
   TrStats ts{0u, 0u, UGP_RAY_OK};
-  const float tau = tr_optical_depth(sc, ray, 0.f, sh.dist[j], sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
+  // a negative distance marks a light sample of an emissive primitive: it counts when the
+  // point lies before saturation (T > 0) and is not scaled by T
+  const float dist = sh.dist[j];
+  const float tau = tr_optical_depth(sc, ray, 0.f, fabsf(dist), sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
   const float T = fmaxf(0.f, 1.f - tau);
   if (T > 0.f) {
+    const float s = dist < 0.f ? 1.f : T;
     const int p = sh.path[j];
-    ps.lr[p] += T * sh.cr[j];
-    ps.lg[p] += T * sh.cg[j];
-    ps.lb[p] += T * sh.cb[j];
+    ps.lr[p] += s * sh.cr[j];
+    ps.lg[p] += s * sh.cg[j];
+    ps.lb[p] += s * sh.cb[j];
   }
   if (ts.st != UGP_RAY_OK && rays) atomicAdd(rays + 2, 1ull);
   if (stats) add_counters(stats + 6, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);
@@ -536,6 +588,12 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   const TraceScene sc = trace_scene(bvh);
   const uint2 key = make_uint2(uint32_t(params->seed & 0xffffffffu), uint32_t(params->seed >> 32));
   unsigned long long* stats = trace_counters();
+  if (params->emitters && (reinterpret_cast<uintptr_t>(params->emitters) & 255))
+    return fail(UGP_ERR_INVALID_ARG, "ugp_render: emitter table must be 256-byte aligned");
+  const EmitterDev Em = emitter_dev(params->emitters, bvh);
+  // the shadow queue holds one ray per path and bounce
+  if (Em.cdf && params->nee && Ld.has_quad)
+    return fail(UGP_ERR_INVALID_ARG, "ugp_render: light sampling of emitters and of the area light in one render");
 
   GuidedShade gs{};
   GuideDev gd{};
@@ -587,13 +645,13 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
       if (guide)
         k_shade<true><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
                                                 counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count,
-                                                scan_next, gs);
+                                                scan_next, gs, Em);
       else
         k_shade<false><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps,
                                                  queue[cur], counts + cur, queue[nxt], counts + nxt, sh, counts + 2,
-                                                 dq.count, scan_next, gs);
+                                                 dq.count, scan_next, gs, Em);
       prof_end(kStShade, st);
-      if (params->nee && Ld.has_quad) {
+      if ((params->nee && Ld.has_quad) || Em.cdf) {
         prof_begin(kStShadow, st);
         k_shadow<<<g_shadow, kTrBlock, 0, st>>>(sc, sh, counts + 2, ps, ray_counts, stats);
         prof_end(kStShadow, st);

@@ -53,7 +53,7 @@ class UgpRenderParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("nee", C.c_int32), ("seed", C.c_uint64), ("spawn_mode", C.c_int32),
                 ("guide_log", C.c_int32), ("guide", C.POINTER(UgpGuide)), ("guide_alpha", C.c_float),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("emitters", C.c_void_p)]
 
 
 class UgpError(RuntimeError):
@@ -110,6 +110,10 @@ def lib():
         L.ugp_render_radiance_field.restype = C.c_int
         L.ugp_render_radiance_field.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, C.POINTER(C.c_float), vp, vp, vp,
                                                 C.c_size_t, vp]
+        L.ugp_emitter_table_size.restype = C.c_size_t
+        L.ugp_emitter_table_size.argtypes = [C.c_int64]
+        L.ugp_build_emitter_table.restype = C.c_int
+        L.ugp_build_emitter_table.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.ugp_sample_free_flight_exponential.restype = C.c_int
         L.ugp_sample_free_flight_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_trace_transmittance_exponential.restype = C.c_int
@@ -379,11 +383,12 @@ class Renderer:
     def render(self, bvh: Bvh, mats: Materials, camera: UgpCamera, lights: UgpLights, spp: int,
                max_depth: int, seed: int = 0, spp_begin: int = 0, nee: bool = True, spawn_mode: int = 0,
                accum=None, accum_sq=None, ray_counts=None, stream=None, guide=None, guide_alpha: float = 0.5,
-               guide_log: bool = False):
+               guide_log: bool = False, emitters=None):
         """Adds spp samples per pixel into accum / accum_sq ((H, W, 3) float32, created if None).
 
         With ``guide`` (a ``Guide``) the renderer samples directions by one-sample MIS between
         the guide and phase sampling; ``guide_log`` records the vertices for ``Guide.train_from``.
+        ``emitters`` (from ``build_emitter_table``) adds light sampling of emissive primitives.
         """
         dev = self.workspace.device
         shape = (self.height, self.width, 3)
@@ -401,7 +406,8 @@ class Renderer:
             raise ValueError("camera size does not match the renderer")
         prm = UgpRenderParams(int(spp), int(spp_begin), int(max_depth), int(bool(nee)), int(seed),
                               int(spawn_mode), int(bool(guide_log)),
-                              C.pointer(guide.c) if guide is not None else None, float(guide_alpha), 0)
+                              C.pointer(guide.c) if guide is not None else None, float(guide_alpha), 0,
+                              emitters.data_ptr() if emitters is not None else None)
         if guide is not None:
             need = guided_workspace_size(self.width, self.height, max_depth)
             if self.workspace.numel() < need:
@@ -412,6 +418,16 @@ class Renderer:
                                 _p(self.workspace), self.workspace.numel(), _p(ray_counts),
                                 C.c_void_p(_stream(stream))), "ugp_render")
         return accum, accum_sq
+
+
+def build_emitter_table(bvh: Bvh, mats, stream=None):
+    """Device table for light sampling of the emissive primitives of ``bvh`` with materials
+    ``mats`` (a ``Materials``): pass it to ``Renderer.render(emitters=...)``."""
+    nb = int(lib().ugp_emitter_table_size(int(bvh.n)))
+    table = torch.empty(max(nb, 256), dtype=torch.uint8, device=bvh.workspace.device)
+    _check(lib().ugp_build_emitter_table(C.c_void_p(bvh.handle), C.byref(mats.c), _p(table), table.numel(),
+                                         C.c_void_p(_stream(stream))), "ugp_build_emitter_table")
+    return table
 
 
 def set_trace_counters(counters=None):

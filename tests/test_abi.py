@@ -80,6 +80,16 @@ def test_exponential_entry_points_validate_on_host(libugp):
     assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()
 
 
+def test_emitter_table_entry_points_validate_on_host(libugp):
+    libugp.ugp_last_error.restype = ctypes.c_char_p
+    libugp.ugp_emitter_table_size.restype = ctypes.c_size_t
+    libugp.ugp_emitter_table_size.argtypes = [ctypes.c_int64]
+    assert libugp.ugp_emitter_table_size(1000) >= 76 * 1000
+    assert libugp.ugp_emitter_table_size(-1) == 0
+    st = libugp.ugp_build_emitter_table(None, None, None, ctypes.c_size_t(0), None)
+    assert st == 6 and b"invalid BVH handle" in libugp.ugp_last_error()
+
+
 def test_guide_entry_points_validate_on_host(libugp):
     libugp.ugp_guide_workspace_size.restype = ctypes.c_size_t
     libugp.ugp_render_guided_workspace_size.restype = ctypes.c_size_t
@@ -103,8 +113,9 @@ def test_guide_struct_layouts_match_the_header():
     from paper_2406_09733_gb300 import ugp
     assert ctypes.sizeof(ugp.UgpGuide) == 80
     assert ugp.UgpGuide.kappa_max.offset == 76
-    assert ctypes.sizeof(ugp.UgpRenderParams) == 48
+    assert ctypes.sizeof(ugp.UgpRenderParams) == 56
     assert ugp.UgpRenderParams.guide.offset == 32 and ugp.UgpRenderParams.guide_alpha.offset == 40
+    assert ugp.UgpRenderParams.emitters.offset == 48
 
 
 def test_batch_entry_points_validate_on_host(libugp):
