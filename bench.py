@@ -65,6 +65,7 @@ def parse_args(argv=None):
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving study")
     p.add_argument("--no-rf", action="store_true", help="skip the radiance-field render study")
     p.add_argument("--no-exp", action="store_true", help="skip the exponential-variant query study")
+    p.add_argument("--no-emitters", action="store_true", help="skip the emitter light-sampling study")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-spp-max", type=int, default=4,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
@@ -542,6 +543,12 @@ def run_ugp(args):
     expo = None
     if rank == 0 and world == 1 and not args.no_exp:
         expo = exponential_study(args, d, scene, dev)
+    emit = None
+    if rank == 0 and world == 1 and not args.no_emitters:
+        try:
+            emit = emitter_study(args, d, mats, scene, dev)
+        except Exception as e:  # reported in the line; the measured step above stands
+            emit = {"error": repr(e)}
 
     if rank == 0:
         clk = clocks.summary()
@@ -562,7 +569,7 @@ def run_ugp(args):
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf, "serving": serving,
-            "exponential_variant": expo,
+            "exponential_variant": expo, "emitter_light_sampling": emit,
             "radiance_field": rf,
         }
         print(json.dumps(line), flush=True)
@@ -647,6 +654,55 @@ def exponential_study(args, d, scene, dev, reps=10):
             out[name]["collided"] = float((res[0] >= 0).float().mean().item())
         else:
             out[name]["mean_T"] = float(res[0].mean().item())
+    return out
+
+
+def emitter_study(args, d, mats, scene, dev, spp=4):
+    """Light sampling of the emissive primitives (a tenth of the room scene's) under the paper's
+    lighting B: no area light, no background. The same frames (bench image and depth) with and
+    without the emitter table: CUDA-event time per spp after one warm-up spp, queries, and the
+    mean per-pixel sample variance; efficiency = (variance x time) without over with."""
+    import torch
+    from paper_2406_09733_gb300 import ugp
+    cam = scene.camera
+    W, H = args.width, args.height
+    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, W, H)
+    lights = ugp.lights_struct(False, (0, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0.0, 0.0, 0.0))
+    bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t0, t1 = ev(), ev()
+    torch.cuda.synchronize(dev)
+    t0.record()
+    table = ugp.build_emitter_table(bvh, mats)
+    t1.record()
+    torch.cuda.synchronize(dev)
+    out = {"lighting": "emissive primitives only (no area light, no background)", "image": f"{W}x{H}",
+           "spp": spp, "depth": args.depth, "table_build_ms": t0.elapsed_time(t1),
+           "n_emitters": int(table[:8].cpu().view(torch.int64)[0])}
+    r = ugp.Renderer(W, H, device=dev)
+    res = {}
+    for name, tab in (("phase_only", None), ("light_sampling", table)):
+        r.render(bvh, mats, camera, lights, spp=1, max_depth=args.depth, seed=3, emitters=tab)
+        torch.cuda.synchronize(dev)
+        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+        acc = torch.zeros((H, W, 3), dtype=torch.float32, device=dev)
+        acc2 = torch.zeros_like(acc)
+        t0.record()
+        r.render(bvh, mats, camera, lights, spp=spp, max_depth=args.depth, seed=5, accum=acc, accum_sq=acc2,
+                 ray_counts=cnt, emitters=tab)
+        t1.record()
+        torch.cuda.synchronize(dev)
+        ms = t0.elapsed_time(t1)
+        mean = acc.double() / spp
+        var = ((acc2.double() / spp - mean ** 2).clamp(min=0) * spp / (spp - 1)).mean().item()
+        c = cnt.cpu().tolist()
+        res[name] = (var, ms)
+        out[name] = {"ms_per_spp": ms / spp, "Mrays_per_s": (c[0] + c[1]) / (ms / 1e3) / 1e6,
+                     "extend_queries": c[0], "shadow_queries": c[1], "queries_with_error_status": c[2],
+                     "mean_rgb": mean.mean((0, 1)).tolist(), "mean_pixel_variance": var}
+    vp, tp = res["phase_only"]
+    vl, tl = res["light_sampling"]
+    out["efficiency_gain"] = (vp * tp) / (vl * tl) if vl > 0 and tl > 0 else None
     return out
 
 
