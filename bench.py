@@ -658,51 +658,64 @@ def exponential_study(args, d, scene, dev, reps=10):
 
 
 def emitter_study(args, d, mats, scene, dev, spp=4):
-    """Light sampling of the emissive primitives (a tenth of the room scene's) under the paper's
-    lighting B: no area light, no background. The same frames (bench image and depth) with and
-    without the emitter table: CUDA-event time per spp after one warm-up spp, queries, and the
-    mean per-pixel sample variance; efficiency = (variance x time) without over with."""
+    """Light sampling of emissive primitives, no area light, no background, on two scenes of the
+    bench's size: the bench scene's own emitters (a tenth of the surface shapes), and the
+    generator's lighting B (the paper's night: 12,000 small emissive aggregate primitives added).
+    The same frames (bench image and depth) with and without the emitter table: CUDA-event time
+    per spp after one warm-up spp, queries, and the mean per-pixel sample variance; efficiency =
+    (variance x time) without over with."""
+    import numpy as np
     import torch
-    from paper_2406_09733_gb300 import ugp
-    cam = scene.camera
+    from paper_2406_09733_gb300 import scenes, ugp
     W, H = args.width, args.height
-    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, W, H)
     lights = ugp.lights_struct(False, (0, 0, 0), (0, 0, 0), (0, 0, 0), (0, 0, 0), (0.0, 0.0, 0.0))
-    bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
     ev = lambda: torch.cuda.Event(enable_timing=True)
     t0, t1 = ev(), ev()
-    torch.cuda.synchronize(dev)
-    t0.record()
-    table = ugp.build_emitter_table(bvh, mats)
-    t1.record()
-    torch.cuda.synchronize(dev)
-    out = {"lighting": "emissive primitives only (no area light, no background)", "image": f"{W}x{H}",
-           "spp": spp, "depth": args.depth, "table_build_ms": t0.elapsed_time(t1),
-           "n_emitters": int(table[:8].cpu().view(torch.int64)[0])}
     r = ugp.Renderer(W, H, device=dev)
-    res = {}
-    for name, tab in (("phase_only", None), ("light_sampling", table)):
-        r.render(bvh, mats, camera, lights, spp=1, max_depth=args.depth, seed=3, emitters=tab)
+
+    def one(sc, arrays, m):
+        cam = sc.camera
+        camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, W, H)
+        bvh = ugp.build_bvh(arrays["mean"], arrays["quat"], arrays["scale"], arrays["magnitude"])
         torch.cuda.synchronize(dev)
-        cnt = torch.zeros(3, dtype=torch.int64, device=dev)
-        acc = torch.zeros((H, W, 3), dtype=torch.float32, device=dev)
-        acc2 = torch.zeros_like(acc)
         t0.record()
-        r.render(bvh, mats, camera, lights, spp=spp, max_depth=args.depth, seed=5, accum=acc, accum_sq=acc2,
-                 ray_counts=cnt, emitters=tab)
+        table = ugp.build_emitter_table(bvh, m)
         t1.record()
         torch.cuda.synchronize(dev)
-        ms = t0.elapsed_time(t1)
-        mean = acc.double() / spp
-        var = ((acc2.double() / spp - mean ** 2).clamp(min=0) * spp / (spp - 1)).mean().item()
-        c = cnt.cpu().tolist()
-        res[name] = (var, ms)
-        out[name] = {"ms_per_spp": ms / spp, "Mrays_per_s": (c[0] + c[1]) / (ms / 1e3) / 1e6,
-                     "extend_queries": c[0], "shadow_queries": c[1], "queries_with_error_status": c[2],
-                     "mean_rgb": mean.mean((0, 1)).tolist(), "mean_pixel_variance": var}
-    vp, tp = res["phase_only"]
-    vl, tl = res["light_sampling"]
-    out["efficiency_gain"] = (vp * tp) / (vl * tl) if vl > 0 and tl > 0 else None
+        out = {"table_build_ms": t0.elapsed_time(t1), "n_emitters": int(table[:8].cpu().view(torch.int64)[0])}
+        res = {}
+        for name, tab in (("phase_only", None), ("light_sampling", table)):
+            r.render(bvh, m, camera, lights, spp=1, max_depth=args.depth, seed=3, emitters=tab)
+            torch.cuda.synchronize(dev)
+            cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+            acc = torch.zeros((H, W, 3), dtype=torch.float32, device=dev)
+            acc2 = torch.zeros_like(acc)
+            t0.record()
+            r.render(bvh, m, camera, lights, spp=spp, max_depth=args.depth, seed=5, accum=acc, accum_sq=acc2,
+                     ray_counts=cnt, emitters=tab)
+            t1.record()
+            torch.cuda.synchronize(dev)
+            ms = t0.elapsed_time(t1)
+            mean = acc.double() / spp
+            var = ((acc2.double() / spp - mean ** 2).clamp(min=0) * spp / (spp - 1)).mean().item()
+            c = cnt.cpu().tolist()
+            res[name] = (var, ms)
+            out[name] = {"ms_per_spp": ms / spp, "Mrays_per_s": (c[0] + c[1]) / (ms / 1e3) / 1e6,
+                         "extend_queries": c[0], "shadow_queries": c[1], "queries_with_error_status": c[2],
+                         "mean_rgb": mean.mean((0, 1)).tolist(), "mean_pixel_variance": var}
+        vp, tp = res["phase_only"]
+        vl, tl = res["light_sampling"]
+        out["efficiency_gain"] = (vp * tp) / (vl * tl) if vl > 0 and tl > 0 else None
+        return out
+
+    out = {"image": f"{W}x{H}", "spp": spp, "depth": args.depth,
+           "lights": "emissive primitives only (no area light, no background)"}
+    out["bench_scene_emitters"] = one(scene, d, mats)
+    sb = scenes.room_scene(args.n_prims, width=W, height=H, lighting="B")
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    db = {"mean": t(sb.mean), "quat": t(sb.quat), "scale": t(sb.scale), "magnitude": t(sb.magnitude)}
+    mb = ugp.Materials(t(sb.sggx), t(sb.mtype), t(sb.albedo), t(sb.roughness), t(sb.emission))
+    out["lighting_B"] = one(sb, db, mb)
     return out
 
 
