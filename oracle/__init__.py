@@ -314,6 +314,14 @@ def _register_phase(L):
     L.orc_phase_eval.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d, C.c_int, d]
     L.orc_phase_sample.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d, d, i32p]
     L.orc_phase_pdf_approx.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d]
+    L.orc_disney_f.argtypes = [d, d, C.c_int64, d, d, d, d]
+    L.orc_disney_pdf.argtypes = [d, d, d, d, C.c_int64, d, d]
+    L.orc_disney_sample.argtypes = [d, d, d, d, C.c_int64, d, d, d, i32p]
+    L.orc_gtr1_D.argtypes = [C.c_double, C.c_double]
+    L.orc_gtr1_D.restype = C.c_double
+    L.orc_phase_eval_disney.argtypes = [d, d, d, d, C.c_int64, d, d, d]
+    L.orc_phase_sample_disney.argtypes = [d, d, d, d, C.c_int64, d, d, d, i32p]
+    L.orc_phase_pdf_approx_disney.argtypes = [d, d, d, d, C.c_int64, d, d]
     L.orc_render.argtypes = [C.POINTER(OrcScene), C.POINTER(OrcCamera), C.POINTER(OrcLights),
                              C.POINTER(OrcParams), C.c_int64, C.c_int64, d, d,
                              C.POINTER(C.c_int64)]
@@ -412,6 +420,67 @@ def phase_eval(mtype, albedo, alpha, S6, wo, wi, U6=None, mode=0):
     out = np.zeros((n, 3))
     lib().orc_phase_eval(int(mtype), _ptr(albedo, f64p), float(alpha), _ptr(S6, f64p), _ptr(wo, f64p), n,
                          _ptr(wi, f64p), _ptr(U6, f64p), int(mode), _ptr(out, f64p))
+    return out
+
+
+# Disney principled base (Sec. 6): dis = (metallic, subsurface, specular, specular tint, roughness,
+# sheen, sheen tint, clearcoat, clearcoat gloss), C the base colour.
+def disney_f(C, dis, wi, wo, nrm):
+    """Cosine-weighted base BSDF f <n.wi> for directions wi (n x 3)."""
+    wi = _d(wi).reshape(-1, 3)
+    out = np.zeros_like(wi)
+    lib().orc_disney_f(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), wi.shape[0], _ptr(wi, f64p), _ptr(_d(wo), f64p),
+                       _ptr(_d(nrm), f64p), _ptr(out, f64p))
+    return out
+
+
+def disney_pdf(C, dis, wo, nrm, wi):
+    wi = _d(wi).reshape(-1, 3)
+    out = np.zeros(wi.shape[0])
+    lib().orc_disney_pdf(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), _ptr(_d(wo), f64p), _ptr(_d(nrm), f64p),
+                         wi.shape[0], _ptr(wi, f64p), _ptr(out, f64p))
+    return out
+
+
+def disney_sample(C, dis, wo, nrm, U2):
+    """(wi, weight, ok) of the base sampler from two uniforms per sample."""
+    U = _d(U2).reshape(-1, 2)
+    n = U.shape[0]
+    wi, w = np.zeros((n, 3)), np.zeros((n, 3))
+    ok = np.zeros(n, np.int32)
+    lib().orc_disney_sample(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), _ptr(_d(wo), f64p), _ptr(_d(nrm), f64p), n,
+                            _ptr(U, f64p), _ptr(wi, f64p), _ptr(w, f64p), _ptr(ok, i32p))
+    return wi, w, ok.astype(bool)
+
+
+def gtr1_D(a, c):
+    return float(lib().orc_gtr1_D(float(a), float(c)))
+
+
+def phase_eval_disney(C, dis, S6, wo, wi, U6):
+    wi = _d(wi).reshape(-1, 3)
+    n = wi.shape[0]
+    out = np.zeros((n, 3))
+    lib().orc_phase_eval_disney(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), _ptr(_d(S6), f64p), _ptr(_d(wo), f64p), n,
+                                _ptr(wi, f64p), _ptr(_d(U6).reshape(n, 6), f64p), _ptr(out, f64p))
+    return out
+
+
+def phase_sample_disney(C, dis, S6, wo, U4):
+    U = _d(U4).reshape(-1, 4)
+    n = U.shape[0]
+    wi, w = np.zeros((n, 3)), np.zeros((n, 3))
+    ok = np.zeros(n, np.int32)
+    lib().orc_phase_sample_disney(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), _ptr(_d(S6), f64p), _ptr(_d(wo), f64p), n,
+                                  _ptr(U, f64p), _ptr(wi, f64p), _ptr(w, f64p), _ptr(ok, i32p))
+    return wi, w, ok.astype(bool)
+
+
+def phase_pdf_approx_disney(C, dis, S6, wo, wi):
+    wi = _d(wi).reshape(-1, 3)
+    out = np.zeros(wi.shape[0])
+    lib().orc_phase_pdf_approx_disney(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), _ptr(_d(S6), f64p), _ptr(_d(wo), f64p),
+                                      wi.shape[0], _ptr(wi, f64p), _ptr(out, f64p))
     return out
 
 

@@ -322,6 +322,59 @@ void orc_phase_pdf_approx(int type, const double* albedo3, double alpha, const d
   for (int64_t i = 0; i < n; ++i) out[i] = phase_pdf_approx(m, d3v(wi3 + 3 * i), d3v(wo));
 }
 
+// ------------------------------------------------------------------ Disney base BSDF
+static Material disney_mat(const double* C3, const double* dis9, const double* S6) {
+  Material m = mat_of(kMatDisney, C3, 0.0, S6);
+  for (int k = 0; k < 9; ++k) m.dis[k] = dis9[k];
+  return m;
+}
+static const double kIdentityS6[6] = {1, 1, 1, 0, 0, 0};
+
+// Cosine-weighted base BSDF f <n.wi> at n directions wi3 (normal nrm, outgoing wo).
+void orc_disney_f(const double* C3, const double* dis9, int64_t n, const double* wi3, const double* wo,
+                  const double* nrm, double* out3) {
+  const Material m = disney_mat(C3, dis9, kIdentityS6);
+  for (int64_t i = 0; i < n; ++i) put3(out3 + 3 * i, disney_f(m, d3v(wi3 + 3 * i), d3v(wo), d3v(nrm)));
+}
+void orc_disney_pdf(const double* C3, const double* dis9, const double* wo, const double* nrm, int64_t n,
+                    const double* wi3, double* out) {
+  const Material m = disney_mat(C3, dis9, kIdentityS6);
+  for (int64_t i = 0; i < n; ++i) out[i] = disney_pdf(m, d3v(wi3 + 3 * i), d3v(wo), d3v(nrm));
+}
+void orc_disney_sample(const double* C3, const double* dis9, const double* wo, const double* nrm, int64_t n,
+                       const double* U2, double* wi3, double* weight3, int32_t* ok) {
+  const Material m = disney_mat(C3, dis9, kIdentityS6);
+  for (int64_t i = 0; i < n; ++i) {
+    V3 wi = v3(0, 0, 0), w = v3(0, 0, 0);
+    ok[i] = disney_sample(m, d3v(wo), d3v(nrm), U2 + 2 * i, &wi, &w) ? 1 : 0;
+    put3(wi3 + 3 * i, wi);
+    put3(weight3 + 3 * i, w);
+  }
+}
+double orc_gtr1_D(double a, double c) { return gtr1_D(a, c); }
+
+// The phase function of Eq. 12 with a Disney base: stochastic evaluation, sampling, App. B pdf.
+void orc_phase_eval_disney(const double* C3, const double* dis9, const double* S6, const double* wo, int64_t n,
+                           const double* wi3, const double* U6, double* out3) {
+  const Material m = disney_mat(C3, dis9, S6);
+  for (int64_t i = 0; i < n; ++i) put3(out3 + 3 * i, phase_eval(m, d3v(wi3 + 3 * i), d3v(wo), U6 + 6 * i));
+}
+void orc_phase_sample_disney(const double* C3, const double* dis9, const double* S6, const double* wo, int64_t n,
+                             const double* U4, double* wi3, double* weight3, int32_t* ok) {
+  const Material m = disney_mat(C3, dis9, S6);
+  for (int64_t i = 0; i < n; ++i) {
+    V3 wi = v3(0, 0, 0), w = v3(0, 0, 0);
+    ok[i] = phase_sample(m, d3v(wo), U4 + 4 * i, &wi, &w) ? 1 : 0;
+    put3(wi3 + 3 * i, wi);
+    put3(weight3 + 3 * i, w);
+  }
+}
+void orc_phase_pdf_approx_disney(const double* C3, const double* dis9, const double* S6, const double* wo,
+                                 int64_t n, const double* wi3, double* out) {
+  const Material m = disney_mat(C3, dis9, S6);
+  for (int64_t i = 0; i < n; ++i) out[i] = phase_pdf_approx(m, d3v(wi3 + 3 * i), d3v(wo));
+}
+
 // ------------------------------------------------------------------ path tracer (Table 1)
 typedef struct {
   float eye[3], look[3], up[3];

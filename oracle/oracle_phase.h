@@ -10,14 +10,32 @@ namespace orc {
 constexpr int kMatDiffuse = 0;
 constexpr int kMatGGX = 1;
 constexpr int kMatEmissive = 2;
+constexpr int kMatDisney = 3;
 
 struct Material {
   int type;
-  V3 albedo;     // Lambertian rho, or GGX F0
+  V3 albedo;     // Lambertian rho, GGX F0, or the Disney base colour
   double alpha;  // GGX roughness
   V3 emission;   // emissive primitives
   double S[6];   // SGGX matrix (Sxx, Syy, Szz, Sxy, Sxz, Syz)
+  // Disney base: metallic, subsurface, specular, specular tint, roughness, sheen, sheen tint,
+  // clearcoat, clearcoat gloss
+  double dis[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+// Disney principled base BSDF (disney.cpp): derived constants and the sampler's lobe choice.
+struct DisneyLobes {
+  V3 spec0, sheen;
+  double alpha, alpha_c;
+  double p_diffuse, p_spec, p_coat;
+};
+DisneyLobes disney_lobes(const Material& m);
+double gtr1_D(double a, double cos_h);
+V3 disney_f_diffuse(const Material& m, V3 wi, V3 wo, V3 n);
+V3 disney_f_glossy(const Material& m, V3 wi, V3 wo, V3 n);
+V3 disney_f(const Material& m, V3 wi, V3 wo, V3 n);
+double disney_pdf(const Material& m, V3 wi, V3 wo, V3 n);
+bool disney_sample(const Material& m, V3 wo, V3 n, const double U[2], V3* wi, V3* weight);
 
 Material material_of(const SceneIn& s, int64_t i);
 

@@ -221,6 +221,7 @@ V3 cos_sample(V3 n, double U1, double U2) {
 static double mis(double a, double b) { return a + b > 0 ? a / (a + b) : 0.0; }
 
 static V3 base_f(const Material& m, V3 wi, V3 wo, V3 n) {
+  if (m.type == kMatDisney) return disney_f(m, wi, wo, n);
   return m.type == kMatGGX ? ggx_f(m.albedo, m.alpha, wi, wo, n) : lambert_f(m.albedo, wi, wo, n);
 }
 
@@ -236,6 +237,27 @@ V3 phase_eval_stochastic(const Material& m, V3 wi, V3 wo, const double U[6]) {
   const double* s6 = m.S;
   const V3 n1 = sggx_sample_vndf(s6, wo, U[0], U[1]);
   const double p1 = sggx_Dvis(s6, wo, n1);
+  if (m.type == kMatDisney) {
+    // each part with its own pair of techniques: the glossy part (specular and clearcoat) with
+    // n2 around the half vector, the diffuse part (diffuse, subsurface, sheen) with n3 about wi
+    const double a = disney_lobes(m).alpha;
+    const V3 h = normalize(wi + wo);
+    const V3 n2 = micro_sample(a, h, U[2], U[3]);
+    const double q2 = micro_pdf(a, n2, h);
+    V3 est = mis(p1, micro_pdf(a, n1, h)) * disney_f_glossy(m, wi, wo, n1);
+    if (q2 > 0) {
+      const double dv = sggx_Dvis(s6, wo, n2);
+      est = est + (dv / q2 * mis(q2, dv)) * disney_f_glossy(m, wi, wo, n2);
+    }
+    const V3 n3 = cos_sample(wi, U[4], U[5]);
+    const double q3 = std::max(0.0, dot(n3, wi)) / kPi;
+    est = est + mis(p1, std::max(0.0, dot(n1, wi)) / kPi) * disney_f_diffuse(m, wi, wo, n1);
+    if (q3 > 0) {
+      const double dv = sggx_Dvis(s6, wo, n3);
+      est = est + (dv / q3 * mis(q3, dv)) * disney_f_diffuse(m, wi, wo, n3);
+    }
+    return est;
+  }
   if (m.type == kMatGGX) {
     const V3 h = normalize(wi + wo);
     const V3 n2 = micro_sample(m.alpha, h, U[2], U[3]);
@@ -275,6 +297,7 @@ V3 phase_eval(const Material& m, V3 wi, V3 wo, const double U[6]) {
 // f / pdf is the base BSDF's own (the VNDF sampling is exact).  U holds four uniforms.
 bool phase_sample(const Material& m, V3 wo, const double U[4], V3* wi, V3* weight) {
   const V3 n = sggx_sample_vndf(m.S, wo, U[0], U[1]);
+  if (m.type == kMatDisney) return disney_sample(m, wo, n, U + 2, wi, weight);
   if (m.type == kMatGGX) {
     const V3 h = ggx_sample_vn(m.alpha, wo, n, U[2], U[3]);
     const double oh = dot(wo, h);
@@ -305,6 +328,18 @@ double phase_pdf_approx(const Material& m, V3 wi, V3 wo) {
     double r6[6];
     sggx_roughen(m.S, m.alpha, r6);
     return sggx_Dvis(r6, wo, h);
+  }
+  if (m.type == kMatDisney) {
+    // the lobes weighted as the sampler picks them (by metallic and base-colour luminance)
+    const DisneyLobes L = disney_lobes(m);
+    double r6[6];
+    sggx_roughen(m.S, L.alpha, r6);
+    double p = L.p_spec * sggx_Dvis(r6, wo, h) + L.p_diffuse * std::max(0.0, dot(h, wo)) / kPi;
+    if (L.p_coat > 0) {
+      sggx_roughen(m.S, L.alpha_c, r6);
+      p += L.p_coat * sggx_Dvis(r6, wo, h);
+    }
+    return p;
   }
   return std::max(0.0, dot(h, wo)) / kPi;
 }

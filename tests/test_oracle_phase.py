@@ -238,3 +238,120 @@ def test_approximate_pdf_covers_the_phase_function(orc):
         p = orc.phase_pdf_approx(mtype, [0.5, 0.5, 0.5], 0.3, S6, wo, d)
         assert np.all(np.isfinite(p)) and np.all(p >= 0)
         assert np.all(p[f > 1e-6] > 0)
+
+
+# ---------------------------------------------------------------------------- f4: Disney base
+DIS = np.array([0.2, 0.3, 0.5, 0.2, 0.4, 0.3, 0.5, 0.6, 0.7])  # metallic .. clearcoat gloss
+C_BASE = np.array([0.8, 0.5, 0.3])
+
+
+def _dis(**kw):
+    names = ["metallic", "subsurface", "specular", "specular_tint", "roughness", "sheen", "sheen_tint",
+             "clearcoat", "clearcoat_gloss"]
+    d = DIS.copy()
+    for k, v in kw.items():
+        d[names.index(k)] = v
+    return d
+
+
+def test_disney_special_cases(orc):
+    """Metallic 1 without clearcoat is the GGX base with F0 = C and alpha = roughness^2 (the
+    pinned GGX of the oracle); at normal incidence (wi = wo = n) the diffuse term is C / pi for
+    any roughness, the subsurface term 0.625 C / pi, and sheen vanishes."""
+    rng = np.random.default_rng(30)
+    n = np.array([0.0, 0.0, 1.0])
+    for r in (0.1, 0.45, 0.9):
+        d = _dis(metallic=1.0, clearcoat=0.0, roughness=r)
+        wo = np.array([0.3, -0.4, 0.85]); wo /= np.linalg.norm(wo)
+        wi = unit(rng, 200)
+        wi[:, 2] = np.abs(wi[:, 2])
+        got = orc.disney_f(C_BASE, d, wi, wo, n)
+        ref = np.stack([orc.base_bsdf(GGX, C_BASE, max(1e-3, r * r), w, wo, n)[0] for w in wi])
+        np.testing.assert_allclose(got, ref, rtol=1e-13, atol=1e-15)
+    for r in (0.0, 0.5, 1.0):
+        base = dict(metallic=0.0, specular=0.0, clearcoat=0.0, roughness=r)
+        f0 = orc.disney_f(C_BASE, _dis(subsurface=0.0, sheen=0.0, **base), n, n, n)[0]
+        np.testing.assert_allclose(f0, C_BASE / np.pi, rtol=1e-14)
+        f1 = orc.disney_f(C_BASE, _dis(subsurface=1.0, sheen=0.0, **base), n, n, n)[0]
+        np.testing.assert_allclose(f1, 0.625 * C_BASE / np.pi, rtol=1e-14)
+        f2 = orc.disney_f(C_BASE, _dis(subsurface=0.0, sheen=1.0, **base), n, n, n)[0]
+        np.testing.assert_allclose(f2, C_BASE / np.pi, rtol=1e-14)
+
+
+def test_disney_reciprocity(orc):
+    """f(wi, wo) = f(wo, wi) for the BRDF (the cosine-weighted value divided by <n.wi>)."""
+    rng = np.random.default_rng(31)
+    n = np.array([0.0, 0.0, 1.0])
+    for _ in range(20):
+        d = rng.random(9)
+        C = rng.random(3)
+        a, b = unit(rng), unit(rng)
+        a[2], b[2] = abs(a[2]) + 0.05, abs(b[2]) + 0.05
+        a /= np.linalg.norm(a); b /= np.linalg.norm(b)
+        fab = orc.disney_f(C, d, a, b, n)[0] / a[2]
+        fba = orc.disney_f(C, d, b, a, n)[0] / b[2]
+        np.testing.assert_allclose(fab, fba, rtol=1e-12)
+
+
+def test_gtr1_is_normalised(orc):
+    """int D(n.h) (n.h) dh = 1 over the hemisphere, by quadrature."""
+    from scipy import integrate
+    for a in (0.001, 0.01, 0.1, 0.5, 0.99):
+        v, _ = integrate.quad(lambda t: orc.gtr1_D(a, math.cos(t)) * math.cos(t) * math.sin(t), 0, math.pi / 2,
+                              epsabs=0, epsrel=1e-11, limit=400, points=[min(0.1, 10 * a)])
+        assert abs(2 * math.pi * v - 1) < 1e-8, (a, 2 * math.pi * v)
+
+
+@pytest.mark.parametrize("seed", [32, 33, 34])
+def test_disney_sampler_matches_its_pdf_and_the_albedo(orc, seed):
+    """The base sampler's accepted samples have the mixture density: the pdf integrates (by
+    quadrature) to the acceptance rate, and the mean weight f <n.wi> / pdf equals the directional
+    albedo int f <n.wi> dwi by quadrature."""
+    rng = np.random.default_rng(seed)
+    d, C = rng.random(9), rng.random(3)
+    n = np.array([0.0, 0.0, 1.0])
+    wo = unit(rng); wo[2] = abs(wo[2]) + 0.1; wo /= np.linalg.norm(wo)
+    pts, wts = sphere_grid(200, 400)
+    up = pts[:, 2] > 0
+    p = orc.disney_pdf(C, d, wo, n, pts[up])
+    f = orc.disney_f(C, d, pts[up], wo, n)
+    N = 400000
+    wi, w, ok = orc.disney_sample(C, d, wo, n, rng.random((N, 2)))
+    acc = ok.mean()
+    assert abs((wts[up] * p).sum() - acc) < 4 * math.sqrt(acc * (1 - acc) / N) + 2e-4, ((wts[up] * p).sum(), acc)
+    albedo = (wts[up, None] * f).sum(0)
+    m, se = w.mean(0), w.std(0) / math.sqrt(N)
+    assert np.all(np.abs(m - albedo) < 4 * se + 1e-3 * albedo.max()), (m, albedo, se)
+
+
+def test_disney_phase_function(orc):
+    """With a Disney base: the stochastic evaluation of Eq. 12 averages to its quadrature over
+    flake normals, phase sampling averages to the phase function's integral (an independent
+    uniform-direction estimate), and the App. B pdf is positive wherever the phase function is."""
+    rng = np.random.default_rng(35)
+    d = _dis(metallic=0.3, roughness=0.5, clearcoat=0.4)
+    S6, _ = random_S(rng, 0.3, 1.0)
+    wo = unit(rng)
+    pts, wts = sphere_grid(90, 180)
+    for _ in range(2):
+        wi = wo + 0.8 * unit(rng)
+        wi /= np.linalg.norm(wi)
+        dv = orc.sggx_dvis(S6, wo, pts)
+        m = dv > 0
+        fb = np.stack([orc.disney_f(C_BASE, d, wi, wo, nn)[0] for nn in pts[m]])
+        ref = (wts[m, None] * dv[m, None] * fb).sum(0)
+        N = 200000
+        est = orc.phase_eval_disney(C_BASE, d, S6, wo, np.tile(wi, (N, 1)), rng.random((N, 6)))
+        mean, se = est.mean(0), est.std(0) / math.sqrt(N)
+        assert np.all(np.abs(mean - ref) < 4 * se + 2e-3 * ref.max()), (mean, ref, se)
+    g = lambda v: 1.0 + v @ np.array([0.3, -0.5, 0.7])
+    N = 200000
+    wi, w, ok = orc.phase_sample_disney(C_BASE, d, S6, wo, rng.random((N, 4)))
+    lhs, lse = (w[:, 0] * g(wi)).mean(), (w[:, 0] * g(wi)).std() / math.sqrt(N)
+    dirs = unit(rng, N)
+    f = orc.phase_eval_disney(C_BASE, d, S6, wo, dirs, rng.random((N, 6)))[:, 0]
+    vals = 4 * np.pi * f * g(dirs)
+    rhs, rse = vals.mean(), vals.std() / math.sqrt(N)
+    assert abs(lhs - rhs) < 4 * math.hypot(lse, rse) + 1e-3, (lhs, rhs, lse, rse)
+    p = orc.phase_pdf_approx_disney(C_BASE, d, S6, wo, dirs[:4000])
+    assert np.all(np.isfinite(p)) and np.all(p[f[:4000] > 1e-6] > 0)
