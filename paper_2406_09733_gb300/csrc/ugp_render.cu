@@ -13,6 +13,8 @@
 //    emission, and no light sampling from a vertex that cannot scatter again.
 //  * Emissive primitives are pure emitters; escape adds the background, or the area light's
 //    radiance if the ray reaches its front face.
+//  * With an emitter table, each scattering vertex also takes a light sample of an emissive
+//    primitive (ugp_emitters.cuh), balanced against phase sampling; one light sample per vertex.
 //  * Scattered and shadow rays start at the centre of the chosen primitive's clipped interval
 //    and skip that primitive (Sec. 6).
 //  * With a learned guide, a vertex draws its direction from the guide with probability alpha,
