@@ -64,6 +64,9 @@ def lib():
                                     i32p]
         L.orc_sample_free_flight_paper_rule.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
                                                         f32p, f32p, f32p, f32p, i32p]
+        L.orc_kd_sample_free_flight.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p,
+                                                f32p, f32p, i32p, f64p, C.POINTER(C.c_int64),
+                                                C.POINTER(C.c_int64)]
         L.orc_decomposition_exponential.argtypes = [C.c_double, C.c_int32]
         L.orc_decomposition_exponential.restype = C.c_double
         L.orc_prim_quadratic.argtypes = [C.POINTER(OrcScene), C.c_int64, f32p, f32p, f64p]
@@ -261,6 +264,26 @@ def sample_free_flight_paper_rule(scene, rays, u, u2, eps=0.01):
     lib().orc_sample_free_flight_paper_rule(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
                                             _ptr(t1, f32p), _ptr(u, f32p), _ptr(u2, f32p), _ptr(prim, i32p))
     return prim
+
+
+def kd_sample_free_flight(scene, rays, u, u2, eps=0.01):
+    """The paper's own free-flight sampler over an SAH kd-tree (Sec. 5.2): per-leaf accumulation in
+    front-to-back order and its disambiguation rule. A diagnostic, not a parity target. Returns a
+    dict of prim (-1: escape), ambiguous_start (start of the ambiguous segment used, NaN if none),
+    nodes and prims (kd-tree nodes visited and primitives tested)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d = _c(rays.o, np.float32), _c(rays.d, np.float32)
+    t0, t1 = _c(rays.t0, np.float32), _c(rays.t1, np.float32)
+    u, u2 = _c(u, np.float32), _c(u2, np.float32)
+    prim = np.zeros(n, np.int32)
+    amb = np.zeros(n)
+    nodes, prims = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    i64p = C.POINTER(C.c_int64)
+    lib().orc_kd_sample_free_flight(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p), _ptr(t1, f32p),
+                                    _ptr(u, f32p), _ptr(u2, f32p), _ptr(prim, i32p), _ptr(amb, f64p),
+                                    nodes.ctypes.data_as(i64p), prims.ctypes.data_as(i64p))
+    return dict(prim=prim, ambiguous_start=amb, nodes=nodes, prims=prims)
 
 
 def band_rays(scene, rays, rel=1e-5, eps=0.01):

@@ -231,6 +231,25 @@ void orc_sample_free_flight_paper_rule(const orc_scene* s, double cutoff_eps, in
                                                 t0[r], t1[r], u[r], u2[r]);
 }
 
+// The paper's own sampler over an SAH kd-tree (built once per call): primitive (-1: escape),
+// the start of the ambiguous segment it used (NaN if none), and the nodes and primitives it visited.
+void orc_kd_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3, const float* d3,
+                               const float* t0, const float* t1, const float* u, const float* u2, int32_t* prim_out,
+                               double* ambiguous_start_out, int64_t* nodes_out, int64_t* prims_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+  const KdTree T = kd_build(prims, k);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r) {
+    KdStats st;
+    prim_out[r] = kd_sample_free_flight(T, prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r], t1[r], k, u[r], u2[r],
+                                        &st);
+    ambiguous_start_out[r] = st.ambiguous_start;
+    nodes_out[r] = st.nodes_visited;
+    prims_out[r] = st.prims_tested;
+  }
+}
+
 double orc_decomposition_exponential(double u, int32_t k) { return decomposition_exponential(u, k); }
 
 // App. A quantities of primitive i along a ray (no clipping): A, t* = -B/2A, d2 = C - B^2/4A.

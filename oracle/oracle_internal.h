@@ -131,6 +131,28 @@ ExpFreeFlight sample_free_flight_exponential(const std::vector<Prim>& prims, V3 
 double transmittance_exponential(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1, double k,
                                  int32_t exclude, double* depth_out);
 
+// The paper's own sampler over an SAH kd-tree (kdtree.cpp): a diagnostic of the paper-faithful
+// variant, not a parity target.
+struct KdNode {
+  int axis = -1;     // -1: leaf
+  double pos = 0.0;  // split plane
+  int child[2] = {-1, -1};
+  int32_t first = 0, count = 0;  // leaf: range in KdTree::leaf_ids
+};
+struct KdTree {
+  std::vector<KdNode> nodes;  // nodes[0] is the root
+  std::vector<int32_t> leaf_ids;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+};
+struct KdStats {
+  int64_t nodes_visited = 0, prims_tested = 0;
+  double F_end = 0.0;            // the CDF reached (1/2 sum I when the ray escapes)
+  double ambiguous_start = 0.0;  // start of the ambiguous segment used (NaN if none)
+};
+KdTree kd_build(const std::vector<Prim>& prims, double k);
+int32_t kd_sample_free_flight(const KdTree& T, const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
+                              double k, double u, double u2, KdStats* stats);
+
 double erfinv(double y);
 double race_exponential(double u2, int32_t k);
 

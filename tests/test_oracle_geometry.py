@@ -720,3 +720,94 @@ def test_paper_rule_bias_at_the_saturating_distance(orc):
     bias = np.abs(p_rule - p_exact).max()
     print(f"paper rule: max |P_rule - P_exact| = {bias:.4f} over {act.sum()} ambiguous primitives")
     assert bias > 0.01
+
+
+# ---------------------------------------------------------------------------- f2: the paper's kd-tree sampler
+def _rule_law(s, o, d, h, s0):
+    """P(k) of the paper's rule when its ambiguous segment starts at s0: 1/2 I_k up to s0, then
+    int_s0^t_sat I_k(s0, t) / sum_A I_j(s0, t) dF(t), from the densities of Eq. 1 on a grid; also
+    the exact law 1/2 I_k(a_k, min(b_k, t_sat)) from the same grid."""
+    tg, G = _grid_profiles(s, o, d, h, 0.0, 2.0, 400001)
+    dt = tg[1] - tg[0]
+    Ik = np.concatenate([np.zeros((G.shape[0], 1)), np.cumsum(0.5 * (G[:, 1:] + G[:, :-1]) * dt, 1)], 1)
+    t_sat = np.interp(1.0, 0.5 * Ik.sum(0), tg)
+    at = lambda row, x: np.interp(x, tg, row)
+    act = (h["a"] <= s0) & (h["b"] > s0)
+    p = np.array([0.5 * at(Ik[j], s0) for j in range(len(h["ids"]))])
+    sel = (tg > s0) & (tg <= t_sat)
+    Iseg = Ik[:, sel] - np.array([at(Ik[j], s0) for j in range(len(h["ids"]))])[:, None]
+    dF = 0.5 * G[:, sel].sum(0) * dt
+    for j in np.nonzero(act)[0]:
+        p[j] += np.sum(Iseg[j] / Iseg[act].sum(0) * dF)
+    exact = np.array([0.5 * at(Ik[j], t_sat) for j in range(len(h["ids"]))])
+    return p, act, exact
+
+
+def test_kd_sampler_escapes_exactly_when_the_exact_sampler_does(orc):
+    """Per-leaf accumulation over a kd-tree reaches the same F(t1): the escape decision matches
+    the order-free sampler's for the same u (Eq. 8)."""
+    s = scenes.tiny_scene(n=300, seed=130)
+    s.magnitude[:] *= 4.0
+    r = scenes.random_rays(3000, seed=131)
+    u, u2 = scenes.uniforms24(132, r.n), scenes.uniforms24(133, r.n)
+    kd = orc.kd_sample_free_flight(s, r, u, u2)
+    ex = orc.sample_free_flight(s, r, u, u2)
+    near = np.abs(u - ex["F_end"]) < 1e-12
+    assert np.array_equal((kd["prim"] < 0)[~near], (ex["prim"] < 0)[~near])
+    assert 0.2 < (kd["prim"] < 0).mean() < 0.9 and kd["nodes"].mean() > 3
+
+
+def test_kd_sampler_is_exact_away_from_saturation(orc):
+    """On a ray that never saturates, every leaf accumulates primitive by primitive and the
+    sampler draws P(k) = 1/2 I_k (chi^2 against quadrature)."""
+    from scipy.stats import chi2 as chi2d
+    s = _dense_cluster(n=8, seed=60, boost=0.15)
+    o, d = _exp_ray()
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    p = np.array([0.5 * integrate.quad(lambda t: density(s, i, o.astype(np.float64) + t * d.astype(np.float64)),
+                                       h["a"][j], h["b"][j], epsabs=0, epsrel=1e-12)[0]
+                  for j, i in enumerate(h["ids"])])
+    n = 200000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    kd = orc.kd_sample_free_flight(s, r, scenes.uniforms24(134, n), scenes.uniforms24(135, n))
+    assert np.all(np.isnan(kd["ambiguous_start"]))
+    counts = np.array([(kd["prim"] == i).sum() for i in h["ids"]] + [(kd["prim"] < 0).sum()], np.float64)
+    exp = np.concatenate([p, [1 - p.sum()]]) * n
+    assert ((counts - exp) ** 2 / exp).sum() < chi2d.ppf(0.999, len(exp) - 1)
+
+
+def _line_cluster(n=30, seed=140, boost=6.0):
+    """Primitives strung along the z axis, overlapping their neighbours: a kd-tree splits them
+    into several leaves along a ray down the axis, which saturates in the middle."""
+    s = scenes.tiny_scene(n=n, seed=seed)
+    rng = np.random.default_rng(seed)
+    s.mean[:] = np.stack([0.5 + rng.normal(scale=0.004, size=n), 0.5 + rng.normal(scale=0.004, size=n),
+                          np.linspace(0.1, 0.9, n)], 1)
+    s.scale[:] = rng.uniform(0.015, 0.03, size=(n, 3))
+    s.magnitude[:] = (rng.uniform(0.5, 1.5, n) * boost * (2 * np.pi) ** 1.5
+                      * s.scale.astype(np.float64).prod(1)).astype(np.float32)
+    return s
+
+
+def test_kd_sampler_follows_the_rule_law_at_its_ambiguous_segment(orc):
+    """With several primitives straddling t_sat, the kd sampler walks its leaves front to back,
+    and its ambiguous segment starts at a leaf boundary or an interval end s0. Its samples follow
+    the rule's law for that s0 (grid integration of Eq. 1), and reject the exact law."""
+    from scipy.stats import chi2 as chi2d
+    s = _line_cluster()
+    o = np.array([0.5, 0.5, 0.0], np.float32)
+    d = np.array([0.001, -0.0005, 1.0]); d = (d / np.linalg.norm(d)).astype(np.float32)
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    n = 400000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    kd = orc.kd_sample_free_flight(s, r, scenes.uniforms24(136, n), scenes.uniforms24(137, n))
+    assert kd["nodes"].mean() > 3   # several leaves along the ray
+    amb = kd["ambiguous_start"][np.isfinite(kd["ambiguous_start"])]
+    assert amb.size > 0.05 * n and np.ptp(amb) == 0.0   # one ambiguous segment per ray
+    p_rule, act, exact = _rule_law(s, o, d, h, float(amb[0]))
+    assert act.sum() >= 2 and abs(p_rule.sum() - 1) < 1e-3
+    counts = np.array([(kd["prim"] == i).sum() for i in h["ids"]], np.float64)
+    m = p_rule * n > 5
+    dof = int(m.sum()) - 1
+    assert ((counts[m] - p_rule[m] * n) ** 2 / (p_rule[m] * n)).sum() < chi2d.ppf(0.999, dof)
+    assert ((counts[m] - exact[m] * n) ** 2 / np.maximum(exact[m] * n, 1e-9)).sum() > 10 * chi2d.ppf(0.999, dof)
