@@ -364,6 +364,23 @@ def workload_config(args, l2_note):
     }
 
 
+def host_cpu() -> str:
+    """The host processor: architecture, and the model name (x86) or implementer/part (Arm) of
+    /proc/cpuinfo when it has them."""
+    import platform
+    desc = platform.machine()
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return desc
+    for key in ("model name", "CPU implementer", "CPU part"):
+        for line in info:
+            if line.startswith(key):
+                desc += f", {key}: {line.split(':', 1)[1].strip()}"
+                break
+    return desc
+
+
 def cpu_baseline_run(scene, args, pixels, spp=1, seed=0):
     """The FP64 oracle on a bounded sample of the workload: `pixels` consecutive pixels of the
     middle image row(s), one sample each."""
@@ -402,7 +419,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator)",
         "config": workload_config(args, "n/a (CPU)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -527,7 +545,7 @@ def run_ugp(args):
         v, cores, r, dt = cpu_baseline_run(scene, args, args.cpu_pixels)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_pixels} pixels x 1 spp of the middle row, {r} queries in {dt:.1f} s, "
-                         f"brute force over all primitives, FP64"}
+                         f"brute force over all primitives, FP64", "cpu": host_cpu()}
 
     guide_perf = None
     mse = None
