@@ -92,3 +92,32 @@ def test_full_size_queries_sampled_parity(orc):
     assert np.all(np.abs(tsp[idx][same] - ref["t_spawn"][same]) <= REL * span[same])
     esc = p < 0
     assert np.all(tu[idx][esc] == r.t1[esc])
+
+
+def test_full_size_white_furnace():
+    """The renderer at the benchmark's size (1M-primitive room, 1024 x 1024, one launch sequence
+    as the benchmark runs it) on a property that holds at any size: with every primitive a
+    Lambertian of albedo 1, no emitters, no area light and a unit background, a path's weight
+    stays exactly 1, so every sample is 1 (it escaped) or 0 (it reached the depth limit)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_09733_gb300 import build, ugp
+    build.build()
+    W = H = 1024
+    s = scenes.room_scene(1_000_000, width=W, height=H)
+    s.mtype[:] = scenes.MAT_DIFFUSE
+    s.albedo[:] = 1.0
+    s.emission[:] = 0.0
+    s.lights = scenes.Lights(bg=(1.0, 1.0, 1.0))
+    bvh, mats, cam, li = ugp.scene_to_device(s)
+    r = ugp.Renderer(W, H)
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+    acc, _ = r.render(bvh, mats, cam, li, 1, 14, seed=7, ray_counts=cnt)
+    torch.cuda.synchronize()
+    a = acc.double().cpu().numpy()
+    c = cnt.cpu().numpy()
+    assert c[2] == 0 and c[0] > W * H
+    assert np.all(np.abs(a - np.round(a)) < 1e-5) and a.min() >= 0.0 and a.max() <= 1.0 + 1e-5
+    escaped = np.round(a[..., 0]).mean()
+    assert 0.05 < escaped < 1.0   # the room is open on the camera's side
