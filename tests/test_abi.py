@@ -127,3 +127,24 @@ def test_batch_entry_points_validate_on_host(libugp):
     st = libugp.ugp_render_batch(0, None, ctypes.byref(bad), 4, None, ctypes.c_size_t(0), None, None, None)
     assert st == 1
     assert ctypes.sizeof(ugp.UgpRequest) == 168 and ugp.UgpRequest.seed.offset == 144
+
+
+def test_binding_rejects_host_tensors():
+    """The binding has no CPU path: host tensors are refused before the library is called."""
+    torch = pytest.importorskip("torch")
+    from paper_2406_09733_gb300 import ugp
+
+    class FakeBvh:
+        handle = 0
+        n = 1
+        workspace = torch.zeros(1)
+
+    o = torch.zeros((4, 3))
+    d = torch.zeros((4, 3))
+    t = torch.zeros(4)
+    for call in (lambda: ugp.trace_transmittance(FakeBvh(), o, d, t, t),
+                 lambda: ugp.trace_transmittance_exponential(FakeBvh(), o, d, t, t),
+                 lambda: ugp.sample_free_flight_exponential(FakeBvh(), o, d, t, t, t),
+                 lambda: ugp.collect_hits(FakeBvh(), o, d, t, t, 4)):
+        with pytest.raises(TypeError, match="CUDA tensor"):
+            call()
