@@ -141,10 +141,14 @@ def _stream(stream=None) -> int:
     return int(s.cuda_stream)
 
 
-def _dev(t, dtype, name, shape_last=None):
+def _dev(t, dtype, name, shape_last=None, n=None, device=None, cuda=True):
+    """Checks a tensor handed to the library: dtype, contiguous; with `shape_last`, shape
+    (rows, shape_last); with `n`, exactly n rows (n elements for a flat array); with `device`,
+    that device; with `cuda`, a CUDA tensor. The kernels index every per-ray array up to n, so a
+    short array would be read past its end on the device."""
     if t is None:
         return None
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+    if not isinstance(t, torch.Tensor):
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
@@ -152,7 +156,40 @@ def _dev(t, dtype, name, shape_last=None):
         raise ValueError(f"{name} must be contiguous")
     if shape_last is not None and (t.dim() != 2 or t.shape[1] != shape_last):
         raise ValueError(f"{name} must have shape (n, {shape_last})")
+    if n is not None:
+        rows = t.shape[0] if shape_last is not None else t.numel()
+        if rows != n:
+            raise ValueError(f"{name} must hold {n} {'rows' if shape_last is not None else 'elements'}, got {rows}")
+    if device is not None and t.device != torch.device(device):
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if cuda and not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
     return t
+
+
+def _rays(o, d, t0, t1, exclude=None, **more):
+    """Validates a batch of rays (o, d: (n, 3); t0, t1 and the optional per-ray arrays: n
+    elements, all float32 except `exclude` (int32), all on o's device). Returns n."""
+    _dev(o, torch.float32, "o", 3, cuda=False)
+    n = int(o.shape[0])
+    checks = [(d, torch.float32, "d", 3), (t0, torch.float32, "t0", None), (t1, torch.float32, "t1", None),
+              (exclude, torch.int32, "exclude", None)] + [(t, torch.float32, nm, None) for nm, t in more.items()]
+    for t, dt, nm, last in checks:           # sizes and devices first, so that a short array is
+        _dev(t, dt, nm, last, n=n, device=o.device, cuda=False)   # named even on a host tensor
+    _dev(o, torch.float32, "o", 3)
+    for t, dt, nm, last in checks:
+        _dev(t, dt, nm, last)
+    return n
+
+
+def _workspace(workspace, nbytes, device):
+    """The caller's workspace after the same checks as every other device argument (a uint8 CUDA
+    tensor on `device`), or a new one when none is given or it is too small."""
+    if workspace is not None:
+        _dev(workspace, torch.uint8, "workspace", device=device)
+        if workspace.numel() >= nbytes:
+            return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
 
 
 def _p(t):
@@ -195,14 +232,14 @@ def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=Non
     """Builds the BVH; `workspace` (uint8 CUDA tensor) is reused when given and large enough."""
     n = int(mean.shape[0])
     _dev(mean, torch.float32, "mean", 3)
-    _dev(quat, torch.float32, "quat", 4)
-    _dev(scale, torch.float32, "scale", 3)
-    _dev(magnitude, torch.float32, "magnitude")
+    _dev(quat, torch.float32, "quat", 4, n=n, device=mean.device)
+    _dev(scale, torch.float32, "scale", 3, n=n, device=mean.device)
+    _dev(magnitude, torch.float32, "magnitude", n=n, device=mean.device)
     ws_bytes = build_bvh_workspace_size(n)
     if ws_bytes == 0:
         raise UgpError("ugp_build_bvh_workspace_size failed")
     if workspace is not None:
-        _dev(workspace, torch.uint8, "workspace")
+        _dev(workspace, torch.uint8, "workspace", device=mean.device)
         if workspace.numel() < ws_bytes:
             raise ValueError(f"workspace needs {ws_bytes} bytes")
         ws = workspace
@@ -216,12 +253,7 @@ def build_bvh(mean, quat, scale, magnitude, cutoff_eps: float = 0.01, stream=Non
 
 
 def trace_transmittance(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
-    n = int(o.shape[0])
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    _dev(t0, torch.float32, "t0")
-    _dev(t1, torch.float32, "t1")
-    _dev(exclude, torch.int32, "exclude")
+    n = _rays(o, d, t0, t1, exclude)
     T = torch.empty(n, dtype=torch.float32, device=o.device)
     st = torch.empty(n, dtype=torch.uint8, device=o.device)
     _check(lib().ugp_trace_transmittance(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
@@ -231,15 +263,9 @@ def trace_transmittance(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
 
 
 def sample_free_flight(bvh: Bvh, o, d, t0, t1, u, u2, exclude=None, stream=None, workspace=None):
-    n = int(o.shape[0])
+    n = _rays(o, d, t0, t1, exclude, u=u, u2=u2)
     nb = int(lib().ugp_sample_free_flight_workspace_size(n))
-    if workspace is None or workspace.numel() < nb:
-        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=o.device)
-    for t, nm in ((t0, "t0"), (t1, "t1"), (u, "u"), (u2, "u2")):
-        _dev(t, torch.float32, nm)
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    _dev(exclude, torch.int32, "exclude")
+    workspace = _workspace(workspace, nb, o.device)
     prim = torch.empty(n, dtype=torch.int32, device=o.device)
     tu = torch.empty(n, dtype=torch.float32, device=o.device)
     tsp = torch.empty(n, dtype=torch.float32, device=o.device)
@@ -256,15 +282,10 @@ def render_radiance_field(bvh: Bvh, o, d, t0, t1, emission, background=None, str
     """Radiance-field forward render (Sec. 7, Eq. rf): per ray the emission-weighted 1/2 I of
     every primitive clipped at the saturating distance, plus the unsaturated remainder times
     the background. Returns (rgb (n, 3), status (n,))."""
-    n = int(o.shape[0])
+    n = _rays(o, d, t0, t1)
     nb = int(lib().ugp_render_radiance_field_workspace_size(n))
-    if workspace is None or workspace.numel() < nb:
-        workspace = torch.empty(max(nb, 256), dtype=torch.uint8, device=o.device)
-    for t, nm in ((t0, "t0"), (t1, "t1")):
-        _dev(t, torch.float32, nm)
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    _dev(emission, torch.float32, "emission", 3)
+    workspace = _workspace(workspace, nb, o.device)
+    _dev(emission, torch.float32, "emission", 3, n=bvh.n, device=o.device)
     rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
     st = torch.empty(n, dtype=torch.uint8, device=o.device)
     bg = None if background is None else (C.c_float * 3)(*[float(x) for x in background])
@@ -279,12 +300,7 @@ def sample_free_flight_exponential(bvh: Bvh, o, d, t0, t1, u, exclude=None, stre
     """Exponential variant by analog decomposition tracking (sigma_t = sum_k G_k): per ray the
     nearest per-primitive exponential collision keyed by the uniform u. Returns (prim (-1:
     escape), t (t1 on escape), status)."""
-    n = int(o.shape[0])
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    for t, nm in ((t0, "t0"), (t1, "t1"), (u, "u")):
-        _dev(t, torch.float32, nm)
-    _dev(exclude, torch.int32, "exclude")
+    n = _rays(o, d, t0, t1, exclude, u=u)
     prim = torch.empty(n, dtype=torch.int32, device=o.device)
     t = torch.empty(n, dtype=torch.float32, device=o.device)
     st = torch.empty(n, dtype=torch.uint8, device=o.device)
@@ -297,12 +313,7 @@ def sample_free_flight_exponential(bvh: Bvh, o, d, t0, t1, u, exclude=None, stre
 
 def trace_transmittance_exponential(bvh: Bvh, o, d, t0, t1, exclude=None, stream=None):
     """exp(-sum_k I_k) over each ray's [t0, t1] (exponential variant). Returns (T, status)."""
-    n = int(o.shape[0])
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    _dev(t0, torch.float32, "t0")
-    _dev(t1, torch.float32, "t1")
-    _dev(exclude, torch.int32, "exclude")
+    n = _rays(o, d, t0, t1, exclude)
     T = torch.empty(n, dtype=torch.float32, device=o.device)
     st = torch.empty(n, dtype=torch.uint8, device=o.device)
     _check(lib().ugp_trace_transmittance_exponential(C.c_void_p(bvh.handle), n, _p(o), _p(d), _p(t0), _p(t1),
@@ -313,12 +324,7 @@ def trace_transmittance_exponential(bvh: Bvh, o, d, t0, t1, exclude=None, stream
 
 def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
     """All clipped intervals per ray: (ids, a, b) of shape (n, cap), count (n,), status."""
-    n = int(o.shape[0])
-    _dev(o, torch.float32, "o", 3)
-    _dev(d, torch.float32, "d", 3)
-    _dev(t0, torch.float32, "t0")
-    _dev(t1, torch.float32, "t1")
-    _dev(exclude, torch.int32, "exclude")
+    n = _rays(o, d, t0, t1, exclude)
     ids = torch.full((n, cap), -1, dtype=torch.int32, device=o.device)
     a = torch.zeros((n, cap), dtype=torch.float32, device=o.device)
     b = torch.zeros((n, cap), dtype=torch.float32, device=o.device)
@@ -335,10 +341,12 @@ class Materials:
 
     def __init__(self, sggx6, mtype, albedo3, roughness, emission3):
         _dev(sggx6, torch.float32, "sggx6", 6)
-        _dev(mtype, torch.uint8, "type")
-        _dev(albedo3, torch.float32, "albedo3", 3)
-        _dev(roughness, torch.float32, "roughness")
-        _dev(emission3, torch.float32, "emission3", 3)
+        n, dev = int(sggx6.shape[0]), sggx6.device
+        _dev(mtype, torch.uint8, "type", n=n, device=dev)
+        _dev(albedo3, torch.float32, "albedo3", 3, n=n, device=dev)
+        _dev(roughness, torch.float32, "roughness", n=n, device=dev)
+        _dev(emission3, torch.float32, "emission3", 3, n=n, device=dev)
+        self.n, self.device = n, dev
         self.tensors = (sggx6, mtype, albedo3, roughness, emission3)
         self.c = UgpMaterials(*[_p(t) for t in self.tensors])
 
@@ -396,12 +404,15 @@ class Renderer:
             accum = torch.zeros(shape, dtype=torch.float32, device=dev)
         if accum_sq is None:
             accum_sq = torch.zeros(shape, dtype=torch.float32, device=dev)
-        _dev(accum, torch.float32, "accum")
-        _dev(accum_sq, torch.float32, "accum_sq")
+        _dev(accum, torch.float32, "accum", device=dev)
+        _dev(accum_sq, torch.float32, "accum_sq", device=dev)
         if tuple(accum.shape) != shape or tuple(accum_sq.shape) != shape:
             raise ValueError(f"accumulators must have shape {shape}")
         if ray_counts is not None:
-            _dev(ray_counts, torch.int64, "ray_counts")
+            _dev(ray_counts, torch.int64, "ray_counts", n=3, device=dev)
+        _check_scene(bvh, mats, dev)
+        if emitters is not None:
+            _dev(emitters, torch.uint8, "emitters", device=dev)
         if camera.width != self.width or camera.height != self.height:
             raise ValueError("camera size does not match the renderer")
         prm = UgpRenderParams(int(spp), int(spp_begin), int(max_depth), int(bool(nee)), int(seed),
@@ -420,9 +431,18 @@ class Renderer:
         return accum, accum_sq
 
 
+def _check_scene(bvh: Bvh, mats: "Materials", device):
+    """The materials must describe the BVH's primitives and sit on the render's device."""
+    if mats.n != bvh.n:
+        raise ValueError(f"materials hold {mats.n} primitives, the BVH {bvh.n}")
+    if mats.device != torch.device(device) or bvh.workspace.device != torch.device(device):
+        raise ValueError(f"scene arrays must be on {device}")
+
+
 def build_emitter_table(bvh: Bvh, mats, stream=None):
     """Device table for light sampling of the emissive primitives of ``bvh`` with materials
     ``mats`` (a ``Materials``): pass it to ``Renderer.render(emitters=...)``."""
+    _check_scene(bvh, mats, bvh.workspace.device)
     nb = int(lib().ugp_emitter_table_size(int(bvh.n)))
     table = torch.empty(max(nb, 256), dtype=torch.uint8, device=bvh.workspace.device)
     _check(lib().ugp_build_emitter_table(C.c_void_p(bvh.handle), C.byref(mats.c), _p(table), table.numel(),
@@ -527,8 +547,9 @@ class Guide:
     def forward(self, x3, wo3, head=True, mix=True, stream=None):
         """(head outputs (n, 40), mixtures (n, 40)) for vertices x3, wo3 ((n, 3) float32)."""
         n = int(x3.shape[0])
-        _dev(x3, torch.float32, "x3", 3)
-        _dev(wo3, torch.float32, "wo3", 3)
+        dev = self.params.device
+        _dev(x3, torch.float32, "x3", 3, device=dev)
+        _dev(wo3, torch.float32, "wo3", 3, n=n, device=dev)
         Y = torch.empty((n, 40), dtype=torch.float32, device=x3.device) if head else None
         M = torch.empty((n, 40), dtype=torch.float32, device=x3.device) if mix else None
         _check(lib().ugp_guide_forward(C.byref(self.c), n, _p(x3), _p(wo3), _p(Y), _p(M), _p(self.workspace),
@@ -538,9 +559,10 @@ class Guide:
     def grad(self, x3, wo3, wi3, weight, stream=None):
         """(gradient of the mean loss (GUIDE_NPARAMS,), mean loss (1,)) on the device."""
         n = int(x3.shape[0])
+        dev = self.params.device
         for t, nm in ((x3, "x3"), (wo3, "wo3"), (wi3, "wi3")):
-            _dev(t, torch.float32, nm, 3)
-        _dev(weight, torch.float32, "weight")
+            _dev(t, torch.float32, nm, 3, n=n, device=dev)
+        _dev(weight, torch.float32, "weight", n=n, device=dev)
         g = torch.empty(GUIDE_NPARAMS, dtype=torch.float32, device=self.params.device)
         loss = torch.empty(1, dtype=torch.float32, device=self.params.device)
         _check(lib().ugp_guide_grad(C.byref(self.c), n, _p(x3), _p(wo3), _p(wi3), _p(weight), _p(g), _p(loss),
@@ -549,7 +571,7 @@ class Guide:
         return g, loss
 
     def adam_step(self, grad, stream=None):
-        _dev(grad, torch.float32, "grad")
+        _dev(grad, torch.float32, "grad", n=GUIDE_NPARAMS, device=self.params.device)
         _check(lib().ugp_guide_adam_step(C.byref(self.c), _p(grad), C.c_void_p(_stream(stream))), "ugp_guide_adam_step")
 
     def train_from(self, renderer: "Renderer", max_samples: int = 1 << 20, minibatch: int = 1 << 16,
@@ -570,7 +592,7 @@ class Guide:
 def mixture_pdf(mix, wi3, stream=None):
     n = int(mix.shape[0])
     _dev(mix, torch.float32, "mix", 40)
-    _dev(wi3, torch.float32, "wi3", 3)
+    _dev(wi3, torch.float32, "wi3", 3, n=n, device=mix.device)
     out = torch.empty(n, dtype=torch.float32, device=mix.device)
     _check(lib().ugp_guide_mixture_pdf(n, _p(mix), _p(wi3), _p(out), C.c_void_p(_stream(stream))),
            "ugp_guide_mixture_pdf")
@@ -580,7 +602,7 @@ def mixture_pdf(mix, wi3, stream=None):
 def mixture_sample(mix, u3, stream=None):
     n = int(mix.shape[0])
     _dev(mix, torch.float32, "mix", 40)
-    _dev(u3, torch.float32, "u3", 3)
+    _dev(u3, torch.float32, "u3", 3, n=n, device=mix.device)
     wi = torch.empty((n, 3), dtype=torch.float32, device=mix.device)
     pdf = torch.empty(n, dtype=torch.float32, device=mix.device)
     _check(lib().ugp_guide_mixture_sample(n, _p(mix), _p(u3), _p(wi), _p(pdf), C.c_void_p(_stream(stream))),
@@ -623,9 +645,10 @@ class Request:
         self.accum = accum if accum is not None else torch.zeros(shape, dtype=torch.float32, device=device)
         self.accum_sq = accum_sq if accum_sq is not None else torch.zeros(shape, dtype=torch.float32, device=device)
         for t, nm in ((self.accum, "accum"), (self.accum_sq, "accum_sq")):
-            _dev(t, torch.float32, nm)
+            _dev(t, torch.float32, nm, device=self.accum.device)
             if tuple(t.shape) != shape:
                 raise ValueError(f"{nm} must have shape {shape}")
+        _check_scene(bvh, mats, self.accum.device)
         self.bvh, self.mats = bvh, mats
         self.c = UgpRequest(C.c_void_p(bvh.handle).value, C.pointer(mats.c), camera, lights, int(spp), int(max_depth),
                             int(bool(nee)), int(spawn_mode), int(seed), _p(self.accum).value,
@@ -665,7 +688,7 @@ class BatchRenderer:
         arr = (UgpRequest * max(n, 1))(*[r.c for r in requests])
         lat = (C.c_double * max(n, 1))()
         if ray_counts is not None:
-            _dev(ray_counts, torch.int64, "ray_counts")
+            _dev(ray_counts, torch.int64, "ray_counts", n=3, device=self.workspace.device)
         self._ensure(self.cfg.pool_log2)
         _check(lib().ugp_render_batch(n, arr, C.byref(self.cfg), self.max_requests, _p(self.workspace),
                                       self.workspace.numel(), lat, _p(ray_counts), C.c_void_p(_stream(stream))),

@@ -148,3 +148,33 @@ def test_binding_rejects_host_tensors():
                  lambda: ugp.collect_hits(FakeBvh(), o, d, t, t, 4)):
         with pytest.raises(TypeError, match="CUDA tensor"):
             call()
+
+
+def test_binding_checks_lengths_and_devices():
+    """Per-ray arrays shorter than the ray count, and a workspace on another device than the
+    rays, are refused before the library is called (the kernels would read or write past the
+    array, or write through a host pointer)."""
+    torch = pytest.importorskip("torch")
+    from paper_2406_09733_gb300 import ugp
+
+    class FakeBvh:
+        handle = 0
+        n = 4
+        workspace = torch.zeros(1)
+
+    o, d, t = torch.zeros((4, 3)), torch.zeros((4, 3)), torch.zeros(4)
+    short, d_short = torch.zeros(3), torch.zeros((3, 3))
+    ex_short = torch.zeros(3, dtype=torch.int32)
+    for call in (lambda: ugp.trace_transmittance(FakeBvh(), o, d, short, t),
+                 lambda: ugp.trace_transmittance(FakeBvh(), o, d_short, t, t),
+                 lambda: ugp.trace_transmittance(FakeBvh(), o, d, t, t, exclude=ex_short),
+                 lambda: ugp.sample_free_flight(FakeBvh(), o, d, t, t, t, short),
+                 lambda: ugp.sample_free_flight_exponential(FakeBvh(), o, d, t, t, short),
+                 lambda: ugp.collect_hits(FakeBvh(), o, d, t, short, 4)):
+        with pytest.raises(ValueError, match="must hold"):
+            call()
+    host_ws = torch.zeros(1 << 12, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="expected cuda"):
+        ugp._workspace(host_ws, 256, torch.device("cuda", 0))
+    with pytest.raises(TypeError, match="uint8"):
+        ugp._workspace(torch.zeros(1 << 12), 256, torch.device("cuda", 0))
