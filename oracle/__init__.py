@@ -338,6 +338,7 @@ def _register_phase(L):
     L.orc_phase_sample.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d, d, i32p]
     L.orc_phase_pdf_approx.argtypes = [C.c_int, d, C.c_double, d, d, C.c_int64, d, d]
     L.orc_disney_f.argtypes = [d, d, C.c_int64, d, d, d, d]
+    L.orc_disney_f_diffuse.argtypes = [d, d, C.c_int64, d, d, d, d]
     L.orc_disney_pdf.argtypes = [d, d, d, d, C.c_int64, d, d]
     L.orc_disney_sample.argtypes = [d, d, d, d, C.c_int64, d, d, d, i32p]
     L.orc_gtr1_D.argtypes = [C.c_double, C.c_double]
@@ -454,6 +455,15 @@ def disney_f(C, dis, wi, wo, nrm):
     out = np.zeros_like(wi)
     lib().orc_disney_f(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), wi.shape[0], _ptr(wi, f64p), _ptr(_d(wo), f64p),
                        _ptr(_d(nrm), f64p), _ptr(out, f64p))
+    return out
+
+
+def disney_f_diffuse(C, dis, wi, wo, nrm):
+    """The diffuse, subsurface and sheen part of the base, times <n.wi>, for directions wi (n x 3)."""
+    wi = _d(wi).reshape(-1, 3)
+    out = np.zeros_like(wi)
+    lib().orc_disney_f_diffuse(_ptr(_d(C), f64p), _ptr(_d(dis), f64p), wi.shape[0], _ptr(wi, f64p),
+                               _ptr(_d(wo), f64p), _ptr(_d(nrm), f64p), _ptr(out, f64p))
     return out
 
 

@@ -370,6 +370,13 @@ void orc_disney_sample(const double* C3, const double* dis9, const double* wo, c
     put3(weight3 + 3 * i, w);
   }
 }
+// The diffuse, subsurface and sheen part alone (times <n.wi>), so that tests can pin it apart from
+// the glossy lobes.
+void orc_disney_f_diffuse(const double* C3, const double* dis9, int64_t n, const double* wi3, const double* wo,
+                          const double* nrm, double* out3) {
+  const Material m = disney_mat(C3, dis9, kIdentityS6);
+  for (int64_t i = 0; i < n; ++i) put3(out3 + 3 * i, disney_f_diffuse(m, d3v(wi3 + 3 * i), d3v(wo), d3v(nrm)));
+}
 double orc_gtr1_D(double a, double c) { return gtr1_D(a, c); }
 
 // The phase function of Eq. 12 with a Disney base: stochastic evaluation, sampling, App. B pdf.

@@ -16,9 +16,10 @@
 //    Smith masking of roughness 0.25.
 // lum(C) = 0.3 R + 0.6 G + 0.1 B as in the published model.
 // Pins: the GGX reduction (metallic 1, no clearcoat), the normal-incidence values of the diffuse,
-// subsurface and sheen terms, reciprocity, the GTR1 normalisation, and the sampler against its
-// pdf and the albedo by quadrature. The grazing-angle shape of the diffuse, subsurface and sheen
-// terms (F_D90, F_ss90, the sheen weight) has no pin beyond these: parity unpinned there.
+// subsurface and sheen terms, their grazing and 60-degree values where the published formulas
+// reduce to exact numbers (retro-reflection (1/2 + 2 roughness)^2 at grazing, the Schlick weight,
+// F_ss90, the sheen colour at theta_d = 90 degrees; a hand-derived fixture), reciprocity, the GTR1
+// normalisation, and the sampler against its pdf and the albedo by quadrature.
 #include <algorithm>
 #include <cmath>
 

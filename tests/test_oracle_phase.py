@@ -5,6 +5,7 @@ numpy's eigen-decomposition are the independent references; statistical checks
 use fixed seeds and chi^2 / standard-error bounds.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -355,3 +356,40 @@ def test_disney_phase_function(orc):
     assert abs(lhs - rhs) < 4 * math.hypot(lse, rse) + 1e-3, (lhs, rhs, lse, rse)
     p = orc.phase_pdf_approx_disney(C_BASE, d, S6, wo, dirs[:4000])
     assert np.all(np.isfinite(p)) and np.all(p[f[:4000] > 1e-6] > 0)
+
+
+def _golden_disney():
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "disney_diffuse_grazing.txt")
+    rows = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, dis, wi, wo, a, b, c, rtol = [x.strip() for x in line.split("|")]
+        rows.append((name, np.array([float(x) for x in dis.split()]), [float(x) for x in wi.split()],
+                     [float(x) for x in wo.split()], *[float(Fraction(x)) for x in (a, b, c)], float(rtol)))
+    return rows
+
+
+def _dir(cos_t, phi_deg):
+    s = math.sqrt(max(0.0, 1.0 - cos_t * cos_t))
+    p = math.radians(phi_deg)
+    return np.array([s * math.cos(p), s * math.sin(p), cos_t])
+
+
+def test_disney_diffuse_grazing_golden(orc):
+    """The diffuse, subsurface and sheen terms at grazing and intermediate angles equal the values
+    that Burley's published formulas reduce to there (hand-derived in the fixture): retro-
+    reflection up to (1/2 + 2 roughness)^2 at grazing, Lambertian when F_D90 = 1, the Schlick
+    weight (1 - cos)^5 at 60 degrees, the subsurface term's F_ss90 = roughness cos^2(theta_d), and
+    the sheen weight reaching the sheen colour at theta_d = 90 degrees."""
+    C = np.array([0.6, 0.3, 0.9])
+    n = np.array([0.0, 0.0, 1.0])
+    rows = _golden_disney()
+    assert len(rows) == 12
+    for name, dis, wi, wo, a, b, c, rtol in rows:
+        w_i, w_o = _dir(*wi), _dir(*wo)
+        got = orc.disney_f_diffuse(C, dis, w_i, w_o, n)[0] / w_i[2]
+        want = a * C / np.pi + b + c * C / 0.45
+        np.testing.assert_allclose(got, want, rtol=rtol, err_msg=name)
