@@ -1,20 +1,22 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the GB300 Gaussian-primitive path tracer.
 
-Workload (the mid-size configuration): a procedural room of 1,000,000 Gaussian primitives
-(70 % surface splats on planes, spheres and boxes, 30 % isotropic aggregates in 300
-clusters; 50 / 40 / 10 % diffuse / GGX / emissive shapes) lit by a 0.3 x 0.3 area light
-and a background, rendered at 1024 x 1024 with max depth 8.  One step = BVH build over
-the primitives + one sample per pixel of the wavefront path tracer (camera, free-flight
-extend, shading with light sampling + MIS, shadow transmittance, accumulation); 64 steps
-are the full 64-spp frame.  Inputs are synthetic (seeded generator).
+Workload (the paper-scale configuration, the analogue of the paper's largest timed scene): a
+procedural room of 5,500,000 Gaussian primitives (70 % surface splats on planes, spheres and
+boxes, 30 % isotropic aggregates in 300 clusters; 50 / 40 / 10 % diffuse / GGX / emissive
+shapes, a tenth of the shapes near-specular GGX with roughness 0.02) lit by a 0.3 x 0.3 area
+light and a background (lighting A), rendered at 1920 x 1080 with max depth 12.  One step =
+BVH build over the primitives + one sample per pixel of the wavefront path tracer (camera,
+free-flight extend, shading with light sampling + MIS, shadow transmittance, accumulation);
+256 steps are the full 256-spp frame.  Inputs are synthetic (seeded generator).
 
 Metric: Mrays/s = (free-flight queries + shadow queries) / time, plus the equal-time MSE of
 the learned-guide renderer against plain phase sampling: on the same scene and BVH at a
 reduced image size, a converged plain reference is rendered first; then the plain renderer
 runs for a budget of spp and the guided renderer (trained online during its first spp, the
 training time counted) runs for the same wall time; both MSEs are taken against the reference
-with the reference's own variance subtracted.
+with the reference's own variance subtracted.  The many-small-emitter lighting (B) of the same
+scene is timed as a study in the same line.
 
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ugp|reference]
 For N > 1 run under torch.distributed.run: every rank renders its own replica of the
@@ -45,19 +47,24 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=16)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ugp", "reference"], default="ugp")
-    p.add_argument("--n-prims", type=int, default=1_000_000)
-    p.add_argument("--width", type=int, default=1024)
-    p.add_argument("--height", type=int, default=1024)
-    p.add_argument("--depth", type=int, default=8)
+    p.add_argument("--n-prims", type=int, default=5_500_000)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--depth", type=int, default=12)
+    p.add_argument("--lighting", choices=["A", "B"], default="A",
+                   help="A: quad area light + background; B: 12,000 small emissive primitives")
+    p.add_argument("--near-specular", type=float, default=0.1,
+                   help="fraction of surface shapes made near-specular GGX (roughness 0.02)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-pixels", type=int, default=1024, help="pixels of the CPU-baseline sample")
+    p.add_argument("--cpu-pixels", type=int, default=128, help="pixels of the CPU-baseline sample")
     p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
-    p.add_argument("--mse-res", type=int, default=384, help="image side of the MSE study")
-    p.add_argument("--mse-ref-spp", type=int, default=512, help="spp of the plain reference")
-    p.add_argument("--mse-budget-spp", type=int, default=64, help="plain spp that set the time budget")
+    p.add_argument("--mse-width", type=int, default=480, help="image width of the MSE study")
+    p.add_argument("--mse-height", type=int, default=270, help="image height of the MSE study")
+    p.add_argument("--mse-ref-spp", type=int, default=2048, help="spp of the plain reference")
+    p.add_argument("--mse-budget-spp", type=int, default=256, help="plain spp that set the time budget")
     p.add_argument("--mse-train-spp", type=int, default=32, help="guided spp that also train the guide")
     p.add_argument("--mse-minibatch", type=int, default=1 << 14)
     p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
@@ -67,7 +74,7 @@ def parse_args(argv=None):
     p.add_argument("--no-exp", action="store_true", help="skip the exponential-variant query study")
     p.add_argument("--no-emitters", action="store_true", help="skip the emitter light-sampling study")
     p.add_argument("--serve-requests", type=int, default=64)
-    p.add_argument("--serve-spp-max", type=int, default=4,
+    p.add_argument("--serve-spp-max", type=int, default=64,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
     p.add_argument("--guide-lr", type=float, default=1e-3)
     return p.parse_args(argv)
@@ -100,14 +107,24 @@ GUIDE_FWD_FLOP = 2 * (4 * 64 * 64 + 40 * 64)
 GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 
 
-# DRAM bytes (read + write) per k_extend launch of the default workload, averaged over the nine
-# launches of one step, from one ncu capture of the current kernel
-# (profiles/k_extend_dram_room1M_1024.md); None for any other workload.
-EXTEND_TRAFFIC_BYTES = {(1_000_000, 1024, 1024, 8): 472.27e6}
+# DRAM bytes (read + write) per k_extend launch of a workload, averaged over the launches of one
+# step, from one ncu capture of the current kernel (profiles/k_extend_dram_*.md); None for any
+# other workload, and to be reset whenever k_extend changes.
+EXTEND_TRAFFIC_BYTES = {}
+
+
+def workload_key(args):
+    return (args.n_prims, args.width, args.height, args.depth, args.lighting, args.near_specular)
 
 
 def extend_traffic(args):
-    return EXTEND_TRAFFIC_BYTES.get((args.n_prims, args.width, args.height, args.depth))
+    return EXTEND_TRAFFIC_BYTES.get(workload_key(args))
+
+
+def bench_scene(args, lighting=None):
+    from paper_2406_09733_gb300 import scenes
+    return scenes.room_scene(args.n_prims, width=args.width, height=args.height,
+                             near_specular_frac=args.near_specular, lighting=lighting or args.lighting)
 
 
 def guide_kernel_timing(dev, rows=1 << 20, reps=10):
@@ -218,15 +235,15 @@ def equal_time_mse(args, d, mats, scene, dev):
     import numpy as np
     import torch
     from paper_2406_09733_gb300 import scenes, ugp
-    R = args.mse_res
+    MW, MH = args.mse_width, args.mse_height
     cam = scene.camera
-    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, R, R)
+    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, MW, MH)
     li = scene.lights
     lights = ugp.lights_struct(li.has_quad, li.quad_corner, li.quad_e1, li.quad_e2, li.quad_Le, li.bg)
     bvh = ugp.build_bvh(d["mean"], d["quat"], d["scale"], d["magnitude"])
     info = bvh.info()
-    r = ugp.Renderer(R, R, device=dev)
-    z = lambda: torch.zeros((R, R, 3), dtype=torch.float32, device=dev)
+    r = ugp.Renderer(MW, MH, device=dev)
+    z = lambda: torch.zeros((MH, MW, 3), dtype=torch.float32, device=dev)
     depth = args.depth
 
     # converged plain reference (different seed), in chunks of 64 spp
@@ -283,7 +300,7 @@ def equal_time_mse(args, d, mats, scene, dev):
             "train_spp": min(args.mse_train_spp, k), "train_samples": n_train, "adam_steps": g.step,
             "loss_first_last": [losses[0], losses[-1]] if losses else None,
             "reference_spp": args.mse_ref_spp, "reference_var_subtracted": ref_var_mean,
-            "image": f"{R}x{R}", "max_depth": depth, "guide_alpha": args.guide_alpha,
+            "image": f"{MW}x{MH} (the bench scene and camera at a reduced image size)", "max_depth": depth, "guide_alpha": args.guide_alpha,
             "curve_ms_mse": {"plain": curve_p, "guided": curve_g},
             "note": "MSE over linear RGB, no clamping; times include the guide's training"}
 
@@ -354,12 +371,15 @@ def aggregate(elapsed_ms: float, units: float, dist):
 
 
 def workload_config(args, l2_note):
+    light = ("lighting A (0.3x0.3 area light + background 0.2)" if args.lighting == "A"
+             else "lighting B (12,000 small emissive primitives, no area light)")
     return {
         "workload": (f"procedural room, {args.n_prims} Gaussian primitives (70% surface splats, 30% "
-                     f"aggregate clusters), area light + background, {args.width}x{args.height}, "
-                     f"1 spp per step, max depth {args.depth}"),
+                     f"aggregate clusters; {args.near_specular:g} of the surface shapes near-specular GGX "
+                     f"0.02), {light}, {args.width}x{args.height}, 1 spp per step, max depth {args.depth}"),
         "n_prims": args.n_prims, "width": args.width, "height": args.height, "spp_per_step": 1,
-        "max_depth": args.depth, "step": "BVH build + 1 spp wavefront render", "l2": l2_note,
+        "max_depth": args.depth, "lighting": args.lighting, "near_specular_frac": args.near_specular,
+        "step": "BVH build + 1 spp wavefront render", "l2": l2_note,
         "parallelism": f"replicas x{args.gpus}",
     }
 
@@ -400,7 +420,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2406_09733_gb300 import scenes
-    scene = scenes.room_scene(args.n_prims, width=args.width, height=args.height)
+    scene = bench_scene(args)
     px = max(16, args.cpu_pixels // 2)
     for w in range(args.warmup):
         cpu_baseline_run(scene, args, px, seed=1000 + w)
@@ -441,7 +461,7 @@ def run_ugp(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    scene = scenes.room_scene(args.n_prims, width=args.width, height=args.height)
+    scene = bench_scene(args)
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(scene, k)))
             for k in ("mean", "quat", "scale", "magnitude", "sggx", "mtype", "albedo", "roughness", "emission")}
     d = {k: v.to(dev) for k, v in host.items()}
@@ -729,7 +749,7 @@ def emitter_study(args, d, mats, scene, dev, spp=4):
     out = {"image": f"{W}x{H}", "spp": spp, "depth": args.depth,
            "lights": "emissive primitives only (no area light, no background)"}
     out["bench_scene_emitters"] = one(scene, d, mats)
-    sb = scenes.room_scene(args.n_prims, width=W, height=H, lighting="B")
+    sb = bench_scene(args, lighting="B")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     db = {"mean": t(sb.mean), "quat": t(sb.quat), "scale": t(sb.scale), "magnitude": t(sb.magnitude)}
     mb = ugp.Materials(t(sb.sggx), t(sb.mtype), t(sb.albedo), t(sb.roughness), t(sb.emission))
@@ -745,7 +765,7 @@ def run_kernel_case(args):
     from paper_2406_09733_gb300 import scenes, ugp
     dev = torch.device("cuda")
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    s = scenes.room_scene(args.n_prims)
+    s = scenes.room_scene(args.n_prims, near_specular_frac=args.near_specular)
     bvh = ugp.build_bvh(t(s.mean), t(s.quat), t(s.scale), t(s.magnitude))
     cam = s.camera
     d = pinhole_rays(cam, 512, 512)

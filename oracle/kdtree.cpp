@@ -1,5 +1,5 @@
-// FP64 oracle: the paper's own free-flight sampler (Sec. 5.2 and its listing), a diagnostic for
-// the paper-faithful variant; the order-free sampler of geometry.cpp is the parity target.
+// FP64 oracle: the paper's own free-flight sampler (Sec. 5.2, Eq. 8-10), a diagnostic for the
+// paper-faithful variant; the order-free sampler of geometry.cpp is the parity target.
 //
 // TEST INFRASTRUCTURE ONLY.
 //  * An SAH kd-tree over the primitives' k-ellipsoid boxes (primitives straddling a plane go to
@@ -7,12 +7,12 @@
 //  * Front-to-back traversal: each leaf covers a range [ta, tb] of the ray, and the leaves'
 //    ranges partition [t0, t1]; a primitive contributes I_k over its clipped interval within the
 //    range.
-//  * In a leaf with one primitive, or whose contributions keep the running CDF below 1, the
-//    primitives accumulate 1/2 I_k one by one (in the leaf's order) and the first one whose
-//    running sum passes u is returned. Otherwise the leaf range is cut into segments of constant
-//    active set; a segment with one primitive or whose CDF stays below 1 accumulates the same
-//    way, and the segment where the CDF reaches 1 (the ambiguous one) solves F(t_u) = u and picks
-//    among its active primitives proportionally to I_k(s0, t_u), with u_seg = F(s0) + u2 (u - F(s0)).
+//  * The CDF is the running sum of 1/2 I_k in the order the walk meets the primitives. A leaf
+//    (or, inside a leaf, a segment of constant overlap set) that cannot bring it to 1 adds its
+//    masses in order, and the sample is the primitive whose mass u falls in.
+//  * Where the CDF reaches 1, no order can be trusted: t_u solves F(t_u) = u in that segment and
+//    the primitive is chosen among the segment's overlapping ones with probability proportional
+//    to I_k(s0, t_u) (Eq. 10), using u2.
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -153,6 +153,54 @@ bool part(const KdSample& S, int32_t i, double ta, double tb, Hit* h) {
   return h->a < h->b;
 }
 
+// Takes masses one after another (the front-to-back accumulation of Sec. 5.2): if u falls below
+// cdf + the running sum, the primitive whose mass it falls in is the sample; otherwise the masses
+// are added to cdf. Returns whether a primitive was chosen.
+bool take_in_order(KdSample& S, const std::vector<int32_t>& ids, const std::vector<double>& mass) {
+  double total = 0.0;
+  for (double m : mass) total += m;
+  if (!(S.u < S.cdf + total)) {
+    S.cdf += total;
+    return false;
+  }
+  double c = S.cdf;
+  size_t k = 0;
+  while (k + 1 < mass.size() && !(S.u < c + mass[k])) c += mass[k++];
+  S.result = ids[k];
+  S.done = true;
+  return true;
+}
+
+// F(t) = u inside a segment [s0, s1] whose active primitives bring the CDF from S.cdf below u to
+// at least 1 > u at s1 (Eq. 8-9): safeguarded Newton, F' = 1/2 sum G_k.
+double solve_in_segment(const KdSample& S, const std::vector<const Hit*>& act, double s0, double s1) {
+  double lo = s0, hi = s1, t = 0.5 * (s0 + s1);
+  for (int it = 0; it < 400; ++it) {
+    double f = S.cdf - S.u, fp = 0.0;
+    for (const Hit* h : act) {
+      f += 0.5 * ray_integral(*h, s0, t);
+      fp += 0.5 * gauss_at(*h, t);
+    }
+    if (f == 0.0) break;
+    (f < 0 ? lo : hi) = t;
+    double tn = fp > 0 ? t - f / fp : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const bool stop = std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) ||
+                      hi - lo <= 1e-16 * std::max(1.0, std::fabs(t));
+    t = tn;
+    if (stop) break;
+  }
+  return t;
+}
+
+// One leaf of the front-to-back walk: the primitives' intervals clipped to the leaf's range
+// [ta, tb] of the ray.
+//  * If the leaf cannot bring the CDF to 1, or holds one primitive, its masses 1/2 I_k are taken
+//    in the leaf's order.
+//  * Otherwise the range splits at every interval end into segments of constant overlap set.
+//    Segments before the one where the CDF reaches 1 (and any with one primitive) are taken the
+//    same way; in the segment where it reaches 1, t_u solves F(t_u) = u and the primitive is
+//    chosen with probability proportional to I_k(s0, t_u) (Eq. 10), using u2.
 void leaf(KdSample& S, const KdTree& T, const KdNode& nd, double ta, double tb) {
   std::vector<Hit> hs;
   for (int j = 0; j < nd.count; ++j) {
@@ -161,74 +209,55 @@ void leaf(KdSample& S, const KdTree& T, const KdNode& nd, double ta, double tb) 
     if (part(S, T.leaf_ids[size_t(nd.first + j)], ta, tb, &h)) hs.push_back(h);
   }
   if (hs.empty()) return;
-  double sum = 0.0;
-  for (const Hit& h : hs) sum += 0.5 * ray_integral(h, h.a, h.b);
-  if (hs.size() == 1 || S.cdf + sum < 1.0) {
-    for (const Hit& h : hs) {
-      S.cdf += 0.5 * ray_integral(h, h.a, h.b);
-      if (S.u < S.cdf) {
-        S.result = h.id;
-        S.done = true;
-        return;
-      }
-    }
+  std::vector<int32_t> ids;
+  std::vector<double> mass;
+  double leaf_mass = 0.0;
+  for (const Hit& h : hs) {
+    ids.push_back(h.id);
+    mass.push_back(0.5 * ray_integral(h, h.a, h.b));
+    leaf_mass += mass.back();
+  }
+  if (hs.size() == 1 || S.cdf + leaf_mass < 1.0) {
+    take_in_order(S, ids, mass);
     return;
   }
-  // segments of constant active set inside the leaf's range
-  std::vector<double> ev;
+  std::vector<double> ends;
   for (const Hit& h : hs) {
-    ev.push_back(h.a);
-    ev.push_back(h.b);
+    ends.push_back(h.a);
+    ends.push_back(h.b);
   }
-  std::sort(ev.begin(), ev.end());
-  ev.erase(std::unique(ev.begin(), ev.end()), ev.end());
-  for (size_t s = 0; s + 1 < ev.size(); ++s) {
-    const double s0 = ev[s], s1 = ev[s + 1];
+  std::sort(ends.begin(), ends.end());
+  ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+  for (size_t s = 0; s + 1 < ends.size(); ++s) {
+    const double s0 = ends[s], s1 = ends[s + 1];
     std::vector<const Hit*> act;
+    std::vector<int32_t> act_ids;
+    std::vector<double> seg_mass;
+    double seg_total = 0.0;
     for (const Hit& h : hs)
-      if (h.a <= s0 && h.b >= s1) act.push_back(&h);
-    if (act.empty()) continue;
-    double dF = 0.0;
-    for (const Hit* h : act) dF += 0.5 * ray_integral(*h, s0, s1);
-    if (act.size() == 1 || S.cdf + dF < 1.0) {
-      for (const Hit* h : act) {
-        S.cdf += 0.5 * ray_integral(*h, s0, s1);
-        if (S.u < S.cdf) {
-          S.result = h->id;
-          S.done = true;
-          return;
-        }
+      if (h.a <= s0 && h.b >= s1) {
+        act.push_back(&h);
+        act_ids.push_back(h.id);
+        seg_mass.push_back(0.5 * ray_integral(h, s0, s1));
+        seg_total += seg_mass.back();
       }
+    if (act.empty()) continue;
+    if (act.size() == 1 || S.cdf + seg_total < 1.0) {
+      if (take_in_order(S, act_ids, seg_mass)) return;
       continue;
     }
-    // ambiguous segment: u < 1 <= cdf + dF, so t_u lies inside; bracketed Newton
-    double lo = s0, hi = s1, t = 0.5 * (s0 + s1);
-    for (int it = 0; it < 400; ++it) {
-      double f = S.cdf - S.u, fp = 0.0;
-      for (const Hit* h : act) {
-        f += 0.5 * ray_integral(*h, s0, t);
-        fp += 0.5 * gauss_at(*h, t);
-      }
-      if (f == 0.0) break;
-      if (f < 0) lo = t; else hi = t;
-      double tn = fp > 0 ? t - f / fp : 0.5 * (lo + hi);
-      if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
-      const bool stop = std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) ||
-                        hi - lo <= 1e-16 * std::max(1.0, std::fabs(t));
-      t = tn;
-      if (stop) break;
-    }
+    const double t_u = solve_in_segment(S, act, s0, s1);
     S.st.ambiguous_start = s0;
-    const double u_seg = S.cdf + S.u2 * (S.u - S.cdf);
+    std::vector<double> w;
+    double w_total = 0.0;
     for (const Hit* h : act) {
-      S.cdf += 0.5 * ray_integral(*h, s0, t);
-      if (u_seg < S.cdf) {
-        S.result = h->id;
-        S.done = true;
-        return;
-      }
+      w.push_back(ray_integral(*h, s0, t_u));
+      w_total += w.back();
     }
-    S.result = act.back()->id;  // rounding: the running sum ends a hair below u_seg
+    double c = 0.0;
+    size_t k = 0;
+    while (k + 1 < w.size() && !(S.u2 * w_total < c + w[k])) c += w[k++];
+    S.result = act_ids[k];
     S.done = true;
     return;
   }
