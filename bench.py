@@ -57,7 +57,7 @@ def parse_args(argv=None):
                    help="fraction of surface shapes made near-specular GGX (roughness 0.02)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-pixels", type=int, default=128, help="pixels of the CPU-baseline sample")
+    p.add_argument("--cpu-pixels", type=int, default=2048, help="pixels of the CPU-baseline sample")
     p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
@@ -110,7 +110,7 @@ GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 # DRAM bytes (read + write) per k_extend launch of a workload, averaged over the launches of one
 # step, from one ncu capture of the current kernel (profiles/k_extend_dram_*.md); None for any
 # other workload, and to be reset whenever k_extend changes.
-EXTEND_TRAFFIC_BYTES = {}
+EXTEND_TRAFFIC_BYTES = {(5_500_000, 1920, 1080, 12, "A", 0.1): 2269.13e6}
 
 
 def workload_key(args):

@@ -51,4 +51,8 @@ def test_bench_arguments_and_workload_description():
     a = bench.parse_args([])
     assert a.gpus == 1 and a.steps >= 1 and a.warmup >= 3 and a.impl == "ugp"
     cfg = bench.workload_config(a, "flushed")
-    assert cfg["n_prims"] == 1_000_000 and cfg["width"] == 1024 and cfg["max_depth"] == 8
+    # the paper-scale configuration: 5.5M primitives, 1920 x 1080, depth 12, lighting A, a tenth of
+    # the surface shapes near-specular
+    assert cfg["n_prims"] == 5_500_000 and cfg["width"] == 1920 and cfg["height"] == 1080
+    assert cfg["max_depth"] == 12 and cfg["lighting"] == "A" and cfg["near_specular_frac"] == 0.1
+    assert "5500000" in cfg["workload"] and "1920x1080" in cfg["workload"]
