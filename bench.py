@@ -57,7 +57,7 @@ def parse_args(argv=None):
                    help="fraction of surface shapes made near-specular GGX (roughness 0.02)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-pixels", type=int, default=2048, help="pixels of the CPU-baseline sample")
+    p.add_argument("--cpu-pixels", type=int, default=256, help="pixels of the CPU-baseline sample")
     p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
@@ -402,10 +402,10 @@ def host_cpu() -> str:
 
 
 def cpu_baseline_run(scene, args, pixels, spp=1, seed=0):
-    """The FP64 oracle on a bounded sample of the workload: `pixels` consecutive pixels of the
-    middle image row(s), one sample each."""
+    """The FP64 oracle on a bounded sample of the workload: `pixels` consecutive pixels centred
+    in the middle image row, one sample each."""
     import oracle
-    mid = (args.height // 2) * args.width
+    mid = (args.height // 2) * args.width + max(0, (args.width - pixels) // 2)
     t0 = time.perf_counter()
     _, _, (ne, ns) = oracle.render(scene, spp=spp, max_depth=args.depth, seed=seed,
                                    pixels=(mid, mid + pixels))
@@ -421,7 +421,7 @@ def run_reference(args):
         return 0
     from paper_2406_09733_gb300 import scenes
     scene = bench_scene(args)
-    px = max(16, args.cpu_pixels // 2)
+    px = max(16, args.cpu_pixels // 8)
     for w in range(args.warmup):
         cpu_baseline_run(scene, args, px, seed=1000 + w)
     rays = 0
@@ -432,7 +432,7 @@ def run_reference(args):
         rays += r
         total += dt
     value = rays / total / 1e6
-    sample = f"{px} pixels x 1 spp of the middle row per step, brute force over all primitives"
+    sample = f"{px} pixels x 1 spp centred in the middle row per step, brute force over all primitives"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
@@ -564,7 +564,7 @@ def run_ugp(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, r, dt = cpu_baseline_run(scene, args, args.cpu_pixels)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_pixels} pixels x 1 spp of the middle row, {r} queries in {dt:.1f} s, "
+               "sample": f"{args.cpu_pixels} pixels x 1 spp centred in the middle row, {r} queries in {dt:.1f} s, "
                          f"brute force over all primitives, FP64", "cpu": host_cpu()}
 
     guide_perf = None

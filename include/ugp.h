@@ -182,6 +182,9 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  *  - n_rays above UGP_NOALLOC_MAX_RAYS is rejected with UGP_ERR_INVALID_ARG.
  *  - The first call on a device looks up the array's device address with that device
  *    current (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is kept for the life of the process and is not valid after
+ *    cudaDeviceReset of that device: do not call this entry point on a device that the
+ *    process has reset.
  *  - Every call uses the same array and leaves its contents behind; the call clears the
  *    part that must start at zero on `stream`.  Calls whose device work overlaps (on
  *    different streams, or from several host threads) race on the array and must be
@@ -194,6 +197,26 @@ ugp_status ugp_sample_free_flight_noalloc(const ugp_bvh* bvh, int64_t n_rays, co
                                           const int32_t* exclude_prim, int32_t* prim_out,
                                           float* t_u_out, float* t_spawn_out, uint8_t* status_out,
                                           void* stream);
+
+/* Phase-function queries (Sec. 6: Eq. 12 with the SGGX visible normals of Eq. 11 and the
+ * base BSDF; App. B for the pdf), for element-wise checks of the shading code.  Record i
+ * has its own material (type 0, 1 or 3 as in ugp_materials; albedo3, roughness and sggx6
+ * as there; disney9 (n x 9) may be NULL, then zeros) and unit directions wo3, wi3 (n x 3,
+ * pointing away from the scattering point).  Outputs, per record:
+ *   eval3_out           the phase function f_p(wi, wo) (Eq. 12): the closed form for
+ *                       isotropic flakes with a Lambertian base, else the stochastic
+ *                       estimate from the six uniforms u_eval6[6 i ..] (n x 6)
+ *   pdf_out             the approximate pdf of App. B at wi
+ *   sample_wi3_out      a direction sampled from wo with the four uniforms u_sample4
+ *   sample_weight3_out  its weight f_p / pdf (zero when sample_ok_out[i] is 0)
+ *   sample_ok_out       1 if the sample carries weight (uint8)
+ * Uniforms lie in [0, 1).  All arrays are device arrays.  Errors: n < 0, or a NULL array
+ * other than disney9, UGP_ERR_INVALID_ARG.  Asynchronous on `stream`. */
+ugp_status ugp_phase_query(int64_t n, const uint8_t* type, const float* albedo3, const float* roughness,
+                           const float* sggx6, const float* disney9, const float* wo3, const float* wi3,
+                           const float* u_eval6, const float* u_sample4, float* eval3_out, float* pdf_out,
+                           float* sample_wi3_out, float* sample_weight3_out, uint8_t* sample_ok_out,
+                           void* stream);
 
 /* All clipped intervals along each ray (hit-set diagnostics).  For ray r,
  * count_out[r] receives the number of primitives whose k-ellipsoid interval
@@ -272,16 +295,24 @@ ugp_status ugp_trace_transmittance_exponential(const ugp_bvh* bvh, int64_t n_ray
 /* ------------------------------------------------------------------ rendering
  * Per-primitive appearance (Sec. 6), device arrays in the caller's order:
  *   sggx6      SGGX matrix S (Sxx, Syy, Szz, Sxy, Sxz, Syz), positive definite (n x 6)
- *   type       0 Lambertian base, 1 GGX base, 2 emissive (pure emitter)      (n, uint8)
- *   albedo3    Lambertian rho, or the GGX base's Schlick F0                  (n x 3)
+ *   type       0 Lambertian base, 1 GGX base, 2 emissive (pure emitter),
+ *              3 Disney principled base (Sec. 6, 12 parameters)             (n, uint8)
+ *   albedo3    Lambertian rho, the GGX base's Schlick F0, or the Disney base
+ *              colour                                                        (n x 3)
  *   roughness  GGX alpha in (0, 1]                                          (n)
- *   emission3  radiance of emissive primitives (isotropic)                  (n x 3) */
+ *   emission3  radiance of emissive primitives (isotropic)                  (n x 3)
+ *   disney9    Disney parameters of type-3 primitives, each in [0, 1]: metallic,
+ *              subsurface, specular, specular tint, roughness, sheen, sheen tint,
+ *              clearcoat, clearcoat gloss (n x 9); read only for type 3.  May be
+ *              NULL: type-3 primitives then take the published defaults (0, 0, 0.5,
+ *              0, 0.5, 0, 0.5, 0, 1). */
 typedef struct ugp_materials {
   const float* sggx6;
   const uint8_t* type;
   const float* albedo3;
   const float* roughness;
   const float* emission3;
+  const float* disney9;
 } ugp_materials;
 
 /* Pinhole camera (host struct).  Pixel (px, py), row 0 at the top, is sampled at

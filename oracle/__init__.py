@@ -28,7 +28,7 @@ u8p = C.POINTER(C.c_uint8)
 class OrcScene(C.Structure):
     _fields_ = [("n", C.c_int64), ("mean3", f32p), ("quat4", f32p), ("scale3", f32p),
                 ("magnitude", f32p), ("sggx6", f32p), ("type", u8p), ("albedo3", f32p),
-                ("roughness", f32p), ("emission3", f32p)]
+                ("roughness", f32p), ("emission3", f32p), ("disney9", f32p)]
 
 
 def lib():
@@ -106,11 +106,14 @@ class _SceneRef:
             sggx=_c(scene.sggx, np.float32), type=_c(scene.mtype, np.uint8),
             albedo=_c(scene.albedo, np.float32), rough=_c(scene.roughness, np.float32),
             emit=_c(scene.emission, np.float32))
+        dis = getattr(scene, "disney", None)
+        if dis is not None:
+            self.arrs["disney"] = _c(dis, np.float32)
         a = self.arrs
         self.s = OrcScene(scene.n, _ptr(a["mean"], f32p), _ptr(a["quat"], f32p),
                           _ptr(a["scale"], f32p), _ptr(a["mag"], f32p), _ptr(a["sggx"], f32p),
                           _ptr(a["type"], u8p), _ptr(a["albedo"], f32p), _ptr(a["rough"], f32p),
-                          _ptr(a["emit"], f32p))
+                          _ptr(a["emit"], f32p), _ptr(a["disney"], f32p) if dis is not None else None)
 
     @property
     def ref(self):

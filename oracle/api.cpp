@@ -27,6 +27,7 @@ typedef struct {
   const float* albedo3;
   const float* roughness;
   const float* emission3;
+  const float* disney9;  // n x 9 Disney parameters of type-3 primitives, or NULL
 } orc_scene;
 
 static SceneIn scene_in(const orc_scene* s) {

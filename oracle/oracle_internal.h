@@ -51,6 +51,7 @@ struct SceneIn {
   const float* albedo3;
   const float* roughness;
   const float* emission3;
+  const float* disney9;  // n x 9, read for type-3 (Disney) primitives; NULL: published defaults
 };
 
 Prim make_prim(const float* mean3, const float* quat4, const float* scale3, float magnitude);

@@ -46,6 +46,12 @@ Material material_of(const SceneIn& s, int64_t i) {
   m.alpha = s.roughness[i];
   m.emission = load3(s.emission3 + 3 * i);
   for (int k = 0; k < 6; ++k) m.S[k] = s.sggx6[6 * i + k];
+  if (m.type == kMatDisney) {
+    // Burley's published defaults where the scene gives no parameters: metallic 0, subsurface 0,
+    // specular 0.5, specular tint 0, roughness 0.5, sheen 0, sheen tint 0.5, clearcoat 0, gloss 1
+    static const double kDefault[9] = {0, 0, 0.5, 0, 0.5, 0, 0.5, 0, 1};
+    for (int k = 0; k < 9; ++k) m.dis[k] = s.disney9 ? double(s.disney9[9 * i + k]) : kDefault[k];
+  }
   return m;
 }
 

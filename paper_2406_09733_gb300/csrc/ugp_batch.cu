@@ -637,7 +637,7 @@ extern "C" ugp_status ugp_render_batch(int32_t n_req, const ugp_request* reqs, c
     if (!(q.camera.vfov_deg > 0.f && q.camera.vfov_deg < 180.f))
       return fail(UGP_ERR_INVALID_ARG, "ugp_render_batch: request %d: vfov_deg must be in (0, 180)", r);
     BReq& b = hr[size_t(slot)];
-    b.md = MatDev{m.sggx6, m.type, m.albedo3, m.roughness, m.emission3};
+    b.md = MatDev{m.sggx6, m.type, m.albedo3, m.roughness, m.emission3, m.disney9};
     b.L = lights_dev(&q.lights);
     const ugp_status cs = camera_dev(&q.camera, "ugp_render_batch", &b.cam);
     if (cs != UGP_OK) return cs;

@@ -1,8 +1,7 @@
 // Free-flight sampling for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running while a CUDA graph is being captured
-// with an allocation-free policy, plug-ins whose host application owns every device allocation,
-// or real-time loops that must not hit the allocator.  ugp_sample_free_flight_noalloc is
+// Some callers cannot call cudaMalloc at all: plug-ins whose host application owns every device
+// allocation, or real-time loops that must not hit the allocator.  ugp_sample_free_flight_noalloc is
 // ugp_sample_free_flight with its scratch queue in a fixed device array that lives in the
 // library image, so the caller passes only inputs and outputs.
 #include <mutex>
@@ -20,7 +19,10 @@ constexpr size_t kNoallocBytes = 256 + kDenseCols * ((size_t(kNoallocMaxRays) * 
 
 static __device__ __align__(256) unsigned char g_ff_scratch[kNoallocBytes];
 
-// Device address of g_ff_scratch per device, looked up once with that device current.
+// Device address of g_ff_scratch per device, looked up once with that device current. The cache
+// lives as long as the process: after cudaDeviceReset the library image is loaded again and the
+// cached address is stale, so a process that resets a device must not call this entry point on
+// that device afterwards.
 struct ScratchSlot {
   int device;
   void* ptr;

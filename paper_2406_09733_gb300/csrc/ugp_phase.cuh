@@ -1,8 +1,9 @@
 // Appearance of a Gaussian primitive (Sec. 6, Eq. 11-12, App. B) in float32 device code.
 //
 // The phase function is the SGGX visible-normal distribution D_wo(n) (Heitz et al. 2015)
-// combined with a cosine-weighted base BSDF f(wi, wo; n): Lambertian (rho / pi <n.wi>) or GGX
-// (F D G2 / (4 <n.wo>), height-correlated Smith, Schlick Fresnel with F0 = albedo).
+// combined with a cosine-weighted base BSDF f(wi, wo; n): Lambertian (rho / pi <n.wi>), GGX
+// (F D G2 / (4 <n.wo>), height-correlated Smith, Schlick Fresnel with F0 = albedo), or the
+// isotropic Disney principled BRDF with its 12 parameters (base colour and nine scalars).
 // Directions point away from the scattering point: wo to the viewer, wi to the light.
 #pragma once
 
@@ -11,7 +12,7 @@
 namespace ugp {
 
 constexpr float kPiF = 3.14159265358979f;
-constexpr int kMatDiffuse = 0, kMatGGX = 1, kMatEmissive = 2;
+constexpr int kMatDiffuse = 0, kMatGGX = 1, kMatEmissive = 2, kMatDisney = 3;
 
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
@@ -27,9 +28,12 @@ __device__ __forceinline__ float3 normalize3(float3 a) { return rsqrtf(dot3(a, a
 
 struct Material {
   int type;
-  float3 albedo;
+  float3 albedo;  // albedo, F0 of the GGX base, or the Disney base colour
   float alpha;
   float S[6];  // SGGX matrix (Sxx, Syy, Szz, Sxy, Sxz, Syz)
+  // Disney parameters (type 3 only): metallic, subsurface, specular, specular tint, roughness,
+  // sheen, sheen tint, clearcoat, clearcoat gloss.
+  float dis[9];
 };
 
 // Orthonormal basis completing a unit vector (Duff et al., JCGT 2017).
@@ -212,6 +216,140 @@ __device__ __forceinline__ float3 cos_sample(float3 n, float U1, float U2) {
 
 __device__ __forceinline__ float mis_w(float a, float b) { return a + b > 0.f ? a / (a + b) : 0.f; }
 
+// ---------------------------------------------------------------------------- Disney base
+// The isotropic principled BRDF (Burley 2012) as the base of Eq. 12, cosine-weighted like the
+// others: a diffuse part (retro-reflective diffuse blended with the subsurface approximation,
+// plus sheen, all scaled by 1 - metallic) and a glossy part (GGX specular with height-correlated
+// Smith masking and Schlick Fresnel from the specular colour, plus a GTR1 clearcoat with
+// separable Smith masking of roughness 1/4).
+struct DisneyLobes {
+  float3 spec0;    // specular colour at normal incidence
+  float3 sheen_c;  // sheen colour
+  float alpha, alpha_c;
+  float p_diffuse, p_spec, p_coat;  // lobe choice of the sampler (also the App. B weights)
+};
+
+__device__ __forceinline__ float lum3(float3 c) { return 0.3f * c.x + 0.6f * c.y + 0.1f * c.z; }
+__device__ __forceinline__ float schlick_w(float c) {
+  const float m1 = fminf(1.f, fmaxf(0.f, 1.f - c)), m2 = m1 * m1;
+  return m2 * m2 * m1;
+}
+__device__ __forceinline__ float3 lerp3(float3 a, float3 b, float t) {
+  return f3(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y), fmaf(t, b.z - a.z, a.z));
+}
+
+__device__ __forceinline__ DisneyLobes disney_lobes(const Material& m) {
+  DisneyLobes L;
+  const float l = lum3(m.albedo);
+  const float3 one = f3(1.f, 1.f, 1.f);
+  const float3 tint = l > 0.f ? (1.f / l) * m.albedo : one;
+  const float metallic = m.dis[0], clearcoat = m.dis[7];
+  L.spec0 = lerp3((0.08f * m.dis[2]) * lerp3(one, tint, m.dis[3]), m.albedo, metallic);
+  L.sheen_c = lerp3(one, tint, m.dis[6]);
+  L.alpha = fmaxf(1e-3f, m.dis[4] * m.dis[4]);
+  L.alpha_c = fmaf(m.dis[8], 0.001f - 0.1f, 0.1f);
+  const float wd = (1.f - metallic) * l;
+  const float ws = lum3(L.spec0) + 0.04f;
+  const float wc = 0.01f * clearcoat + (clearcoat > 0.f ? 0.02f : 0.f);
+  const float inv = 1.f / (wd + ws + wc);
+  L.p_diffuse = wd * inv;
+  L.p_spec = ws * inv;
+  L.p_coat = wc * inv;
+  return L;
+}
+
+// Clearcoat normal distribution (generalised Trowbridge-Reitz, exponent 1), normalised so that
+// its projected integral over the hemisphere is 1.
+__device__ __forceinline__ float gtr1_D(float a, float ch) {
+  if (ch <= 0.f) return 0.f;
+  if (a >= 1.f) return 1.f / kPiF;
+  const float a2 = a * a;
+  return (a2 - 1.f) / (kPiF * logf(a2) * fmaf(a2 - 1.f, ch * ch, 1.f));
+}
+__device__ __forceinline__ float smith_g1_sep(float c, float a) {
+  const float c2 = c * c, a2 = a * a;
+  return 2.f * c / (c + sqrtf(a2 + c2 - a2 * c2));
+}
+
+// Diffuse, subsurface and sheen (times <n.wi>).
+__device__ inline float3 disney_f_diffuse(const Material& m, const DisneyLobes& L, float3 wi, float3 wo, float3 n) {
+  const float cl = dot3(n, wi), cv = dot3(n, wo);
+  if (cl <= 0.f || cv <= 0.f) return f3(0.f, 0.f, 0.f);
+  const float3 h = normalize3(wi + wo);
+  const float cd = dot3(wi, h);
+  const float FL = schlick_w(cl), FV = schlick_w(cv), FH = schlick_w(cd);
+  const float r = m.dis[4], cd2 = cd * cd;
+  const float fd90 = fmaf(2.f * r, cd2, 0.5f);
+  const float Fd = fmaf(fd90 - 1.f, FL, 1.f) * fmaf(fd90 - 1.f, FV, 1.f);
+  const float fss90 = r * cd2;
+  const float Fss = fmaf(fss90 - 1.f, FL, 1.f) * fmaf(fss90 - 1.f, FV, 1.f);
+  const float ss = 1.25f * fmaf(Fss, 1.f / (cl + cv) - 0.5f, 0.5f);
+  const float diff = fmaf(m.dis[1], ss - Fd, Fd) * (1.f / kPiF);
+  const float k = (1.f - m.dis[0]) * cl;
+  const float sh = FH * m.dis[5];
+  return f3(k * fmaf(diff, m.albedo.x, sh * L.sheen_c.x), k * fmaf(diff, m.albedo.y, sh * L.sheen_c.y),
+            k * fmaf(diff, m.albedo.z, sh * L.sheen_c.z));
+}
+
+// Specular and clearcoat (times <n.wi>).
+__device__ inline float3 disney_f_glossy(const Material& m, const DisneyLobes& L, float3 wi, float3 wo, float3 n) {
+  const float cl = dot3(n, wi), cv = dot3(n, wo);
+  if (cl <= 0.f || cv <= 0.f) return f3(0.f, 0.f, 0.f);
+  float3 f = ggx_f(L.spec0, L.alpha, wi, wo, n);
+  if (m.dis[7] > 0.f) {
+    const float3 h = normalize3(wi + wo);
+    const float Fr = fmaf(0.96f, schlick_w(dot3(wi, h)), 0.04f);
+    const float G = smith_g1_sep(cl, 0.25f) * smith_g1_sep(cv, 0.25f);
+    const float c = 0.25f * m.dis[7] * Fr * gtr1_D(L.alpha_c, dot3(n, h)) * G / (4.f * cv);
+    f = f + f3(c, c, c);
+  }
+  return f;
+}
+
+// Density of the lobe-mixture sampler below (cosine, GGX visible normals, GTR1 half vectors).
+__device__ inline float disney_pdf(const DisneyLobes& L, float3 wi, float3 wo, float3 n) {
+  const float cl = dot3(n, wi), cv = dot3(n, wo);
+  if (cl <= 0.f || cv <= 0.f) return 0.f;
+  const float3 h = normalize3(wi + wo);
+  const float ch = dot3(n, h), oh = dot3(wo, h);
+  float p = L.p_diffuse * cl / kPiF;
+  p += L.p_spec * ggx_D(L.alpha, ch) / ((1.f + ggx_lambda(L.alpha, cv)) * 4.f * cv);
+  if (L.p_coat > 0.f && oh > 0.f) p += L.p_coat * gtr1_D(L.alpha_c, ch) * ch / (4.f * oh);
+  return p;
+}
+
+// One sample about the micro-normal n: U[0] picks the lobe and, rescaled within the lobe's share,
+// drives its sampler with U[1]. The weight is f <n.wi> over the mixture's density.
+__device__ inline bool disney_sample(const Material& m, float3 wo, float3 n, const float U[2], float3& wi,
+                                     float3& weight) {
+  const DisneyLobes L = disney_lobes(m);
+  weight = f3(0.f, 0.f, 0.f);
+  if (dot3(n, wo) <= 0.f) return false;
+  const float u = U[0];
+  if (u < L.p_diffuse) {
+    wi = cos_sample(n, u / L.p_diffuse, U[1]);
+  } else if (u < L.p_diffuse + L.p_spec || L.p_coat <= 0.f) {
+    const float u1 = fminf(0.99999994f, (u - L.p_diffuse) / L.p_spec);
+    const float3 h = ggx_sample_vn(L.alpha, wo, n, u1, U[1]);
+    wi = normalize3((2.f * dot3(wo, h)) * h - wo);
+  } else {
+    const float u1 = fminf(0.99999994f, (u - L.p_diffuse - L.p_spec) / L.p_coat);
+    const float a2 = L.alpha_c * L.alpha_c;
+    const float c2 = (1.f - powf(a2, 1.f - u1)) / (1.f - a2);
+    const float c = sqrtf(fmaxf(0.f, fminf(1.f, c2))), sn = sqrtf(fmaxf(0.f, 1.f - c * c));
+    float sp, cp;
+    sincospif(2.f * U[1], &sp, &cp);
+    float3 t1, t2;
+    onb3(n, t1, t2);
+    const float3 h = normalize3((sn * cp) * t1 + (sn * sp) * t2 + c * n);
+    wi = normalize3((2.f * dot3(wo, h)) * h - wo);
+  }
+  const float p = disney_pdf(L, wi, wo, n);
+  if (!(p > 0.f)) return false;
+  weight = (1.f / p) * (disney_f_diffuse(m, L, wi, wo, n) + disney_f_glossy(m, L, wi, wo, n));
+  return true;
+}
+
 __device__ __forceinline__ float3 base_f(const Material& m, float3 wi, float3 wo, float3 n) {
   return m.type == kMatGGX ? ggx_f(m.albedo, m.alpha, wi, wo, n) : lambert_f(m.albedo, wi, wo, n);
 }
@@ -226,6 +364,27 @@ __device__ __forceinline__ bool sggx_isotropic(const float S[6]) {
 __device__ inline float3 phase_eval_stochastic(const Material& m, float3 wi, float3 wo, const float U[6]) {
   const float3 n1 = sggx_sample_vndf(m.S, wo, U[0], U[1]);
   const float p1 = sggx_dvis(m.S, wo, n1);
+  if (m.type == kMatDisney) {
+    // each part with its own pair of techniques: the glossy part with micro-normals about the half
+    // vector, the diffuse part with normals from the cosine lobe about wi
+    const DisneyLobes L = disney_lobes(m);
+    const float3 h = normalize3(wi + wo);
+    const float3 n2 = micro_sample(L.alpha, h, U[2], U[3]);
+    const float q2 = micro_pdf(L.alpha, n2, h);
+    float3 est = mis_w(p1, micro_pdf(L.alpha, n1, h)) * disney_f_glossy(m, L, wi, wo, n1);
+    if (q2 > 0.f) {
+      const float dv = sggx_dvis(m.S, wo, n2);
+      est = est + (dv / q2 * mis_w(q2, dv)) * disney_f_glossy(m, L, wi, wo, n2);
+    }
+    const float3 n3 = cos_sample(wi, U[4], U[5]);
+    const float q3 = fmaxf(0.f, dot3(n3, wi)) / kPiF;
+    est = est + mis_w(p1, fmaxf(0.f, dot3(n1, wi)) / kPiF) * disney_f_diffuse(m, L, wi, wo, n1);
+    if (q3 > 0.f) {
+      const float dv = sggx_dvis(m.S, wo, n3);
+      est = est + (dv / q3 * mis_w(q3, dv)) * disney_f_diffuse(m, L, wi, wo, n3);
+    }
+    return est;
+  }
   if (m.type == kMatGGX) {
     const float3 h = normalize3(wi + wo);
     const float3 n2 = micro_sample(m.alpha, h, U[2], U[3]);
@@ -265,6 +424,7 @@ __device__ __forceinline__ float3 phase_eval(const Material& m, float3 wi, float
 __device__ __forceinline__ bool phase_sample(const Material& m, float3 wo, const float U[4], float3& wi,
                                              float3& weight) {
   const float3 n = sggx_sample_vndf(m.S, wo, U[0], U[1]);
+  if (m.type == kMatDisney) return disney_sample(m, wo, n, U + 2, wi, weight);
   if (m.type == kMatGGX) {
     const float3 h = ggx_sample_vn(m.alpha, wo, n, U[2], U[3]);
     const float oh = dot3(wo, h);
@@ -291,6 +451,18 @@ __device__ inline float phase_pdf_approx(const Material& m, float3 wi, float3 wo
     float r[6];
     sggx_roughen(m.S, m.alpha, r);
     return sggx_dvis(r, wo, h);
+  }
+  if (m.type == kMatDisney) {
+    // the lobes weighted as the sampler picks them (by metallic and base-colour luminance)
+    const DisneyLobes L = disney_lobes(m);
+    float r[6];
+    sggx_roughen(m.S, L.alpha, r);
+    float p = fmaf(L.p_spec, sggx_dvis(r, wo, h), L.p_diffuse * fmaxf(0.f, dot3(h, wo)) / kPiF);
+    if (L.p_coat > 0.f) {
+      sggx_roughen(m.S, L.alpha_c, r);
+      p = fmaf(L.p_coat, sggx_dvis(r, wo, h), p);
+    }
+    return p;
   }
   return fmaxf(0.f, dot3(h, wo)) / kPiF;
 }

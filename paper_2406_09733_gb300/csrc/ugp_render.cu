@@ -586,7 +586,8 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
     const ugp_status cs = camera_dev(camera, "ugp_render", &cd);
     if (cs != UGP_OK) return cs;
   }
-  const MatDev md{materials->sggx6, materials->type, materials->albedo3, materials->roughness, materials->emission3};
+  const MatDev md{materials->sggx6, materials->type, materials->albedo3, materials->roughness, materials->emission3,
+                  materials->disney9};
   const TraceScene sc = trace_scene(bvh);
   const uint2 key = make_uint2(uint32_t(params->seed & 0xffffffffu), uint32_t(params->seed >> 32));
   unsigned long long* stats = trace_counters();

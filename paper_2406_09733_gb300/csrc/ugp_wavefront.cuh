@@ -50,6 +50,7 @@ struct MatDev {
   const float* albedo3;
   const float* roughness;
   const float* emission3;
+  const float* disney9;  // may be null (published defaults for type 3)
 };
 
 namespace wf {
@@ -101,6 +102,14 @@ __device__ __forceinline__ Material load_material(const MatDev& m, int k) {
   M.albedo = f3(m.albedo3[3 * k], m.albedo3[3 * k + 1], m.albedo3[3 * k + 2]);
   M.alpha = m.roughness[k];
   for (int j = 0; j < 6; ++j) M.S[j] = m.sggx6[6 * k + j];
+  if (M.type == kMatDisney) {
+    if (m.disney9) {
+      for (int j = 0; j < 9; ++j) M.dis[j] = m.disney9[9 * size_t(k) + j];
+    } else {
+      const float def[9] = {0.f, 0.f, 0.5f, 0.f, 0.5f, 0.f, 0.5f, 0.f, 1.f};
+      for (int j = 0; j < 9; ++j) M.dis[j] = def[j];
+    }
+  }
   return M;
 }
 

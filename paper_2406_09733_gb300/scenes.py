@@ -32,6 +32,7 @@ import numpy as np
 MAT_DIFFUSE = 0
 MAT_GGX = 1
 MAT_EMISSIVE = 2
+MAT_DISNEY = 3
 
 
 def _rng(seed: int) -> np.random.Generator:
@@ -72,6 +73,9 @@ class Scene:
     emission: np.ndarray      # (N,3) float32
     camera: Camera = None
     lights: Lights = field(default_factory=Lights)
+    # (N,9) float32 Disney parameters of MAT_DISNEY primitives (metallic, subsurface, specular,
+    # specular tint, roughness, sheen, sheen tint, clearcoat, clearcoat gloss), or None
+    disney: np.ndarray = None
 
     @property
     def n(self) -> int:
@@ -81,7 +85,32 @@ class Scene:
         idx = np.asarray(idx)
         return Scene(self.mean[idx], self.quat[idx], self.scale[idx], self.magnitude[idx],
                      self.sggx[idx], self.mtype[idx], self.albedo[idx], self.roughness[idx],
-                     self.emission[idx], self.camera, self.lights)
+                     self.emission[idx], self.camera, self.lights,
+                     None if self.disney is None else self.disney[idx])
+
+
+def random_disney_params(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n parameter sets of the Disney base: metallic, subsurface, specular, specular tint,
+    sheen, sheen tint and clearcoat gloss uniform in [0, 1], roughness uniform in [0.3, 0.9],
+    clearcoat uniform in [0, 1] on half of the sets and 0 on the rest."""
+    d = rng.random((n, 9))
+    d[:, 4] = rng.uniform(0.3, 0.9, n)
+    d[:, 7] *= rng.random(n) < 0.5
+    return d
+
+
+def with_disney(scene: Scene, frac: float, seed: int = 0) -> Scene:
+    """The scene with a random fraction `frac` of its non-emissive primitives turned into Disney
+    primitives (base colour = their albedo) with random parameters."""
+    rng = _rng(seed)
+    mtype = scene.mtype.copy()
+    cand = np.flatnonzero(mtype != MAT_EMISSIVE)
+    pick = cand[rng.random(cand.size) < frac]
+    mtype[pick] = MAT_DISNEY
+    dis = np.zeros((scene.n, 9))
+    dis[pick] = random_disney_params(rng, pick.size)
+    return Scene(scene.mean, scene.quat, scene.scale, scene.magnitude, scene.sggx, mtype, scene.albedo,
+                 scene.roughness, scene.emission, scene.camera, scene.lights, _f32(dis))
 
 
 def random_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:

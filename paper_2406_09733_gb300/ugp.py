@@ -30,7 +30,8 @@ class UgpBvhInfo(C.Structure):
 
 
 class UgpMaterials(C.Structure):
-    _fields_ = [("sggx6", vp), ("type", vp), ("albedo3", vp), ("roughness", vp), ("emission3", vp)]
+    _fields_ = [("sggx6", vp), ("type", vp), ("albedo3", vp), ("roughness", vp), ("emission3", vp),
+                ("disney9", vp)]
 
 
 class UgpCamera(C.Structure):
@@ -118,6 +119,8 @@ def lib():
         L.ugp_sample_free_flight_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_trace_transmittance_exponential.restype = C.c_int
         L.ugp_trace_transmittance_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ugp_phase_query.restype = C.c_int
+        L.ugp_phase_query.argtypes = [C.c_int64] + [vp] * 15
         L.ugp_set_trace_counters.restype = C.c_int
         L.ugp_set_trace_counters.argtypes = [vp]
         for fn in _EXTRA:
@@ -322,6 +325,27 @@ def trace_transmittance_exponential(bvh: Bvh, o, d, t0, t1, exclude=None, stream
     return T, st
 
 
+def phase_query(mtype, albedo3, roughness, sggx6, wo3, wi3, u_eval6, u_sample4, disney9=None, stream=None):
+    """Phase-function queries on independent records (Sec. 6, App. B): returns (eval (n, 3),
+    App. B pdf (n,), sampled wi (n, 3), sample weight (n, 3), sample ok (n,) uint8)."""
+    _dev(mtype, torch.uint8, "type", cuda=False)
+    n, dev = int(mtype.numel()), mtype.device
+    for t, nm, last in ((albedo3, "albedo3", 3), (roughness, "roughness", None), (sggx6, "sggx6", 6),
+                        (disney9, "disney9", 9), (wo3, "wo3", 3), (wi3, "wi3", 3), (u_eval6, "u_eval6", 6),
+                        (u_sample4, "u_sample4", 4)):
+        _dev(t, torch.float32, nm, last, n=n, device=dev)
+    _dev(mtype, torch.uint8, "type")
+    ev = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    pdf = torch.empty(n, dtype=torch.float32, device=dev)
+    swi = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    sw = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    ok = torch.empty(n, dtype=torch.uint8, device=dev)
+    _check(lib().ugp_phase_query(n, _p(mtype), _p(albedo3), _p(roughness), _p(sggx6), _p(disney9), _p(wo3),
+                                 _p(wi3), _p(u_eval6), _p(u_sample4), _p(ev), _p(pdf), _p(swi), _p(sw), _p(ok),
+                                 C.c_void_p(_stream(stream))), "ugp_phase_query")
+    return ev, pdf, swi, sw, ok
+
+
 def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
     """All clipped intervals per ray: (ids, a, b) of shape (n, cap), count (n,), status."""
     n = _rays(o, d, t0, t1, exclude)
@@ -337,17 +361,19 @@ def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):
 
 
 class Materials:
-    """Device copies of the per-primitive appearance arrays (kept alive with the struct)."""
+    """Device copies of the per-primitive appearance arrays (kept alive with the struct).
+    ``disney9`` ((n, 9) float32 or None) holds the Disney parameters of type-3 primitives."""
 
-    def __init__(self, sggx6, mtype, albedo3, roughness, emission3):
+    def __init__(self, sggx6, mtype, albedo3, roughness, emission3, disney9=None):
         _dev(sggx6, torch.float32, "sggx6", 6)
         n, dev = int(sggx6.shape[0]), sggx6.device
         _dev(mtype, torch.uint8, "type", n=n, device=dev)
         _dev(albedo3, torch.float32, "albedo3", 3, n=n, device=dev)
         _dev(roughness, torch.float32, "roughness", n=n, device=dev)
         _dev(emission3, torch.float32, "emission3", 3, n=n, device=dev)
+        _dev(disney9, torch.float32, "disney9", 9, n=n, device=dev)
         self.n, self.device = n, dev
-        self.tensors = (sggx6, mtype, albedo3, roughness, emission3)
+        self.tensors = (sggx6, mtype, albedo3, roughness, emission3, disney9)
         self.c = UgpMaterials(*[_p(t) for t in self.tensors])
 
 
@@ -366,7 +392,9 @@ def scene_to_device(scene, device="cuda", cutoff_eps: float = 0.01):
     """Uploads a ``scenes.Scene`` and builds its BVH: returns (bvh, materials, camera, lights)."""
     t = lambda a: torch.from_numpy(__import__("numpy").ascontiguousarray(a)).to(device)
     bvh = build_bvh(t(scene.mean), t(scene.quat), t(scene.scale), t(scene.magnitude), cutoff_eps)
-    mats = Materials(t(scene.sggx), t(scene.mtype), t(scene.albedo), t(scene.roughness), t(scene.emission))
+    dis = getattr(scene, "disney", None)
+    mats = Materials(t(scene.sggx), t(scene.mtype), t(scene.albedo), t(scene.roughness), t(scene.emission),
+                     None if dis is None else t(dis))
     cam = scene.camera
     li = scene.lights
     return (bvh, mats, camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, cam.width, cam.height),

@@ -134,3 +134,36 @@ def test_shortest_first_serves_small_requests_first(ugp):
     torch.cuda.synchronize()
     for a, b in zip(reqs, reqs2):
         assert torch.allclose(a.accum, b.accum, rtol=1e-5, atol=1e-6)
+
+
+def test_batch_matches_oracle(ugp, orc):
+    """Four small requests of one batch (different scenes, sizes, depths, lightings, one with a
+    Disney material mix) against the FP64 oracle's render of each request, at 3 standard errors
+    per pixel and channel with at most 1 % failing."""
+    base = [scenes.room_scene(2500, seed=31, lighting="A", width=12, height=12, n_clusters=2),
+            scenes.room_scene(2000, seed=32, lighting="B", n_small_emitters=60, width=10, height=10, n_clusters=2),
+            scenes.with_disney(scenes.room_scene(2500, seed=33, lighting="A", width=8, height=12, n_clusters=2),
+                               0.5, seed=5),
+            scenes.tiny_scene(n=400, seed=34, width=12, height=8)]
+    base[3].lights = scenes.Lights(bg=(0.3, 0.3, 0.3))
+    depth = [4, 3, 4, 5]
+    spp_g, spp_o = 4096, 1024
+    devs = [ugp.scene_to_device(s) for s in base]
+    reqs = []
+    for i, (s, (bvh, mats, cam, lights)) in enumerate(zip(base, devs)):
+        reqs.append(ugp.Request(bvh, mats, cam, lights, spp_g, depth[i], seed=50 + i))
+    br = ugp.BatchRenderer(max_requests=4, pool_log2=16, tile=8, use_graph=True)
+    rc = torch.zeros(3, dtype=torch.int64, device="cuda")
+    br.render(reqs, ray_counts=rc)
+    torch.cuda.synchronize()
+    assert rc[2].item() == 0
+    for i, (s, q) in enumerate(zip(base, reqs)):
+        a_o, q_o, _ = orc.render(s, spp=spp_o, max_depth=depth[i], seed=60 + i)
+        a_g, q_g = q.accum.double().cpu().numpy(), q.accum_sq.double().cpu().numpy()
+        mg, mo = a_g / spp_g, a_o / spp_o
+        sg = np.sqrt(np.maximum(q_g / spp_g - mg ** 2, 0) / spp_g)
+        so = np.sqrt(np.maximum(q_o / spp_o - mo ** 2, 0) / spp_o)
+        z = np.abs(mg - mo) / np.maximum(np.sqrt(sg ** 2 + so ** 2), 1e-9)
+        bad = (z > 3.0) & (np.abs(mg - mo) > 1e-6)
+        print(f"request {i}: {bad.mean():.4f} of pixel-channels beyond 3 SE, mean {mg.mean():.4f} vs {mo.mean():.4f}")
+        assert bad.mean() <= 0.01, (i, bad.mean(), np.sort(z.ravel())[-6:])

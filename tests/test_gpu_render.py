@@ -97,9 +97,10 @@ def test_render_matches_oracle_lit_scene(gpu, orc):
 
 
 def test_render_matches_oracle_tiny_scene_config(gpu, orc):
-    """The 1,000-primitive random scene (one emissive primitive, no background) at 32 x 32."""
-    s = scenes.tiny_scene(width=32, height=32)
-    spp_g, spp_o = 8192, 2048
+    """The 1,000-primitive random scene (one emissive primitive, no background, max depth 4) at
+    64 x 64 with 4096 samples per pixel on both sides."""
+    s = scenes.tiny_scene(width=64, height=64)
+    spp_g, spp_o = 4096, 4096
     a_g, q_g, cnt = gpu_render(gpu, s, spp_g, max_depth=4, seed=7, chunks=4)
     a_o, q_o, _ = orc.render(s, spp=spp_o, max_depth=4, seed=8)
     assert (a_o > 0).mean() > 0.01   # one emitter, no background: sparse signal

@@ -6,7 +6,8 @@ ray is finished by a warp that rebuilds its intervals by traversal, where the re
 point finishes most rays on 16 lanes from the slot list.  Through the C ABI it must give the
 same samples bit for bit (the finish sums in fixed point, so neither the collection path nor
 the lane count may change a result), on two calls in a row (the second reuses the array the
-first left behind), and reject more rays than the array holds.  This file runs last so a
+first left behind) and on a third with exactly as many rays as the array holds (the last column
+of its layout in use), and reject more rays than the array holds.  This file runs last so a
 failure here leaves every other test already run.
 """
 import ctypes as C
@@ -58,8 +59,9 @@ def test_noalloc_matches_regular_entry_point_twice(env):
     # dense aggregates, so the scratch queue is really used
     s = scenes.room_scene(100_000, seed=3, n_clusters=30)
     bvh = ugp.build_bvh(dev(s.mean), dev(s.quat), dev(s.scale), dev(s.magnitude))
-    for call, seed in enumerate((5, 6)):
-        r = scenes.random_rays(40000 + 17 * call, seed=seed, centre=(0.5, 0.5, 0.5), radius=1.2)
+    # two calls in a row, then one that fills the fixed array exactly
+    for seed, n in ((5, 40000), (6, 40017), (7, MAX_RAYS)):
+        r = scenes.random_rays(n, seed=seed, centre=(0.5, 0.5, 0.5), radius=1.2)
         u, u2 = scenes.uniforms24(seed + 10, r.n), scenes.uniforms24(seed + 20, r.n)
         status, prim, tu, tsp, st = _noalloc(torch, ugp, L, bvh, r, u, u2)
         assert status == 0, L.ugp_last_error()
