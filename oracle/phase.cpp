@@ -124,14 +124,16 @@ void sggx_roughen(const double s6[6], double alpha, double out6[6]) {
         }
       }
   }
-  double ev[3] = {A[0], A[4], A[8]};
-  int order[3] = {0, 1, 2};
-  std::sort(order, order + 3, [&](int x, int y) { return ev[x] < ev[y]; });
-  const double s3 = ev[order[2]];
+  // App. B keeps the largest eigenvalue s3 and adds alpha^2 s3 to the other two. Where the
+  // largest eigenvalue is shared (isotropic flakes), the eigenvector of the last such axis is
+  // kept.
+  const double ev[3] = {A[0], A[4], A[8]};
+  int m = 0;
+  for (int i = 1; i < 3; ++i)
+    if (ev[i] >= ev[m]) m = i;
+  const double s3 = ev[m];
   double nv[3];
-  nv[order[0]] = ev[order[0]] + alpha * alpha * s3;
-  nv[order[1]] = ev[order[1]] + alpha * alpha * s3;
-  nv[order[2]] = s3;
+  for (int i = 0; i < 3; ++i) nv[i] = i == m ? s3 : ev[i] + alpha * alpha * s3;
   double R[9] = {0};
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
