@@ -125,9 +125,9 @@ __device__ inline void sggx_roughen(const float S[6], float alpha, float out[6])
         }
       }
   }
-  int m = 0;
-  if (A[1][1] > A[m][m]) m = 1;
-  if (A[2][2] > A[m][m]) m = 2;
+  int m = 0;  // the largest eigenvalue; where it is shared, the last such axis
+  if (A[1][1] >= A[m][m]) m = 1;
+  if (A[2][2] >= A[m][m]) m = 2;
   const float s3 = A[m][m], add = alpha * alpha * s3;
   const float3 v = f3(V[0][m], V[1][m], V[2][m]);
   out[0] = S[0] + add * (1.f - v.x * v.x);
