@@ -315,6 +315,39 @@ typedef struct ugp_materials {
   const float* disney9;
 } ugp_materials;
 
+/* Codebook-quantised primitive records (the random-access compression the paper combines
+ * with its level-of-detail scheme).  A record is 24 bytes: the mean (3 float) and magnitude
+ * (float) exact, then 16-bit codes of four attribute groups, each the index of the nearest of
+ * 4096 entries of its codebook: scale (as log s, 3 values), rotation (unit quaternion with
+ * w >= 0, 4), SGGX (6), material (albedo 3, roughness, emission 3, Disney 9: 16), and the
+ * material type in the top 4 bits of the last code.  Layout of record i (little endian):
+ *   bytes 0-11 mean, 12-15 magnitude, 16-17 scale code, 18-19 rotation code, 20-21 SGGX
+ *   code, 22-23 material code | type << 12.
+ * The codebook is 4096 x 29 floats (row k: log scale 3, quaternion 4, SGGX 6, material 16).
+ *
+ * ugp_codebook_encode fits the four codebooks to the caller's primitives by `iters` Lloyd
+ * iterations on the device (every primitive to its nearest entry by squared distance, ties to
+ * the lower index; every entry with primitives to their mean, summed in 64-bit fixed point so
+ * that the fit is reproducible), entries starting at the primitives of index floor(k n / 4096);
+ * then writes the codebook (ugp_codebook_size() bytes, 16-byte aligned) and n records (24 n
+ * bytes, 4-byte aligned).  prims and materials as for ugp_build_bvh and ugp_render
+ * (disney9 may be NULL: zeros).  Workspace: ugp_codebook_workspace_size(n) bytes, 256-byte
+ * aligned.  Errors: n not in [1, 2^30], iters not in [0, 100], a NULL or misaligned array,
+ * UGP_ERR_INVALID_ARG; a short workspace, UGP_ERR_WORKSPACE_TOO_SMALL.
+ *
+ * ugp_codebook_decode expands n records into the arrays of ugp_prims and ugp_materials
+ * (scale = exp of the entry, quaternion normalised; disney9 may be NULL to skip it).  Each
+ * record is decoded on its own (random access).  Asynchronous on `stream`. */
+size_t ugp_codebook_size(void);
+size_t ugp_codebook_workspace_size(int64_t n_prims);
+ugp_status ugp_codebook_encode(const ugp_prims* prims, const ugp_materials* materials, int32_t iters,
+                               void* codebook, void* records, void* workspace, size_t workspace_bytes,
+                               void* stream);
+ugp_status ugp_codebook_decode(int64_t n, const void* records, const void* codebook, float* mean3,
+                               float* quat4, float* scale3, float* magnitude, float* sggx6, uint8_t* type,
+                               float* albedo3, float* roughness, float* emission3, float* disney9,
+                               void* stream);
+
 /* Pinhole camera (host struct).  Pixel (px, py), row 0 at the top, is sampled at
  * (px + jx, py + jy) with a Philox jitter (bounce 15, slot 0). */
 typedef struct ugp_camera {

@@ -10,6 +10,8 @@
 //   5. k_records       64-byte hot records in leaf order (W = S^-1 R^T, mu, g0, index) and
 //                      the low float parts of W (48 B, read only by ill-conditioned hits)
 //   6. k_refit         bottom-up child boxes with one atomic counter per node
+//   7. k_collapse4     the 4-wide quantised tree: each binary internal node at even depth with
+//                      its children and grandchildren (layout in ugp_internal.cuh)
 #include <cub/cub.cuh>
 
 #include <math.h>
@@ -22,7 +24,7 @@ namespace {
 
 
 struct Layout {
-  size_t prims, nodes, wlo, persistent;
+  size_t prims, nodes, nodes4, wlo, persistent;
   size_t aabb, keys0, keys1, vals0, vals1, parent, flags, bounds, cub, total;
   size_t cub_bytes;
 };
@@ -168,9 +170,10 @@ __global__ void k_hierarchy(int n, const uint32_t* __restrict__ keys, int4* __re
   if (i == 0) parent_int[0] = -1;
 }
 
-__global__ void k_single_root(int4* nodes, int32_t* parent_leaf) {
+__global__ void k_single_root(int4* nodes, int32_t* parent_leaf, int32_t* parent_int) {
   nodes[3] = make_int4(~0, kEmptyChild, 0, 0);
   parent_leaf[0] = 0;
+  parent_int[0] = -1;
 }
 
 // Hot record of the primitive in leaf slot `slot` (layout in ugp_internal.cuh), plus the
@@ -263,6 +266,109 @@ __global__ void k_refit(int n, const int32_t* __restrict__ order, const float4* 
   }
 }
 
+// One 4-wide node per binary internal node at even depth (the root has depth 0): its children,
+// with every internal child replaced by that child's two children (odd-depth nodes are absorbed
+// into their parent). Boxes are quantised outwards to 8 bits per face against a grid of spacing
+// 2^e_a per axis anchored at the union's low corner.
+__global__ void k_collapse4(int n_int, const float4* __restrict__ nodes, const int32_t* __restrict__ depth,
+                            uint4* __restrict__ nodes4) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_int) return;
+  if (depth[i] & 1) return;
+  float box[4][6];
+  int ref[4];
+  int m = 0;
+  auto child_of = [&](int node, int side, float b[6], int& r) {
+    const float4* nd = nodes + 4 * size_t(node);
+    const float4 n0 = nd[0], n1 = nd[1], n2 = nd[2];
+    const int4 n3 = reinterpret_cast<const int4*>(nd)[3];
+    r = side ? n3.y : n3.x;
+    if (side == 0) { b[0] = n0.x; b[1] = n0.y; b[2] = n0.z; b[3] = n0.w; b[4] = n1.x; b[5] = n1.y; }
+    else           { b[0] = n1.z; b[1] = n1.w; b[2] = n2.x; b[3] = n2.y; b[4] = n2.z; b[5] = n2.w; }
+  };
+  for (int side = 0; side < 2; ++side) {
+    float b[6];
+    int r;
+    child_of(i, side, b, r);
+    if (r == kEmptyChild) continue;
+    if (r < 0) {
+      for (int k = 0; k < 6; ++k) box[m][k] = b[k];
+      ref[m++] = r;
+      continue;
+    }
+    for (int s2 = 0; s2 < 2; ++s2) {
+      float g[6];
+      int rg;
+      child_of(r, s2, g, rg);
+      if (rg == kEmptyChild) continue;
+      for (int k = 0; k < 6; ++k) box[m][k] = g[k];
+      ref[m++] = rg;
+    }
+  }
+  float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+  for (int c = 0; c < m; ++c)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(lo[a], box[c][a]);
+      hi[a] = fmaxf(hi[a], box[c][3 + a]);
+    }
+  uint32_t qlo[3] = {0u, 0u, 0u}, qhi[3] = {0u, 0u, 0u}, ex = 0u;
+  for (int a = 0; a < 3; ++a) {
+    // a power-of-two spacing 2^e >= extent / 254 (frexp: extent / 254 = f 2^e, f in [1/2, 1));
+    // the spare step absorbs the rounding of o + q 2^e
+    const float ext = hi[a] - lo[a];
+    int e = -126;
+    if (ext > 0.f) {
+      frexpf(ext * (1.f / 254.f) * (1.f + 1e-6f), &e);
+      e = max(-126, min(e, 126));
+    }
+    const float sp = ldexpf(1.f, e), isp = ldexpf(1.f, -e);
+    for (int c = 0; c < m; ++c) {
+      int ql = int(floorf((box[c][a] - lo[a]) * isp));
+      int qh = int(ceilf((box[c][3 + a] - lo[a]) * isp));
+      ql = max(0, min(ql, 255));
+      qh = max(0, min(qh, 255));
+      while (ql > 0 && fmaf(float(ql), sp, lo[a]) > box[c][a]) --ql;
+      while (qh < 255 && fmaf(float(qh), sp, lo[a]) < box[c][3 + a]) ++qh;
+      qlo[a] |= uint32_t(ql) << (8 * c);
+      qhi[a] |= uint32_t(qh) << (8 * c);
+    }
+    ex |= uint32_t(e + 128) << (8 * a);
+  }
+  int r4[4] = {kEmptyChild, kEmptyChild, kEmptyChild, kEmptyChild};
+  for (int c = 0; c < m; ++c) r4[c] = ref[c];
+  uint4* q = nodes4 + 4 * size_t(i);
+  q[0] = make_uint4(__float_as_uint(lo[0]), __float_as_uint(lo[1]), __float_as_uint(lo[2]), ex);
+  q[1] = make_uint4(qlo[0], qlo[1], qlo[2], qhi[0]);
+  q[2] = make_uint4(qhi[1], qhi[2], 0u, 0u);
+  q[3] = make_uint4(uint32_t(r4[0]), uint32_t(r4[1]), uint32_t(r4[2]), uint32_t(r4[3]));
+}
+
+// Depth of every internal node by pointer jumping: each round adds the distance to the current
+// ancestor and jumps to that ancestor's ancestor, so kJumps rounds reach the root of any tree up
+// to 2^kJumps deep (binary radix trees over 32-bit keys with index tie-breaks are at most 64 deep).
+constexpr int kJumps = 7;
+__global__ void k_depth_init(int n_int, const int32_t* __restrict__ parent_int, int32_t* __restrict__ anc,
+                             int32_t* __restrict__ dist) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_int) return;
+  const int p = parent_int[i];
+  anc[i] = p >= 0 ? (p >> 1) : -1;
+  dist[i] = p >= 0 ? 1 : 0;
+}
+__global__ void k_depth_jump(int n_int, const int32_t* __restrict__ anc_in, const int32_t* __restrict__ dist_in,
+                             int32_t* __restrict__ anc_out, int32_t* __restrict__ dist_out) {
+  const int i = int(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_int) return;
+  const int a = anc_in[i];
+  if (a >= 0) {
+    dist_out[i] = dist_in[i] + dist_in[a];
+    anc_out[i] = anc_in[a];
+  } else {
+    dist_out[i] = dist_in[i];
+    anc_out[i] = -1;
+  }
+}
+
 __global__ void k_init_bounds(int* bounds, int* n_flags_zero_dummy) {
   if (threadIdx.x < 6) bounds[threadIdx.x] = f2o(3.0e38f);
 }
@@ -280,6 +386,7 @@ bool layout_for(int64_t n, Layout* L) {
   size_t off = 0;
   L->prims = off;      off = align256(off + N * 64);
   L->nodes = off;      off = align256(off + ni * 64);
+  L->nodes4 = off;     off = align256(off + ni * 64);
   L->wlo = off;        off = align256(off + N * 48);
   L->bounds = off;     off = align256(off + 64);   // 6 ordered-int bounds, root box, invalid count
   L->persistent = off;
@@ -347,6 +454,7 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   b->prims = reinterpret_cast<const float4*>(ws + L.prims);
   b->wlo = reinterpret_cast<const float4*>(ws + L.wlo);
   b->nodes = reinterpret_cast<const float4*>(ws + L.nodes);
+  b->nodes4 = reinterpret_cast<const uint4*>(ws + L.nodes4);
   b->persistent_bytes = L.persistent;
   b->bounds_dev = reinterpret_cast<const float*>(ws + L.bounds);
   if (n == 0) {
@@ -379,7 +487,7 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   int32_t* order = v0;
   if (n == 1) {
     UGP_CUDA_CHECK(cudaMemsetAsync(v0, 0, 4, st));
-    k_single_root<<<1, 1, 0, st>>>(nodes_i, parent_leaf);
+    k_single_root<<<1, 1, 0, st>>>(nodes_i, parent_leaf, parent_int);
     k_single_refit<<<1, 1, 0, st>>>(aabb, nodes_f, root_box);
   } else {
     k_morton<<<G, T, 0, st>>>(n, aabb, bounds, k0, v0);
@@ -396,8 +504,21 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   k_records<<<G, T, 0, st>>>(n, order, prims->mean3, prims->quat4, prims->scale3, prims->magnitude,
                              reinterpret_cast<float4*>(ws + L.prims), reinterpret_cast<float4*>(ws + L.wlo));
   UGP_CUDA_CHECK(cudaGetLastError());
+  {
+    // depths by pointer jumping in the sort's key and value arrays (free after k_records)
+    const int n_int = int(b->n_nodes);
+    const unsigned Gi = unsigned((n_int + T - 1) / T);
+    int32_t* anc[2] = {reinterpret_cast<int32_t*>(k0), v0};
+    int32_t* dist[2] = {reinterpret_cast<int32_t*>(k1), flags};
+    k_depth_init<<<Gi, T, 0, st>>>(n_int, parent_int, anc[0], dist[0]);
+    for (int r = 0; r < kJumps; ++r)
+      k_depth_jump<<<Gi, T, 0, st>>>(n_int, anc[r & 1], dist[r & 1], anc[(r + 1) & 1], dist[(r + 1) & 1]);
+    k_collapse4<<<Gi, T, 0, st>>>(n_int, reinterpret_cast<const float4*>(ws + L.nodes), dist[kJumps & 1],
+                                  reinterpret_cast<uint4*>(ws + L.nodes4));
+    UGP_CUDA_CHECK(cudaGetLastError());
+  }
   // own kernels plus the radix sort's (histogram, scan and one pass per 8-bit digit of 30 bits)
-  prof_end(kStBuild, st, n == 1 ? 5 : 6 + 6);
+  prof_end(kStBuild, st, (n == 1 ? 5 : 6 + 6) + 2 + kJumps);
   b->stream = st;
   *out = b;
   return UGP_OK;

@@ -45,7 +45,7 @@
 
 namespace ugp {
 
-constexpr int kLeafQ = 4;      // primitives a lane may hold back before testing them
+constexpr int kLeafQ = 6;      // primitives a lane may hold back before testing them
 constexpr int kLeafBatch = 16;  // lanes with held-back primitives that start a joint leaf phase
 
 // Bins hold 1/2 I in fixed point, units of 2^-30, with saturating adds: integer sums do not depend
@@ -268,7 +268,8 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       continue;
     }
     const unsigned pend = __ballot_sync(kFull, busy && nq > 0);
-    const bool urgent = __any_sync(kFull, busy && (nq >= kLeafQ - 1 || (tdone && nq > 0)));
+    // a node step may add four held-back primitives: it runs only while every lane has room
+    const bool urgent = __any_sync(kFull, busy && (nq > kLeafQ - 4 || (tdone && nq > 0)));
     if (pend && (__popc(pend) >= kLeafBatch || urgent)) {
       // ---- leaf step: one held-back primitive per lane
       if (busy && nq > 0) {
@@ -279,54 +280,53 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
         below = v.below;
       }
     } else if (busy && !tdone) {
-      // ---- node step: one node of the nearest-first traversal
+      // ---- node step: one 4-wide node of the nearest-first traversal
       if (unsigned(node) >= unsigned(c.sc.n_nodes)) {
         c.st = UGP_RAY_BAD_NODE;
         node = 0;
       }
-      const float4* nd = c.sc.nodes + 4 * node;
-      const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
-      const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
+      float en[4];
+      int ch[4];
+      unsigned hm = node4_test(c.sc.nodes4, node, c.ray, lo, hi, en, ch);
       ++c.n_nodes;
-      const int ch[2] = {n3.x, n3.y};
-      if ((ch[0] < 0 && ~ch[0] >= c.sc.n_prims) || (ch[1] < 0 && ch[1] != kEmptyChild && ~ch[1] >= c.sc.n_prims))
-        c.st = UGP_RAY_BAD_NODE;
-      float en[2];
-      bool hc[2];
-      hc[0] = slab(n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, c.ray, lo, hi, en[0]);
-      hc[1] = ch[1] != kEmptyChild && slab(n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, c.ray, lo, hi, en[1]);
-      if (c.st != UGP_RAY_OK) hc[0] = hc[1] = false;
+      float tk[4];
+      int rk[4];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (!hc[k]) continue;
-        if (en[k] > limit) {
-          hc[k] = false;
-          continue;
+      for (int k = 0; k < 4; ++k) {
+        tk[k] = INFINITY;
+        rk[k] = -1;
+        if (!((hm >> k) & 1u)) continue;
+        if ((ch[k] < 0 && ~ch[k] >= c.sc.n_prims) || (ch[k] >= 0 && ch[k] >= c.sc.n_nodes)) c.st = UGP_RAY_BAD_NODE;
+        if (en[k] > limit || c.st != UGP_RAY_OK) continue;
+        if (ch[k] < 0) {
+          ++c.n_prims;
+          sm.lq[nq][c.tid] = ~ch[k];  // nq <= kLeafQ - 4 here: a node adds at most four
+          ++nq;
+        } else {
+          tk[k] = en[k];
+          rk[k] = ch[k];
         }
-        if (ch[k] >= 0) continue;
-        hc[k] = false;
-        ++c.n_prims;
-        sm.lq[nq][c.tid] = ~ch[k];  // nq <= kLeafQ - 2 here: a node adds at most two
-        ++nq;
       }
+      sort4(tk, rk);
+      const int nk = (rk[0] >= 0) + (rk[1] >= 0) + (rk[2] >= 0) + (rk[3] >= 0);
       if (c.st != UGP_RAY_OK) {
         tdone = true;
         nq = 0;
-      } else if (hc[0] && hc[1]) {
-        const bool first0 = en[0] <= en[1];
-        if (sp == kFFStack) {
+      } else if (nk > 0) {
+        if (sp + nk - 1 > kFFStack) {
           c.st = UGP_RAY_STACK_OVERFLOW;
           tdone = true;
           nq = 0;
         } else {
-          sm.stk[sp][c.tid] = first0 ? ch[1] : ch[0];
-          ++sp;
-          node = first0 ? ch[0] : ch[1];
+          // the farther children go on the stack, farthest first, so the nearer pop first
+#pragma unroll
+          for (int k = 3; k >= 1; --k)
+            if (rk[k] >= 0) {
+              sm.stk[sp][c.tid] = rk[k];
+              ++sp;
+            }
+          node = rk[0];
         }
-      } else if (hc[0]) {
-        node = ch[0];
-      } else if (hc[1]) {
-        node = ch[1];
       } else if (sp == 0) {
         tdone = true;
       } else {

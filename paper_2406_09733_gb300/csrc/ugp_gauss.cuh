@@ -248,6 +248,58 @@ __device__ __forceinline__ bool slab(float lx, float ly, float lz, float hx, flo
   return tl <= th + 4e-7f * fabsf(th);
 }
 
+// Byte c of w as a float: the byte goes into the low mantissa of 2^23 (exact), which is then
+// subtracted.
+__device__ __forceinline__ float byte_f(uint32_t w, int c) {
+  const uint32_t sel = uint32_t(c) | 0x7440u;  // bytes: (w.c, 0, 0, 0x4B) from {0x4B000000 : w}
+  return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.f;
+}
+
+// Slab test of the four children of a 4-wide quantised node (layout in ugp_internal.cuh)
+// against [tmin, tmax]: returns the mask of children hit and writes their references and entry
+// distances. Child c's face along axis a is o_a + q 2^e_a, so its ray distance is
+// q (2^e_a inv_a) + (o_a - ray.o_a) inv_a: two products per axis and node, one fma per face.
+__device__ __forceinline__ unsigned node4_test(const uint4* __restrict__ n4, int node, const Ray& r, float tmin,
+                                               float tmax, float en[4], int ch[4]) {
+  const uint4* nd = n4 + 4 * size_t(node);
+  const uint4 w0 = __ldg(nd), w1 = __ldg(nd + 1), w2 = __ldg(nd + 2), w3 = __ldg(nd + 3);
+  // 2^e from the stored byte e + 128: the float exponent field is e + 127
+  const float sx = __uint_as_float(((w0.w & 255u) - 1u) << 23);
+  const float sy = __uint_as_float((((w0.w >> 8) & 255u) - 1u) << 23);
+  const float sz = __uint_as_float((((w0.w >> 16) & 255u) - 1u) << 23);
+  const float ax = sx * r.inv.x, bx = (__uint_as_float(w0.x) - r.o.x) * r.inv.x;
+  const float ay = sy * r.inv.y, by = (__uint_as_float(w0.y) - r.o.y) * r.inv.y;
+  const float az = sz * r.inv.z, bz = (__uint_as_float(w0.z) - r.o.z) * r.inv.z;
+  ch[0] = int(w3.x);
+  ch[1] = int(w3.y);
+  ch[2] = int(w3.z);
+  ch[3] = int(w3.w);
+  unsigned hit = 0u;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float x0 = fmaf(byte_f(w1.x, c), ax, bx), x1 = fmaf(byte_f(w1.w, c), ax, bx);
+    const float y0 = fmaf(byte_f(w1.y, c), ay, by), y1 = fmaf(byte_f(w2.x, c), ay, by);
+    const float z0 = fmaf(byte_f(w1.z, c), az, bz), z1 = fmaf(byte_f(w2.y, c), az, bz);
+    const float tl = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
+    const float th = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    en[c] = tl;
+    if (ch[c] != kEmptyChild && tl <= th + 4e-7f * fabsf(th)) hit |= 1u << c;
+  }
+  return hit;
+}
+
+// Orders (t, ref) pairs of the children hit by entry distance (misses last), a sorting network
+// on four entries.
+__device__ __forceinline__ void sort4(float t[4], int r[4]) {
+  auto cs = [&](int i, int j) {
+    if (t[j] < t[i]) {
+      const float tt = t[i]; t[i] = t[j]; t[j] = tt;
+      const int rr = r[i]; r[i] = r[j]; r[j] = rr;
+    }
+  };
+  cs(0, 1); cs(2, 3); cs(0, 2); cs(1, 3); cs(1, 2);
+}
+
 __device__ __forceinline__ float3 ld3(const float* __restrict__ p, int64_t i) {
   return make_float3(__ldg(p + 3 * i), __ldg(p + 3 * i + 1), __ldg(p + 3 * i + 2));
 }

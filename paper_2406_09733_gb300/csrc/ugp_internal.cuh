@@ -29,6 +29,19 @@ constexpr int kNodeF4 = 4;
 // Child reference of the unused second child of a one-primitive tree's root.
 constexpr int kEmptyChild = INT32_MIN;
 
+// Device layout of one 4-wide node (64 B) of the collapsed tree the hot traversals walk: the
+// binary internal nodes at even depth, each with the (up to four) children and grandchildren
+// below it, their boxes quantised to 8 bits per face against a per-node grid.
+//   w0 = (o.x, o.y, o.z as float bits, exponents: byte a = e_a + 128 for axes a = 0, 1, 2)
+//   w1 = (lo_x, lo_y, lo_z, hi_x)  byte c of each word: child c's quantised face
+//   w2 = (hi_y, hi_z, 0, 0)
+//   w3 = (child0, child1, child2, child3) as int: >= 0 the 4-wide node of that (binary)
+//        index, < 0 and != kEmptyChild the leaf holding primitive slot ~child, kEmptyChild none.
+// Child c's box along axis a is [o_a + lo_a(c) 2^e_a, o_a + hi_a(c) 2^e_a]; the faces are rounded
+// outwards, so the quantised box contains the exact one. A 4-wide node sits at the index of its
+// binary node (the array has holes at odd depths, which are never read).
+constexpr int kNode4U4 = 4;
+
 }  // namespace ugp
 
 struct ugp_bvh {
@@ -39,6 +52,7 @@ struct ugp_bvh {
   float k;
   float k2;
   const float4* nodes;
+  const uint4* nodes4;       // the 4-wide quantised tree (same indices as nodes, even depths only)
   const float4* prims;
   const float4* wlo;         // low float parts of W, 3 float4 per leaf slot
   const float* bounds_dev;   // in the workspace: ordered-int centroid bounds, root box, invalid count

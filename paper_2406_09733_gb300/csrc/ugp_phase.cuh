@@ -414,15 +414,18 @@ __device__ __forceinline__ float3 phase_eval_lambert_sphere(float3 rho, float3 w
   return v * rho;
 }
 
-__device__ __forceinline__ float3 phase_eval(const Material& m, float3 wi, float3 wo, const float U[6]) {
+// The three entry points the shading kernels call (evaluation, sampling, App. B pdf) are not
+// inlined: every kernel that shades (the renderer's and the batch server's) then runs the same
+// compiled arithmetic, so a path gets the same value in both, bit for bit.
+static __device__ __noinline__ float3 phase_eval(const Material& m, float3 wi, float3 wo, const float U[6]) {
   if (m.type == kMatDiffuse && sggx_isotropic(m.S)) return phase_eval_lambert_sphere(m.albedo, wi, wo);
   return phase_eval_stochastic(m, wi, wo, U);
 }
 
 // Importance sampling (Sec. 6): n from the VNDF, wi from the base BSDF about n; the weight is
 // the base BSDF's own f / pdf.  Returns false if the sample carries no weight.
-__device__ __forceinline__ bool phase_sample(const Material& m, float3 wo, const float U[4], float3& wi,
-                                             float3& weight) {
+static __device__ __noinline__ bool phase_sample(const Material& m, float3 wo, const float U[4], float3& wi,
+                                                 float3& weight) {
   const float3 n = sggx_sample_vndf(m.S, wo, U[0], U[1]);
   if (m.type == kMatDisney) return disney_sample(m, wo, n, U + 2, wi, weight);
   if (m.type == kMatGGX) {
@@ -442,7 +445,7 @@ __device__ __forceinline__ bool phase_sample(const Material& m, float3 wo, const
 
 // Approximate phase pdf of App. B, taken as written: D~_wo(w_h) with the roughened SGGX for a
 // GGX base, <w_h.wo> / pi for a Lambertian base, w_h = normalize(wi + wo).
-__device__ inline float phase_pdf_approx(const Material& m, float3 wi, float3 wo) {
+static __device__ __noinline__ float phase_pdf_approx(const Material& m, float3 wi, float3 wo) {
   const float3 s = wi + wo;
   const float l2 = dot3(s, s);
   if (l2 <= 1e-24f) return 0.f;

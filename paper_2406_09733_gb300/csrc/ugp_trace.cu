@@ -100,6 +100,7 @@ k_collect_hits(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, cons
 TraceScene trace_scene(const ugp_bvh* b) {
   TraceScene s;
   s.nodes = b->nodes;
+  s.nodes4 = b->nodes4;
   s.prims = b->prims;
   s.wlo = b->wlo;
   s.n_prims = b->n_prims;

@@ -9,12 +9,13 @@ constexpr int kTrBlock = 128;      // transmittance: threads per block
 constexpr int kTrStack = 48;       // transmittance: traversal stack depth
 constexpr int kTrBlocksPerSM = 8;  // transmittance: resident blocks per SM (24 KB shared, <= 64 registers)
 constexpr int kFFBlock = 128;      // free flight: threads per block of the scan
-constexpr int kFFStack = 36;       // free flight: traversal stack depth
+constexpr int kFFStack = 34;       // free flight: traversal stack depth (4-wide nodes)
 constexpr int kFFBlocksPerSM = 6;  // free flight: resident scan blocks per SM (36 KB shared, <= 80 registers)
 constexpr int kB = 32;             // free flight: bins of the scan
 
 struct TraceScene {
-  const float4* nodes;
+  const float4* nodes;   // binary nodes
+  const uint4* nodes4;   // 4-wide quantised nodes (ugp_internal.cuh)
   const float4* prims;
   const float4* wlo;
   int64_t n_prims;

@@ -119,6 +119,15 @@ def lib():
         L.ugp_sample_free_flight_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_trace_transmittance_exponential.restype = C.c_int
         L.ugp_trace_transmittance_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ugp_codebook_size.restype = C.c_size_t
+        L.ugp_codebook_size.argtypes = []
+        L.ugp_codebook_workspace_size.restype = C.c_size_t
+        L.ugp_codebook_workspace_size.argtypes = [C.c_int64]
+        L.ugp_codebook_encode.restype = C.c_int
+        L.ugp_codebook_encode.argtypes = [C.POINTER(UgpPrims), C.POINTER(UgpMaterials), C.c_int32, vp, vp, vp,
+                                          C.c_size_t, vp]
+        L.ugp_codebook_decode.restype = C.c_int
+        L.ugp_codebook_decode.argtypes = [C.c_int64] + [vp] * 13
         L.ugp_phase_query.restype = C.c_int
         L.ugp_phase_query.argtypes = [C.c_int64] + [vp] * 15
         L.ugp_set_trace_counters.restype = C.c_int
@@ -344,6 +353,46 @@ def phase_query(mtype, albedo3, roughness, sggx6, wo3, wi3, u_eval6, u_sample4, 
                                  _p(wi3), _p(u_eval6), _p(u_sample4), _p(ev), _p(pdf), _p(swi), _p(sw), _p(ok),
                                  C.c_void_p(_stream(stream))), "ugp_phase_query")
     return ev, pdf, swi, sw, ok
+
+
+CODEBOOK_ENTRIES, CODEBOOK_FEATURES, RECORD_BYTES = 4096, 29, 24
+
+
+def codebook_encode(mean, quat, scale, magnitude, mats: "Materials", iters: int = 8, stream=None):
+    """Codebook-quantised records of a scene: returns (codebook (4096, 29) float32, records
+    (n, 24) uint8)."""
+    n = int(mean.shape[0])
+    dev = mean.device
+    _dev(mean, torch.float32, "mean", 3)
+    _dev(quat, torch.float32, "quat", 4, n=n, device=dev)
+    _dev(scale, torch.float32, "scale", 3, n=n, device=dev)
+    _dev(magnitude, torch.float32, "magnitude", n=n, device=dev)
+    if mats.n != n or mats.device != dev:
+        raise ValueError("materials must describe the same primitives on the same device")
+    book = torch.empty((CODEBOOK_ENTRIES, CODEBOOK_FEATURES), dtype=torch.float32, device=dev)
+    rec = torch.empty((n, RECORD_BYTES), dtype=torch.uint8, device=dev)
+    ws = torch.empty(max(int(lib().ugp_codebook_workspace_size(n)), 256), dtype=torch.uint8, device=dev)
+    prims = UgpPrims(n, _p(mean), _p(quat), _p(scale), _p(magnitude))
+    _check(lib().ugp_codebook_encode(C.byref(prims), C.byref(mats.c), int(iters), _p(book), _p(rec), _p(ws),
+                                     ws.numel(), C.c_void_p(_stream(stream))), "ugp_codebook_encode")
+    return book, rec
+
+
+def codebook_decode(records, codebook, disney=True, stream=None):
+    """Decodes records into a dict of the scene arrays (mean, quat, scale, magnitude, sggx, mtype,
+    albedo, roughness, emission, disney)."""
+    _dev(records, torch.uint8, "records", RECORD_BYTES)
+    n, dev = int(records.shape[0]), records.device
+    _dev(codebook, torch.float32, "codebook", CODEBOOK_FEATURES, n=CODEBOOK_ENTRIES, device=dev)
+    f = lambda *shape: torch.empty(shape, dtype=torch.float32, device=dev)
+    out = dict(mean=f(n, 3), quat=f(n, 4), scale=f(n, 3), magnitude=f(n), sggx=f(n, 6),
+               mtype=torch.empty(n, dtype=torch.uint8, device=dev), albedo=f(n, 3), roughness=f(n),
+               emission=f(n, 3), disney=f(n, 9) if disney else None)
+    _check(lib().ugp_codebook_decode(n, _p(records), _p(codebook), _p(out["mean"]), _p(out["quat"]),
+                                     _p(out["scale"]), _p(out["magnitude"]), _p(out["sggx"]), _p(out["mtype"]),
+                                     _p(out["albedo"]), _p(out["roughness"]), _p(out["emission"]),
+                                     _p(out["disney"]), C.c_void_p(_stream(stream))), "ugp_codebook_decode")
+    return out
 
 
 def collect_hits(bvh: Bvh, o, d, t0, t1, cap: int, exclude=None, stream=None):

@@ -102,7 +102,10 @@ def test_batch_many_requests_small_pool(ugp):
         c = s.camera
         a, _ = ugp.Renderer(W, H).render(bvh, mats, ugp.camera_struct(c.eye, c.look, c.up, c.vfov_deg, W, H), lights,
                                          spp=spp, max_depth=depth, seed=seed)
-        assert torch.allclose(q.accum, a, rtol=2e-6 * spp, atol=1e-6)
+        d = (q.accum - a).abs()
+        assert torch.allclose(q.accum, a, rtol=2e-6 * spp, atol=1e-6), (
+            sc_i, W, H, spp, depth, d.max().item(), (d / (a.abs() + 1e-6)).max().item(),
+            int((d > 1e-6 + 2e-6 * spp * a.abs()).sum().item()))
     assert np.all(lat > 0)
 
 
