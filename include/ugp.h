@@ -218,6 +218,44 @@ ugp_status ugp_phase_query(int64_t n, const uint8_t* type, const float* albedo3,
                            float* sample_wi3_out, float* sample_weight3_out, uint8_t* sample_ok_out,
                            void* stream);
 
+/* The paper's own free-flight sampler (Sec. 5.1-5.2), a comparison variant of
+ * ugp_sample_free_flight over an SAH kd-tree: front-to-back traversal, the CDF accumulated
+ * primitive by primitive in each leaf's order, and in a leaf where the CDF reaches 1 the
+ * paper's GPU partition of the ray-node interval into 8 equal bins, each classified again, with
+ * the disambiguation of Eq. 10 in the bin where it reaches 1 (t_u solved in the bin, the
+ * primitive drawn proportionally to I_k(bin start, t_u) among the intervals overlapping the
+ * bin, using u2).  The rule depends on the tree and is biased where several primitives straddle
+ * the saturating distance; ugp_sample_free_flight is exact.
+ *
+ * ugp_build_kdtree builds the tree on the device over the k-ellipsoid boxes of a built BVH's
+ * primitives (binned surface-area heuristic, 8 planes per axis, traversal cost 1, intersection
+ * cost 1.5; primitives straddling a plane go to both sides; at most 28 levels; leaves list
+ * their primitives in ascending order).  It reads two counts per level back to the host, so it
+ * returns after the build has finished on `stream`.  Workspace:
+ * ugp_build_kdtree_workspace_size(n) bytes (256-byte aligned); the tree lives in its first part
+ * and uses the BVH's records, so both must outlive the handle.  Errors: an invalid BVH,
+ * UGP_ERR_NOT_BUILT; NULL or misaligned workspace, UGP_ERR_INVALID_ARG; more than 4 n
+ * primitive references, UGP_ERR_WORKSPACE_TOO_SMALL.
+ * ugp_kdtree_get_info: nodes, references, depth and root box (each output may be NULL).
+ * ugp_kdtree_export copies the nodes (n_nodes x 4 int32 host array: interior (axis, plane as
+ * float bits, left, right), leaf (3, count, first reference, 0)) and the references (n_refs
+ * int32, as the caller's primitive indices) to host memory; synchronous.
+ * ugp_sample_free_flight_kdtree: arguments as for ugp_sample_free_flight, without t_u and
+ * workspace; t_spawn_out (may be NULL) receives the centre of the chosen primitive's clipped
+ * interval.  Asynchronous on `stream`. */
+typedef struct ugp_kdtree ugp_kdtree;
+size_t ugp_build_kdtree_workspace_size(int64_t n_prims);
+ugp_status ugp_build_kdtree(const ugp_bvh* bvh, void* workspace, size_t workspace_bytes, void* stream,
+                            ugp_kdtree** out);
+void ugp_kdtree_release(ugp_kdtree* kd);
+ugp_status ugp_kdtree_get_info(const ugp_kdtree* kd, int64_t* n_nodes, int64_t* n_refs, int32_t* depth,
+                               float* box6);
+ugp_status ugp_kdtree_export(const ugp_kdtree* kd, int32_t* nodes4_host, int32_t* refs_host);
+ugp_status ugp_sample_free_flight_kdtree(const ugp_kdtree* kd, int64_t n_rays, const float* o3, const float* d3,
+                                         const float* t0, const float* t1, const float* u, const float* u2,
+                                         const int32_t* exclude_prim, int32_t* prim_out, float* t_spawn_out,
+                                         uint8_t* status_out, void* stream);
+
 /* All clipped intervals along each ray (hit-set diagnostics).  For ray r,
  * count_out[r] receives the number of primitives whose k-ellipsoid interval
  * meets [t0, t1] (Eq. 4 cut-off, the same test as the queries above); the

@@ -64,6 +64,8 @@ def lib():
                                     i32p]
         L.orc_sample_free_flight_paper_rule.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p,
                                                         f32p, f32p, f32p, f32p, i32p]
+        L.orc_kd_sample_tree.argtypes = [C.POINTER(OrcScene), C.c_double, i32p, C.c_int64, i32p, C.c_int64, f32p,
+                                         C.c_int32, C.c_int64, f32p, f32p, f32p, f32p, f32p, f32p, i32p, f64p]
         L.orc_kd_sample_free_flight.argtypes = [C.POINTER(OrcScene), C.c_double, C.c_int64, f32p, f32p, f32p, f32p,
                                                 f32p, f32p, i32p, f64p, C.POINTER(C.c_int64),
                                                 C.POINTER(C.c_int64)]
@@ -267,6 +269,26 @@ def sample_free_flight_paper_rule(scene, rays, u, u2, eps=0.01):
     lib().orc_sample_free_flight_paper_rule(sr.ref, eps, n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
                                             _ptr(t1, f32p), _ptr(u, f32p), _ptr(u2, f32p), _ptr(prim, i32p))
     return prim
+
+
+def kd_sample_tree(scene, nodes4, refs, box6, rays, u, u2, nbins=8, eps=0.01):
+    """The paper's sampler over a given kd-tree (nodes4 (m, 4) int32, refs int32 primitive indices,
+    box6 the root box), with an ambiguous leaf cut into nbins equal bins of its ray interval (the
+    paper's GPU partition; 0: exact segments). Returns (prim, start of the disambiguated segment
+    or NaN)."""
+    sr = _SceneRef(scene)
+    n = rays.n
+    o, d, t0, t1 = (_c(x, np.float32) for x in (rays.o, rays.d, rays.t0, rays.t1))
+    nodes4 = _c(nodes4, np.int32)
+    refs = _c(refs, np.int32)
+    box6 = _c(box6, np.float32)
+    u, u2 = _c(u, np.float32), _c(u2, np.float32)
+    prim = np.zeros(n, np.int32)
+    amb = np.zeros(n)
+    lib().orc_kd_sample_tree(sr.ref, eps, _ptr(nodes4, i32p), nodes4.shape[0], _ptr(refs, i32p), refs.size,
+                             _ptr(box6, f32p), int(nbins), n, _ptr(o, f32p), _ptr(d, f32p), _ptr(t0, f32p),
+                             _ptr(t1, f32p), _ptr(u, f32p), _ptr(u2, f32p), _ptr(prim, i32p), _ptr(amb, f64p))
+    return prim, amb
 
 
 def kd_sample_free_flight(scene, rays, u, u2, eps=0.01):

@@ -234,6 +234,47 @@ void orc_sample_free_flight_paper_rule(const orc_scene* s, double cutoff_eps, in
 
 // The paper's own sampler over an SAH kd-tree (built once per call): primitive (-1: escape),
 // the start of the ambiguous segment it used (NaN if none), and the nodes and primitives it visited.
+// The paper's sampler over a kd-tree given as arrays (interior node: axis, plane as float bits,
+// left, right; leaf: 3, count, first reference, 0; references are primitive indices), with the
+// root box, and the ambiguous leaf partitioned into nbins equal bins (0: exact segments).
+void orc_kd_sample_tree(const orc_scene* s, double cutoff_eps, const int32_t* nodes4, int64_t n_nodes,
+                        const int32_t* refs, int64_t n_refs, const float* box6, int32_t nbins, int64_t nr,
+                        const float* o3, const float* d3, const float* t0, const float* t1, const float* u,
+                        const float* u2, int32_t* prim_out, double* ambiguous_start_out) {
+  const std::vector<Prim> prims = make_prims(scene_in(s));
+  const double k = cutoff_k(cutoff_eps);
+  KdTree T;
+  T.nodes.resize(size_t(n_nodes));
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    const int32_t* q = nodes4 + 4 * i;
+    KdNode& nd = T.nodes[size_t(i)];
+    if (q[0] == 3) {
+      nd.axis = -1;
+      nd.count = q[1];
+      nd.first = q[2];
+    } else {
+      float pos;
+      std::memcpy(&pos, &q[1], 4);
+      nd.axis = q[0];
+      nd.pos = pos;
+      nd.child[0] = q[2];
+      nd.child[1] = q[3];
+    }
+  }
+  T.leaf_ids.assign(refs, refs + n_refs);
+  for (int a = 0; a < 3; ++a) {
+    T.lo[a] = box6[a];
+    T.hi[a] = box6[3 + a];
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < nr; ++r) {
+    KdStats st;
+    prim_out[r] = kd_sample_free_flight(T, prims, load3(o3 + 3 * r), load3(d3 + 3 * r), t0[r], t1[r], k, u[r], u2[r],
+                                        &st, nbins);
+    ambiguous_start_out[r] = st.ambiguous_start;
+  }
+}
+
 void orc_kd_sample_free_flight(const orc_scene* s, double cutoff_eps, int64_t nr, const float* o3, const float* d3,
                                const float* t0, const float* t1, const float* u, const float* u2, int32_t* prim_out,
                                double* ambiguous_start_out, int64_t* nodes_out, int64_t* prims_out) {

@@ -139,6 +139,7 @@ struct KdSample {
   const std::vector<Prim>& prims;
   V3 o, d;
   double t0, t1, k, u, u2;
+  int nbins = 0;  // > 0: the paper's GPU partition of an ambiguous leaf into nbins equal bins
   double cdf = 0.0;
   int32_t result = -1;
   bool done = false;
@@ -221,6 +222,71 @@ void leaf(KdSample& S, const KdTree& T, const KdNode& nd, double ta, double tb) 
     take_in_order(S, ids, mass);
     return;
   }
+  if (S.nbins > 0) {
+    // the paper's GPU partition: equal bins of the ray-node interval [ta, tb], each classified
+    // like a leaf; in the bin where the CDF reaches 1, t_u is solved from the bin's start and the
+    // primitive drawn proportionally to I_k(bin start, t_u) among those overlapping the bin
+    const double w = (tb - ta) / S.nbins;
+    for (int b = 0; b < S.nbins; ++b) {
+      const double s0 = ta + w * b, s1 = b + 1 == S.nbins ? tb : ta + w * (b + 1);
+      std::vector<const Hit*> act;
+      std::vector<int32_t> act_ids;
+      std::vector<double> bin_mass;
+      double bin_total = 0.0;
+      for (const Hit& h : hs) {
+        const double x = std::max(h.a, s0), y = std::min(h.b, s1);
+        if (!(x < y)) continue;
+        act.push_back(&h);
+        act_ids.push_back(h.id);
+        bin_mass.push_back(0.5 * ray_integral(h, x, y));
+        bin_total += bin_mass.back();
+      }
+      if (act.empty()) continue;
+      if (act.size() == 1 || S.cdf + bin_total < 1.0) {
+        if (take_in_order(S, act_ids, bin_mass)) return;
+        continue;
+      }
+      // F(t) = cdf + sum 1/2 I_k(max(a_k, s0), min(b_k, t)) = u, bracketed Newton
+      auto F = [&](double t, double* fp) {
+        double f = S.cdf - S.u, g = 0.0;
+        for (const Hit* h : act) {
+          const double x = std::max(h->a, s0), y = std::min(h->b, t);
+          if (x < y) f += 0.5 * ray_integral(*h, x, y);
+          if (h->a <= t && t <= h->b) g += 0.5 * gauss_at(*h, t);
+        }
+        *fp = g;
+        return f;
+      };
+      double lo = s0, hi = s1, t = 0.5 * (s0 + s1);
+      for (int it = 0; it < 400; ++it) {
+        double fp;
+        const double f = F(t, &fp);
+        if (f == 0.0) break;
+        (f < 0 ? lo : hi) = t;
+        double tn = fp > 0 ? t - f / fp : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        const bool stop = std::fabs(tn - t) <= 1e-16 * std::max(1.0, std::fabs(t)) ||
+                          hi - lo <= 1e-16 * std::max(1.0, std::fabs(t));
+        t = tn;
+        if (stop) break;
+      }
+      S.st.ambiguous_start = s0;
+      std::vector<double> wk;
+      double w_total = 0.0;
+      for (const Hit* h : act) {
+        const double x = std::max(h->a, s0), y = std::min(h->b, t);
+        wk.push_back(x < y ? ray_integral(*h, x, y) : 0.0);
+        w_total += wk.back();
+      }
+      double c = 0.0;
+      size_t k = 0;
+      while (k + 1 < wk.size() && !(wk[k] > 0.0 && S.u2 * w_total < c + wk[k])) c += wk[k++];
+      S.result = act_ids[k];
+      S.done = true;
+      return;
+    }
+    return;
+  }
   std::vector<double> ends;
   for (const Hit& h : hs) {
     ends.push_back(h.a);
@@ -292,8 +358,9 @@ void traverse(KdSample& S, const KdTree& T, int node, double ta, double tb) {
 }  // namespace
 
 int32_t kd_sample_free_flight(const KdTree& T, const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
-                              double k, double u, double u2, KdStats* stats) {
+                              double k, double u, double u2, KdStats* stats, int nbins) {
   KdSample S{prims, o, d, t0, t1, k, u, u2};
+  S.nbins = nbins;
   S.st.ambiguous_start = std::numeric_limits<double>::quiet_NaN();
   if (!T.nodes.empty()) {
     // the ray's range inside the root box

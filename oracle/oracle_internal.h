@@ -151,8 +151,10 @@ struct KdStats {
   double ambiguous_start = 0.0;  // start of the ambiguous segment used (NaN if none)
 };
 KdTree kd_build(const std::vector<Prim>& prims, double k);
+// nbins = 0: exact line-sweep segments in a leaf where the CDF reaches 1 (the paper's CPU
+// partition); nbins > 0: that many equal bins of the ray-node interval (its GPU partition).
 int32_t kd_sample_free_flight(const KdTree& T, const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
-                              double k, double u, double u2, KdStats* stats);
+                              double k, double u, double u2, KdStats* stats, int nbins = 0);
 
 double erfinv(double y);
 double race_exponential(double u2, int32_t k);

@@ -119,6 +119,19 @@ def lib():
         L.ugp_sample_free_flight_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.ugp_trace_transmittance_exponential.restype = C.c_int
         L.ugp_trace_transmittance_exponential.argtypes = [vp, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.ugp_build_kdtree_workspace_size.restype = C.c_size_t
+        L.ugp_build_kdtree_workspace_size.argtypes = [C.c_int64]
+        L.ugp_build_kdtree.restype = C.c_int
+        L.ugp_build_kdtree.argtypes = [vp, vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.ugp_kdtree_release.restype = None
+        L.ugp_kdtree_release.argtypes = [vp]
+        L.ugp_kdtree_get_info.restype = C.c_int
+        L.ugp_kdtree_get_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                          C.POINTER(C.c_float)]
+        L.ugp_kdtree_export.restype = C.c_int
+        L.ugp_kdtree_export.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.ugp_sample_free_flight_kdtree.restype = C.c_int
+        L.ugp_sample_free_flight_kdtree.argtypes = [vp, C.c_int64] + [vp] * 10 + [vp]
         L.ugp_codebook_size.restype = C.c_size_t
         L.ugp_codebook_size.argtypes = []
         L.ugp_codebook_workspace_size.restype = C.c_size_t
@@ -353,6 +366,61 @@ def phase_query(mtype, albedo3, roughness, sggx6, wo3, wi3, u_eval6, u_sample4, 
                                  _p(wi3), _p(u_eval6), _p(u_sample4), _p(ev), _p(pdf), _p(swi), _p(sw), _p(ok),
                                  C.c_void_p(_stream(stream))), "ugp_phase_query")
     return ev, pdf, swi, sw, ok
+
+
+class KdTree:
+    """The paper's SAH kd-tree over a built BVH's primitives (the comparison sampler's structure)."""
+
+    def __init__(self, bvh: Bvh, stream=None):
+        nb = int(lib().ugp_build_kdtree_workspace_size(int(bvh.n)))
+        if nb == 0:
+            raise UgpError("ugp_build_kdtree_workspace_size failed")
+        self.bvh = bvh
+        self.workspace = torch.empty(nb, dtype=torch.uint8, device=bvh.workspace.device)
+        h = vp()
+        _check(lib().ugp_build_kdtree(C.c_void_p(bvh.handle), _p(self.workspace), nb, C.c_void_p(_stream(stream)),
+                                      C.byref(h)), "ugp_build_kdtree")
+        self.handle = h.value
+
+    def info(self) -> dict:
+        nn, nr, dp = C.c_int64(), C.c_int64(), C.c_int32()
+        box = (C.c_float * 6)()
+        _check(lib().ugp_kdtree_get_info(C.c_void_p(self.handle), C.byref(nn), C.byref(nr), C.byref(dp), box),
+               "ugp_kdtree_get_info")
+        return dict(n_nodes=nn.value, n_refs=nr.value, depth=dp.value, box=list(box))
+
+    def export(self):
+        """(nodes (m, 4) int32, refs int32 primitive indices, root box (6,) float32) on the host."""
+        import numpy as np
+        inf = self.info()
+        nodes = np.zeros((inf["n_nodes"], 4), np.int32)
+        refs = np.zeros(inf["n_refs"], np.int32)
+        i32 = C.POINTER(C.c_int32)
+        _check(lib().ugp_kdtree_export(C.c_void_p(self.handle), nodes.ctypes.data_as(i32), refs.ctypes.data_as(i32)),
+               "ugp_kdtree_export")
+        return nodes, refs, np.array(inf["box"], np.float32)
+
+    def sample_free_flight(self, o, d, t0, t1, u, u2, exclude=None, stream=None):
+        """(prim (-1: escape), t_spawn, status) of the paper's sampler."""
+        n = _rays(o, d, t0, t1, exclude, u=u, u2=u2)
+        prim = torch.empty(n, dtype=torch.int32, device=o.device)
+        tsp = torch.empty(n, dtype=torch.float32, device=o.device)
+        st = torch.empty(n, dtype=torch.uint8, device=o.device)
+        _check(lib().ugp_sample_free_flight_kdtree(C.c_void_p(self.handle), n, _p(o), _p(d), _p(t0), _p(t1), _p(u),
+                                                   _p(u2), _p(exclude), _p(prim), _p(tsp), _p(st),
+                                                   C.c_void_p(_stream(stream))), "ugp_sample_free_flight_kdtree")
+        return prim, tsp, st
+
+    def release(self):
+        if getattr(self, "handle", 0):
+            lib().ugp_kdtree_release(C.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
 
 CODEBOOK_ENTRIES, CODEBOOK_FEATURES, RECORD_BYTES = 4096, 29, 24

@@ -723,16 +723,18 @@ def test_paper_rule_bias_at_the_saturating_distance(orc):
 
 
 # ---------------------------------------------------------------------------- f2: the paper's kd-tree sampler
-def _rule_law(s, o, d, h, s0):
+def _rule_law(s, o, d, h, s0, s1=None):
     """P(k) of the paper's rule when its ambiguous segment starts at s0: 1/2 I_k up to s0, then
     int_s0^t_sat I_k(s0, t) / sum_A I_j(s0, t) dF(t), from the densities of Eq. 1 on a grid; also
-    the exact law 1/2 I_k(a_k, min(b_k, t_sat)) from the same grid."""
+    the exact law 1/2 I_k(a_k, min(b_k, t_sat)) from the same grid. The active set A holds the
+    intervals containing s0, or with `s1` (a bin [s0, s1] of the GPU partition) every interval
+    overlapping the bin."""
     tg, G = _grid_profiles(s, o, d, h, 0.0, 2.0, 400001)
     dt = tg[1] - tg[0]
     Ik = np.concatenate([np.zeros((G.shape[0], 1)), np.cumsum(0.5 * (G[:, 1:] + G[:, :-1]) * dt, 1)], 1)
     t_sat = np.interp(1.0, 0.5 * Ik.sum(0), tg)
     at = lambda row, x: np.interp(x, tg, row)
-    act = (h["a"] <= s0) & (h["b"] > s0)
+    act = (h["a"] <= s0) & (h["b"] > s0) if s1 is None else (h["a"] < s1) & (h["b"] > s0)
     p = np.array([0.5 * at(Ik[j], s0) for j in range(len(h["ids"]))])
     sel = (tg > s0) & (tg <= t_sat)
     Iseg = Ik[:, sel] - np.array([at(Ik[j], s0) for j in range(len(h["ids"]))])[:, None]
@@ -811,3 +813,48 @@ def test_kd_sampler_follows_the_rule_law_at_its_ambiguous_segment(orc):
     dof = int(m.sum()) - 1
     assert ((counts[m] - p_rule[m] * n) ** 2 / (p_rule[m] * n)).sum() < chi2d.ppf(0.999, dof)
     assert ((counts[m] - exact[m] * n) ** 2 / np.maximum(exact[m] * n, 1e-9)).sum() > 10 * chi2d.ppf(0.999, dof)
+
+
+def _one_leaf_tree(s):
+    """A kd-tree of one leaf holding every primitive in index order, and a root box around them."""
+    nodes = np.array([[3, s.n, 0, 0]], np.int32)
+    return nodes, np.arange(s.n, dtype=np.int32), np.array([-10, -10, -10, 10, 10, 10], np.float32)
+
+
+def test_kd_gpu_partition_follows_the_rule_law_in_its_ambiguous_bin(orc):
+    """The paper's GPU partition (Sec. 5.2): the ambiguous leaf's ray interval cut into equal
+    bins, each classified like a segment. On a one-leaf tree over a saturating ray, bins before
+    the saturating one take their primitives' masses in order, and the saturating bin [s0, s1]
+    picks proportionally to I_k(s0, t_u) among the intervals overlapping it: the samples follow
+    that law (grid integration of Eq. 1) and reject the exact law; the same tree with exact
+    segments disambiguates at a different start."""
+    from scipy.stats import chi2 as chi2d
+    s = _dense_cluster(n=8, seed=60, boost=5.0)
+    o, d = _exp_ray()
+    h = orc.hits(s, o, d, 0.0, 2.0)
+    nodes, refs, box = _one_leaf_tree(s)
+    n = 400000
+    r = scenes.Rays(np.tile(o, (n, 1)), np.tile(d, (n, 1)), np.zeros(n, np.float32), np.full(n, 2.0, np.float32))
+    u, u2 = scenes.uniforms24(150, n), scenes.uniforms24(151, n)
+    k, amb = orc.kd_sample_tree(s, nodes, refs, box, r, u, u2, nbins=8)
+    amb_f = amb[np.isfinite(amb)]
+    assert amb_f.size > 0.05 * n and np.ptp(amb_f) == 0.0
+    s0 = float(amb_f[0])
+    # the bin the partition used: the ray-node interval is the ray clipped to the root box
+    ta, tb = 0.0, 2.0
+    w = (tb - ta) / 8
+    j = int(round((s0 - ta) / w))
+    assert abs(ta + j * w - s0) < 1e-12
+    p_rule, act, exact = _rule_law(s, o, d, h, s0, ta + (j + 1) * w)
+    assert act.sum() >= 2 and abs(p_rule.sum() - 1) < 1e-3
+    counts = np.array([(k == i).sum() for i in h["ids"]], np.float64)
+    m = p_rule * n > 5
+    dof = int(m.sum()) - 1
+    assert ((counts[m] - p_rule[m] * n) ** 2 / (p_rule[m] * n)).sum() < chi2d.ppf(0.999, dof)
+    assert ((counts[m] - exact[m] * n) ** 2 / np.maximum(exact[m] * n, 1e-9)).sum() > 10 * chi2d.ppf(0.999, dof)
+    _, amb0 = orc.kd_sample_tree(s, nodes, refs, box, r, u, u2, nbins=0)
+    assert np.nanmax(amb0) != s0
+    # escape where the exact sampler escapes
+    ex = orc.sample_free_flight(s, r, u, u2)
+    near = np.abs(u - ex["F_end"]) < 1e-12
+    assert np.array_equal((k < 0)[~near], (ex["prim"] < 0)[~near])
