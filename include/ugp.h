@@ -175,7 +175,7 @@ size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
  * call cudaMalloc or hand the library a workspace -- for example code that runs while a
  * host application owns every device allocation, or a real-time loop that must not
  * touch the allocator.  The scratch queue lives in a fixed array of device memory inside
- * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 5.0 MB); every GPU that
+ * the library image, sized for UGP_NOALLOC_MAX_RAYS rays (about 9.7 MB); every GPU that
  * loads the library holds it until the process exits.  Without the per-ray slot lists of
  * the regular entry point, its warp pass finds dense intervals by traversal; the results
  * are the same.

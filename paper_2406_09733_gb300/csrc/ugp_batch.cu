@@ -501,7 +501,7 @@ ugp_status launch_wave(const BState& S, const WaveGrids& g, cudaGraphConditional
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }
-constexpr int kWaveKernels = 10;
+constexpr int kWaveKernels = 9;  // claim, regen, extend, the two finish passes, shade, shadow, retire, cond
 
 // Instantiated graphs: one per (workspace, pool, device); the body reads everything else from
 // the workspace, so a graph serves every batch that fits its workspace.

@@ -12,13 +12,14 @@
 //      F' = 1/2 sum G (Eq. 9) summed across its lanes, and draws the primitive with the
 //      exponential race (smallest E_k / G_k(x_{t_u})) as an argmin across its lanes.
 // A ray whose slot list overflowed, or that has more intervals than a half-warp holds (128), goes
-// to k_dense_big<256>: one warp per ray rebuilds the intervals from the list or by a warp-parallel
-// traversal (up to 32 nodes per step from a shared stack) and solves with 32 lanes. Beyond 256
-// intervals the ray goes on to k_dense_big<1024>, one warp per block; rays through the cores of
-// dense clusters need it: there hundreds of ellipsoids contain the root itself, so no narrower
-// bracket would hold fewer. Beyond 1024 every interval's contribution goes to 32 sub-bins of the
-// bracket (fixed-point shared-memory atomics), the bracket moves to the crossing sub-bin, and the
-// rebuild repeats.
+// to k_dense_big: one warp per ray rebuilds the intervals from the list or by a warp-parallel
+// traversal (up to 32 nodes per step from a shared stack) and solves with 32 lanes. Its intervals
+// (up to kBigCap = 2048) live in a slot of global memory that the warp owns, so the pass is not
+// held to a few warps per SM by shared memory; rays through the cores of dense clusters need the
+// room: there hundreds of ellipsoids contain the root itself, so no narrower bracket would hold
+// fewer. Beyond kBigCap every interval's contribution goes to 32 sub-bins of the bracket
+// (fixed-point shared-memory atomics), the bracket moves to the crossing sub-bin, and the rebuild
+// repeats.
 //
 // The result is the same function of (u, u2) as the per-thread paths: the same F, root and race.
 // It is also bit-for-bit independent of the order in which the intervals were collected and of
@@ -36,9 +37,7 @@ namespace {
 constexpr int kDWarps = 4;           // warps per block of the main pass (two rays each)
 constexpr int kHalf = 16;            // lanes of the main pass that finish one ray
 constexpr int kDCap = 128;           // intervals a half-warp of the main pass holds
-constexpr int kDCapW = 256;          // intervals per ray of k_dense_big<256> (4 warps per block)
-constexpr int kDCapH = 1024;         // intervals per ray of k_dense_big<1024> (1 warp per block)
-constexpr int kDStackMin = 1024;     // traversal stack of a big-pass warp (2 kCap when larger)
+constexpr int kDStack = 1024;        // traversal stack of a big-pass warp
 constexpr int kDLevels = 8;          // bracket refinements when the intervals do not fit
 constexpr int kDNewton = 64;
 constexpr int kDBisectAfter = 24;    // Newton / false-position steps before plain bisection
@@ -97,14 +96,12 @@ struct Intervals {
 struct WarpSmem {  // main pass: the two half-warps' slices
   Intervals<2 * kDCap> iv;
 };
-template <int kCap>
-struct WarpSmemBig {  // big passes: one ray per warp
-  static constexpr int kStack = 2 * kCap > kDStackMin ? 2 * kCap : kDStackMin;
-  Intervals<kCap> iv;
+struct WarpSmemBig {  // big pass: one ray per warp, its intervals in global memory
+  static constexpr int kStack = kDStack;
   int stk[kStack];             // traversal stack
   unsigned long long bin[32];  // sub-bins, units of 2^-40
 };
-static_assert(kDCap >= kHalf && kDCapW >= kListCap && kDCapH > kDCapW, "capacities");
+static_assert(kDCap >= kHalf && kBigCap >= kListCap, "capacities");
 
 constexpr float kFScale = 1099511627776.f;  // 2^40: unit of the fixed-point F sums
 constexpr float kFUnit = 9.094947017729282e-13f;
@@ -418,7 +415,7 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
       big = n > kDCap;
     }
     const unsigned tp = g.total(np);
-    if (big) {  // k_dense_big<256> rebuilds and finishes the ray
+    if (big) {  // k_dense_big rebuilds and finishes the ray
       if (g.lane == 0) {
         hand_on(q.count + 2, q.wide, j);
         if (O.stats) atomicAdd(O.stats + 1, (unsigned long long)tp);
@@ -432,18 +429,21 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
   }
 }
 
-// The rays a smaller pass handed on (count of them in `list`), one warp each, kWarps warps per
-// block, up to kCap intervals per ray; a ray with more is handed on to the next pass when there
-// is one (`next_count`), else its bracket is narrowed by sub-bins.
+// The rays the first pass handed on (count of them in `list`), one warp each, kWarps warps per
+// block, up to kCap intervals per ray in the warp's slot of q.big_iv; a ray with more has its
+// bracket narrowed by sub-bins (or is handed on to a next pass when `next_count` is given).
 template <int kCap, int kWarps>
 __global__ void __launch_bounds__(32 * kWarps) k_dense_big(TraceScene sc0, DenseQueue q, const int* count_p,
                                                            const int* __restrict__ list, int* next_count,
                                                            int* __restrict__ next_list, Outputs O) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  WarpSmemBig<kCap>& W = reinterpret_cast<WarpSmemBig<kCap>*>(dsm)[threadIdx.x >> 5];
+  WarpSmemBig& W = reinterpret_cast<WarpSmemBig*>(dsm)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const Grp<32> gw{kFull, lane, 0};
-  const Iv iv = W.iv.view(0, kCap);
+  // this warp's interval slot (the grid has at most q.big_slots warps)
+  float* slot = q.big_iv + size_t(blockIdx.x * kWarps + (threadIdx.x >> 5)) * (size_t(kCap) * 9);
+  const Iv iv{slot, slot + kCap, slot + 2 * kCap, slot + 3 * kCap, slot + 4 * kCap, slot + 5 * kCap,
+              slot + 6 * kCap, slot + 7 * kCap, reinterpret_cast<int*>(slot + 8 * kCap), kCap};
   const int count = *reinterpret_cast<const volatile int*>(count_p);
   for (int h = blockIdx.x * kWarps + (threadIdx.x >> 5); h < count; h += gridDim.x * kWarps) {
     const int j = list[h];
@@ -462,8 +462,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_dense_big(TraceScene sc0, Dense
           collect_one(gw, iv, R.sc, R.ray, lo, hi, R.t0, R.t1, R.excl, e < R.nlist ? __ldg(R.list + e) : -1, n, np);
         }
       } else {
-        warp_traverse<WarpSmemBig<kCap>::kStack>(W.stk, R.sc, R.ray, lo, hi, lane, st, nn, [&](int slot) {
-          collect_one(gw, iv, R.sc, R.ray, lo, hi, R.t0, R.t1, R.excl, slot, n, np);
+        warp_traverse<WarpSmemBig::kStack>(W.stk, R.sc, R.ray, lo, hi, lane, st, nn, [&](int s) {
+          collect_one(gw, iv, R.sc, R.ray, lo, hi, R.t0, R.t1, R.excl, s, n, np);
         });
       }
       __syncwarp();
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_dense_big(TraceScene sc0, Dense
             bin_one(e < R.nlist ? __ldg(R.list + e) : -1);
           }
         } else {
-          warp_traverse<WarpSmemBig<kCap>::kStack>(W.stk, R.sc, R.ray, lo, hi, lane, st, nn, bin_one);
+          warp_traverse<WarpSmemBig::kStack>(W.stk, R.sc, R.ray, lo, hi, lane, st, nn, bin_one);
         }
         __syncwarp();
         if (st != UGP_RAY_OK) break;
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_dense_big(TraceScene sc0, Dense
 }  // namespace
 
 // Resident-block grid of each pass (set once, before any capture).
-static int g_dense_grid = 0, g_wide_grid = 0, g_heavy_grid = 0;
+static int g_dense_grid = 0, g_wide_grid = 0;
 constexpr int kWideWarps = 4;
 
 template <class K>
@@ -570,10 +570,9 @@ ugp_status dense_prepare() {
   UGP_CUDA_CHECK(cudaGetDevice(&dev));
   UGP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (sms <= 0) sms = 1;
-  ugp_status s = big_grid(k_dense_big<kDCapW, kWideWarps>, 32 * kWideWarps,
-                          sizeof(WarpSmemBig<kDCapW>) * kWideWarps, sms, &g_wide_grid);
+  ugp_status s = big_grid(k_dense_big<kBigCap, kWideWarps>, 32 * kWideWarps, sizeof(WarpSmemBig) * kWideWarps, sms,
+                          &g_wide_grid);
   if (s != UGP_OK) return s;
-  if ((s = big_grid(k_dense_big<kDCapH, 1>, 32, sizeof(WarpSmemBig<kDCapH>), sms, &g_heavy_grid)) != UGP_OK) return s;
   int grid = 0;
   if ((s = big_grid(k_dense, 32 * kDWarps, sizeof(WarpSmem) * kDWarps, sms, &grid)) != UGP_OK) return s;
   g_dense_grid = grid;
@@ -591,12 +590,13 @@ ugp_status launch_dense(const TraceScene& sc, const DenseQueue& q, int64_t n_hos
   prof_begin(kStDense, stream);
   k_dense<<<cap_grid((max_slots + 64 * kDWarps - 1) / (64 * kDWarps), g_dense_grid), 32 * kDWarps,
             sizeof(WarpSmem) * kDWarps, stream>>>(sc, q, n_host, n_dev, O);
-  k_dense_big<kDCapW, kWideWarps><<<cap_grid((max_slots + kWideWarps - 1) / kWideWarps, g_wide_grid),
-                                    32 * kWideWarps, sizeof(WarpSmemBig<kDCapW>) * kWideWarps, stream>>>(
-      sc, q, q.count + 2, q.wide, q.count + 3, q.heavy, O);
-  k_dense_big<kDCapH, 1><<<cap_grid(max_slots, g_heavy_grid), 32, sizeof(WarpSmemBig<kDCapH>), stream>>>(
-      sc, q, q.count + 3, q.heavy, nullptr, nullptr, O);
-  prof_end(kStDense, stream, 3);
+  // at most one warp per interval slot
+  const int slot_blocks = q.big_slots / kWideWarps;
+  k_dense_big<kBigCap, kWideWarps><<<cap_grid((max_slots + kWideWarps - 1) / kWideWarps,
+                                              g_wide_grid < slot_blocks ? g_wide_grid : slot_blocks),
+                                     32 * kWideWarps, sizeof(WarpSmemBig) * kWideWarps, stream>>>(
+      sc, q, q.count + 2, q.wide, nullptr, nullptr, O);
+  prof_end(kStDense, stream, 2);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }

@@ -21,9 +21,11 @@ struct DenseQueue {
   int* nlist;    // primitive slots the scan recorded for the ray (> kListCap: list incomplete)
   int* scene;    // index of the ray's scene in `scenes` (batched rendering)
   int* wide;     // slots the finish's first pass handed to its second (count[2] of them)
-  int* heavy;    // slots its second pass handed to its third (count[3] of them)
+  int* heavy;    // unused
   const int* list;  // per-ray slot lists, kListCap ints at list + idx * kListCap (NULL: none)
   const TraceScene* scenes;  // device table of scenes (NULL: every ray uses the launch's scene)
+  float* big_iv;  // interval storage of the second pass: big_slots slots of kBigCap intervals
+  int big_slots;
 };
 
 constexpr int kDenseCols = 19;
@@ -32,9 +34,18 @@ constexpr int kDenseCols = 19;
 constexpr int kListCap = 256;
 inline size_t slot_list_bytes(int64_t n) { return align256(size_t(n) * kListCap * 4); }
 
-// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header); the slot
-// lists, when used, take slot_list_bytes(cap) more.
-inline size_t dense_queue_bytes(int64_t cap) { return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4); }
+// The finish's second pass keeps each ray's intervals (up to kBigCap, 9 words each) in a slot of
+// global memory owned by one warp; a queue for `cap` rays has big_slots(cap) of them, one per
+// 1024 rays between 4 and 2432 (the warps a GB300 keeps resident in that pass).
+constexpr int kBigCap = 2048;
+constexpr int64_t big_slots(int64_t cap) { return cap / 1024 < 4 ? 4 : (cap / 1024 > 2432 ? 2432 : cap / 1024); }
+constexpr size_t big_slot_bytes() { return size_t(kBigCap) * 9 * 4; }
+
+// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header, then the
+// second pass's interval slots); the slot lists, when used, take slot_list_bytes(cap) more.
+constexpr size_t dense_queue_bytes(int64_t cap) {
+  return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4) + size_t(big_slots(cap)) * big_slot_bytes();
+}
 
 inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   char* p = static_cast<char*>(base);
@@ -53,6 +64,8 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   q.heavy = reinterpret_cast<int*>(F(18));
   q.list = nullptr;
   q.scenes = nullptr;
+  q.big_iv = reinterpret_cast<float*>(p + 256 + kDenseCols * col);
+  q.big_slots = int(big_slots(cap));
   return q;
 }
 

@@ -70,7 +70,7 @@ void clear_error();
 // Trace statistics pointer (device), or nullptr.
 unsigned long long* trace_counters();
 
-inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Launch accounting and optional event timing (defined in ugp_api.cu).  Wrap each launch:
 //   prof_begin(stage, stream); kernel<<<...>>>(...); prof_end(stage, stream, n_kernels);

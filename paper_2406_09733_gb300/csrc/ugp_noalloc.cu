@@ -12,10 +12,11 @@
 namespace ugp {
 namespace {
 
-// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header and kDenseCols columns of
-// 4-byte entries, each padded to 256 bytes (the layout of dense_queue_at).
+// Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header, kDenseCols columns of
+// 4-byte entries, each padded to 256 bytes, and the second finish pass's interval slots (the
+// layout of dense_queue_at).
 constexpr int64_t kNoallocMaxRays = UGP_NOALLOC_MAX_RAYS;
-constexpr size_t kNoallocBytes = 256 + kDenseCols * ((size_t(kNoallocMaxRays) * 4 + 255) & ~size_t(255));
+constexpr size_t kNoallocBytes = dense_queue_bytes(kNoallocMaxRays);
 
 static __device__ __align__(256) unsigned char g_ff_scratch[kNoallocBytes];
 

@@ -370,8 +370,8 @@ def _rays_at_centre(n, seed, radius, jitter):
 
 def test_free_flight_hundreds_of_overlaps(gpu, orc):
     """A cluster core inside several hundred ellipsoids: most sampled points lie in hundreds of
-    intervals, more than the finish's first two passes hold (128 and 256), so these rays go to
-    its third (up to 1024 intervals)."""
+    intervals, more than the finish's first pass holds (128), so these rays go to its second (up
+    to 2048 intervals, in global memory)."""
     from paper_2406_09733_gb300 import ugp
     torch = gpu
     s = _cluster_scene(800, 51, 0.01, 0.02, 0.04, 0.3)
@@ -387,12 +387,12 @@ def test_free_flight_hundreds_of_overlaps(gpu, orc):
 
 
 def test_free_flight_overlap_limit_is_reported(gpu):
-    """More ellipsoids containing the sampled point than the finish's third pass holds (1024): the
-    bracket cannot be narrowed below them, and such a ray ends with UGP_RAY_ITER_LIMIT (a status,
-    not a silent escape); rays that miss the core are unaffected."""
+    """More ellipsoids containing the sampled point than the finish's second pass holds (2048):
+    the bracket cannot be narrowed below them, and such a ray ends with UGP_RAY_ITER_LIMIT (a
+    status, not a silent escape); rays that miss the core are unaffected."""
     from paper_2406_09733_gb300 import ugp
     torch = gpu
-    s = _cluster_scene(1600, 55, 0.005, 0.03, 0.05, 0.05)
+    s = _cluster_scene(3200, 55, 0.005, 0.03, 0.05, 0.025)
     r = _rays_at_centre(64, 56, 0.4, 0.002)
     far = _rays_at_centre(64, 57, 0.4, 0.002)
     far.o[:] += np.float32(1.0)             # parallel rays 1.0 away: they miss every ellipsoid
