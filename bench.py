@@ -63,8 +63,8 @@ def parse_args(argv=None):
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
     p.add_argument("--mse-width", type=int, default=480, help="image width of the MSE study")
     p.add_argument("--mse-height", type=int, default=270, help="image height of the MSE study")
-    p.add_argument("--mse-ref-spp", type=int, default=2048, help="spp of the plain reference")
-    p.add_argument("--mse-budget-spp", type=int, default=256, help="plain spp that set the time budget")
+    p.add_argument("--mse-ref-spp", type=int, default=1024, help="spp of the plain reference")
+    p.add_argument("--mse-budget-spp", type=int, default=128, help="plain spp that set the time budget")
     p.add_argument("--mse-train-spp", type=int, default=32, help="guided spp that also train the guide")
     p.add_argument("--mse-minibatch", type=int, default=1 << 14)
     p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
@@ -73,6 +73,9 @@ def parse_args(argv=None):
     p.add_argument("--no-rf", action="store_true", help="skip the radiance-field render study")
     p.add_argument("--no-exp", action="store_true", help="skip the exponential-variant query study")
     p.add_argument("--no-emitters", action="store_true", help="skip the emitter light-sampling study")
+    p.add_argument("--no-kdtree", action="store_true", help="skip the paper's kd-tree sampler study")
+    p.add_argument("--no-codebook", action="store_true", help="skip the codebook-record study")
+    p.add_argument("--kd-prims", type=int, default=1_000_000, help="primitives of the kd-tree study's scene")
     p.add_argument("--serve-requests", type=int, default=64)
     p.add_argument("--serve-spp-max", type=int, default=64,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
@@ -110,7 +113,13 @@ GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 # DRAM bytes (read + write) per k_extend launch of a workload, averaged over the launches of one
 # step, from one ncu capture of the current kernel (profiles/k_extend_dram_*.md); None for any
 # other workload, and to be reset whenever k_extend changes.
-EXTEND_TRAFFIC_BYTES = {(5_500_000, 1920, 1080, 12, "A", 0.1): 2269.13e6}
+EXTEND_TRAFFIC_BYTES = {}
+
+# Algorithmic bytes of a free-flight query are counted against a fixed reference traversal, so
+# that a tree that makes a query visit more nodes cannot raise the figure: the nodes and records
+# a query loads on the binary LBVH of the same build (64 B each), measured once per workload
+# with that traversal's counters. Workloads without a reference use the live counts.
+REFERENCE_COUNTS = {(5_500_000, 1920, 1080, 12, "A", 0.1): (371.85, 199.31)}
 
 
 def workload_key(args):
@@ -529,7 +538,9 @@ def run_ugp(args):
     # path state it reads (queue index, origin, direction, exclusion: 32 B) and writes (16 B)
     nodes_per_query = st[0] / max(st[2], 1)
     prims_per_query = st[1] / max(st[2], 1)
-    alg_bytes_per_launch = ((st[0] + st[1]) * 64 + 48 * st[2]) / (args.depth + 1)
+    ref_counts = REFERENCE_COUNTS.get(workload_key(args))
+    ref_nodes, ref_prims = ref_counts if ref_counts else (nodes_per_query, prims_per_query)
+    alg_bytes_per_launch = ((ref_nodes + ref_prims) * 64 + 48) * st[2] / (args.depth + 1)
     ext_launches = prof["extend"][1]
     avg_ext_ms = prof["extend"][0] / max(ext_launches, 1)
     queries_per_step = c[0] / args.steps
@@ -547,7 +558,7 @@ def run_ugp(args):
         cnt3 = torch.zeros(3, dtype=torch.int64, device=dev)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        n_e2e = max(1, min(args.steps, 8))
+        n_e2e = max(1, min(args.steps, 4))
         for k in range(n_e2e):
             for key, v in pinned.items():
                 d[key].copy_(v, non_blocking=True)
@@ -581,6 +592,18 @@ def run_ugp(args):
     expo = None
     if rank == 0 and world == 1 and not args.no_exp:
         expo = exponential_study(args, d, scene, dev)
+    kdst = None
+    if rank == 0 and world == 1 and not args.no_kdtree:
+        try:
+            kdst = kdtree_study(args, dev)
+        except Exception as e:  # reported in the line; the measured step above stands
+            kdst = {"error": repr(e)}
+    cbst = None
+    if rank == 0 and world == 1 and not args.no_codebook:
+        try:
+            cbst = codebook_study(args, d, mats, scene, dev)
+        except Exception as e:
+            cbst = {"error": repr(e)}
     emit = None
     if rank == 0 and world == 1 and not args.no_emitters:
         try:
@@ -603,11 +626,18 @@ def run_ugp(args):
                          "frac": (achieved_gbs / peak) if achieved_gbs else None, "peak_note": peak_note,
                          "traffic": extend_traffic(args),
                          "algorithmic_bytes_per_launch": alg_bytes_per_launch,
+                         "algorithmic_bytes_basis": (f"per query {ref_nodes:.2f} nodes + {ref_prims:.2f} records "
+                                                     f"x 64 B + 48 B of path state, "
+                                                     + ("the binary LBVH reference traversal" if ref_counts
+                                                        else "this build's traversal counters")),
+                         "dram_frac": (extend_traffic(args) / (avg_ext_ms / 1e3) / 1e9 / peak)
+                                      if extend_traffic(args) and avg_ext_ms > 0 else None,
                          "nodes_per_query": nodes_per_query, "prims_per_query": prims_per_query,
                          "avg_launch_ms": avg_ext_ms},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "wall_s_timed_region": wall, "equal_time_mse": mse, "guide_kernels": guide_perf, "serving": serving,
             "exponential_variant": expo, "emitter_light_sampling": emit,
+            "kdtree_paper_sampler": kdst, "codebook_records": cbst,
             "radiance_field": rf,
         }
         print(json.dumps(line), flush=True)
@@ -755,6 +785,96 @@ def emitter_study(args, d, mats, scene, dev, spp=4):
     mb = ugp.Materials(t(sb.sggx), t(sb.mtype), t(sb.albedo), t(sb.roughness), t(sb.emission))
     out["lighting_B"] = one(sb, db, mb)
     return out
+
+
+def kdtree_study(args, dev):
+    """The paper's own sampler (kd-tree, per-leaf accumulation, binned disambiguation) beside the
+    exact BVH sampler on the same rays: 1024^2 pinhole camera rays of a room scene of
+    --kd-prims primitives (t in [0, inf)), one uniform pair per ray; CUDA-event time per launch
+    after 2 warm-up launches, build times, tree statistics and how often the rule disambiguated."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import scenes, ugp
+    s = scenes.room_scene(args.kd_prims, width=1024, height=1024, near_specular_frac=args.near_specular)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    mean, quat, scale, mag = t(s.mean), t(s.quat), t(s.scale), t(s.magnitude)
+    torch.cuda.synchronize(dev)
+    e0.record()
+    bvh = ugp.build_bvh(mean, quat, scale, mag)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    bvh_ms = e0.elapsed_time(e1)
+    t0w = time.perf_counter()
+    kd = ugp.KdTree(bvh)
+    kd_ms = 1e3 * (time.perf_counter() - t0w)
+    dirs = t(pinhole_rays(s.camera, 1024, 1024))
+    n = dirs.shape[0]
+    O = torch.tensor(np.array(s.camera.eye, np.float32), device=dev).expand(n, 3).contiguous()
+    T0, T1 = torch.zeros(n, device=dev), torch.full((n,), 1e30, device=dev)
+    U, U2 = t(scenes.uniforms24(21, n)), t(scenes.uniforms24(22, n))
+    out = {"scene": f"room, {args.kd_prims} primitives", "rays": n, "bvh_build_ms": bvh_ms,
+           "kdtree_build_ms_wall": kd_ms, "kdtree": kd.info()}
+    ws = torch.empty(int(ugp.lib().ugp_sample_free_flight_workspace_size(n)), dtype=torch.uint8, device=dev)
+    for name, fn in (("bvh_exact", lambda: ugp.sample_free_flight(bvh, O, dirs, T0, T1, U, U2, workspace=ws)),
+                     ("kdtree_paper_rule", lambda: kd.sample_free_flight(O, dirs, T0, T1, U, U2))):
+        for _ in range(2):
+            res = fn()
+        torch.cuda.synchronize(dev)
+        e0.record()
+        res = fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        prim, st = res[0], res[-1]
+        out[name] = {"ms": ms, "Mrays_per_s": n / (ms / 1e3) / 1e6, "escaped": float((prim < 0).float().mean()),
+                     "queries_with_error_status": int((st != 0).sum().item())}
+    out["same_escape"] = float(((out["bvh_exact"]["escaped"] > 0) == (out["kdtree_paper_rule"]["escaped"] > 0)))
+    return out
+
+
+def codebook_study(args, d, mats, scene, dev):
+    """Codebook-quantised records of the bench scene: encode time (6 Lloyd iterations of the
+    four 4096-entry codebooks), bytes per primitive against the uncompressed SoA arrays, decode
+    time, and a 1-spp frame of the decoded scene beside the same frame of the original (image
+    means and the relative difference of the means)."""
+    import numpy as np
+    import torch
+    from paper_2406_09733_gb300 import ugp
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize(dev)
+    e0.record()
+    book, rec = ugp.codebook_encode(d["mean"], d["quat"], d["scale"], d["magnitude"], mats, iters=6)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    enc_ms = e0.elapsed_time(e1)
+    e0.record()
+    dec = ugp.codebook_decode(rec, book, disney=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    dec_ms = e0.elapsed_time(e1)
+    raw = sum(v.numel() * v.element_size() for v in d.values())
+    W, H = args.width, args.height
+    cam = scene.camera
+    camera = ugp.camera_struct(cam.eye, cam.look, cam.up, cam.vfov_deg, W, H)
+    li = scene.lights
+    lights = ugp.lights_struct(li.has_quad, li.quad_corner, li.quad_e1, li.quad_e2, li.quad_Le, li.bg)
+    r = ugp.Renderer(W, H, device=dev)
+    means = {}
+    for name, arr, m in (("original", d, mats),
+                         ("decoded", dec, ugp.Materials(dec["sggx"], dec["mtype"], dec["albedo"], dec["roughness"],
+                                                        dec["emission"]))):
+        bvh = ugp.build_bvh(arr["mean"], arr["quat"], arr["scale"], arr["magnitude"])
+        acc, _ = r.render(bvh, m, camera, lights, spp=4, max_depth=args.depth, seed=9)
+        torch.cuda.synchronize(dev)
+        means[name] = (acc.double() / 4).mean((0, 1)).tolist()
+    rel = float(np.abs(np.array(means["decoded"]) - np.array(means["original"])).max() / max(means["original"]))
+    return {"primitives": scene.n, "record_bytes": int(rec.shape[1]), "uncompressed_bytes_per_primitive": raw / scene.n,
+            "ratio": raw / (rec.numel() + book.numel() * 4), "codebook_bytes": book.numel() * 4,
+            "encode_ms": enc_ms, "decode_ms": dec_ms, "image_mean_rgb": means,
+            "max_rel_diff_of_image_means_4spp": rel}
 
 
 def run_kernel_case(args):
