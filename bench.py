@@ -63,8 +63,8 @@ def parse_args(argv=None):
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
     p.add_argument("--mse-width", type=int, default=480, help="image width of the MSE study")
     p.add_argument("--mse-height", type=int, default=270, help="image height of the MSE study")
-    p.add_argument("--mse-ref-spp", type=int, default=1024, help="spp of the plain reference")
-    p.add_argument("--mse-budget-spp", type=int, default=128, help="plain spp that set the time budget")
+    p.add_argument("--mse-ref-spp", type=int, default=2048, help="spp of the plain reference")
+    p.add_argument("--mse-budget-spp", type=int, default=256, help="plain spp that set the time budget")
     p.add_argument("--mse-train-spp", type=int, default=32, help="guided spp that also train the guide")
     p.add_argument("--mse-minibatch", type=int, default=1 << 14)
     p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
