@@ -57,7 +57,7 @@ def parse_args(argv=None):
                    help="fraction of surface shapes made near-specular GGX (roughness 0.02)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-pixels", type=int, default=256, help="pixels of the CPU-baseline sample")
+    p.add_argument("--cpu-pixels", type=int, default=4096, help="pixels of the CPU-baseline sample")
     p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
@@ -410,16 +410,66 @@ def host_cpu() -> str:
     return desc
 
 
-def cpu_baseline_run(scene, args, pixels, spp=1, seed=0):
+def cpu_baseline_run(scene, args, pixels, spp=1, seed=0, accel=False, threads=None):
     """The FP64 oracle on a bounded sample of the workload: `pixels` consecutive pixels centred
-    in the middle image row, one sample each."""
+    in the middle image row, one sample each. With `accel` the oracle finds each ray's intervals
+    with its own BVH (the same intervals and results as brute force); the BVH's build time,
+    taken by a call that renders no pixel, is not counted."""
     import oracle
     mid = (args.height // 2) * args.width + max(0, (args.width - pixels) // 2)
+    if threads:
+        oracle.set_num_threads(threads)
+    # calls that render no pixel: the first builds the BVH (kept by the oracle for the same
+    # arrays), the second times the per-call set-up (the primitives' records) that the timed call
+    # also pays
+    build = setup = 0.0
+    for k in range(2 if accel else 1):
+        t0 = time.perf_counter()
+        oracle.render(scene, spp=spp, max_depth=args.depth, seed=seed, pixels=(mid, mid), accel=accel)
+        if k == 0 and accel:
+            build = time.perf_counter() - t0
+        else:
+            setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     _, _, (ne, ns) = oracle.render(scene, spp=spp, max_depth=args.depth, seed=seed,
-                                   pixels=(mid, mid + pixels))
+                                   pixels=(mid, mid + pixels), accel=accel)
+    dt = max(time.perf_counter() - t0 - setup, 1e-9)
+    cores = oracle.num_threads()
+    if threads:
+        oracle.set_num_threads(os.cpu_count() or 1)
+    return (ne + ns) / dt / 1e6, cores, ne + ns, dt, build
+
+
+def cpu_baseline_configs(args):
+    """The oracle's timings on the three plain configurations of the workload set: the
+    1,000-primitive scene in full (128^2, 4 spp, depth 4, brute force), and 64^2 = 4096 pixels
+    around the image centre (consecutive in row order) of the 1M-primitive room (1 spp, depth 8)
+    and of the bench scene (1 spp, depth 12), both with the oracle's BVH; rates in Mrays/s on all
+    host cores, BVH builds excluded and reported."""
+    import oracle
+    from paper_2406_09733_gb300 import scenes
+    out = {}
+    s1 = scenes.tiny_scene()
+    t0 = time.perf_counter()
+    _, _, (ne, ns) = oracle.render(s1, spp=4, max_depth=4, seed=0)
     dt = time.perf_counter() - t0
-    return (ne + ns) / dt / 1e6, oracle.num_threads(), ne + ns, dt
+    out["tiny_1000_full_128x128_4spp"] = {"Mrays_per_s": (ne + ns) / dt / 1e6, "queries": ne + ns, "s": dt}
+    for name, sc, depth in (("room_1M_4096_pixels", scenes.room_scene(1_000_000, width=1024, height=1024), 8),
+                            ("bench_scene_4096_pixels", bench_scene(args), args.depth)):
+        W, H = sc.camera.width, sc.camera.height
+        p0 = (H // 2) * W + W // 2 - 2048   # 4096 consecutive pixels (64^2) around the image centre
+        ts = []
+        for _ in range(2):   # BVH build, then the per-call set-up alone
+            t0 = time.perf_counter()
+            oracle.render(sc, spp=1, max_depth=depth, seed=0, pixels=(p0, p0), accel=True)
+            ts.append(time.perf_counter() - t0)
+        build = ts[0] - ts[1]
+        t0 = time.perf_counter()
+        _, _, (ne, ns) = oracle.render(sc, spp=1, max_depth=depth, seed=0, pixels=(p0, p0 + 4096), accel=True)
+        dt = max(time.perf_counter() - t0 - ts[1], 1e-9)
+        out[name] = {"Mrays_per_s": (ne + ns) / dt / 1e6, "queries": ne + ns, "s": dt, "bvh_build_s": build}
+    out["cores"] = oracle.num_threads()
+    return out
 
 
 # ------------------------------------------------------------------------------- arms
@@ -430,14 +480,14 @@ def run_reference(args):
         return 0
     from paper_2406_09733_gb300 import scenes
     scene = bench_scene(args)
-    px = max(16, args.cpu_pixels // 8)
+    px = max(16, args.cpu_pixels // 128)
     for w in range(args.warmup):
         cpu_baseline_run(scene, args, px, seed=1000 + w)
     rays = 0
     total = 0.0
     cores = None
     for k in range(args.steps):
-        v, cores, r, dt = cpu_baseline_run(scene, args, px, seed=k)
+        v, cores, r, dt, _ = cpu_baseline_run(scene, args, px, seed=k)
         rays += r
         total += dt
     value = rays / total / 1e6
@@ -573,10 +623,16 @@ def run_ugp(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, r, dt = cpu_baseline_run(scene, args, args.cpu_pixels)
+        v, cores, r, dt, build = cpu_baseline_run(scene, args, args.cpu_pixels, accel=True)
+        v1, _, r1, dt1, _ = cpu_baseline_run(scene, args, max(16, args.cpu_pixels // 32), accel=True, threads=1)
+        vb, _, rb, dtb, _ = cpu_baseline_run(scene, args, 32)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_pixels} pixels x 1 spp centred in the middle row, {r} queries in {dt:.1f} s, "
-                         f"brute force over all primitives, FP64", "cpu": host_cpu()}
+               "sample": (f"{args.cpu_pixels} pixels x 1 spp centred in the middle row, {r} queries in {dt:.1f} s, "
+                          f"FP64, intervals found with the oracle's own BVH (built in {build:.1f} s, not counted)"),
+               "single_thread": {"value": v1, "queries": r1, "s": dt1},
+               "brute_force": {"value": vb, "queries": rb, "s": dtb,
+                               "sample": "32 pixels centred in the middle row, every primitive tested per query"},
+               "configs": cpu_baseline_configs(args), "cpu": host_cpu()}
 
     guide_perf = None
     mse = None

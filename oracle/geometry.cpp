@@ -106,6 +106,7 @@ double gauss_at(const Hit& h, double t) {
 
 std::vector<Hit> all_hits(const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,
                           double k, int32_t exclude) {
+  if (g_accel && g_accel->prims == &prims) return accel_hits(*g_accel, o, d, t0, t1, k, exclude);
   std::vector<Hit> hits;
   for (size_t i = 0; i < prims.size(); ++i) {
     if (int32_t(i) == exclude) continue;

@@ -151,6 +151,22 @@ struct KdStats {
   double ambiguous_start = 0.0;  // start of the ambiguous segment used (NaN if none)
 };
 KdTree kd_build(const std::vector<Prim>& prims, double k);
+
+// A plain BVH that finds the same intervals as the brute-force loop (accel.cpp). While g_accel
+// points at one built over a primitive list, all_hits over that list uses it.
+struct AccelNode {
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  int left = -1, right = -1;
+  int32_t first = 0, count = 0;
+};
+struct Accel {
+  const std::vector<Prim>* prims = nullptr;
+  std::vector<AccelNode> nodes;
+  std::vector<int32_t> ids;
+};
+Accel accel_build(const std::vector<Prim>& prims, double k);
+std::vector<Hit> accel_hits(const Accel& A, V3 o, V3 d, double t0, double t1, double k, int32_t exclude);
+extern const Accel* g_accel;
 // nbins = 0: exact line-sweep segments in a leaf where the CDF reaches 1 (the paper's CPU
 // partition); nbins > 0: that many equal bins of the ray-node interval (its GPU partition).
 int32_t kd_sample_free_flight(const KdTree& T, const std::vector<Prim>& prims, V3 o, V3 d, double t0, double t1,

