@@ -67,7 +67,7 @@ def parse_args(argv=None):
     p.add_argument("--mse-budget-spp", type=int, default=256, help="plain spp that set the time budget")
     p.add_argument("--mse-train-spp", type=int, default=32, help="guided spp that also train the guide")
     p.add_argument("--mse-minibatch", type=int, default=1 << 14)
-    p.add_argument("--mse-min-steps", type=int, default=16, help="Adam steps per training spp, at least")
+    p.add_argument("--mse-min-steps", type=int, default=128, help="Adam steps per training spp, at least")
     p.add_argument("--guide-alpha", type=float, default=0.5)
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving study")
     p.add_argument("--no-rf", action="store_true", help="skip the radiance-field render study")
@@ -80,6 +80,8 @@ def parse_args(argv=None):
     p.add_argument("--serve-spp-max", type=int, default=64,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
     p.add_argument("--guide-lr", type=float, default=1e-3)
+    p.add_argument("--guide-target", type=int, choices=[0, 1], default=0,
+                   help="guide training target: 0 incident radiance, 1 its product with the phase function")
     return p.parse_args(argv)
 
 
@@ -284,7 +286,7 @@ def equal_time_mse(args, d, mats, scene, dev):
 
     # guided: trained during its first mse_train_spp samples, then frozen, until the same time
     g = ugp.Guide(scenes.guide_init_params(seed=0, bias_scale=0.0), info["bounds_lo"], info["bounds_hi"],
-                  lr=args.guide_lr, device=dev)
+                  lr=args.guide_lr, device=dev, train_target=args.guide_target)
     gacc, gacc2 = z(), z()
     t_g, k, curve_g, n_train, losses = 0.0, 0, [], 0, []
     while t_g < t_plain and k < 64 * args.mse_budget_spp:
@@ -310,6 +312,7 @@ def equal_time_mse(args, d, mats, scene, dev):
             "loss_first_last": [losses[0], losses[-1]] if losses else None,
             "reference_spp": args.mse_ref_spp, "reference_var_subtracted": ref_var_mean,
             "image": f"{MW}x{MH} (the bench scene and camera at a reduced image size)", "max_depth": depth, "guide_alpha": args.guide_alpha,
+            "train_target": ("incident radiance" if args.guide_target == 0 else "phase function x incident radiance"),
             "curve_ms_mse": {"plain": curve_p, "guided": curve_g},
             "note": "MSE over linear RGB, no clamping; times include the guide's training"}
 

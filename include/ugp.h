@@ -436,6 +436,10 @@ typedef struct ugp_guide {
   float lr, beta1, beta2, eps;   /* Adam hyper-parameters (e.g. 1e-3, 0.9, 0.99, 1e-8) */
   float pos_lo[3], pos_hi[3];    /* input normalisation box, pos_hi > pos_lo */
   float kappa_min, kappa_max;    /* lobe sharpness range, 0 < kappa_min <= kappa_max */
+  int32_t train_target;  /* training from render logs: 0 incident radiance L_i (weight L_i / p),
+                            1 its product with the phase function (weight f_p L_i / p: the
+                            radiance the path gathered after the vertex over the throughput
+                            before it), whose minimiser is q proportional to f_p L_i */
 } ugp_guide;
 
 /* Bytes of the scratch every guide call takes (packed BF16 weights, per-block gradient
@@ -522,7 +526,7 @@ ugp_status ugp_build_emitter_table(const ugp_bvh* bvh, const ugp_materials* mate
  * per-path primitive-slot lists, 1236 bytes per pixel plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
- * workspace, the per-path mixtures (160 bytes per pixel), the training log (76 bytes per
+ * workspace, the per-path mixtures (160 bytes per pixel), the training log (88 bytes per
  * pixel and vertex) and the guide's packed weights. */
 size_t ugp_render_guided_workspace_size(int32_t width, int32_t height, int32_t max_depth);
 

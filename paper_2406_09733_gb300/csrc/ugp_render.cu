@@ -43,9 +43,9 @@ namespace {
 // of E = max_depth * n floats:
 //   0-2 vertex position, 3-5 wo, 6-8 sampled wi, 9 pdf of wi (alpha q + (1 - alpha) p~; 0:
 //   no vertex), 10-12 throughput after the vertex, 13-15 path radiance before anything the
-//   path gathers after the vertex (written at bounce b + 1), 16 training weight L / pdf,
-//   17 selection key (int), 18 selected entry indices (int).
-constexpr int kLogCols = 19;
+//   path gathers after the vertex (written at bounce b + 1), 16 training weight,
+//   17 selection key (int), 18 selected entry indices (int), 19-21 throughput before the vertex.
+constexpr int kLogCols = 22;
 struct GuideLog {
   float* c[kLogCols];
   int64_t E;
@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
         }
       }
       if (sampled) {
+        const float3 beta_in = beta;
         beta = beta * wgt;
         if (beta.x > 0.f || beta.y > 0.f || beta.z > 0.f) {
           ps.pdf_prev[p] = pdf_s;
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
             c[6][e] = wi.x; c[7][e] = wi.y; c[8][e] = wi.z;
             c[9][e] = pdf_s;
             c[10][e] = beta.x; c[11][e] = beta.y; c[12][e] = beta.z;
+            c[19][e] = beta_in.x; c[20][e] = beta_in.y; c[21][e] = beta_in.z;
           }
           ps.ox[p] = x.x; ps.oy[p] = x.y; ps.oz[p] = x.z;
           ps.dx[p] = wi.x; ps.dy[p] = wi.y; ps.dz[p] = wi.z;
@@ -410,8 +412,10 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   return x;
 }
 
-// Incident-radiance estimate and training weight of every logged vertex; counts the usable ones.
-__global__ void __launch_bounds__(256) k_log_finalize(GuideLog L, int n, PathSoA ps, int* count) {
+// Training weight of every logged vertex; counts the usable ones. Target 0: the incident-
+// radiance estimate L_i (gathered radiance over the throughput after the vertex) over the pdf;
+// target 1: f_p L_i / pdf, the gathered radiance over the throughput before the vertex.
+__global__ void __launch_bounds__(256) k_log_finalize(GuideLog L, int n, PathSoA ps, int* count, int target) {
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < L.E; e += int64_t(gridDim.x) * blockDim.x) {
     const float pdf = L.c[9][e];
     float w = 0.f;
@@ -422,10 +426,10 @@ __global__ void __launch_bounds__(256) k_log_finalize(GuideLog L, int n, PathSoA
       float Li = 0.f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float b = L.c[10 + c][e];
+        const float b = L.c[(target == 1 ? 19 : 10) + c][e];
         if (b > 0.f) Li += lum[c] * fmaxf(0.f, (Lf[c] - L.c[13 + c][e]) / b);
       }
-      w = Li / pdf;
+      w = target == 1 ? Li : Li / pdf;
       if (!(w > 0.f) || !isfinite(w)) w = 0.f;
     }
     L.c[16][e] = w;
@@ -703,7 +707,7 @@ extern "C" ugp_status ugp_guide_train_from_render(ugp_guide* g, const void* rend
   UGP_CUDA_CHECK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
   const int grid = grid_for((const void*)k_log_finalize, 256, RL.E);
   prof_begin(kStGuide, st);
-  k_log_finalize<<<grid, 256, 0, st>>>(L, int(n), ps, cnt);
+  k_log_finalize<<<grid, 256, 0, st>>>(L, int(n), ps, cnt, g->train_target == 1 ? 1 : 0);
   prof_end(kStGuide, st);
   prof_begin(kStGuide, st);
   k_log_thin<<<grid, 256, 0, st>>>(L, cnt, max_samples);

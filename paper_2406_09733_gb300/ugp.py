@@ -47,7 +47,8 @@ class UgpLights(C.Structure):
 class UgpGuide(C.Structure):
     _fields_ = [("params", vp), ("adam_m", vp), ("adam_v", vp), ("step", C.c_int64), ("lr", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("pos_lo", C.c_float * 3),
-                ("pos_hi", C.c_float * 3), ("kappa_min", C.c_float), ("kappa_max", C.c_float)]
+                ("pos_hi", C.c_float * 3), ("kappa_min", C.c_float), ("kappa_max", C.c_float),
+                ("train_target", C.c_int32)]
 
 
 class UgpRenderParams(C.Structure):
@@ -669,7 +670,7 @@ class Guide:
     the device; the C struct points at them."""
 
     def __init__(self, params, pos_lo=(0.0, 0.0, 0.0), pos_hi=(1.0, 1.0, 1.0), kappa_min=0.1, kappa_max=1e4,
-                 lr=1e-3, beta1=0.9, beta2=0.99, eps=1e-8, device="cuda"):
+                 lr=1e-3, beta1=0.9, beta2=0.99, eps=1e-8, device="cuda", train_target=0):
         p = torch.as_tensor(params, dtype=torch.float32).to(device).contiguous().clone()
         if p.numel() != GUIDE_NPARAMS:
             raise ValueError(f"guide needs {GUIDE_NPARAMS} parameters")
@@ -680,7 +681,7 @@ class Guide:
         _check(lib().ugp_guide_reset_workspace(_p(self.workspace), C.c_void_p(_stream())), "ugp_guide_reset_workspace")
         self.c = UgpGuide(_p(self.params), _p(self.adam_m), _p(self.adam_v), 0, float(lr), float(beta1), float(beta2),
                           float(eps), (C.c_float * 3)(*pos_lo), (C.c_float * 3)(*pos_hi), float(kappa_min),
-                          float(kappa_max))
+                          float(kappa_max), int(train_target))
 
     @property
     def step(self) -> int:
