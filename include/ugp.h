@@ -523,7 +523,8 @@ ugp_status ugp_build_emitter_table(const ugp_bvh* bvh, const ugp_materials* mate
                                    size_t table_bytes, void* stream);
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 1236 bytes per pixel plus alignment). */
+ * per-path primitive-slot lists, 1236 bytes per pixel, plus one 73,728-byte interval slot of the
+ * free-flight finish per 64 pixels, at most 2432 of them, plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain
  * workspace, the per-path mixtures (160 bytes per pixel), the training log (88 bytes per

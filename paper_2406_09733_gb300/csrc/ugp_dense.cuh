@@ -35,19 +35,22 @@ constexpr int kListCap = 256;
 inline size_t slot_list_bytes(int64_t n) { return align256(size_t(n) * kListCap * 4); }
 
 // The finish's second pass keeps each ray's intervals (up to kBigCap, 9 words each) in a slot of
-// global memory owned by one warp; a queue for `cap` rays has big_slots(cap) of them, one per
-// 1024 rays between 4 and 2432 (the warps a GB300 keeps resident in that pass).
+// global memory owned by one warp; a queue for `cap` rays has big_slots(cap) of them by default,
+// one per 64 rays between 4 and 2432 (the warps a GB300 keeps resident in that pass), so that a
+// launch of a few hundred thousand rays already fills the GPU.
 constexpr int kBigCap = 2048;
-constexpr int64_t big_slots(int64_t cap) { return cap / 1024 < 4 ? 4 : (cap / 1024 > 2432 ? 2432 : cap / 1024); }
+constexpr int64_t big_slots(int64_t cap) { return cap / 64 < 4 ? 4 : (cap / 64 > 2432 ? 2432 : cap / 64); }
 constexpr size_t big_slot_bytes() { return size_t(kBigCap) * 9 * 4; }
 
-// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header, then the
-// second pass's interval slots); the slot lists, when used, take slot_list_bytes(cap) more.
-constexpr size_t dense_queue_bytes(int64_t cap) {
-  return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4) + size_t(big_slots(cap)) * big_slot_bytes();
+// Bytes of a queue for `cap` rays (256-byte aligned columns after a 256-byte header, then
+// `slots` interval slots of the second pass); the slot lists, when used, take
+// slot_list_bytes(cap) more.
+constexpr size_t dense_queue_bytes(int64_t cap, int64_t slots) {
+  return 256 + size_t(kDenseCols) * align256(size_t(cap) * 4) + size_t(slots) * big_slot_bytes();
 }
+constexpr size_t dense_queue_bytes(int64_t cap) { return dense_queue_bytes(cap, big_slots(cap)); }
 
-inline DenseQueue dense_queue_at(void* base, int64_t cap) {
+inline DenseQueue dense_queue_at(void* base, int64_t cap, int64_t slots) {
   char* p = static_cast<char*>(base);
   const size_t col = align256(size_t(cap) * 4);
   auto F = [&](int k) { return reinterpret_cast<float*>(p + 256 + k * col); };
@@ -65,9 +68,10 @@ inline DenseQueue dense_queue_at(void* base, int64_t cap) {
   q.list = nullptr;
   q.scenes = nullptr;
   q.big_iv = reinterpret_cast<float*>(p + 256 + kDenseCols * col);
-  q.big_slots = int(big_slots(cap));
+  q.big_slots = int(slots);
   return q;
 }
+inline DenseQueue dense_queue_at(void* base, int64_t cap) { return dense_queue_at(base, cap, big_slots(cap)); }
 
 // Fills slot j with a bracketed ray whose results go to output index idx.
 __device__ __forceinline__ void dense_push(const DenseQueue& q, int j, int idx, float lo, float hi, float Flo, float u,

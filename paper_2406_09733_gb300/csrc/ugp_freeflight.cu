@@ -71,10 +71,12 @@ int scan_grid(const void* kernel) {
 ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
                               const float* t0, const float* t1, const float* u, const float* u2,
                               const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
-                              void* workspace, bool with_lists, cudaStream_t stream) {
+                              void* workspace, bool with_lists, cudaStream_t stream, int64_t slots) {
   unsigned long long* ctr = trace_counters();
-  DenseQueue dq = dense_queue_at(workspace, n);
-  if (with_lists) dq.list = reinterpret_cast<const int*>(static_cast<char*>(workspace) + dense_queue_bytes(n));
+  if (slots < 0) slots = big_slots(n);
+  DenseQueue dq = dense_queue_at(workspace, n, slots);
+  if (with_lists)
+    dq.list = reinterpret_cast<const int*>(static_cast<char*>(workspace) + dense_queue_bytes(n, slots));
   int* next = dq.count + 1;  // the scan's ray counter, in the queue header next to the queue length
   UGP_CUDA_CHECK(cudaMemsetAsync(dq.count, 0, 2 * sizeof(int), stream));
   const void* kern = ctr ? (const void*)k_free_flight<true> : (const void*)k_free_flight<false>;

@@ -13,10 +13,12 @@ namespace ugp {
 namespace {
 
 // Room for the queue of UGP_NOALLOC_MAX_RAYS rays: a 256-byte header, kDenseCols columns of
-// 4-byte entries, each padded to 256 bytes, and the second finish pass's interval slots (the
-// layout of dense_queue_at).
+// 4-byte entries, each padded to 256 bytes, and 64 interval slots of the second finish pass (the
+// layout of dense_queue_at; fewer slots than a workspace of that size gets, to keep the array
+// small: the second pass then runs 64 warps).
 constexpr int64_t kNoallocMaxRays = UGP_NOALLOC_MAX_RAYS;
-constexpr size_t kNoallocBytes = dense_queue_bytes(kNoallocMaxRays);
+constexpr int64_t kNoallocSlots = 64;
+constexpr size_t kNoallocBytes = dense_queue_bytes(kNoallocMaxRays, kNoallocSlots);
 
 static __device__ __align__(256) unsigned char g_ff_scratch[kNoallocBytes];
 
@@ -70,7 +72,7 @@ extern "C" ugp_status ugp_sample_free_flight_noalloc(const ugp_bvh* bvh, int64_t
   if (n_rays > 0 && (!u || !u2 || !prim_out || !t_u_out || !t_spawn_out))
     return fail(UGP_ERR_INVALID_ARG, "ugp_sample_free_flight_noalloc: NULL uniform or output array");
   if (n_rays == 0) return UGP_OK;
-  if (dense_queue_bytes(kNoallocMaxRays) > kNoallocBytes)
+  if (dense_queue_bytes(n_rays, kNoallocSlots) > kNoallocBytes)
     return fail(UGP_ERR_INVALID_ARG, "ugp_sample_free_flight_noalloc: scratch layout mismatch");
   void* scratch = nullptr;
   s = scratch_for_current_device(&scratch);
@@ -79,5 +81,6 @@ extern "C" ugp_status ugp_sample_free_flight_noalloc(const ugp_bvh* bvh, int64_t
   // lists, so the dense pass collects its intervals by traversal); launch_free_flight clears
   // its counter on `stream` before use.
   return launch_free_flight(trace_scene(bvh), n_rays, o3, d3, t0, t1, u, u2, exclude_prim, prim_out, t_u_out,
-                            t_spawn_out, status_out, scratch, false, static_cast<cudaStream_t>(stream));
+                            t_spawn_out, status_out, scratch, false, static_cast<cudaStream_t>(stream),
+                            kNoallocSlots);
 }

@@ -32,9 +32,11 @@ ugp_status launch_transmittance(const TraceScene& sc, int64_t n, const float* o3
                                 const float* t0, const float* t1, const int32_t* excl, float* T,
                                 uint8_t* st, cudaStream_t stream);
 
+// The workspace holds the finish's queue for n rays (dense_queue_bytes(n, slots)) and, with
+// `with_lists`, the slot lists after it; slots < 0 takes the default number of interval slots.
 ugp_status launch_free_flight(const TraceScene& sc, int64_t n, const float* o3, const float* d3,
                               const float* t0, const float* t1, const float* u, const float* u2,
                               const int32_t* excl, int32_t* prim, float* tu, float* tsp, uint8_t* st,
-                              void* workspace, bool with_lists, cudaStream_t stream);
+                              void* workspace, bool with_lists, cudaStream_t stream, int64_t slots = -1);
 
 }  // namespace ugp
