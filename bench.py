@@ -213,7 +213,7 @@ def serving_study(args, dev):
 
     br = ugp.BatchRenderer(len(specs), pool_log2=20, tile=16, use_graph=True, shortest_first=True, device=dev)
     t0 = time.perf_counter()
-    (tile, lg), table = br.autotune(make_reqs()[:16], probe_spp=1, pool_log2_range=(20, 22))
+    (tile, lg), table = br.autotune(make_reqs()[:16], probe_spp=1, pool_log2_range=(20, 24))
     t_tune = time.perf_counter() - t0
     br.render(make_reqs())   # builds the graph of the chosen pool once
     reqs = make_reqs()
@@ -237,7 +237,7 @@ def serving_study(args, dev):
                        "latency_p99_ms": float(np.percentile(lat_seq, 99))},
         "same_rays": rays_b == rays_seq, "max_rel_diff_images": rel,
         "autotune": {"seconds": t_tune, "probe": "first 16 requests at 1 spp",
-                     "ms": {f"tile{k[0]}_pool2^{k[1]}": v for k, v in table.items()}},
+                     "pool_range": "2^20..2^24", "ms": {f"tile{k[0]}_pool2^{k[1]}": v for k, v in table.items()}},
     }
 
 
