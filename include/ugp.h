@@ -486,6 +486,9 @@ ugp_status ugp_guide_adam_step(ugp_guide* g, const float* grad, void* stream);
  *                   mixture pdf alpha q + (1 - alpha) p~ is the MIS partner of light sampling.
  *   guide_log       1: record every scattering vertex of this call for training
  *                   (ugp_guide_train_from_render); requires spp == 1 and a guide
+ *   guide_min_roughness  vertices whose base is glossier (GGX alpha, or the Disney
+ *                   specular's max(1e-3, roughness^2), below this value) scatter by phase
+ *                   sampling alone even with a guide (0: every vertex mixes in the guide)
  *   emitters        NULL, or a device table from ugp_build_emitter_table for this BVH and
  *                   these materials: each scattering vertex then also samples a point of an
  *                   emissive primitive (light sampling, balanced against phase sampling). A
@@ -498,7 +501,7 @@ typedef struct ugp_render_params {
   int32_t spawn_mode, guide_log;
   const ugp_guide* guide;
   float guide_alpha;
-  int32_t reserved;
+  float guide_min_roughness;
   const void* emitters;
 } ugp_render_params;
 

@@ -403,7 +403,8 @@ class OrcParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("seed", C.c_uint64), ("cutoff_eps", C.c_double), ("nee", C.c_int32),
                 ("spawn_mode", C.c_int32), ("guide", f32p), ("guide_cfg", OrcGuideCfg),
-                ("guide_alpha", C.c_double), ("nee_emitters", C.c_int32), ("accel", C.c_int32)]
+                ("guide_alpha", C.c_double), ("nee_emitters", C.c_int32), ("accel", C.c_int32),
+                ("guide_min_roughness", C.c_double)]
 
 
 def _d(a):
@@ -561,7 +562,8 @@ def phase_pdf_approx(mtype, albedo, alpha, S6, wo, wi):
 
 
 def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1, spawn_mode=0,
-           pixels=None, threads=None, guide=None, guide_alpha=0.5, nee_emitters=0, accel=False):
+           pixels=None, threads=None, guide=None, guide_alpha=0.5, nee_emitters=0, accel=False,
+           guide_min_roughness=0.0):
     """Per-pixel sums of sample values and squares, shape (H, W, 3) each, plus query counts.
 
     ``pixels`` = (p_begin, p_end) renders only that row-major pixel range (others stay zero).
@@ -582,7 +584,8 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
         gp = _c(guide[0], np.float32)
         gcfg = _guide_cfg(guide[1])
     p = OrcParams(int(spp), int(spp_begin), int(max_depth), int(seed), float(cutoff_eps), int(nee),
-                  int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha), int(nee_emitters), int(bool(accel)))
+                  int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha), int(nee_emitters), int(bool(accel)),
+                  float(guide_min_roughness))
     acc = np.zeros((H, W, 3))
     acc2 = np.zeros((H, W, 3))
     counts = (C.c_int64 * 2)(0, 0)

@@ -468,6 +468,7 @@ typedef struct {
   double guide_alpha;
   int32_t nee_emitters;  // 1: next-event estimation toward emissive primitives as well
   int32_t accel;         // 1: intervals found with a BVH (the same ones; for timing large scenes)
+  double guide_min_roughness;  // glossier vertices scatter by phase sampling alone
 } orc_params;
 
 static GuideCfg guide_cfg_of(const orc_guide_cfg* g) {
@@ -495,6 +496,7 @@ void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, co
   P.guide_alpha = p->guide_alpha;
   P.nee_emitters = p->nee_emitters;
   P.accel = p->accel;
+  P.guide_min_roughness = p->guide_min_roughness;
   int64_t ne = 0, ns = 0;
   render_pixels(scene_in(s), cam, L, P, p_begin, p_end, accum, accum_sq, &ne, &ns);
   if (counts) {

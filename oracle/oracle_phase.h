@@ -88,6 +88,9 @@ struct RenderParams {
   double guide_alpha = 0.5;
   int nee_emitters = 0;  // 1: also next-event estimation toward emissive primitives, with MIS
   int accel = 0;         // 1: find intervals with a BVH (same intervals, for timing large scenes)
+  // Vertices whose base is glossier than this (GGX alpha, or the Disney specular's
+  // max(1e-3, roughness^2), below it) scatter by phase sampling alone even with a guide.
+  double guide_min_roughness = 0.0;
 };
 
 // Next-event estimation toward emissive primitives (not specified by the paper): emitter j is

@@ -290,7 +290,9 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
         const V3 x = o + (P.spawn_mode == 1 ? ff.t_u : ff.t_spawn) * d;
         const V3 wo = -d;
         const bool guided = P.guide != nullptr;
-        const double al = P.guide_alpha;
+        const bool smooth = (m.type == kMatGGX && m.alpha < P.guide_min_roughness) ||
+                            (m.type == kMatDisney && std::max(1e-3, double(m.dis[4]) * m.dis[4]) < P.guide_min_roughness);
+        const double al = smooth ? 0.0 : P.guide_alpha;
         Mixture mix{};
         if (guided) {
           double Y[kGOut];

@@ -350,6 +350,14 @@ __device__ inline bool disney_sample(const Material& m, float3 wo, float3 n, con
   return true;
 }
 
+// Whether a material's base is glossier than `min_rough` (GGX alpha, or the Disney specular's
+// alpha = max(1e-3, roughness^2), below it).
+__device__ __forceinline__ bool guide_smooth(const Material& m, float min_rough) {
+  if (m.type == kMatGGX) return m.alpha < min_rough;
+  if (m.type == kMatDisney) return fmaxf(1e-3f, m.dis[4] * m.dis[4]) < min_rough;
+  return false;
+}
+
 __device__ __forceinline__ float3 base_f(const Material& m, float3 wi, float3 wo, float3 n) {
   return m.type == kMatGGX ? ggx_f(m.albedo, m.alpha, wi, wo, n) : lambert_f(m.albedo, wi, wo, n);
 }

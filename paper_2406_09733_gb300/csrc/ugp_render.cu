@@ -54,6 +54,7 @@ struct GuideLog {
 struct GuidedShade {
   const float* mix;  // n x 40 mixtures, by path
   float alpha;
+  float min_rough;   // vertices with a smoother glossy base use phase sampling alone
   int log;           // 1: write the training log
   GuideLog L;
   int n;             // paths per frame
@@ -184,6 +185,10 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
       const Material M = load_material(mats, k);
       const float t = ps.tsp[p];
       const float3 x = o + t * d, wo = -d;
+      // the guide's share at this vertex: none where the base is glossier than min_rough (its
+      // lobe is already sampled well; the guide, trained on radiance alone, would spread samples
+      // outside it)
+      const float al_v = kGuided && !guide_smooth(M, gs.min_rough) ? gs.alpha : 0.f;
       float mix[kGuided ? kGOut : 1];
       if (kGuided) {
         const float4* m4 = reinterpret_cast<const float4*>(gs.mix + size_t(p) * kGOut);
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
           const float3 f = phase_eval(M, wl, wo, Ue);
           if (f.x > 0.f || f.y > 0.f || f.z > 0.f) {
             float ps_l = phase_pdf_approx(M, wl, wo);
-            if (kGuided) ps_l = gs.alpha * mixture_pdf(mix, wl) + (1.f - gs.alpha) * ps_l;
+            if (kGuided) ps_l = al_v * mixture_pdf(mix, wl) + (1.f - al_v) * ps_l;
             const float wm = mis_w(pl, ps_l);
             const float3 contrib = (wm / pl) * (beta * (f * L.Le));
             const int j = queue_append(cnt_shadow);
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
           const float3 f = phase_eval(M, wl, wo, Ue);
           if (f.x > 0.f || f.y > 0.f || f.z > 0.f) {
             float ps_l = phase_pdf_approx(M, wl, wo);
-            if (kGuided) ps_l = gs.alpha * mixture_pdf(mix, wl) + (1.f - gs.alpha) * ps_l;
+            if (kGuided) ps_l = al_v * mixture_pdf(mix, wl) + (1.f - al_v) * ps_l;
             const float3 c = f3(m0.w, m1.w, m2.w) - x;
             const float wm = mis_w(2.f * dot3(c, c) * pj, m3.x * ps_l);
             const float3 contrib = (wm * 0.5f * m3.x / (r2 * pj)) * (beta * (f * f3(m3.y, m3.z, m3.w)));
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
         sampled = phase_sample(M, wo, U4, wi, wgt);
         if (sampled) pdf_s = phase_pdf_approx(M, wi, wo);
       } else {
-        const float al = gs.alpha;
+        const float al = al_v;
         const float4 G = rng(key, p, sample, bounce, 2);
         if (G.y < al) {
           wi = mixture_sample(mix, G.x, G.z, G.w);
@@ -607,6 +612,7 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   if (guide) {
     gs.mix = reinterpret_cast<const float*>(ws + RL.mix);
     gs.alpha = params->guide_alpha;
+    gs.min_rough = params->guide_min_roughness;
     gs.log = params->guide_log;
     gs.L = log_at(ws, RL);
     gs.n = int(n);

@@ -55,7 +55,7 @@ class UgpRenderParams(C.Structure):
     _fields_ = [("spp", C.c_int32), ("spp_begin", C.c_int32), ("max_depth", C.c_int32),
                 ("nee", C.c_int32), ("seed", C.c_uint64), ("spawn_mode", C.c_int32),
                 ("guide_log", C.c_int32), ("guide", C.POINTER(UgpGuide)), ("guide_alpha", C.c_float),
-                ("reserved", C.c_int32), ("emitters", C.c_void_p)]
+                ("guide_min_roughness", C.c_float), ("emitters", C.c_void_p)]
 
 
 class UgpError(RuntimeError):
@@ -537,7 +537,7 @@ class Renderer:
     def render(self, bvh: Bvh, mats: Materials, camera: UgpCamera, lights: UgpLights, spp: int,
                max_depth: int, seed: int = 0, spp_begin: int = 0, nee: bool = True, spawn_mode: int = 0,
                accum=None, accum_sq=None, ray_counts=None, stream=None, guide=None, guide_alpha: float = 0.5,
-               guide_log: bool = False, emitters=None):
+               guide_log: bool = False, emitters=None, guide_min_roughness: float = 0.0):
         """Adds spp samples per pixel into accum / accum_sq ((H, W, 3) float32, created if None).
 
         With ``guide`` (a ``Guide``) the renderer samples directions by one-sample MIS between
@@ -563,7 +563,8 @@ class Renderer:
             raise ValueError("camera size does not match the renderer")
         prm = UgpRenderParams(int(spp), int(spp_begin), int(max_depth), int(bool(nee)), int(seed),
                               int(spawn_mode), int(bool(guide_log)),
-                              C.pointer(guide.c) if guide is not None else None, float(guide_alpha), 0,
+                              C.pointer(guide.c) if guide is not None else None, float(guide_alpha),
+                              float(guide_min_roughness),
                               emitters.data_ptr() if emitters is not None else None)
         if guide is not None:
             need = guided_workspace_size(self.width, self.height, max_depth)

@@ -111,10 +111,11 @@ def test_guide_entry_points_validate_on_host(libugp):
 def test_guide_struct_layouts_match_the_header():
     """The ctypes mirrors have the C layout (offsets follow the header's field order)."""
     from paper_2406_09733_gb300 import ugp
-    assert ctypes.sizeof(ugp.UgpGuide) == 80
-    assert ugp.UgpGuide.kappa_max.offset == 76
+    assert ctypes.sizeof(ugp.UgpGuide) == 88
+    assert ugp.UgpGuide.kappa_max.offset == 76 and ugp.UgpGuide.train_target.offset == 80
     assert ctypes.sizeof(ugp.UgpRenderParams) == 56
     assert ugp.UgpRenderParams.guide.offset == 32 and ugp.UgpRenderParams.guide_alpha.offset == 40
+    assert ugp.UgpRenderParams.guide_min_roughness.offset == 44
     assert ugp.UgpRenderParams.emitters.offset == 48
 
 

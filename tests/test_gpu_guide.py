@@ -170,19 +170,23 @@ def _z(a1, q1, spp1, a0, q0, spp0):
     return np.abs(m1 - m0) / np.maximum(np.sqrt(se1 ** 2 + se0 ** 2), 1e-12), m1, m0, se1, se0
 
 
-def test_guided_render_matches_oracle(ugp, orc):
-    """GPU guided render (fixed guide) vs the oracle's guided render: per-pixel 3.5 SE."""
+@pytest.mark.parametrize("min_rough", [0.0, 0.5])
+def test_guided_render_matches_oracle(ugp, orc, min_rough):
+    """GPU guided render (fixed guide) vs the oracle's guided render: per-pixel 3.5 SE; with
+    min_rough, vertices with a glossier GGX base scatter by phase sampling alone on both sides."""
     s = _lit_scene()
     p = scenes.guide_init_params(seed=21, bias_scale=1.0)
     g = ugp.Guide(p, CFG.pos_lo, CFG.pos_hi, CFG.kappa_min, CFG.kappa_max)
     bvh, mats, cam, lights = ugp.scene_to_device(s)
     r = ugp.Renderer(6, 6)
     spp = 16384
-    acc, acc2 = r.render(bvh, mats, cam, lights, spp=spp, max_depth=3, seed=5, guide=g, guide_alpha=0.5)
+    acc, acc2 = r.render(bvh, mats, cam, lights, spp=spp, max_depth=3, seed=5, guide=g, guide_alpha=0.5,
+                         guide_min_roughness=min_rough)
     torch.cuda.synchronize()
     g.check()
     a1, q1 = acc.cpu().numpy().astype(np.float64), acc2.cpu().numpy().astype(np.float64)
-    a0, q0, _ = orc.render(s, spp=4096, max_depth=3, seed=6, guide=(p, CFG), guide_alpha=0.5)
+    a0, q0, _ = orc.render(s, spp=4096, max_depth=3, seed=6, guide=(p, CFG), guide_alpha=0.5,
+                           guide_min_roughness=min_rough)
     z, m1, m0, se1, se0 = _z(a1, q1, spp, a0, q0, 4096)
     assert (z > 3.5).mean() <= 0.03, np.sort(z.ravel())[-5:]
     zi = abs(m1.sum() - m0.sum()) / math.sqrt((se1 ** 2).sum() + (se0 ** 2).sum())
