@@ -631,10 +631,12 @@ ugp_status ugp_render_batch_autotune(int32_t n_req, const ugp_request* reqs, int
  * zero-initialised uint64, later tracing calls on any stream add (atomically)
  *   [0] nodes loaded, [1] primitive records loaded, [2] rays traced,
  *   [3] per-thread traversal passes, [4] free-flight rays handed to the finish passes
- *   (whose node and record loads are added to [0] and [1])
+ *   (whose node and record loads are added to [0] and [1]), [5] free-flight rays the
+ *   finish's first pass handed to its second (more intervals than 16 lanes hold, or an
+ *   overflowed slot list)
  * for free-flight and transmittance queries (standalone, and the renderer's extend
- * pass), and the same five quantities at [6..10] for the renderer's shadow rays;
- * [5] and [11] are reserved.  NULL turns counting off (the default).  Host-side
+ * pass), and the first five quantities at [6..10] for the renderer's shadow rays;
+ * [11] is reserved.  NULL turns counting off (the default).  Host-side
  * setting, not thread safe against concurrent tracing calls. */
 ugp_status ugp_set_trace_counters(unsigned long long* counters);
 

@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(32 * kDWarps) k_dense(TraceScene sc0, DenseQue
     if (big) {  // k_dense_big rebuilds and finishes the ray
       if (g.lane == 0) {
         hand_on(q.count + 2, q.wide, j);
-        if (O.stats) atomicAdd(O.stats + 1, (unsigned long long)tp);
+        if (O.stats) {
+          atomicAdd(O.stats + 1, (unsigned long long)tp);
+          atomicAdd(O.stats + 5, 1ull);
+        }
       }
       g.sync();
       continue;

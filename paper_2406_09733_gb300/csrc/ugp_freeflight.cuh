@@ -17,7 +17,10 @@
 // found in two exact passes, in the spirit of the paper's GPU binning (Sec. 5.2):
 //
 //  * scan (this header, one lane per ray, one traversal).  A nearest-first traversal adds
-//    each interval's contribution to kB equal bins of [t0, scene exit].  The first bin whose
+//    each interval's contribution to kB bins of the ray's span inside the scene box, [lo, hi];
+//    bin j ends at lo + (hi - lo) ((j + 1) / kB)^2, so bins are finest near the ray's start,
+//    where the crossing lies for rays that start in or near dense matter (their pruning limit
+//    and finish bracket then shrink with the free path).  The first bin whose
 //    prefix passes u, the crossing bin j, can only move earlier as intervals arrive, so subtrees
 //    starting after its end are pruned, and bins after it are no longer updated.  The slots of
 //    the primitives met before its end are recorded in the ray's slot list.  Afterwards F(e_j)
@@ -73,7 +76,7 @@ struct ScanState {
   Ray ray;
   float t0, t1;
   int ex;
-  float lo, hi, w;   // bins of width w over [lo, hi]
+  float lo, hi;      // bins over [lo, hi] (bin_edge)
   int jc;            // crossing bin (kB: none)
   unsigned n_nodes, n_prims;
   uint8_t st;
@@ -83,8 +86,9 @@ struct ScanState {
 
 #define FB(arr, i) sm.arr[(i)][tid]
 
-// Exit distance of the ray from the scene's bounding box (both children of the root).
-static __device__ float scene_exit(const TraceScene& sc, const Ray& r, float lo, float hi) {
+// Span [entry, exit] of the ray inside the scene's bounding box (both children of the root),
+// clipped to [lo, hi] and widened by a few ulps so that every clipped interval lies inside it.
+static __device__ float2 scene_span(const TraceScene& sc, const Ray& r, float lo, float hi) {
   const float4* nd = sc.nodes;
   const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
   const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
@@ -97,8 +101,17 @@ static __device__ float scene_exit(const TraceScene& sc, const Ray& r, float lo,
   const float x0 = (lx - r.o.x) * r.inv.x, x1 = (hx - r.o.x) * r.inv.x;
   const float y0 = (ly - r.o.y) * r.inv.y, y1 = (hy - r.o.y) * r.inv.y;
   const float z0 = (lz - r.o.z) * r.inv.z, z1 = (hz - r.o.z) * r.inv.z;
+  const float tl = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fminf(z0, z1));
   const float th = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
-  return fminf(hi, fmaxf(lo, th * (1.f + 1e-6f) + 1e-6f));
+  const float e = fminf(hi, fmaxf(lo, th * (1.f + 1e-6f) + 1e-6f));
+  const float b = fminf(e, fmaxf(lo, tl - 1e-6f * fabsf(tl) - 1e-6f));
+  return make_float2(b, e);
+}
+
+// Edge j of the scan's bins over [lo, hi] (L = hi - lo): lo + L (j / kB)^2, hi for j >= kB.
+// (j / kB)^2 is exact in float and the products round monotonically, so edges never decrease.
+__device__ __forceinline__ float bin_edge(float lo, float hi, float L, int j) {
+  return j >= kB ? hi : fmaf(L, float(j * j) * (1.f / float(kB * kB)), lo);
 }
 
 // Result of a finished scan.
@@ -117,8 +130,8 @@ static __device__ FFResult scan_result(FFSmem& sm, int tid, const ScanState& s, 
   for (int k = 0; k < s.jc; ++k) acc += FB(bin, k);
   const float Flo = float(acc) * kBinUnit;
   r.pending = true;
-  r.lo = s.lo + s.w * float(s.jc);
-  r.hi = s.jc + 1 >= kB ? s.hi : s.lo + s.w * float(s.jc + 1);
+  r.lo = bin_edge(s.lo, s.hi, s.hi - s.lo, s.jc);
+  r.hi = bin_edge(s.lo, s.hi, s.hi - s.lo, s.jc + 1);
   r.Flo = Flo;
   r.nlist = s.nlist;
   return r;
@@ -145,10 +158,10 @@ struct ScanCtx {
 
 struct ScanBins {
   ScanCtx& c;
-  float lo, hi, w, target;
+  float lo, hi, L, target;
   int jc;           // crossing bin (kB: none yet)
   long long below;  // sum of the bins before the crossing bin (of all bins while there is none)
-  __device__ float edge(int j) const { return j >= kB ? hi : lo + w * float(j); }
+  __device__ float edge(int j) const { return bin_edge(lo, hi, L, j); }
   // The interval's contribution goes to the bins up to the crossing bin; the crossing bin (and
   // the pruning limit) may move earlier; primitives met before its end go into the slot list.
   __device__ void leaf(int slot, float& limit) {
@@ -156,18 +169,30 @@ struct ScanBins {
     if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
     const float x = fmaxf(h.a, lo), y = fminf(h.b, hi);
     if (!(x < y)) return;
-    int j = min(kB - 1, max(0, int((x - lo) / w)));
+    int j = min(kB - 1, max(0, int(float(kB) * sqrtf((x - lo) / L))));
     while (j > 0 && x < edge(j)) --j;
     while (j < kB - 1 && x >= edge(j + 1)) ++j;
     if (j > jc) return;  // starts after the crossing bin: cannot matter any more
     const int kend = jc < kB ? jc + 1 : kB;
-    for (int k = j; k < kend && edge(k) < y; ++k) {
+    // The share of bin k is 1/2 I between consecutive cut points (App. A): a difference of erf
+    // values, taken as erfc(|tau|) at each cut point (same-sign pairs without cancellation), so
+    // each cut point costs one erfc however many bins the interval spans.
+    const float amp = h.e0 * (0.25f * kSqrtPi) / h.s;
+    float tp = (h.a_end && x == h.a) ? -h.th : tau_at(x, h.tn, h.ts, h.s);
+    float ep = erfcf(fabsf(tp));
+    for (int k = j; k < kend; ++k) {
       const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
+      if (!(xa < y)) break;
       if (xa < ya) {
+        const float tq = (h.b_end && ya == h.b) ? h.th : tau_at(ya, h.tn, h.ts, h.s);
+        const float eq = erfcf(fabsf(tq));
+        const float diff = tp >= 0.f ? ep - eq : (tq <= 0.f ? eq - ep : 2.f - ep - eq);
         const int old = c.sm.bin[k][c.tid];
-        const int nb = bin_add(old, seg_half_integral(xa, ya, h.a, h.b, h.a_end, h.b_end, h.tn, h.ts, h.s, h.e0, h.th));
+        const int nb = bin_add(old, amp * diff);
         c.sm.bin[k][c.tid] = nb;
         if (k < jc) below += nb - old;
+        tp = tq;
+        ep = eq;
       }
     }
     // Bins are non-negative, so while the bins before the crossing bin sum to at most u no
@@ -214,7 +239,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
   bool busy = false, exhausted = false, tdone = false;
   int node = 0, sp = 0, jc = kB, nq = 0;
   long long below = 0;
-  float lo = 0.f, hi = 0.f, w = 0.f, target = 0.f, limit = 0.f;
+  float lo = 0.f, hi = 0.f, L = 0.f, target = 0.f, limit = 0.f;
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !busy && !exhausted);
     const unsigned working = __ballot_sync(kFull, busy);
@@ -240,15 +265,19 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
             c.list = s.list;
             c.nlist = 0;
             target = u;
-            lo = c.t0;
-            hi = (c.sc.n_prims > 0 && c.t0 < c.t1) ? scene_exit(c.sc, c.ray, c.t0, c.t1) : lo;
+            lo = hi = c.t0;
+            if (c.sc.n_prims > 0 && c.t0 < c.t1) {
+              const float2 sp2 = scene_span(c.sc, c.ray, c.t0, c.t1);
+              lo = sp2.x;
+              hi = sp2.y;
+            }
             if (!(lo < hi)) {  // nothing to traverse: the ray escapes
               s.n_nodes = s.n_prims = 0u;
               s.st = UGP_RAY_OK;
               s.nlist = 0;
               src.finish(s, scan_result(sm, c.tid, s, false));
             } else {
-              w = (hi - lo) / float(kB);
+              L = hi - lo;
               for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0;
               jc = kB;
               below = 0;
@@ -274,7 +303,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       // ---- leaf step: one held-back primitive per lane
       if (busy && nq > 0) {
         --nq;
-        ScanBins v{c, lo, hi, w, target, jc, below};
+        ScanBins v{c, lo, hi, L, target, jc, below};
         v.leaf(sm.lq[nq][c.tid], limit);
         jc = v.jc;
         below = v.below;
@@ -337,7 +366,6 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
     if (busy && tdone && nq == 0) {
       s.lo = lo;
       s.hi = hi;
-      s.w = w;
       s.jc = jc;
       s.st = c.st;
       s.n_nodes = c.n_nodes;
