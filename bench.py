@@ -115,13 +115,14 @@ GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 # DRAM bytes (read + write) per k_extend launch of a workload, averaged over the launches of one
 # step, from one ncu capture of the current kernel (profiles/k_extend_dram_*.md); None for any
 # other workload, and to be reset whenever k_extend changes.
-EXTEND_TRAFFIC_BYTES = {}
+EXTEND_TRAFFIC_BYTES = {(5_500_000, 1920, 1080, 12, "A", 0.1): 1474.83e6}
 
 # Algorithmic bytes of a free-flight query are counted against a fixed reference traversal, so
 # that a tree that makes a query visit more nodes cannot raise the figure: the nodes and records
-# a query loads on the binary LBVH of the same build (64 B each), measured once per workload
-# with that traversal's counters. Workloads without a reference use the live counts.
-REFERENCE_COUNTS = {(5_500_000, 1920, 1080, 12, "A", 0.1): (371.85, 199.31)}
+# a query loads on the binary LBVH of the same build (64 B each) with the same scan (its bins and
+# pruning), measured once per workload with that traversal's counters. Workloads without a
+# reference use the live counts.
+REFERENCE_COUNTS = {(5_500_000, 1920, 1080, 12, "A", 0.1): (264.18, 135.91)}
 
 
 def workload_key(args):

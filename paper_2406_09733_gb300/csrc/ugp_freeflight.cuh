@@ -86,21 +86,25 @@ struct ScanState {
 
 #define FB(arr, i) sm.arr[(i)][tid]
 
-// Span [entry, exit] of the ray inside the scene's bounding box (both children of the root),
-// clipped to [lo, hi] and widened by a few ulps so that every clipped interval lies inside it.
-static __device__ float2 scene_span(const TraceScene& sc, const Ray& r, float lo, float hi) {
+// The scene's bounding box: the union of the root's children (binary node layout).
+static __device__ __forceinline__ void scene_box(const TraceScene& sc, float3& lo, float3& hi) {
   const float4* nd = sc.nodes;
   const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2);
   const int4 n3 = __ldg(reinterpret_cast<const int4*>(nd) + 3);
-  const float lx = fminf(n0.x, n3.y != kEmptyChild ? n1.z : n0.x);
-  const float ly = fminf(n0.y, n3.y != kEmptyChild ? n1.w : n0.y);
-  const float lz = fminf(n0.z, n3.y != kEmptyChild ? n2.x : n0.z);
-  const float hx = fmaxf(n0.w, n3.y != kEmptyChild ? n2.y : n0.w);
-  const float hy = fmaxf(n1.x, n3.y != kEmptyChild ? n2.z : n1.x);
-  const float hz = fmaxf(n1.y, n3.y != kEmptyChild ? n2.w : n1.y);
-  const float x0 = (lx - r.o.x) * r.inv.x, x1 = (hx - r.o.x) * r.inv.x;
-  const float y0 = (ly - r.o.y) * r.inv.y, y1 = (hy - r.o.y) * r.inv.y;
-  const float z0 = (lz - r.o.z) * r.inv.z, z1 = (hz - r.o.z) * r.inv.z;
+  lo = make_float3(fminf(n0.x, n3.y != kEmptyChild ? n1.z : n0.x), fminf(n0.y, n3.y != kEmptyChild ? n1.w : n0.y),
+                   fminf(n0.z, n3.y != kEmptyChild ? n2.x : n0.z));
+  hi = make_float3(fmaxf(n0.w, n3.y != kEmptyChild ? n2.y : n0.w), fmaxf(n1.x, n3.y != kEmptyChild ? n2.z : n1.x),
+                   fmaxf(n1.y, n3.y != kEmptyChild ? n2.w : n1.y));
+}
+
+// Span [entry, exit] of the ray inside the scene's bounding box, clipped to [lo, hi] and widened
+// by a few ulps so that every clipped interval lies inside it.
+static __device__ float2 scene_span(const TraceScene& sc, const Ray& r, float lo, float hi) {
+  float3 bl, bh;
+  scene_box(sc, bl, bh);
+  const float x0 = (bl.x - r.o.x) * r.inv.x, x1 = (bh.x - r.o.x) * r.inv.x;
+  const float y0 = (bl.y - r.o.y) * r.inv.y, y1 = (bh.y - r.o.y) * r.inv.y;
+  const float z0 = (bl.z - r.o.z) * r.inv.z, z1 = (bh.z - r.o.z) * r.inv.z;
   const float tl = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fminf(z0, z1));
   const float th = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
   const float e = fminf(hi, fmaxf(lo, th * (1.f + 1e-6f) + 1e-6f));
