@@ -35,12 +35,14 @@
 // lanes of a warp fetch together (one atomic) once kRefill of them are idle, so a warp does not
 // wait for its slowest ray before starting new ones (per-ray work varies several-fold; on camera
 // rays of a 1M-primitive room the mean over a warp is 0.58 of its maximum). Each loop step is
-// either a node step (every lane with nodes left visits one) or a leaf step (every lane with
-// held-back primitives tests one and bins it): primitives met in node steps are held back
-// until kLeafBatch lanes have some (or a lane's queue is nearly full or its traversal is over),
-// so the expensive primitive test and binning run with most lanes together instead of inside a
-// node step that most lanes skip. Holding a primitive back can only delay a lowering of the
-// pruning limit, never skip a node that matters.
+// either a node step (every lane with nodes left visits one) or a leaf step: primitives met in
+// node steps are held back until the warp holds 32 of them (or a lane's queue is nearly full or
+// its traversal is over), and a leaf step then spreads them over the lanes, one per lane
+// whichever ray it belongs to, so the expensive primitive test and binning run on all lanes
+// (with one primitive per lane of its own ray, the leaf steps of the bench's rays kept 10 of 32
+// lanes busy). A lane bins into the owning ray's bins with shared-memory atomics; the owner
+// moves its crossing bin after the step. Holding a primitive back can only delay a lowering of
+// the pruning limit, never skip a node that matters.
 #include "ugp_dense.cuh"
 #include "ugp_gauss.cuh"
 #include "ugp_philox.cuh"
@@ -48,26 +50,26 @@
 
 namespace ugp {
 
-constexpr int kLeafQ = 6;      // primitives a lane may hold back before testing them
-constexpr int kLeafBatch = 16;  // lanes with held-back primitives that start a joint leaf phase
+constexpr int kLeafQ = 6;  // primitives a lane may hold back before they are tested
 
-// Bins hold 1/2 I in fixed point, units of 2^-30, with saturating adds: integer sums do not depend
-// on the order the contributions arrive in, so a ray's result does not depend on which rays share
-// its warp. Bins before the crossing bin sum to less than u <= 1; a bin that saturates (>= 2) lies
-// at or after it, where only "exceeds u" matters. Contributions below 2^-31 are dropped.
-constexpr float kBinScale = 1073741824.f;         // 2^30
-constexpr float kBinUnit = 9.313225746154785e-10f;  // 2^-30
-
-__device__ __forceinline__ int bin_add(int b, float v) {
-  const float f = fminf(fmaxf(v, 0.f) * kBinScale, 2147483520.f);
-  const long long t = (long long)b + (long long)__float2int_rn(f);
-  return t > 2147483647ll ? 2147483647 : int(t);
-}
+// Bins hold 1/2 I in fixed point, units of 2^-29: integer sums do not depend on the order the
+// contributions arrive in, so a ray's result does not depend on which rays share its warp or
+// which lanes test its primitives. A contribution is capped at kBinCap, just above 1, and a bin
+// that already holds kBinCap or more takes no more: the bins before the crossing bin sum to at
+// most u <= 1, so such a bin lies at or after the crossing, where only "exceeds u" matters. A
+// step adds to one ray's bins from at most kLeafQ lanes, so no bin or running sum passes
+// 7 kBinCap < 2^32. Contributions below 2^-30 are dropped.
+constexpr float kBinScale = 536870912.f;            // 2^29
+constexpr float kBinUnit = 1.862645149230957e-09f;  // 2^-29
+constexpr unsigned kBinCap = (1u << 29) + 1u;       // just above 1 in bin units
+static_assert((kLeafQ + 1ull) * kBinCap < (1ull << 32), "bins must not wrap");
 
 struct FFSmem {
-  int bin[kB][kFFBlock];     // fixed-point bins
+  unsigned bin[kB][kFFBlock];  // fixed-point bins
   int stk[kFFStack][kFFBlock];
-  int lq[kLeafQ][kFFBlock];  // held-back primitive slots
+  int lq[kLeafQ][kFFBlock];    // held-back primitive slots
+  unsigned below[kFFBlock];    // sum of the bins before the crossing bin (all bins while none)
+  int nlist[kFFBlock];         // slots recorded in the ray's list
 };
 
 // A ray as handed to and returned from the scan (Src::begin fills the ray fields, the driver
@@ -130,7 +132,7 @@ struct FFResult {
 static __device__ FFResult scan_result(FFSmem& sm, int tid, const ScanState& s, bool traversed) {
   FFResult r{-1, s.t1, s.t1, false, 0.f, 0.f, 0.f, 0};
   if (!traversed || s.st != UGP_RAY_OK || s.jc == kB) return r;  // F(end) <= u: escape
-  long long acc = 0;
+  unsigned long long acc = 0;
   for (int k = 0; k < s.jc; ++k) acc += FB(bin, k);
   const float Flo = float(acc) * kBinUnit;
   r.pending = true;
@@ -145,8 +147,8 @@ static __device__ FFResult scan_result(FFSmem& sm, int tid, const ScanState& s, 
 
 constexpr int kRefill = 2;  // idle lanes of a warp that trigger a joint fetch of new rays
 
-// Traversal context of one lane (the scene, the ray and its counters) and the bin visitor of a
-// primitive met by the traversal, as used by the persistent driver below.
+// Traversal context of one lane: the scene, the ray and its counters, as used by the
+// persistent driver below.
 struct ScanCtx {
   FFSmem& sm;
   int tid;
@@ -157,70 +159,70 @@ struct ScanCtx {
   unsigned n_nodes, n_prims;
   uint8_t st;
   int* list;
-  int nlist;
 };
 
-struct ScanBins {
-  ScanCtx& c;
-  float lo, hi, L, target;
-  int jc;           // crossing bin (kB: none yet)
-  long long below;  // sum of the bins before the crossing bin (of all bins while there is none)
+// What a lane needs to test and bin a held-back primitive of another lane's ray (the owner).
+struct OwnerRay {
+  const float4* prims;
+  const float4* wlo;
+  float k2;
+  Ray ray;
+  float t0, t1;
+  int ex;
+  float lo, hi, L;
+  int jc;     // the owner's crossing bin at the start of the step (it only moves earlier)
+  int* list;
+  int tid;    // the owner's thread index in the block (its column of the shared arrays)
   __device__ float edge(int j) const { return bin_edge(lo, hi, L, j); }
-  // The interval's contribution goes to the bins up to the crossing bin; the crossing bin (and
-  // the pruning limit) may move earlier; primitives met before its end go into the slot list.
-  __device__ void leaf(int slot, float& limit) {
-    PrimHit h;
-    if (!prim_test(c.sc.prims, c.sc.wlo, slot, c.ray, c.t0, c.t1, c.sc.k2, c.ex, h)) return;
-    const float x = fmaxf(h.a, lo), y = fminf(h.b, hi);
-    if (!(x < y)) return;
-    int j = min(kB - 1, max(0, int(float(kB) * sqrtf((x - lo) / L))));
-    while (j > 0 && x < edge(j)) --j;
-    while (j < kB - 1 && x >= edge(j + 1)) ++j;
-    if (j > jc) return;  // starts after the crossing bin: cannot matter any more
-    const int kend = jc < kB ? jc + 1 : kB;
-    // The share of bin k is 1/2 I between consecutive cut points (App. A): a difference of erf
-    // values, taken as erfc(|tau|) at each cut point (same-sign pairs without cancellation), so
-    // each cut point costs one erfc however many bins the interval spans.
-    const float amp = h.e0 * (0.25f * kSqrtPi) / h.s;
-    float tp = (h.a_end && x == h.a) ? -h.th : tau_at(x, h.tn, h.ts, h.s);
-    float ep = erfcf(fabsf(tp));
-    for (int k = j; k < kend; ++k) {
-      const float xa = fmaxf(x, edge(k)), ya = fminf(y, edge(k + 1));
-      if (!(xa < y)) break;
-      if (xa < ya) {
-        const float tq = (h.b_end && ya == h.b) ? h.th : tau_at(ya, h.tn, h.ts, h.s);
-        const float eq = erfcf(fabsf(tq));
-        const float diff = tp >= 0.f ? ep - eq : (tq <= 0.f ? eq - ep : 2.f - ep - eq);
-        const int old = c.sm.bin[k][c.tid];
-        const int nb = bin_add(old, amp * diff);
-        c.sm.bin[k][c.tid] = nb;
-        if (k < jc) below += nb - old;
-        tp = tq;
-        ep = eq;
+};
+
+// Tests primitive `slot` against the owner's ray and adds its interval's contribution to the
+// owner's bins up to the owner's crossing bin, with shared-memory atomics (other lanes may bin
+// primitives of the same ray in the same step); contributions to bins before the crossing bin
+// also go to the owner's running sum of them, and a primitive met before the crossing bin's end
+// goes into the owner's slot list. The owner moves its crossing bin afterwards.
+static __device__ void pooled_leaf(FFSmem& sm, const OwnerRay& w, int slot) {
+  PrimHit h;
+  if (!prim_test(w.prims, w.wlo, slot, w.ray, w.t0, w.t1, w.k2, w.ex, h)) return;
+  const float x = fmaxf(h.a, w.lo), y = fminf(h.b, w.hi);
+  if (!(x < y)) return;
+  int j = min(kB - 1, max(0, int(float(kB) * sqrtf((x - w.lo) / w.L))));
+  while (j > 0 && x < w.edge(j)) --j;
+  while (j < kB - 1 && x >= w.edge(j + 1)) ++j;
+  if (j > w.jc) return;  // starts after the crossing bin: cannot matter any more
+  const int kend = w.jc < kB ? w.jc + 1 : kB;
+  // The share of bin k is 1/2 I between consecutive cut points (App. A): a difference of erf
+  // values, taken as erfc(|tau|) at each cut point (same-sign pairs without cancellation), so
+  // each cut point costs one erfc however many bins the interval spans.
+  const float amp = h.e0 * (0.25f * kSqrtPi) / h.s;
+  float tp = (h.a_end && x == h.a) ? -h.th : tau_at(x, h.tn, h.ts, h.s);
+  float ep = erfcf(fabsf(tp));
+  unsigned long long dbelow = 0;
+  for (int k = j; k < kend; ++k) {
+    const float xa = fmaxf(x, w.edge(k)), ya = fminf(y, w.edge(k + 1));
+    if (!(xa < y)) break;
+    if (xa < ya) {
+      const float tq = (h.b_end && ya == h.b) ? h.th : tau_at(ya, h.tn, h.ts, h.s);
+      const float eq = erfcf(fabsf(tq));
+      const float diff = tp >= 0.f ? ep - eq : (tq <= 0.f ? eq - ep : 2.f - ep - eq);
+      const unsigned add = min(__float2uint_rn(fminf(fmaxf(amp * diff, 0.f) * kBinScale, 2.f * kBinScale)), kBinCap);
+      unsigned* bp = &sm.bin[k][w.tid];
+      if (add != 0u && *reinterpret_cast<volatile unsigned*>(bp) < kBinCap) {
+        atomicAdd(bp, add);
+        if (k < w.jc) dbelow += add;
       }
-    }
-    // Bins are non-negative, so while the bins before the crossing bin sum to at most u no
-    // prefix passes u earlier, and the crossing bin stands; otherwise find the new one.
-    const long long tgt = (long long)(target * kBinScale);  // u is a multiple of 2^-24: exact
-    if (below > tgt) {
-      long long acc = 0;
-      for (int k = 0; k < jc; ++k) {
-        const long long before = acc;
-        acc += c.sm.bin[k][c.tid];
-        if (acc > tgt) {
-          jc = k;
-          limit = edge(jc + 1);
-          below = before;
-          break;
-        }
-      }
-    }
-    if (x < edge(jc + 1) && c.list) {
-      if (c.nlist < kListCap) c.list[c.nlist] = slot;
-      ++c.nlist;
+      tp = tq;
+      ep = eq;
     }
   }
-};
+  // a share above kBinCap makes the running sum exceed u anyway: capping it keeps the sum within
+  // 32 bits
+  if (dbelow != 0ull) atomicAdd(&sm.below[w.tid], unsigned(dbelow < kBinCap ? dbelow : kBinCap));
+  if (x < w.edge(w.jc + 1) && w.list) {
+    const int pos = atomicAdd(&sm.nlist[w.tid], 1);
+    if (pos < kListCap) w.list[pos] = slot;
+  }
+}
 
 // Persistent-lane driver of the scan. Src supplies the rays:
 //   __device__ int count() const                    rays in this launch
@@ -238,11 +240,10 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
   constexpr unsigned kFull = 0xffffffffu;
   const int n = src.count();
   ScanCtx c{sm, int(threadIdx.x), src.scene(), make_ray(make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 1.f)), 0.f,
-            0.f, -1, 0u, 0u, UGP_RAY_OK, nullptr, 0};
+            0.f, -1, 0u, 0u, UGP_RAY_OK, nullptr};
   ScanState s;
   bool busy = false, exhausted = false, tdone = false;
   int node = 0, sp = 0, jc = kB, nq = 0;
-  long long below = 0;
   float lo = 0.f, hi = 0.f, L = 0.f, target = 0.f, limit = 0.f;
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !busy && !exhausted);
@@ -267,7 +268,6 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
             c.n_nodes = c.n_prims = 0u;
             c.st = UGP_RAY_OK;
             c.list = s.list;
-            c.nlist = 0;
             target = u;
             lo = hi = c.t0;
             if (c.sc.n_prims > 0 && c.t0 < c.t1) {
@@ -282,9 +282,10 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
               src.finish(s, scan_result(sm, c.tid, s, false));
             } else {
               L = hi - lo;
-              for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0;
+              for (int j = 0; j < kB; ++j) sm.bin[j][c.tid] = 0u;
+              sm.below[c.tid] = 0u;
+              sm.nlist[c.tid] = 0;
               jc = kB;
-              below = 0;
               limit = hi;
               node = 0;
               sp = 0;
@@ -300,17 +301,68 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       if (__all_sync(kFull, exhausted)) break;
       continue;
     }
-    const unsigned pend = __ballot_sync(kFull, busy && nq > 0);
+    const int mine = busy ? nq : 0;
+    const int total = int(__reduce_add_sync(kFull, unsigned(mine)));
     // a node step may add four held-back primitives: it runs only while every lane has room
     const bool urgent = __any_sync(kFull, busy && (nq > kLeafQ - 4 || (tdone && nq > 0)));
-    if (pend && (__popc(pend) >= kLeafBatch || urgent)) {
-      // ---- leaf step: one held-back primitive per lane
-      if (busy && nq > 0) {
-        --nq;
-        ScanBins v{c, lo, hi, L, target, jc, below};
-        v.leaf(sm.lq[nq][c.tid], limit);
-        jc = v.jc;
-        below = v.below;
+    if (total > 0 && (total >= 32 || urgent)) {
+      // ---- leaf step: the warp's held-back primitives, up to 32, one per lane whichever ray
+      // they belong to; lane i takes item i of the lanes' queues laid end to end
+      int off = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, off, o);
+        if (lane >= o) off += y;
+      }
+      off -= mine;
+      const unsigned has = __ballot_sync(kFull, mine > 0);
+      const unsigned starts = __reduce_or_sync(kFull, (mine > 0 && off < 32) ? (1u << off) : 0u);
+      const bool work = lane < total;
+      const int o = work ? int(__fns(has, 0u, __popc(starts & (0xffffffffu >> (31 - lane))))) : lane;
+      const int off_o = __shfl_sync(kFull, off, o);
+      const int nq_o = __shfl_sync(kFull, mine, o);
+      OwnerRay w;
+      w.prims = reinterpret_cast<const float4*>(
+          __shfl_sync(kFull, reinterpret_cast<unsigned long long>(c.sc.prims), o));
+      w.wlo = reinterpret_cast<const float4*>(__shfl_sync(kFull, reinterpret_cast<unsigned long long>(c.sc.wlo), o));
+      w.k2 = __shfl_sync(kFull, c.sc.k2, o);
+      w.ray.o = make_float3(__shfl_sync(kFull, c.ray.o.x, o), __shfl_sync(kFull, c.ray.o.y, o),
+                            __shfl_sync(kFull, c.ray.o.z, o));
+      w.ray.d = make_float3(__shfl_sync(kFull, c.ray.d.x, o), __shfl_sync(kFull, c.ray.d.y, o),
+                            __shfl_sync(kFull, c.ray.d.z, o));
+      w.ray.inv = make_float3(0.f, 0.f, 0.f);  // not used by the primitive test
+      w.ray.inv_dd = __shfl_sync(kFull, c.ray.inv_dd, o);
+      w.t0 = __shfl_sync(kFull, c.t0, o);
+      w.t1 = __shfl_sync(kFull, c.t1, o);
+      w.ex = __shfl_sync(kFull, c.ex, o);
+      w.lo = __shfl_sync(kFull, lo, o);
+      w.hi = __shfl_sync(kFull, hi, o);
+      w.L = __shfl_sync(kFull, L, o);
+      w.jc = __shfl_sync(kFull, jc, o);
+      w.list = reinterpret_cast<int*>(__shfl_sync(kFull, reinterpret_cast<unsigned long long>(c.list), o));
+      w.tid = (int(threadIdx.x) & ~31) | o;
+      if (work) pooled_leaf(sm, w, sm.lq[nq_o - 1 - (lane - off_o)][w.tid]);
+      __syncwarp();
+      // each ray drops the items taken from the top of its queue and, when its running sum of
+      // the bins before the crossing bin passes u, moves the crossing bin (bins are
+      // non-negative, so while that sum is at most u no prefix passes u earlier)
+      const int taken = min(mine, max(0, 32 - off));
+      if (taken > 0) {
+        nq = mine - taken;
+        const unsigned tgt = unsigned(target * kBinScale);  // u <= 1, a multiple of 2^-24: exact
+        if (sm.below[c.tid] > tgt) {
+          unsigned long long acc = 0;
+          for (int k = 0; k < jc; ++k) {
+            const unsigned long long before = acc;
+            acc += sm.bin[k][c.tid];
+            if (acc > tgt) {
+              jc = k;
+              limit = bin_edge(lo, hi, L, jc + 1);
+              sm.below[c.tid] = unsigned(before);
+              break;
+            }
+          }
+        }
       }
     } else if (busy && !tdone) {
       // ---- node step: one 4-wide node of the nearest-first traversal
@@ -374,7 +426,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       s.st = c.st;
       s.n_nodes = c.n_nodes;
       s.n_prims = c.n_prims;
-      s.nlist = c.nlist;
+      s.nlist = sm.nlist[c.tid];
       src.finish(s, scan_result(sm, c.tid, s, true));
       busy = false;
     }
