@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
 __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene sc, ShadowSoA sh, const int* cnt, PathSoA ps,
                                                      unsigned long long* rays, unsigned long long* stats) {
   __shared__ int stk[kTrStack * kTrBlock];
+  __shared__ unsigned long long tr_acc[kTrBlock];
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0 && rays) atomicAdd(rays + 1, (unsigned long long)count);
   // one ray per thread over a grid sized for the longest queue: the hardware spreads the blocks
@@ -336,7 +337,8 @@ __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene 
   // a negative distance marks a light sample of an emissive primitive: it counts when the
   // point lies before saturation (T > 0) and is not scaled by T
   const float dist = sh.dist[j];
-  const float tau = tr_optical_depth(sc, ray, 0.f, fabsf(dist), sh.excl[j], stk + threadIdx.x, kTrBlock, ts);
+  const float tau = tr_optical_depth(sc, ray, 0.f, fabsf(dist), sh.excl[j], stk + threadIdx.x, kTrBlock,
+                                     tr_acc + threadIdx.x, ts);
   const float T = fmaxf(0.f, 1.f - tau);
   if (T > 0.f) {
     const float s = dist < 0.f ? 1.f : T;

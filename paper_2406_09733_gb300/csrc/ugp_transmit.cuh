@@ -11,39 +11,75 @@ struct TrStats {
   uint8_t st;
 };
 
-constexpr int kTrLeafQ = 6;       // primitives a lane may hold back (top of its stack column)
-constexpr int kTrLeafBatch = 16;  // lanes with held-back primitives that start a joint leaf step
+constexpr int kTrLeafQ = 6;  // primitives a lane may hold back (top of its stack column)
 
 // Returns tau = 1/2 sum_k I_k(clip_k) over [t0, t1], stopping once it reaches 1 (then T = 0).
 // The sum is kept in 64-bit fixed point (units of 2^-40), so it is the same in any traversal
-// order, whatever rays share the warp (terms below 2^-41 are dropped: under 1e-10 in tau for a
-// few hundred of them); nearest-child-first only makes the early exit come sooner.
-// `stk` points at this thread's column of a shared-memory stack with `stride` between levels.
-// The lanes that call together (the active mask) run in steps: a node step visits one node per
-// lane and holds back the primitives it meets (up to kTrLeafQ, kept at the top of the stack
-// column); a leaf step, taken once kTrLeafBatch lanes hold some (or a queue is nearly full or a
-// traversal is over), tests one held-back primitive per lane, so the expensive test and erf run
-// with most lanes together.
+// order and whichever lanes test a ray's primitives (terms below 2^-41 are dropped: under 1e-10
+// in tau for a few hundred of them); nearest-child-first only makes the early exit come sooner.
+// `stk` points at this thread's column of a shared-memory stack with `stride` between levels,
+// and `acc` at this thread's entry of a shared array of sums (its neighbours in the warp are the
+// other lanes' entries). The lanes that call together (the active mask) run in steps: a node
+// step visits one node per lane and holds back the primitives it meets (up to kTrLeafQ, kept at
+// the top of the stack column); a leaf step, taken once the lanes hold a primitive for each of
+// them (or a queue is nearly full or a traversal is over), spreads the held-back primitives over
+// the lanes, one per lane whichever ray it belongs to, and each lane adds its primitive's term to
+// the owner's sum with a shared-memory atomic.
 static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, float t0, float t1, int ex,
-                                         int* stk, int stride, TrStats& ts) {
+                                         int* stk, int stride, unsigned long long* acc, TrStats& ts) {
   const unsigned mask = __activemask();
+  const int lane = int(threadIdx.x) & 31;
+  const unsigned below_me = (1u << lane) - 1u;
+  const int nact = __popc(mask), rank = __popc(mask & below_me);
   constexpr float kScale = 1099511627776.f;  // 2^40
-  constexpr long long kOne = 1ll << 40;
-  long long acc = 0;
+  constexpr unsigned long long kOne = 1ull << 40;
+  *acc = 0ull;
   int sp = 0, node = 0, nq = 0;
   bool tdone = !(sc.n_prims > 0 && t0 < t1), done = tdone;
   int* lq = stk + (kTrStack - kTrLeafQ) * stride;
+  __syncwarp(mask);
   for (;;) {
-    const unsigned pend = __ballot_sync(mask, !done && nq > 0);
+    // queue lengths (below 8) as three bit planes: their sum and each lane's exclusive prefix
+    const int mine = done ? 0 : nq;
+    const unsigned p0 = __ballot_sync(mask, (mine & 1) != 0), p1 = __ballot_sync(mask, (mine & 2) != 0),
+                   p2 = __ballot_sync(mask, (mine & 4) != 0);
+    const int total = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2);
     // a node step may add four held-back primitives: it runs only while every lane has room
     const bool urgent = __any_sync(mask, !done && (nq > kTrLeafQ - 4 || (tdone && nq > 0)));
-    if (pend && (__popc(pend) >= kTrLeafBatch || urgent)) {
-      if (!done && nq > 0) {
-        --nq;
+    if (total > 0 && (total >= nact || urgent)) {
+      // the lane of rank r takes item r of the queues laid end to end (lane order)
+      const int off = __popc(p0 & below_me) + 2 * __popc(p1 & below_me) + 4 * __popc(p2 & below_me);
+      const unsigned starts = __reduce_or_sync(mask, (mine > 0 && off < 32) ? (1u << off) : 0u);
+      const bool work = rank < total;
+      const int o = work ? int(__fns(p0 | p1 | p2, 0u, __popc(starts & (0xffffffffu >> (31 - rank))))) : lane;
+      const int off_o = __shfl_sync(mask, off, o);
+      const int nq_o = __shfl_sync(mask, mine, o);
+      Ray ro;
+      ro.o = make_float3(__shfl_sync(mask, ray.o.x, o), __shfl_sync(mask, ray.o.y, o), __shfl_sync(mask, ray.o.z, o));
+      ro.d = make_float3(__shfl_sync(mask, ray.d.x, o), __shfl_sync(mask, ray.d.y, o), __shfl_sync(mask, ray.d.z, o));
+      ro.inv = make_float3(0.f, 0.f, 0.f);  // not used by the primitive test
+      ro.inv_dd = __shfl_sync(mask, ray.inv_dd, o);
+      const float t0o = __shfl_sync(mask, t0, o), t1o = __shfl_sync(mask, t1, o);
+      const int exo = __shfl_sync(mask, ex, o);
+      const float4* prims = reinterpret_cast<const float4*>(
+          __shfl_sync(mask, reinterpret_cast<unsigned long long>(sc.prims), o));
+      const float4* wlo = reinterpret_cast<const float4*>(
+          __shfl_sync(mask, reinterpret_cast<unsigned long long>(sc.wlo), o));
+      const float k2 = __shfl_sync(mask, sc.k2, o);
+      if (work) {
         PrimHit h;
-        if (prim_test(sc.prims, sc.wlo, lq[nq * stride], ray, t0, t1, sc.k2, ex, h))
-          acc += __float2ll_rn(fminf(fmaxf(hit_half_integral(h), 0.f), 2.f) * kScale);
-        if (acc >= kOne) done = true;  // saturated: T = 0 whatever follows
+        const int slot = lq[(nq_o - 1 - (rank - off_o)) * stride + (o - lane)];
+        if (prim_test(prims, wlo, slot, ro, t0o, t1o, k2, exo, h))
+          atomicAdd(acc + (o - lane),
+                    (unsigned long long)__float2ll_rn(fminf(fmaxf(hit_half_integral(h), 0.f), 2.f) * kScale));
+      }
+      __syncwarp(mask);
+      if (mine > 0) {
+        nq = mine - min(mine, max(0, nact - off));
+        if (*acc >= kOne) {  // saturated: T = 0 whatever follows
+          done = true;
+          nq = 0;
+        }
       }
     } else if (!done && !tdone) {
       if (unsigned(node) >= unsigned(sc.n_nodes)) {
@@ -107,7 +143,8 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
     if (tdone && nq == 0) done = true;
     if (!__any_sync(mask, !done)) break;
   }
-  return acc >= kOne ? 1.f : float(acc) * (1.f / kScale);
+  const unsigned long long a = *acc;
+  return a >= kOne ? 1.f : float(a) * (1.f / kScale);
 }
 
 }  // namespace ugp
