@@ -50,18 +50,18 @@
 
 namespace ugp {
 
-constexpr int kLeafQ = 6;  // primitives a lane may hold back before they are tested
+constexpr int kLeafQ = 12;  // primitives a lane may hold back before they are tested
 
-// Bins hold 1/2 I in fixed point, units of 2^-29: integer sums do not depend on the order the
+// Bins hold 1/2 I in fixed point, units of 2^-28: integer sums do not depend on the order the
 // contributions arrive in, so a ray's result does not depend on which rays share its warp or
 // which lanes test its primitives. A contribution is capped at kBinCap, just above 1, and a bin
 // that already holds kBinCap or more takes no more: the bins before the crossing bin sum to at
 // most u <= 1, so such a bin lies at or after the crossing, where only "exceeds u" matters. A
 // step adds to one ray's bins from at most kLeafQ lanes, so no bin or running sum passes
-// 7 kBinCap < 2^32. Contributions below 2^-30 are dropped.
-constexpr float kBinScale = 536870912.f;            // 2^29
-constexpr float kBinUnit = 1.862645149230957e-09f;  // 2^-29
-constexpr unsigned kBinCap = (1u << 29) + 1u;       // just above 1 in bin units
+// (kLeafQ + 1) kBinCap < 2^32. Contributions below 2^-29 are dropped.
+constexpr float kBinScale = 268435456.f;            // 2^28
+constexpr float kBinUnit = 3.725290298461914e-09f;  // 2^-28
+constexpr unsigned kBinCap = (1u << 28) + 1u;       // just above 1 in bin units
 static_assert((kLeafQ + 1ull) * kBinCap < (1ull << 32), "bins must not wrap");
 
 struct FFSmem {

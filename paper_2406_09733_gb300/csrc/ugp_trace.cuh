@@ -9,8 +9,8 @@ constexpr int kTrBlock = 128;      // transmittance: threads per block
 constexpr int kTrStack = 48;       // transmittance: traversal stack depth
 constexpr int kTrBlocksPerSM = 8;  // transmittance: resident blocks per SM (24 KB shared, <= 64 registers)
 constexpr int kFFBlock = 128;      // free flight: threads per block of the scan
-constexpr int kFFStack = 34;       // free flight: traversal stack depth (4-wide nodes)
-constexpr int kFFBlocksPerSM = 6;  // free flight: resident scan blocks per SM (36 KB shared, <= 80 registers)
+constexpr int kFFStack = 36;       // free flight: traversal stack depth (4-wide nodes)
+constexpr int kFFBlocksPerSM = 5;  // free flight: resident scan blocks per SM (41 KB shared, <= 102 registers)
 constexpr int kB = 32;             // free flight: bins of the scan
 
 struct TraceScene {

@@ -11,7 +11,7 @@ struct TrStats {
   uint8_t st;
 };
 
-constexpr int kTrLeafQ = 6;  // primitives a lane may hold back (top of its stack column)
+constexpr int kTrLeafQ = 10;  // primitives a lane may hold back (top of its stack column)
 
 // Returns tau = 1/2 sum_k I_k(clip_k) over [t0, t1], stopping once it reaches 1 (then T = 0).
 // The sum is kept in 64-bit fixed point (units of 2^-40), so it is the same in any traversal
@@ -25,6 +25,7 @@ constexpr int kTrLeafQ = 6;  // primitives a lane may hold back (top of its stac
 // them (or a queue is nearly full or a traversal is over), spreads the held-back primitives over
 // the lanes, one per lane whichever ray it belongs to, and each lane adds its primitive's term to
 // the owner's sum with a shared-memory atomic.
+static_assert(kTrLeafQ < 16, "queue lengths are summed from four bit planes");
 static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, float t0, float t1, int ex,
                                          int* stk, int stride, unsigned long long* acc, TrStats& ts) {
   const unsigned mask = __activemask();
@@ -39,19 +40,20 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
   int* lq = stk + (kTrStack - kTrLeafQ) * stride;
   __syncwarp(mask);
   for (;;) {
-    // queue lengths (below 8) as three bit planes: their sum and each lane's exclusive prefix
+    // queue lengths (below 16) as four bit planes: their sum and each lane's exclusive prefix
     const int mine = done ? 0 : nq;
     const unsigned p0 = __ballot_sync(mask, (mine & 1) != 0), p1 = __ballot_sync(mask, (mine & 2) != 0),
-                   p2 = __ballot_sync(mask, (mine & 4) != 0);
-    const int total = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2);
+                   p2 = __ballot_sync(mask, (mine & 4) != 0), p3 = __ballot_sync(mask, (mine & 8) != 0);
+    const int total = __popc(p0) + 2 * __popc(p1) + 4 * __popc(p2) + 8 * __popc(p3);
     // a node step may add four held-back primitives: it runs only while every lane has room
     const bool urgent = __any_sync(mask, !done && (nq > kTrLeafQ - 4 || (tdone && nq > 0)));
     if (total > 0 && (total >= nact || urgent)) {
       // the lane of rank r takes item r of the queues laid end to end (lane order)
-      const int off = __popc(p0 & below_me) + 2 * __popc(p1 & below_me) + 4 * __popc(p2 & below_me);
+      const int off = __popc(p0 & below_me) + 2 * __popc(p1 & below_me) + 4 * __popc(p2 & below_me) +
+                      8 * __popc(p3 & below_me);
       const unsigned starts = __reduce_or_sync(mask, (mine > 0 && off < 32) ? (1u << off) : 0u);
       const bool work = rank < total;
-      const int o = work ? int(__fns(p0 | p1 | p2, 0u, __popc(starts & (0xffffffffu >> (31 - rank))))) : lane;
+      const int o = work ? int(__fns(p0 | p1 | p2 | p3, 0u, __popc(starts & (0xffffffffu >> (31 - rank))))) : lane;
       const int off_o = __shfl_sync(mask, off, o);
       const int nq_o = __shfl_sync(mask, mine, o);
       Ray ro;
