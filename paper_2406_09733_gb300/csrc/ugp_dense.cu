@@ -78,21 +78,31 @@ struct Grp {
   __device__ unsigned total(unsigned v) const { return __reduce_add_sync(mask, v); }
 };
 
-// Interval columns of one ray (cap entries each); `full` holds the terms of the first evaluation.
+// Interval columns of one ray (cap entries each). For the interval clipped to the bracket,
+// [x0, y0] = [max(a, lo), min(b, hi)]: `ex0` is erfc(|tau(x0)|) carrying the sign of tau(x0)
+// (tau(x0) >= 0: positive), and `full` is 1/2 I over [x0, y0], both taken when the interval is
+// collected, so that a later term over [x0, t] costs one erfc.
 struct Iv {
-  float *a, *b, *tn, *ts, *s, *e0, *th, *full;
+  float *a, *b, *tn, *ts, *s, *e0, *ex0, *full;
   int* id;  // index with the end-point flags (pack_id)
   int cap;
 };
 
 template <int kCap>
 struct Intervals {
-  float a[kCap], b[kCap], tn[kCap], ts[kCap], s[kCap], e0[kCap], th[kCap], full[kCap];
+  float a[kCap], b[kCap], tn[kCap], ts[kCap], s[kCap], e0[kCap], ex0[kCap], full[kCap];
   int id[kCap];
   __device__ Iv view(int off, int cap) {
-    return Iv{a + off, b + off, tn + off, ts + off, s + off, e0 + off, th + off, full + off, id + off, cap};
+    return Iv{a + off, b + off, tn + off, ts + off, s + off, e0 + off, ex0 + off, full + off, id + off, cap};
   }
 };
+
+// 1/2 I between two cut points of an interval (App. A) from erfc(|tau|) at each, signed as in
+// Iv::ex0: a difference of erf values without cancellation for same-sign pairs.
+__device__ __forceinline__ float cut_diff(float ep_signed, float eq, float tq) {
+  const float ep = fabsf(ep_signed);
+  return !signbit(ep_signed) ? ep - eq : (tq <= 0.f ? eq - ep : 2.f - ep - eq);
+}
 struct WarpSmem {  // main pass: the two half-warps' slices
   Intervals<2 * kDCap> iv;
 };
@@ -135,16 +145,14 @@ __device__ Finish solve(const Grp<G>& g, const Iv& iv, int n, float lo, float hi
   ex = max(ex, -60);  // below 2^-60 every term rounds to zero, which changes no decision
   const float dscale = ldexpf(1.f, 61 - ex), dunit = ldexpf(1.f, ex - 61);
   auto fxF = [](float v) { return __float2ll_rn(fminf(fmaxf(v, 0.f), 64.f) * kFScale); };
-  // full[e]: the term of interval e at t = hi_e, which for an interval ending at or before hi_e is
-  // its whole contribution; later evaluations reuse it for every interval that ends before t, so
-  // only the intervals containing t need the erf.
-  float* full = iv.full;
+  // full[e] is interval e's whole term on the bracket, which is its term at t = hi_e (every
+  // interval ends by bmax); later evaluations reuse it for every interval that ends before t,
+  // so only the intervals containing t need an erfc, one each (its start's is in ex0).
+  const float* full = iv.full;
   auto term = [&](int e, float t) {
-    const float x0 = fmaxf(iv.a[e], lo), x1 = fminf(iv.b[e], t);
-    const int p = iv.id[e];
-    return x0 < x1 ? seg_half_integral(x0, x1, iv.a[e], iv.b[e], packed_a_end(p), packed_b_end(p), iv.tn[e], iv.ts[e],
-                                       iv.s[e], iv.e0[e], iv.th[e])
-                   : 0.f;
+    if (!(fmaxf(iv.a[e], lo) < t)) return 0.f;
+    const float tq = tau_at(t, iv.tn[e], iv.ts[e], iv.s[e]);
+    return iv.e0[e] * (0.25f * kSqrtPi) / iv.s[e] * cut_diff(iv.ex0[e], erfcf(fabsf(tq)), tq);
   };
   auto evalF = [&](float t, float& f, float& fp) {
     long long fl = 0, fpl = 0;
@@ -159,13 +167,8 @@ __device__ Finish solve(const Grp<G>& g, const Iv& iv, int n, float lo, float hi
   float fh;
   {
     long long fl = 0;
-    for (int e = lane; e < n; e += G) {
-      const float v = term(e, hi_e);
-      full[e] = v;
-      fl += fxF(v);
-    }
+    for (int e = lane; e < n; e += G) fl += fxF(full[e]);
     fh = Flo - u + float(g.sum(fl)) * kFUnit;
-    g.sync();
   }
   float t;
   if (!(fh > 0.f)) {
@@ -274,8 +277,14 @@ __device__ __forceinline__ void collect_one(const Grp<G>& g, const Iv& iv, const
   if (ok) {
     const int i = n + __popc(m & g.below());
     if (i < iv.cap) {
+      const float x0 = fmaxf(hh.a, lo), y0 = fminf(hh.b, hi);
+      const float tp = (hh.a_end && x0 == hh.a) ? -hh.th : tau_at(x0, hh.tn, hh.ts, hh.s);
+      const float tq = (hh.b_end && y0 == hh.b) ? hh.th : tau_at(y0, hh.tn, hh.ts, hh.s);
+      const float ep = erfcf(fabsf(tp));
+      const float ex0 = tp >= 0.f ? ep : -ep;
       iv.a[i] = hh.a; iv.b[i] = hh.b; iv.tn[i] = hh.tn; iv.ts[i] = hh.ts;
-      iv.s[i] = hh.s; iv.e0[i] = hh.e0; iv.th[i] = hh.th; iv.id[i] = pack_id(hh);
+      iv.s[i] = hh.s; iv.e0[i] = hh.e0; iv.ex0[i] = ex0; iv.id[i] = pack_id(hh);
+      iv.full[i] = hh.e0 * (0.25f * kSqrtPi) / hh.s * cut_diff(ex0, erfcf(fabsf(tq)), tq);
     }
   }
   n += __popc(m);
