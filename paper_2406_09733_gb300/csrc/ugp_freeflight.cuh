@@ -50,7 +50,7 @@
 
 namespace ugp {
 
-constexpr int kLeafQ = 12;  // primitives a lane may hold back before they are tested
+constexpr int kLeafQ = 12;  // primitives a lane may hold back before they are tested (< 16)
 
 // Bins hold 1/2 I in fixed point, units of 2^-28: integer sums do not depend on the order the
 // contributions arrive in, so a ray's result does not depend on which rays share its warp or
@@ -63,6 +63,7 @@ constexpr float kBinScale = 268435456.f;            // 2^28
 constexpr float kBinUnit = 3.725290298461914e-09f;  // 2^-28
 constexpr unsigned kBinCap = (1u << 28) + 1u;       // just above 1 in bin units
 static_assert((kLeafQ + 1ull) * kBinCap < (1ull << 32), "bins must not wrap");
+static_assert(kLeafQ < 16, "queue lengths are summed from four bit planes");
 
 struct FFSmem {
   unsigned bin[kB][kFFBlock];  // fixed-point bins
@@ -247,7 +248,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
   float lo = 0.f, hi = 0.f, L = 0.f, target = 0.f, limit = 0.f;
   for (;;) {
     const unsigned idle = __ballot_sync(kFull, !busy && !exhausted);
-    const unsigned working = __ballot_sync(kFull, busy);
+    unsigned working = __ballot_sync(kFull, busy);
     if (idle && (__popc(idle) >= kRefill || working == 0)) {
       int base = 0;
       const int leader = __ffs(idle) - 1;
@@ -296,8 +297,9 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
           }
         }
       }
+      working = __ballot_sync(kFull, busy);
     }
-    if (__ballot_sync(kFull, busy) == 0) {
+    if (working == 0) {
       if (__all_sync(kFull, exhausted)) break;
       continue;
     }
@@ -308,14 +310,13 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
     if (total > 0 && (total >= 32 || urgent)) {
       // ---- leaf step: the warp's held-back primitives, up to 32, one per lane whichever ray
       // they belong to; lane i takes item i of the lanes' queues laid end to end
-      int off = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, off, o);
-        if (lane >= o) off += y;
-      }
-      off -= mine;
-      const unsigned has = __ballot_sync(kFull, mine > 0);
+      // each lane's exclusive prefix of the queue lengths (below 16) from four bit planes
+      const unsigned below_me = (1u << lane) - 1u;
+      const unsigned q0 = __ballot_sync(kFull, (mine & 1) != 0), q1 = __ballot_sync(kFull, (mine & 2) != 0),
+                     q2 = __ballot_sync(kFull, (mine & 4) != 0), q3 = __ballot_sync(kFull, (mine & 8) != 0);
+      const int off = __popc(q0 & below_me) + 2 * __popc(q1 & below_me) + 4 * __popc(q2 & below_me) +
+                      8 * __popc(q3 & below_me);
+      const unsigned has = q0 | q1 | q2 | q3;
       const unsigned starts = __reduce_or_sync(kFull, (mine > 0 && off < 32) ? (1u << off) : 0u);
       const bool work = lane < total;
       const int o = work ? int(__fns(has, 0u, __popc(starts & (0xffffffffu >> (31 - lane))))) : lane;

@@ -151,12 +151,14 @@ constexpr float kRefineAbove = 8.f;
 __device__ __forceinline__ bool prim_test(const float4* __restrict__ recs, const float4* __restrict__ wlo,
                                           int slot, const Ray& r, float t0, float t1, float k2, int exclude,
                                           PrimHit& h) {
-  const float4 r3 = __ldg(recs + 4 * slot + 3);
-  const int id = __float_as_int(r3.y);
-  if (id == exclude || r3.z == 0.f) return false;
+  // the whole 64-byte record in one round of loads (the exclusion and validity test rarely ends
+  // the test, so the other three loads need not wait for it)
   const float4 r0 = __ldg(recs + 4 * slot + 0);
   const float4 r1 = __ldg(recs + 4 * slot + 1);
   const float4 r2 = __ldg(recs + 4 * slot + 2);
+  const float4 r3 = __ldg(recs + 4 * slot + 3);
+  const int id = __float_as_int(r3.y);
+  if (id == exclude || r3.z == 0.f) return false;
   float px, lx, py, ly, pz, lz;
   two_sum(r.o.x, -r0.w, px, lx);
   two_sum(r.o.y, -r1.w, py, ly);
