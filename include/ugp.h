@@ -492,9 +492,10 @@ ugp_status ugp_guide_adam_step(ugp_guide* g, const float* grad, void* stream);
  *   emitters        NULL, or a device table from ugp_build_emitter_table for this BVH and
  *                   these materials: each scattering vertex then also samples a point of an
  *                   emissive primitive (light sampling, balanced against phase sampling). A
- *                   table built for another primitive count is ignored. Not combined with
- *                   nee = 1 and an area light (UGP_ERR_INVALID_ARG): one light sample per
- *                   vertex. */
+ *                   table built for another primitive count is ignored. With nee = 1 and an
+ *                   area light as well, a vertex takes one light sample of each (two shadow
+ *                   rays), each balanced against phase sampling alone (the two light kinds do
+ *                   not overlap). */
 typedef struct ugp_render_params {
   int32_t spp, spp_begin, max_depth, nee;
   uint64_t seed;
@@ -526,7 +527,7 @@ ugp_status ugp_build_emitter_table(const ugp_bvh* bvh, const ugp_materials* mate
                                    size_t table_bytes, void* stream);
 
 /* Workspace bytes ugp_render needs for a width x height image (path state, queues and
- * per-path primitive-slot lists, 1236 bytes per pixel, plus one 73,728-byte interval slot of the
+ * per-path primitive-slot lists, 1284 bytes per pixel, plus one 73,728-byte interval slot of the
  * free-flight finish per 64 pixels, at most 2432 of them, plus alignment). */
 size_t ugp_render_workspace_size(int32_t width, int32_t height);
 /* Workspace bytes of a guided render of up to max_depth scattering vertices: the plain

@@ -120,7 +120,7 @@ struct PathScanSrc {
 
 __global__ void __launch_bounds__(kFFBlock, kFFBlocksPerSM) k_extend(TraceScene sc, LightsDev L, uint2 key, int sample, int bounce,
                                                      int spawn_mode, PathSoA ps, const int* __restrict__ q,
-                                                     const int* cnt, int* reset_next, int* reset_shadow,
+                                                     const int* cnt, int* reset_next, int* reset_shadow, int* reset_shadow_e,
                                                      unsigned long long* rays, unsigned long long* stats,
                                                      DenseQueue dq, int* scan_next) {
   __shared__ FFSmem sm;
@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kFFBlock, kFFBlocksPerSM) k_extend(TraceScene 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *reset_next = 0;
     *reset_shadow = 0;
+    *reset_shadow_e = 0;
     if (rays) atomicAdd(rays, (unsigned long long)count);
   }
   PathScanSrc src{sc, spawn_mode, count, ps, q, dq, rays, stats, 0, 0, 0, 0.f, 0.f, 0.f};
@@ -138,6 +139,7 @@ template <bool kGuided>
 __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 key, int sample, int bounce, int max_depth,
                                                int nee, PathSoA ps, const int* __restrict__ q, const int* cnt,
                                                int* __restrict__ q_next, int* cnt_next, ShadowSoA sh, int* cnt_shadow,
+                                               ShadowSoA she, int* cnt_shadow_e,
                                                int* dense_cnt, int* scan_next, GuidedShade gs, EmitterDev E) {
   const bool em_on = emitters_on(E);
   const int count = load_count(cnt);
@@ -253,13 +255,13 @@ __global__ void __launch_bounds__(128) k_shade(MatDev mats, LightsDev L, uint2 k
             const float3 c = f3(m0.w, m1.w, m2.w) - x;
             const float wm = mis_w(2.f * dot3(c, c) * pj, m3.x * ps_l);
             const float3 contrib = (wm * 0.5f * m3.x / (r2 * pj)) * (beta * (f * f3(m3.y, m3.z, m3.w)));
-            const int j = queue_append(cnt_shadow);
-            sh.path[j] = p;
-            sh.ox[j] = x.x; sh.oy[j] = x.y; sh.oz[j] = x.z;
-            sh.dx[j] = wl.x; sh.dy[j] = wl.y; sh.dz[j] = wl.z;
-            sh.dist[j] = -r;  // negative: the contribution counts when T > 0, unscaled
-            sh.excl[j] = k;
-            sh.cr[j] = contrib.x; sh.cg[j] = contrib.y; sh.cb[j] = contrib.z;
+            const int j = queue_append(cnt_shadow_e);
+            she.path[j] = p;
+            she.ox[j] = x.x; she.oy[j] = x.y; she.oz[j] = x.z;
+            she.dx[j] = wl.x; she.dy[j] = wl.y; she.dz[j] = wl.z;
+            she.dist[j] = -r;  // negative: the contribution counts when T > 0, unscaled
+            she.excl[j] = k;
+            she.cr[j] = contrib.x; she.cg[j] = contrib.y; she.cb[j] = contrib.z;
           }
         }
       }
@@ -474,7 +476,7 @@ RenderLayout render_layout(int64_t n, int max_depth = -1) {
   const size_t col = align256(size_t(n) * 4);
   L.state = off;   off += 20 * col;
   L.queues = off;  off += 2 * col;
-  L.shadow = off;  off += 12 * col;
+  L.shadow = off;  off += 24 * col;  // light samples of the area light, then of the emitters
   L.counts = off;  off += 256;
   L.dense = off;   off += dense_queue_bytes(n);
   L.lists = off;   off += slot_list_bytes(n);
@@ -584,8 +586,12 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   ShadowSoA sh{I(RL.shadow, 0), F(RL.shadow, 1), F(RL.shadow, 2), F(RL.shadow, 3), F(RL.shadow, 4),
                F(RL.shadow, 5), F(RL.shadow, 6), F(RL.shadow, 7), I(RL.shadow, 8), F(RL.shadow, 9),
                F(RL.shadow, 10), F(RL.shadow, 11)};
+  ShadowSoA she{I(RL.shadow, 12), F(RL.shadow, 13), F(RL.shadow, 14), F(RL.shadow, 15), F(RL.shadow, 16),
+                F(RL.shadow, 17), F(RL.shadow, 18), F(RL.shadow, 19), I(RL.shadow, 20), F(RL.shadow, 21),
+                F(RL.shadow, 22), F(RL.shadow, 23)};
   int* queue[2] = {I(RL.queues, 0), I(RL.queues, 1)};
-  // [0], [1] queue lengths, [2] shadow rays, [3] scan ray counter
+  // [0], [1] queue lengths, [2] shadow rays toward the area light, [3] scan ray counter,
+  // [4] shadow rays toward emitters
   int* counts = reinterpret_cast<int*>(ws + RL.counts);
   int* scan_next = counts + 3;
   DenseQueue dq = dense_queue_at(ws + RL.dense, n);
@@ -605,9 +611,6 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
   if (params->emitters && (reinterpret_cast<uintptr_t>(params->emitters) & 255))
     return fail(UGP_ERR_INVALID_ARG, "ugp_render: emitter table must be 256-byte aligned");
   const EmitterDev Em = emitter_dev(params->emitters, bvh);
-  // the shadow queue holds one ray per path and bounce
-  if (Em.cdf && params->nee && Ld.has_quad)
-    return fail(UGP_ERR_INVALID_ARG, "ugp_render: light sampling of emitters and of the area light in one render");
 
   GuidedShade gs{};
   GuideDev gd{};
@@ -641,7 +644,7 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
       const int nxt = 1 - cur;
       prof_begin(kStExtend, st);
       k_extend<<<g_ext, kFFBlock, 0, st>>>(sc, Ld, key, sample, b, params->spawn_mode, ps, queue[cur], counts + cur,
-                                            counts + nxt, counts + 2, ray_counts, stats, dq, scan_next);
+                                            counts + nxt, counts + 2, counts + 4, ray_counts, stats, dq, scan_next);
       prof_end(kStExtend, st);
       {
         const ugp_status ds = launch_dense(sc, dq, 0, counts + cur, n, ps.prim, nullptr, ps.tsp, nullptr,
@@ -659,16 +662,23 @@ extern "C" ugp_status ugp_render(const ugp_bvh* bvh, const ugp_materials* materi
       prof_begin(kStShade, st);
       if (guide)
         k_shade<true><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps, queue[cur],
-                                                counts + cur, queue[nxt], counts + nxt, sh, counts + 2, dq.count,
+                                                counts + cur, queue[nxt], counts + nxt, sh, counts + 2, she, counts + 4, dq.count,
                                                 scan_next, gs, Em);
       else
         k_shade<false><<<g_shade, 128, 0, st>>>(md, Ld, key, sample, b, params->max_depth, params->nee, ps,
-                                                 queue[cur], counts + cur, queue[nxt], counts + nxt, sh, counts + 2,
+                                                 queue[cur], counts + cur, queue[nxt], counts + nxt, sh, counts + 2, she, counts + 4,
                                                  dq.count, scan_next, gs, Em);
       prof_end(kStShade, st);
-      if ((params->nee && Ld.has_quad) || Em.cdf) {
+      // one launch per kind of light sample: a path's two shadow rays add to its radiance in
+      // this order, so the sum does not depend on scheduling
+      if (params->nee && Ld.has_quad) {
         prof_begin(kStShadow, st);
         k_shadow<<<g_shadow, kTrBlock, 0, st>>>(sc, sh, counts + 2, ps, ray_counts, stats);
+        prof_end(kStShadow, st);
+      }
+      if (Em.cdf) {
+        prof_begin(kStShadow, st);
+        k_shadow<<<g_shadow, kTrBlock, 0, st>>>(sc, she, counts + 4, ps, ray_counts, stats);
         prof_end(kStShadow, st);
       }
       cur = nxt;

@@ -165,9 +165,27 @@ def test_emitter_table_errors(gpu):
     bvh, mats, cam, li = ugp.scene_to_device(s)
     table = ugp.build_emitter_table(bvh, mats)
     r = ugp.Renderer(cam.width, cam.height)
-    with pytest.raises(ugp.UgpError):
-        r.render(bvh, mats, cam, li, 1, 2, nee=True, emitters=table)
+    with pytest.raises(ugp.UgpError):  # a table off its 256-byte alignment
+        r.render(bvh, mats, cam, li, 1, 2, nee=True, emitters=table[1:])
     acc, _ = r.render(bvh, mats, cam, li, 1, 2, nee=False, emitters=table)
     torch.cuda.synchronize()
     assert torch.isfinite(acc).all()
+
+
+def test_area_light_and_emitters_match_oracle(gpu, orc):
+    """Both light samples at every vertex, one of the area light and one of an emissive primitive,
+    each balanced against phase sampling, against the oracle's render with both."""
+    s = emitter_scene(seed=11)
+    s.lights = scenes.Lights(True, (0.35, 1.05, 0.35), (0.3, 0.0, 0.0), (0.0, 0.0, 0.3), (8.0, 8.0, 8.0),
+                             (0.1, 0.15, 0.2))
+    spp, D = 8192, 3
+    a, q, cnt = gpu_render(gpu, s, spp=spp, max_depth=D, seed=17, emitters=True)
+    a_o, q_o, (ne_o, ns_o) = orc.render(s, spp=spp, max_depth=D, seed=17, nee_emitters=1)
+    assert cnt[1] > 0 and ns_o > 0 and cnt[2] == 0
+    assert abs(cnt[1] / ns_o - 1) < 0.02
+    compare(a, q, spp, a_o, q_o, spp)
+    # the two light samples together against the area light's alone: the same image
+    a1, q1, cnt1 = gpu_render(gpu, s, spp=spp, max_depth=D, seed=19)
+    assert cnt1[1] < cnt[1]
+    compare(a, q, spp, a1, q1, spp, z_max=4.0)
 
