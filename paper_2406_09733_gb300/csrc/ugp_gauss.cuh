@@ -257,10 +257,23 @@ __device__ __forceinline__ float byte_f(uint32_t w, int c) {
   return __uint_as_float(__byte_perm(w, 0x4B000000u, sel)) - 8388608.f;
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Slab test of the four children of a 4-wide quantised node (layout in ugp_internal.cuh)
 // against [tmin, tmax]: returns the mask of children hit and writes their references and entry
 // distances. Child c's face along axis a is o_a + q 2^e_a, so its ray distance is
 // q (2^e_a inv_a) + (o_a - ray.o_a) inv_a: two products per axis and node, one fma per face.
+// The ray's direction signs pick, once per node, which face of each axis is met first, so a
+// child's entry and exit are a three-way max and min (the same values as the min/max pairs).
 __device__ __forceinline__ unsigned node4_test(const uint4* __restrict__ n4, int node, const Ray& r, float tmin,
                                                float tmax, float en[4], int ch[4]) {
   const uint4* nd = n4 + 4 * size_t(node);
@@ -272,6 +285,10 @@ __device__ __forceinline__ unsigned node4_test(const uint4* __restrict__ n4, int
   const float ax = sx * r.inv.x, bx = (__uint_as_float(w0.x) - r.o.x) * r.inv.x;
   const float ay = sy * r.inv.y, by = (__uint_as_float(w0.y) - r.o.y) * r.inv.y;
   const float az = sz * r.inv.z, bz = (__uint_as_float(w0.z) - r.o.z) * r.inv.z;
+  const bool px = r.inv.x >= 0.f, py = r.inv.y >= 0.f, pz = r.inv.z >= 0.f;
+  const uint32_t nx = px ? w1.x : w1.w, fx = px ? w1.w : w1.x;  // near and far faces
+  const uint32_t ny = py ? w1.y : w2.x, fy = py ? w2.x : w1.y;
+  const uint32_t nz = pz ? w1.z : w2.y, fz = pz ? w2.y : w1.z;
   ch[0] = int(w3.x);
   ch[1] = int(w3.y);
   ch[2] = int(w3.z);
@@ -279,11 +296,10 @@ __device__ __forceinline__ unsigned node4_test(const uint4* __restrict__ n4, int
   unsigned hit = 0u;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const float x0 = fmaf(byte_f(w1.x, c), ax, bx), x1 = fmaf(byte_f(w1.w, c), ax, bx);
-    const float y0 = fmaf(byte_f(w1.y, c), ay, by), y1 = fmaf(byte_f(w2.x, c), ay, by);
-    const float z0 = fmaf(byte_f(w1.z, c), az, bz), z1 = fmaf(byte_f(w2.y, c), az, bz);
-    const float tl = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
-    const float th = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), tmax));
+    const float tl = fmaxf(max3f(fmaf(byte_f(nx, c), ax, bx), fmaf(byte_f(ny, c), ay, by), fmaf(byte_f(nz, c), az, bz)),
+                           tmin);
+    const float th = fminf(min3f(fmaf(byte_f(fx, c), ax, bx), fmaf(byte_f(fy, c), ay, by), fmaf(byte_f(fz, c), az, bz)),
+                           tmax);
     en[c] = tl;
     if (ch[c] != kEmptyChild && tl <= th + 4e-7f * fabsf(th)) hit |= 1u << c;
   }
