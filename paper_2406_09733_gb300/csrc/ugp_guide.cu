@@ -118,16 +118,19 @@ struct ArraySrc {
 struct ArrayDst {
   float *head, *mix;
   GuideCfgDev cfg;
-  __device__ void put(int64_t r, const float (&Y)[kGOut]) const {
-    if (head) {
-#pragma unroll
-      for (int j = 0; j < kGOut; ++j) head[kGOut * r + j] = Y[j];
-    }
+  // the mixture when asked for (then a head asked for as well is written here, per thread),
+  // else the head
+  __device__ float* row_out(int64_t r) const { return (mix ? mix : head) + kGOut * r; }
+  __device__ void values(int64_t r, const float (&Y)[kGOut], float (&out)[kGOut]) const {
     if (mix) {
-      float m[kGOut];
-      mixture_from_head(cfg, Y, m);
+      if (head) {
 #pragma unroll
-      for (int j = 0; j < kGOut; ++j) mix[kGOut * r + j] = m[j];
+        for (int j = 0; j < kGOut; ++j) head[kGOut * r + j] = Y[j];
+      }
+      mixture_from_head(cfg, Y, out);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kGOut; ++j) out[j] = Y[j];
     }
   }
 };

@@ -148,48 +148,92 @@ __device__ __forceinline__ int64_t row_count(int64_t n_host, const int* n_dev) {
 }
 
 // ------------------------------------------------------------------ forward
-constexpr uint32_t kFwdX = kImgBytes;              // after W and biases
-constexpr uint32_t kFwdBar = kFwdX + kXTile;       // 58624
-constexpr uint32_t kFwdTmemSlot = kFwdBar + 8;
-constexpr uint32_t kFwdSmem = kFwdBar + 128;
+// A block (one per SM: 512 threads at up to 128 registers) holds kFwdGroups groups of 128
+// threads (warpgroups) that share the weights. Each group runs its own 128-row tiles with its
+// own activation tile, tensor-memory columns and mbarrier, synchronised by a named barrier of its
+// own, so one group's epilogue (the per-thread bias, ReLU and BF16 packing, the encoding of the
+// next tile, the mixture) overlaps the others' MMAs. The group's activation tile doubles as the
+// staging buffer of its output rows, which the group then writes out row by row (coalesced).
+constexpr int kFwdGroups = 4;
+constexpr int kFwdStage = kGOut + 4;  // floats between staged rows: 16-byte stores without bank conflicts
+constexpr uint32_t kFwdBuf = 128 * kFwdStage * 4;               // 22528: X tile or 128 output rows
+constexpr uint32_t kFwdX = kImgBytes;                           // after W and biases
+constexpr uint32_t kFwdValid = kFwdX + kFwdGroups * kFwdBuf;    // per group: 128 row flags
+constexpr uint32_t kFwdBar = kFwdValid + kFwdGroups * 128 * 4;  // weights, then one per group
+constexpr uint32_t kFwdTmemSlot = kFwdBar + 8 * (kFwdGroups + 1);
+constexpr uint32_t kFwdSmem = kFwdTmemSlot + 16;
+constexpr uint32_t kFwdTmemCols = 256;  // kFwdGroups x 64 columns
+static_assert(kFwdBuf >= kXTile && kFwdTmemCols >= 64 * kFwdGroups, "forward buffers");
+static_assert(kFwdSmem <= 227 * 1024, "forward block exceeds shared memory");
+
+// Barrier of the 128 threads of group `grp` (ids 1..kFwdGroups; 0 is __syncthreads).
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, 128;" ::"r"(grp + 1) : "memory");
+}
+// The same barrier, returning whether p held on any of the group's threads.
+__device__ __forceinline__ bool group_any(int grp, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n"
+      " .reg .pred a, b;\n"
+      " setp.ne.u32 a, %1, 0;\n"
+      " bar.red.or.pred b, %2, 128, a;\n"
+      " selp.u32 %0, 1, 0, b;\n"
+      "}\n"
+      : "=r"(r)
+      : "r"(uint32_t(p)), "r"(grp + 1)
+      : "memory");
+  return r != 0;
+}
+
+// Packs two values as BF16 after a ReLU (round to nearest even; the ReLU commutes with it).
+__device__ __forceinline__ uint32_t pack_bf16x2_relu(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 // Src: __device__ bool vertex(int64_t row, float3& x, float3& wo) const  (false: row unused)
-// Dst: __device__ void put(int64_t row, const float (&Y)[40]) const
+// Dst: __device__ float* row_out(int64_t row) const        where the row's 40 output values go
+//      __device__ void values(int64_t row, const float (&Y)[40], float (&out)[40]) const
+//                                                             the output values from the head Y
 template <class Src, class Dst>
-__global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Dst dst, int64_t n_host,
-                                                         const int* n_dev) {
+__global__ void __launch_bounds__(kGThreads * kFwdGroups, 1) k_guide_fwd(GuideDev g, Src src, Dst dst, int64_t n_host,
+                                                                      const int* n_dev) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  const int tid = int(threadIdx.x), warp = tid >> 5;
+  const int tid = int(threadIdx.x), warp = tid >> 5, grp = tid >> 7, t = tid & 127, lane = tid & 31;
   const int64_t n = row_count(n_host, n_dev);
   const int64_t ntiles = (n + kGThreads - 1) / kGThreads;
-  if (int64_t(blockIdx.x) >= ntiles) return;  // whole block, before any resource is taken
-  uint8_t* X = sm + kFwdX;
-  const uint32_t bar = smem_u32(sm + kFwdBar);
+  if (int64_t(blockIdx.x) * kFwdGroups >= ntiles) return;  // whole block, before any resource is taken
+  uint8_t* X = sm + kFwdX + grp * kFwdBuf;
+  float* stage = reinterpret_cast<float*>(X);
+  int* vflag = reinterpret_cast<int*>(sm + kFwdValid) + grp * 128;
+  const uint32_t wbar = smem_u32(sm + kFwdBar), gbar = wbar + 8u * uint32_t(grp + 1);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kFwdTmemSlot);
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int b = 0; b <= kFwdGroups; ++b) mbar_init(wbar + 8u * uint32_t(b), 1);
     fence_mbar_init();
   }
   if (warp == 0) {
-    tmem_alloc(smem_u32(tslot), 64);
+    tmem_alloc(smem_u32(tslot), kFwdTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t lane_addr = tmem + (uint32_t(warp * 32) << 16);
-  uint32_t phase = 0;
-  bool failed = false;
+  const uint32_t tbase = *tslot;
+  const uint32_t tmem = tbase + 64u * uint32_t(grp);
+  const uint32_t lane_addr = tmem + (uint32_t((warp & 3) * 32) << 16);
   if (tid == 0) {
-    mbar_expect_tx(bar, kImgBytes);
-    bulk_g2s(smem_u32(sm), g.img, kImgBytes, bar);
+    mbar_expect_tx(wbar, kImgBytes);
+    bulk_g2s(smem_u32(sm), g.img, kImgBytes, wbar);
   }
-  failed = __syncthreads_or(!mbar_wait(bar, phase, kGWaitNs));
-  phase ^= 1u;
+  bool failed = __syncthreads_or(!mbar_wait(wbar, 0u, kGWaitNs));
+  uint32_t phase = 0;
   const float* bias = reinterpret_cast<const float*>(sm + kImgBias);
-  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int64_t row = tile * kGThreads + tid;
+  for (int64_t tile = int64_t(blockIdx.x) * kFwdGroups + grp; tile < ntiles && !failed;
+       tile += int64_t(gridDim.x) * kFwdGroups) {
+    const int64_t row = tile * kGThreads + t;
     bool valid = false;
     {
       float f[kGWidth];
@@ -201,20 +245,21 @@ __global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Ds
 #pragma unroll
         for (int i = 0; i < kGWidth; ++i) f[i] = 0.f;
       }
-      store_row(X, tid, f);
+      store_row(X, t, f);
     }
+    float out[kGOut];
     for (int l = 0; l <= kGLayers; ++l) {
       fence_async_smem();
       tc_fence_before();
-      __syncthreads();
-      if (tid == 0) {
+      group_sync(grp);
+      if (t == 0) {
         tc_fence_after();
         issue(tmem, kmajor(X, 128), kmajor(sm + kImgW + l * kImgTile, 64), 4, kIdescFwd, false);
-        mma_commit(bar);
+        mma_commit(gbar);
       }
-      const bool ok = mbar_wait(bar, phase, kGWaitNs);
+      const bool ok = mbar_wait(gbar, phase, kGWaitNs);
       phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
+      if (group_any(grp, !ok)) {
         failed = true;
         break;
       }
@@ -223,24 +268,55 @@ __global__ void __launch_bounds__(kGThreads) k_guide_fwd(GuideDev g, Src src, Ds
         float v[kGWidth];
         tmem_row<kGWidth>(lane_addr, v);
 #pragma unroll
-        for (int i = 0; i < kGWidth; ++i) v[i] = fmaxf(v[i] + bias[l * kGWidth + i], 0.f);
-        store_row(X, tid, v);
+        for (int c = 0; c < 8; ++c) {
+          const float* b = bias + l * kGWidth + 8 * c;
+          uint4 q;
+          q.x = pack_bf16x2_relu(v[8 * c] + b[0], v[8 * c + 1] + b[1]);
+          q.y = pack_bf16x2_relu(v[8 * c + 2] + b[2], v[8 * c + 3] + b[3]);
+          q.z = pack_bf16x2_relu(v[8 * c + 4] + b[4], v[8 * c + 5] + b[5]);
+          q.w = pack_bf16x2_relu(v[8 * c + 6] + b[6], v[8 * c + 7] + b[7]);
+          *reinterpret_cast<uint4*>(X + tile_off(uint32_t(t), uint32_t(8 * c), 128u)) = q;
+        }
       } else {
         float v[48];
         tmem_row<48>(lane_addr, v);
         float Y[kGOut];
 #pragma unroll
         for (int i = 0; i < kGOut; ++i) Y[i] = v[i] + bias[kGLayers * kGWidth + i];
-        if (valid) dst.put(row, Y);
+        if (valid) dst.values(row, Y, out);
       }
     }
+    if (failed) break;
+    // the last MMA has read X: stage the rows there and write them out, 160 bytes per row
+    vflag[t] = valid ? 1 : 0;
+    if (valid) {
+      float4* srow = reinterpret_cast<float4*>(stage + t * kFwdStage);
+#pragma unroll
+      for (int j = 0; j < kGOut / 4; ++j) srow[j] = make_float4(out[4 * j], out[4 * j + 1], out[4 * j + 2], out[4 * j + 3]);
+    }
+    group_sync(grp);
+    // warp w of the group writes rows 32 w .. 32 w + 31, three rows (30 lanes) at a time
+    const int wbase = (warp & 3) * 32;
+    for (int i0 = 0; i0 < 32; i0 += 3) {
+      const int i = wbase + i0 + lane / 10, k = lane % 10;
+      if (lane < 30 && i0 + lane / 10 < 32 && vflag[i]) {
+        float* dp = dst.row_out(tile * kGThreads + i);
+        const float4 val = reinterpret_cast<const float4*>(stage + i * kFwdStage)[k];
+        if ((reinterpret_cast<uintptr_t>(dp) & 15) == 0) {
+          reinterpret_cast<float4*>(dp)[k] = val;
+        } else {
+          dp[4 * k] = val.x; dp[4 * k + 1] = val.y; dp[4 * k + 2] = val.z; dp[4 * k + 3] = val.w;
+        }
+      }
+    }
+    group_sync(grp);  // the staged rows are read before the next tile's encoding overwrites them
   }
-  if (failed && tid == 0 && g.err) atomicExch(g.err, int(UGP_ERR_TIMEOUT));
+  if (failed && t == 0 && g.err) atomicExch(g.err, int(UGP_ERR_TIMEOUT));
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, 64);
+    tmem_dealloc(tbase, kFwdTmemCols);
   }
 }
 
@@ -456,9 +532,10 @@ ugp_status launch_guide_forward(const GuideDev& g, const Src& src, const Dst& ds
     attr_set = true;
   }
   const int64_t tiles = (max_rows + kGThreads - 1) / kGThreads;
-  const int64_t cap = int64_t(guide_sm_count()) * 3;
-  const int grid = int(tiles < cap ? (tiles > 0 ? tiles : 1) : cap);
-  kern<<<grid, kGThreads, gk::kFwdSmem, st>>>(g, src, dst, n_host, n_dev);
+  const int64_t need = (tiles + gk::kFwdGroups - 1) / gk::kFwdGroups;
+  const int64_t cap = int64_t(guide_sm_count());  // one block of four groups per SM (registers)
+  const int grid = int(need < cap ? (need > 0 ? need : 1) : cap);
+  kern<<<grid, kGThreads * gk::kFwdGroups, gk::kFwdSmem, st>>>(g, src, dst, n_host, n_dev);
   UGP_CUDA_CHECK(cudaGetLastError());
   return UGP_OK;
 }

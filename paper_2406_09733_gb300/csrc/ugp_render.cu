@@ -387,12 +387,9 @@ struct MixByPathDst {
   const int* q;
   float* mix;
   GuideCfgDev cfg;
-  __device__ void put(int64_t r, const float (&Y)[kGOut]) const {
-    float m[kGOut];
-    mixture_from_head(cfg, Y, m);
-    float4* out = reinterpret_cast<float4*>(mix + size_t(q[r]) * kGOut);
-#pragma unroll
-    for (int j = 0; j < kGOut / 4; ++j) out[j] = make_float4(m[4 * j], m[4 * j + 1], m[4 * j + 2], m[4 * j + 3]);
+  __device__ float* row_out(int64_t r) const { return mix + size_t(q[r]) * kGOut; }
+  __device__ void values(int64_t, const float (&Y)[kGOut], float (&out)[kGOut]) const {
+    mixture_from_head(cfg, Y, out);
   }
 };
 
