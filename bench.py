@@ -58,7 +58,7 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-pixels", type=int, default=4096, help="pixels of the CPU-baseline sample")
-    p.add_argument("--kernel-case", choices=["ff_camera512", "guide_rows256k"], default=None,
+    p.add_argument("--kernel-case", choices=["ff_camera512", "render_960x540", "guide_rows256k"], default=None,
                    help="run one small kernel case for profilers and exit (no bench line)")
     p.add_argument("--no-mse", action="store_true", help="skip the equal-time MSE study")
     p.add_argument("--mse-width", type=int, default=480, help="image width of the MSE study")
@@ -961,6 +961,26 @@ def run_kernel_case(args):
     return 0
 
 
+def run_render_case(args):
+    """One frame of the bench scene (the workload's primitives and lighting) at 960 x 540, 1 spp,
+    max depth 4: a small case for ncu captures of the renderer's kernels (k_extend, k_dense,
+    k_dense_big, k_shade, k_shadow), a few GB on the device."""
+    import torch
+    from paper_2406_09733_gb300 import ugp
+    dev = torch.device("cuda")
+    args.width, args.height = 960, 540
+    scene = bench_scene(args)
+    bvh, mats, camera, lights = ugp.scene_to_device(scene, device=dev)
+    r = ugp.Renderer(args.width, args.height, device=dev)
+    cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+    r.render(bvh, mats, camera, lights, spp=1, max_depth=4, seed=3, ray_counts=cnt)
+    torch.cuda.synchronize()
+    c = cnt.cpu().tolist()
+    print(json.dumps({"kernel_case": args.kernel_case, "extend_queries": c[0], "shadow_queries": c[1],
+                      "queries_with_error_status": c[2]}))
+    return 0
+
+
 def run_guide_case(args):
     """One forward and one gradient call of the guide on 2^18 random vertices (ncu case)."""
     import torch
@@ -982,6 +1002,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.kernel_case == "guide_rows256k":
         return run_guide_case(args)
+    if args.kernel_case == "render_960x540":
+        return run_render_case(args)
     if args.kernel_case:
         return run_kernel_case(args)
     if args.impl == "reference":
