@@ -5,14 +5,13 @@
 //   1. k_prim_bounds   per primitive: rotation from the quaternion, bounding box of
 //                      the k-ellipsoid, block-reduced centroid bounds
 //   2. k_morton        30-bit Morton code of each box centre
-//   3. radix sort      (CUB, on the caller's workspace) of (code, index)
+//   3. radix sort      (ugp_sort.cu, on the caller's workspace) of (code, index), stable
 //   4. k_hierarchy     binary radix tree over the sorted codes (Karras, HPG 2012)
 //   5. k_records       64-byte hot records in leaf order (W = S^-1 R^T, mu, g0, index) and
 //                      the low float parts of W (48 B, read only by ill-conditioned hits)
 //   6. k_refit         bottom-up child boxes with one atomic counter per node
 //   7. k_collapse4     the 4-wide quantised tree: each binary internal node at even depth with
 //                      its children and grandchildren (layout in ugp_internal.cuh)
-#include <cub/cub.cuh>
 
 #include <math.h>
 #include <string.h>
@@ -25,8 +24,7 @@ namespace {
 
 struct Layout {
   size_t prims, nodes, nodes4, wlo, persistent;
-  size_t aabb, keys0, keys1, vals0, vals1, parent, flags, bounds, cub, total;
-  size_t cub_bytes;
+  size_t aabb, keys0, keys1, vals0, vals1, parent, flags, bounds, sort, total;
 };
 
 __device__ __forceinline__ int f2o(float f) {
@@ -397,13 +395,7 @@ bool layout_for(int64_t n, Layout* L) {
   L->vals1 = off;      off = align256(off + N * 4);
   L->parent = off;     off = align256(off + (ni + N) * 4);
   L->flags = off;      off = align256(off + ni * 4);
-  L->cub_bytes = 0;
-  if (N > 1) {
-    if (cub::DeviceRadixSort::SortPairs(nullptr, L->cub_bytes, (uint32_t*)nullptr, (uint32_t*)nullptr,
-                                        (int32_t*)nullptr, (int32_t*)nullptr, int(N), 0, 30) != cudaSuccess)
-      return false;
-  }
-  L->cub = off;        off = align256(off + L->cub_bytes);
+  L->sort = off;       off = align256(off + radix_sort_workspace(int64_t(N)));
   L->total = off;
   return true;
 }
@@ -492,10 +484,11 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
   } else {
     k_morton<<<G, T, 0, st>>>(n, aabb, bounds, k0, v0);
     UGP_CUDA_CHECK(cudaGetLastError());
-    size_t cub_bytes = L.cub_bytes;
-    UGP_CUDA_CHECK(cub::DeviceRadixSort::SortPairs(ws + L.cub, cub_bytes, k0, k1, v0, v1, int(n), 0, 30, st));
-    order = v1;
-    k_hierarchy<<<unsigned((n - 1 + T - 1) / T), T, 0, st>>>(int(n), k1, nodes_i, parent_int, parent_leaf);
+    const ugp_status ss = radix_sort_pairs(k0, k1, v0, v1, n, 30, ws + L.sort, st);
+    if (ss != UGP_OK) return ss;
+    const bool in1 = (radix_sort_passes(30) & 1) != 0;
+    order = in1 ? v1 : v0;
+    k_hierarchy<<<unsigned((n - 1 + T - 1) / T), T, 0, st>>>(int(n), in1 ? k1 : k0, nodes_i, parent_int, parent_leaf);
     UGP_CUDA_CHECK(cudaGetLastError());
     UGP_CUDA_CHECK(cudaMemsetAsync(flags, 0, (n - 1) * 4, st));
     k_refit<<<G, T, 0, st>>>(int(n), order, aabb, parent_int, parent_leaf, flags, nodes_f, root_box);
@@ -517,8 +510,8 @@ extern "C" ugp_status ugp_build_bvh(const ugp_prims* prims, float cutoff_eps, vo
                                   reinterpret_cast<uint4*>(ws + L.nodes4));
     UGP_CUDA_CHECK(cudaGetLastError());
   }
-  // own kernels plus the radix sort's (histogram, scan and one pass per 8-bit digit of 30 bits)
-  prof_end(kStBuild, st, (n == 1 ? 5 : 6 + 6) + 2 + kJumps);
+  // own kernels, the radix sort's three per 8-bit digit of the 30-bit codes among them
+  prof_end(kStBuild, st, (n == 1 ? 5 : 6 + 3 * radix_sort_passes(30)) + 2 + kJumps);
   b->stream = st;
   *out = b;
   return UGP_OK;

@@ -78,6 +78,15 @@ enum ProfStage { kStBuild = 0, kStCamera = 1, kStExtend = 2, kStShade = 3, kStSh
                  kStDense = 7, kStGuide = 8, kStBatch = 9 };
 void prof_begin(int stage, cudaStream_t s);
 void prof_end(int stage, cudaStream_t s, int n_kernels = 1);
+
+// Stable radix sort of (key, value) pairs by the low `bits` bits of the keys (ugp_sort.cu): 8
+// bits per pass, three kernels per pass, the pairs alternating between buffers 0 and 1 (the
+// result is in buffer radix_sort_passes(bits) & 1). `ws` holds radix_sort_workspace(n) bytes,
+// 256-byte aligned.
+size_t radix_sort_workspace(int64_t n);
+int radix_sort_passes(int bits);
+ugp_status radix_sort_pairs(uint32_t* k0, uint32_t* k1, int32_t* v0, int32_t* v1, int64_t n, int bits, void* ws,
+                            cudaStream_t st);
 // While suspended, prof_begin / prof_end neither record events nor count launches (used while
 // launches are captured into a graph, whose bodies cannot hold event records).
 void prof_suspend(bool on);
