@@ -18,3 +18,19 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+# Counts that a parity test tolerates (rounding-level mismatches it has explained), printed at
+# the end of the run so that drift shows even when every test passes.
+_PARITY_NOTES = []
+
+
+def parity_note(msg: str) -> None:
+    _PARITY_NOTES.append(msg)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    if _PARITY_NOTES:
+        terminalreporter.section("parity notes")
+        for m in _PARITY_NOTES:
+            terminalreporter.write_line(m)

@@ -15,6 +15,7 @@ tolerances:
 It builds the largest scene of the suite, so it runs last.
 """
 import numpy as np
+from conftest import parity_note
 import pytest
 
 from paper_2406_09733_gb300 import scenes
@@ -85,6 +86,7 @@ def test_full_size_queries_sampled_parity(orc):
             f = orc.sample_free_flight(s, rj, np.clip(u[idx][j:j + 1] + du, 0, 1 - 2 ** -24), u2[idx][j:j + 1])
             ok |= f["prim"][0] == p[j]
         assert ok, (int(idx[j]), int(p[j]), int(pr[j]))
+    parity_note(f"full size: {len(mism)} of 256 sampled rays pick another primitive than the oracle, all explained")
     assert len(mism) <= 4, len(mism)
     same = (p == pr) & (p >= 0)
     span = (r.t1 - r.t0).astype(np.float64)
