@@ -312,7 +312,10 @@ def equal_time_mse(args, d, mats, scene, dev):
             "train_spp": min(args.mse_train_spp, k), "train_samples": n_train, "adam_steps": g.step,
             "loss_first_last": [losses[0], losses[-1]] if losses else None,
             "reference_spp": args.mse_ref_spp, "reference_var_subtracted": ref_var_mean,
-            "image": f"{MW}x{MH} (the bench scene and camera at a reduced image size)", "max_depth": depth, "guide_alpha": args.guide_alpha,
+            "image": f"{MW}x{MH} (the bench scene and camera at a reduced image size)",
+            "lighting": "B: emissive primitives only, found by phase sampling" if not li.has_quad
+                        else "A: area light (light-sampled) and background",
+            "max_depth": depth, "guide_alpha": args.guide_alpha,
             "train_target": ("incident radiance" if args.guide_target == 0 else "phase function x incident radiance"),
             "curve_ms_mse": {"plain": curve_p, "guided": curve_g},
             "note": "MSE over linear RGB, no clamping; times include the guide's training"}
@@ -638,12 +641,29 @@ def run_ugp(args):
                                "sample": "32 pixels centred in the middle row, every primitive tested per query"},
                "configs": cpu_baseline_configs(args), "cpu": host_cpu()}
 
+    # lighting B (12,000 small emissive primitives, no area light): built once for the studies
+    lit_b = {}
+
+    def lighting_b():
+        if not lit_b:
+            sb = bench_scene(args, lighting="B")
+            tb = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+            db = {"mean": tb(sb.mean), "quat": tb(sb.quat), "scale": tb(sb.scale), "magnitude": tb(sb.magnitude)}
+            mb = ugp.Materials(tb(sb.sggx), tb(sb.mtype), tb(sb.albedo), tb(sb.roughness), tb(sb.emission))
+            lit_b.update(scene=sb, d=db, mats=mb)
+        return lit_b["scene"], lit_b["d"], lit_b["mats"]
+
     guide_perf = None
     mse = None
     serving = None
     if rank == 0 and world == 1 and not args.no_mse:
         guide_perf = guide_kernel_timing(dev)
         mse = equal_time_mse(args, d, mats, scene, dev)
+        try:
+            sb, db, mb = lighting_b()
+            mse["lighting_B"] = equal_time_mse(args, db, mb, sb, dev)
+        except Exception as e:  # reported in the line; the measured step above stands
+            mse["lighting_B"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_study(args, dev)
     rf = None
@@ -667,7 +687,7 @@ def run_ugp(args):
     emit = None
     if rank == 0 and world == 1 and not args.no_emitters:
         try:
-            emit = emitter_study(args, d, mats, scene, dev)
+            emit = emitter_study(args, d, mats, scene, dev, lighting_b)
         except Exception as e:  # reported in the line; the measured step above stands
             emit = {"error": repr(e)}
 
@@ -785,7 +805,7 @@ def exponential_study(args, d, scene, dev, reps=10):
     return out
 
 
-def emitter_study(args, d, mats, scene, dev, spp=4):
+def emitter_study(args, d, mats, scene, dev, lighting_b, spp=4):
     """Light sampling of emissive primitives, no area light, no background, on two scenes of the
     bench's size: the bench scene's own emitters (a tenth of the surface shapes), and the
     generator's lighting B (the paper's night: 12,000 small emissive aggregate primitives added).
@@ -839,10 +859,7 @@ def emitter_study(args, d, mats, scene, dev, spp=4):
     out = {"image": f"{W}x{H}", "spp": spp, "depth": args.depth,
            "lights": "emissive primitives only (no area light, no background)"}
     out["bench_scene_emitters"] = one(scene, d, mats)
-    sb = bench_scene(args, lighting="B")
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    db = {"mean": t(sb.mean), "quat": t(sb.quat), "scale": t(sb.scale), "magnitude": t(sb.magnitude)}
-    mb = ugp.Materials(t(sb.sggx), t(sb.mtype), t(sb.albedo), t(sb.roughness), t(sb.emission))
+    sb, db, mb = lighting_b()
     out["lighting_B"] = one(sb, db, mb)
     return out
 
