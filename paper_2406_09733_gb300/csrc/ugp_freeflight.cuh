@@ -382,7 +382,9 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
         tk[k] = INFINITY;
         rk[k] = -1;
         if (!((hm >> k) & 1u)) continue;
-        if ((ch[k] < 0 && ~ch[k] >= c.sc.n_prims) || (ch[k] >= 0 && ch[k] >= c.sc.n_nodes)) c.st = UGP_RAY_BAD_NODE;
+        // a primitive's slot is checked here (its record is loaded by slot); a child node's
+        // index is checked when it is visited
+        if (ch[k] < 0 && unsigned(~ch[k]) >= unsigned(c.sc.n_prims)) c.st = UGP_RAY_BAD_NODE;
         if (en[k] > limit || c.st != UGP_RAY_OK) continue;
         if (ch[k] < 0) {
           ++c.n_prims;

@@ -101,11 +101,13 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
           tk[k] = INFINITY;
           rk[k] = -1;
           if (!((hm >> k) & 1u)) continue;
-          if ((ch[k] < 0 && ~ch[k] >= sc.n_prims) || (ch[k] >= 0 && ch[k] >= sc.n_nodes)) {
-            bad = true;
-            continue;
-          }
           if (ch[k] < 0) {
+            // a primitive's slot is checked here (its record is loaded by slot); a child node's
+            // index is checked when it is visited
+            if (unsigned(~ch[k]) >= unsigned(sc.n_prims)) {
+              bad = true;
+              continue;
+            }
             ++ts.n_prims;
             lq[nq * stride] = ~ch[k];  // nq <= kTrLeafQ - 4 here: a node adds at most four
             ++nq;
