@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(128) k_b_shade(BState S) {
 __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_b_shadow(BState S) {
   __shared__ int stk[kTrStack * kTrBlock];
   __shared__ unsigned long long tr_acc[kTrBlock];
+  __shared__ int tr_owner[kTrBlock];
   const int count = S.ctl->shadow;
   const BPaths& P = S.P;
   // one ray per thread over a grid sized for the pool: the hardware spreads the blocks
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_b_shadow(BState S)
   const Ray ray = make_ray(f3(S.sh.ox[j], S.sh.oy[j], S.sh.oz[j]), f3(S.sh.dx[j], S.sh.dy[j], S.sh.dz[j]));
   TrStats ts{0u, 0u, UGP_RAY_OK};
   const float tau = tr_optical_depth(sc, ray, 0.f, S.sh.dist[j], S.sh.excl[j], stk + threadIdx.x, kTrBlock,
-                                     tr_acc + threadIdx.x, ts);
+                                     tr_acc + threadIdx.x, tr_owner + threadIdx.x, ts);
   const float T = fmaxf(0.f, 1.f - tau);
   if (T > 0.f) {
     P.ps.lr[p] += T * S.sh.cr[j];

@@ -71,6 +71,7 @@ struct FFSmem {
   int lq[kLeafQ][kFFBlock];    // held-back primitive slots
   unsigned below[kFFBlock];    // sum of the bins before the crossing bin (all bins while none)
   int nlist[kFFBlock];         // slots recorded in the ray's list
+  int owner[kFFBlock];         // leaf steps: lane of each warp's k-th ray with queued primitives
 };
 
 // A ray as handed to and returned from the scan (Src::begin fills the ray fields, the driver
@@ -319,7 +320,10 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       const unsigned has = q0 | q1 | q2 | q3;
       const unsigned starts = __reduce_or_sync(kFull, (mine > 0 && off < 32) ? (1u << off) : 0u);
       const bool work = lane < total;
-      const int o = work ? int(__fns(has, 0u, __popc(starts & (0xffffffffu >> (31 - lane))))) : lane;
+      int* owner_of = sm.owner + (c.tid & ~31);
+      if (mine > 0) owner_of[__popc(has & below_me)] = lane;
+      __syncwarp();
+      const int o = work ? owner_of[__popc(starts & (0xffffffffu >> (31 - lane))) - 1] : lane;
       const int off_o = __shfl_sync(kFull, off, o);
       const int nq_o = __shfl_sync(kFull, mine, o);
       OwnerRay w;

@@ -329,6 +329,7 @@ __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene 
                                                      unsigned long long* rays, unsigned long long* stats) {
   __shared__ int stk[kTrStack * kTrBlock];
   __shared__ unsigned long long tr_acc[kTrBlock];
+  __shared__ int tr_owner[kTrBlock];
   const int count = load_count(cnt);
   if (blockIdx.x == 0 && threadIdx.x == 0 && rays) atomicAdd(rays + 1, (unsigned long long)count);
   // one ray per thread over a grid sized for the longest queue: the hardware spreads the blocks
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kTrBlock, kTrBlocksPerSM) k_shadow(TraceScene 
   // point lies before saturation (T > 0) and is not scaled by T
   const float dist = sh.dist[j];
   const float tau = tr_optical_depth(sc, ray, 0.f, fabsf(dist), sh.excl[j], stk + threadIdx.x, kTrBlock,
-                                     tr_acc + threadIdx.x, ts);
+                                     tr_acc + threadIdx.x, tr_owner + threadIdx.x, ts);
   const float T = fmaxf(0.f, 1.f - tau);
   if (T > 0.f) {
     const float s = dist < 0.f ? 1.f : T;

@@ -19,11 +19,13 @@ k_transmittance(TraceScene sc, int64_t n_rays, const float* __restrict__ o3, con
                 unsigned long long* __restrict__ ctr) {
   __shared__ int stk[kTrStack * kTrBlock];
   __shared__ unsigned long long tr_acc[kTrBlock];
+  __shared__ int tr_owner[kTrBlock];
   const int64_t r = int64_t(blockIdx.x) * kTrBlock + threadIdx.x;
   if (r >= n_rays) return;
   TrStats ts{0u, 0u, UGP_RAY_OK};
   const float acc = tr_optical_depth(sc, make_ray(ld3(o3, r), ld3(d3, r)), __ldg(t0a + r), __ldg(t1a + r),
-                                     excl ? __ldg(excl + r) : -1, stk + threadIdx.x, kTrBlock, tr_acc + threadIdx.x, ts);
+                                     excl ? __ldg(excl + r) : -1, stk + threadIdx.x, kTrBlock, tr_acc + threadIdx.x,
+                                     tr_owner + threadIdx.x, ts);
   T_out[r] = fmaxf(0.f, 1.f - acc);
   if (st_out) st_out[r] = ts.st;
   if (STATS) add_counters(ctr, ts.n_nodes, ts.n_prims, 1u, 1u, 0u);

@@ -18,8 +18,8 @@ constexpr int kTrLeafQ = 10;  // primitives a lane may hold back (top of its sta
 // order and whichever lanes test a ray's primitives (terms below 2^-41 are dropped: under 1e-10
 // in tau for a few hundred of them); nearest-child-first only makes the early exit come sooner.
 // `stk` points at this thread's column of a shared-memory stack with `stride` between levels,
-// and `acc` at this thread's entry of a shared array of sums (its neighbours in the warp are the
-// other lanes' entries). The lanes that call together (the active mask) run in steps: a node
+// `acc` at this thread's entry of a shared array of sums and `owner` at its entry of a shared
+// int array (its neighbours in the warp are the other lanes' entries). The lanes that call together (the active mask) run in steps: a node
 // step visits one node per lane and holds back the primitives it meets (up to kTrLeafQ, kept at
 // the top of the stack column); a leaf step, taken once the lanes hold a primitive for each of
 // them (or a queue is nearly full or a traversal is over), spreads the held-back primitives over
@@ -27,7 +27,7 @@ constexpr int kTrLeafQ = 10;  // primitives a lane may hold back (top of its sta
 // the owner's sum with a shared-memory atomic.
 static_assert(kTrLeafQ < 16, "queue lengths are summed from four bit planes");
 static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, float t0, float t1, int ex,
-                                         int* stk, int stride, unsigned long long* acc, TrStats& ts) {
+                                         int* stk, int stride, unsigned long long* acc, int* owner, TrStats& ts) {
   const unsigned mask = __activemask();
   const int lane = int(threadIdx.x) & 31;
   const unsigned below_me = (1u << lane) - 1u;
@@ -53,7 +53,11 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
                       8 * __popc(p3 & below_me);
       const unsigned starts = __reduce_or_sync(mask, (mine > 0 && off < 32) ? (1u << off) : 0u);
       const bool work = rank < total;
-      const int o = work ? int(__fns(p0 | p1 | p2 | p3, 0u, __popc(starts & (0xffffffffu >> (31 - rank))))) : lane;
+      // the k-th calling lane with queued primitives, by a table the owners fill
+      int* owner_of = owner - lane;
+      if (mine > 0) owner_of[__popc((p0 | p1 | p2 | p3) & below_me)] = lane;
+      __syncwarp(mask);
+      const int o = work ? owner_of[__popc(starts & (0xffffffffu >> (31 - rank))) - 1] : lane;
       const int off_o = __shfl_sync(mask, off, o);
       const int nq_o = __shfl_sync(mask, mine, o);
       Ray ro;
