@@ -200,8 +200,11 @@ static __device__ void pooled_leaf(FFSmem& sm, const OwnerRay& w, int slot) {
   float tp = (h.a_end && x == h.a) ? -h.th : tau_at(x, h.tn, h.ts, h.s);
   float ep = erfcf(fabsf(tp));
   unsigned long long dbelow = 0;
+  float e_lo = w.edge(j);
   for (int k = j; k < kend; ++k) {
-    const float xa = fmaxf(x, w.edge(k)), ya = fminf(y, w.edge(k + 1));
+    const float e_hi = w.edge(k + 1);
+    const float xa = fmaxf(x, e_lo), ya = fminf(y, e_hi);
+    e_lo = e_hi;
     if (!(xa < y)) break;
     if (xa < ya) {
       const float tq = (h.b_end && ya == h.b) ? h.th : tau_at(ya, h.tn, h.ts, h.s);
@@ -381,6 +384,7 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
       ++c.n_nodes;
       float tk[4];
       int rk[4];
+      int nk = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         tk[k] = INFINITY;
@@ -397,10 +401,10 @@ __device__ void scan_persistent(FFSmem& sm, Src& src, int* next) {
         } else {
           tk[k] = en[k];
           rk[k] = ch[k];
+          ++nk;
         }
       }
       sort4(tk, rk);
-      const int nk = (rk[0] >= 0) + (rk[1] >= 0) + (rk[2] >= 0) + (rk[3] >= 0);
       if (c.st != UGP_RAY_OK) {
         tdone = true;
         nq = 0;

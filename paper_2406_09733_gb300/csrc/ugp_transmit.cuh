@@ -99,6 +99,7 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
         ++ts.n_nodes;
         float tk[4];
         int rk[4];
+        int nk = 0;
         bool bad = false;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -118,10 +119,10 @@ static __device__ float tr_optical_depth(const TraceScene& sc, const Ray& ray, f
           } else {
             tk[k] = en[k];
             rk[k] = ch[k];
+            ++nk;
           }
         }
         sort4(tk, rk);
-        const int nk = (rk[0] >= 0) + (rk[1] >= 0) + (rk[2] >= 0) + (rk[3] >= 0);
         if (bad) {
           ts.st = UGP_RAY_BAD_NODE;
           tdone = true;
