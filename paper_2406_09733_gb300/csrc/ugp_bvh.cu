@@ -330,6 +330,9 @@ __global__ void k_collapse4(int n_int, const float4* __restrict__ nodes, const i
       qlo[a] |= uint32_t(ql) << (8 * c);
       qhi[a] |= uint32_t(qh) << (8 * c);
     }
+    // an empty child slot gets an inverted box (low face 255, high face 0) that no ray enters,
+    // so the node test needs no separate check for it
+    for (int c = m; c < 4; ++c) qlo[a] |= 255u << (8 * c);
     ex |= uint32_t(e + 128) << (8 * a);
   }
   int r4[4] = {kEmptyChild, kEmptyChild, kEmptyChild, kEmptyChild};

@@ -301,7 +301,7 @@ __device__ __forceinline__ unsigned node4_test(const uint4* __restrict__ n4, int
     const float th = fminf(min3f(fmaf(byte_f(fx, c), ax, bx), fmaf(byte_f(fy, c), ay, by), fmaf(byte_f(fz, c), az, bz)),
                            tmax);
     en[c] = tl;
-    if (ch[c] != kEmptyChild && tl <= th + 4e-7f * fabsf(th)) hit |= 1u << c;
+    if (tl <= th + 4e-7f * fabsf(th)) hit |= 1u << c;  // never for an empty slot (inverted box)
   }
   return hit;
 }

@@ -38,7 +38,8 @@ constexpr int kEmptyChild = INT32_MIN;
 //   w3 = (child0, child1, child2, child3) as int: >= 0 the 4-wide node of that (binary)
 //        index, < 0 and != kEmptyChild the leaf holding primitive slot ~child, kEmptyChild none.
 // Child c's box along axis a is [o_a + lo_a(c) 2^e_a, o_a + hi_a(c) 2^e_a]; the faces are rounded
-// outwards, so the quantised box contains the exact one. A 4-wide node sits at the index of its
+// outwards, so the quantised box contains the exact one. An empty slot's box is inverted
+// (lo = 255, hi = 0 on every axis), so no ray enters it. A 4-wide node sits at the index of its
 // binary node (the array has holes at odd depths, which are never read).
 constexpr int kNode4U4 = 4;
 
