@@ -113,9 +113,9 @@ GUIDE_GRAD_FLOP = 2 * GUIDE_FWD_FLOP + 2 * (3 * 64 * 64 + 40 * 64)
 
 
 # DRAM bytes (read + write) per k_extend launch of a workload, averaged over the launches of one
-# step, from one ncu capture of the current kernel (profiles/k_extend_dram_*.md); None for any
+# step, from one ncu capture of the current kernel (its summary is kept under profiles/); None for any
 # other workload, and to be reset whenever k_extend changes.
-EXTEND_TRAFFIC_BYTES = {}
+EXTEND_TRAFFIC_BYTES = {(5_500_000, 1920, 1080, 12, "A", 0.1): 1371.15e6}
 
 # Algorithmic bytes of a free-flight query are counted against a fixed reference traversal, so
 # that a tree that makes a query visit more nodes cannot raise the figure: the nodes and records
