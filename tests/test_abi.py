@@ -179,3 +179,20 @@ def test_binding_checks_lengths_and_devices():
         ugp._workspace(host_ws, 256, torch.device("cuda", 0))
     with pytest.raises(TypeError, match="uint8"):
         ugp._workspace(torch.zeros(1 << 12), 256, torch.device("cuda", 0))
+
+
+def test_render_workspace_matches_the_documented_size(libugp):
+    """ugp_render_workspace_size against the header's account: 1284 bytes per pixel (path
+    state, queues, shadow queues, finish table, slot lists), one 73,728-byte interval slot of
+    the finish per 64 pixels (4 to 2432 of them), plus 256-byte alignment of each column and a
+    few headers."""
+    libugp.ugp_render_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_render_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    for w, h in ((1920, 1080), (1024, 1024), (64, 64), (7, 3)):
+        n = w * h
+        slots = min(max(n // 64, 4), 2432)
+        expect = 1284 * n + slots * 73728
+        got = libugp.ugp_render_workspace_size(w, h)
+        assert expect <= got <= expect + 400 * 256 + 4096, (w, h, got, expect)
+    assert libugp.ugp_render_workspace_size(0, 5) == 0
+    assert libugp.ugp_render_workspace_size(1 << 16, 1 << 16) == 0
