@@ -166,8 +166,9 @@ ugp_status ugp_sample_free_flight(const ugp_bvh* bvh, int64_t n_rays, const floa
 /* Scratch bytes ugp_sample_free_flight needs for n_rays rays: the table of rays whose root
  * the first pass has bracketed (they are finished by the passes that follow it), the lists of
  * rays handed between those passes, and per ray a list of up to 256 primitive slots met by
- * the first pass (1100 bytes per ray in all).  The workspace must be 256-byte aligned and is
- * only used during the call's device work. */
+ * the first pass (1100 bytes per ray in all), plus one 73,728-byte interval slot of the last
+ * pass per 64 rays (4 to 2432 of them) and alignment.  The workspace must be 256-byte aligned
+ * and is only used during the call's device work. */
 size_t ugp_sample_free_flight_workspace_size(int64_t n_rays);
 
 /* Free-flight sampling without any device allocation (no counterpart in the paper).

@@ -196,3 +196,14 @@ def test_render_workspace_matches_the_documented_size(libugp):
         assert expect <= got <= expect + 400 * 256 + 4096, (w, h, got, expect)
     assert libugp.ugp_render_workspace_size(0, 5) == 0
     assert libugp.ugp_render_workspace_size(1 << 16, 1 << 16) == 0
+
+
+def test_free_flight_workspace_matches_the_documented_size(libugp):
+    libugp.ugp_sample_free_flight_workspace_size.restype = ctypes.c_size_t
+    libugp.ugp_sample_free_flight_workspace_size.argtypes = [ctypes.c_int64]
+    for n in (1, 1000, 65536, 2073600):
+        slots = min(max(n // 64, 4), 2432)
+        expect = 1100 * n + slots * 73728
+        got = libugp.ugp_sample_free_flight_workspace_size(n)
+        assert expect <= got <= expect + 30 * 256 + 256, (n, got, expect)
+    assert libugp.ugp_sample_free_flight_workspace_size(-1) == 0
