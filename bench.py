@@ -80,6 +80,8 @@ def parse_args(argv=None):
     p.add_argument("--serve-spp-max", type=int, default=64,
                    help="spp of the serving requests are log-uniform in [1, this] (64 = the full workload)")
     p.add_argument("--guide-lr", type=float, default=1e-3)
+    p.add_argument("--guide-min-roughness", type=float, default=0.0,
+                   help="vertices with a glossier base scatter by phase sampling alone in the MSE study")
     p.add_argument("--guide-target", type=int, choices=[0, 1], default=0,
                    help="guide training target: 0 incident radiance, 1 its product with the phase function")
     return p.parse_args(argv)
@@ -294,7 +296,8 @@ def equal_time_mse(args, d, mats, scene, dev):
         train = k < args.mse_train_spp
         t0 = time.perf_counter()
         r.render(bvh, mats, camera, lights, spp=1, max_depth=depth, seed=2, spp_begin=k, accum=gacc,
-                 accum_sq=gacc2, guide=g, guide_alpha=args.guide_alpha, guide_log=train)
+                 accum_sq=gacc2, guide=g, guide_alpha=args.guide_alpha, guide_log=train,
+                 guide_min_roughness=args.guide_min_roughness)
         if train:
             ns, loss = g.train_from(r, max_samples=1 << 20, minibatch=args.mse_minibatch,
                                     min_steps=args.mse_min_steps)
@@ -315,7 +318,7 @@ def equal_time_mse(args, d, mats, scene, dev):
             "image": f"{MW}x{MH} (the bench scene and camera at a reduced image size)",
             "lighting": "B: emissive primitives only, found by phase sampling" if not li.has_quad
                         else "A: area light (light-sampled) and background",
-            "max_depth": depth, "guide_alpha": args.guide_alpha,
+            "max_depth": depth, "guide_alpha": args.guide_alpha, "guide_min_roughness": args.guide_min_roughness,
             "train_target": ("incident radiance" if args.guide_target == 0 else "phase function x incident radiance"),
             "curve_ms_mse": {"plain": curve_p, "guided": curve_g},
             "note": "MSE over linear RGB, no clamping; times include the guide's training"}
