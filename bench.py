@@ -452,10 +452,10 @@ def cpu_baseline_run(scene, args, pixels, spp=1, seed=0, accel=False, threads=No
 
 def cpu_baseline_configs(args):
     """The oracle's timings on the three plain configurations of the workload set: the
-    1,000-primitive scene in full (128^2, 4 spp, depth 4, brute force), and 64^2 = 4096 pixels
-    around the image centre (consecutive in row order) of the 1M-primitive room (1 spp, depth 8)
-    and of the bench scene (1 spp, depth 12), both with the oracle's BVH; rates in Mrays/s on all
-    host cores, BVH builds excluded and reported."""
+    1,000-primitive scene in full (128^2, 4 spp, depth 4, brute force), a 128 x 128 centre crop
+    of the 1M-primitive room at 1024^2 (4 spp, depth 8) and a 64 x 64 centre crop of the bench
+    scene (1 spp, the bench's depth), both with the oracle's BVH; rates in Mrays/s on all host
+    cores, BVH builds excluded and reported."""
     import oracle
     from paper_2406_09733_gb300 import scenes
     out = {}
@@ -464,18 +464,19 @@ def cpu_baseline_configs(args):
     _, _, (ne, ns) = oracle.render(s1, spp=4, max_depth=4, seed=0)
     dt = time.perf_counter() - t0
     out["tiny_1000_full_128x128_4spp"] = {"Mrays_per_s": (ne + ns) / dt / 1e6, "queries": ne + ns, "s": dt}
-    for name, sc, depth in (("room_1M_4096_pixels", scenes.room_scene(1_000_000, width=1024, height=1024), 8),
-                            ("bench_scene_4096_pixels", bench_scene(args), args.depth)):
+    for name, sc, depth, crop, spp in (
+            ("room_1M_crop_128x128_4spp", scenes.room_scene(1_000_000, width=1024, height=1024), 8, 128, 4),
+            ("bench_scene_crop_64x64_1spp", bench_scene(args), args.depth, 64, 1)):
         W, H = sc.camera.width, sc.camera.height
-        p0 = (H // 2) * W + W // 2 - 2048   # 4096 consecutive pixels (64^2) around the image centre
+        rect = ((W - crop) // 2, (H - crop) // 2, crop, crop)
         ts = []
-        for _ in range(2):   # BVH build, then the per-call set-up alone
+        for _ in range(2):   # BVH build, then the per-call set-up alone (an empty range)
             t0 = time.perf_counter()
-            oracle.render(sc, spp=1, max_depth=depth, seed=0, pixels=(p0, p0), accel=True)
+            oracle.render(sc, spp=1, max_depth=depth, seed=0, pixels=(0, 0), accel=True)
             ts.append(time.perf_counter() - t0)
         build = ts[0] - ts[1]
         t0 = time.perf_counter()
-        _, _, (ne, ns) = oracle.render(sc, spp=1, max_depth=depth, seed=0, pixels=(p0, p0 + 4096), accel=True)
+        _, _, (ne, ns) = oracle.render(sc, spp=spp, max_depth=depth, seed=0, rect=rect, accel=True)
         dt = max(time.perf_counter() - t0 - ts[1], 1e-9)
         out[name] = {"Mrays_per_s": (ne + ns) / dt / 1e6, "queries": ne + ns, "s": dt, "bvh_build_s": build}
     out["cores"] = oracle.num_threads()

@@ -404,7 +404,7 @@ class OrcParams(C.Structure):
                 ("seed", C.c_uint64), ("cutoff_eps", C.c_double), ("nee", C.c_int32),
                 ("spawn_mode", C.c_int32), ("guide", f32p), ("guide_cfg", OrcGuideCfg),
                 ("guide_alpha", C.c_double), ("nee_emitters", C.c_int32), ("accel", C.c_int32),
-                ("guide_min_roughness", C.c_double)]
+                ("guide_min_roughness", C.c_double), ("crop_x0", C.c_int32), ("crop_x1", C.c_int32)]
 
 
 def _d(a):
@@ -563,10 +563,11 @@ def phase_pdf_approx(mtype, albedo, alpha, S6, wo, wi):
 
 def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1, spawn_mode=0,
            pixels=None, threads=None, guide=None, guide_alpha=0.5, nee_emitters=0, accel=False,
-           guide_min_roughness=0.0):
+           guide_min_roughness=0.0, rect=None):
     """Per-pixel sums of sample values and squares, shape (H, W, 3) each, plus query counts.
 
     ``pixels`` = (p_begin, p_end) renders only that row-major pixel range (others stay zero).
+    ``rect`` = (x0, y0, w, h) renders only that rectangle of pixels (instead of ``pixels``).
     ``guide`` = (params, GuideConfig) renders with the learned guide by one-sample MIS.
     ``nee_emitters`` = 1 adds next-event estimation toward emissive primitives (with MIS).
     ``accel`` finds each ray's intervals with a BVH instead of testing every primitive: the same
@@ -585,11 +586,17 @@ def render(scene, spp, max_depth=4, seed=0, spp_begin=0, cutoff_eps=0.01, nee=1,
         gcfg = _guide_cfg(guide[1])
     p = OrcParams(int(spp), int(spp_begin), int(max_depth), int(seed), float(cutoff_eps), int(nee),
                   int(spawn_mode), _ptr(gp, f32p), gcfg, float(guide_alpha), int(nee_emitters), int(bool(accel)),
-                  float(guide_min_roughness))
+                  float(guide_min_roughness), 0, 0)
     acc = np.zeros((H, W, 3))
     acc2 = np.zeros((H, W, 3))
     counts = (C.c_int64 * 2)(0, 0)
     pb, pe = (0, W * H) if pixels is None else pixels
+    if rect is not None:
+        x0, y0, rw, rh = (int(v) for v in rect)
+        if not (0 <= x0 and 0 <= y0 and rw > 0 and rh > 0 and x0 + rw <= W and y0 + rh <= H):
+            raise ValueError(f"rect {rect} outside the {W}x{H} image")
+        pb, pe = y0 * W, (y0 + rh) * W
+        p.crop_x0, p.crop_x1 = x0, x0 + rw
     sr = _SceneRef(scene)
     if threads:
         set_num_threads(threads)

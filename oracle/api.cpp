@@ -469,6 +469,7 @@ typedef struct {
   int32_t nee_emitters;  // 1: next-event estimation toward emissive primitives as well
   int32_t accel;         // 1: intervals found with a BVH (the same ones; for timing large scenes)
   double guide_min_roughness;  // glossier vertices scatter by phase sampling alone
+  int32_t crop_x0, crop_x1;    // columns [crop_x0, crop_x1) of the range only (x1 <= x0: all)
 } orc_params;
 
 static GuideCfg guide_cfg_of(const orc_guide_cfg* g) {
@@ -484,7 +485,8 @@ static GuideCfg guide_cfg_of(const orc_guide_cfg* g) {
 }
 
 // Adds the per-pixel sums of sample values and of their squares (3 channels) for pixels
-// [p_begin, p_end) into accum / accum_sq (full-image arrays).  counts[0] += extend queries,
+// [p_begin, p_end) (within columns [crop_x0, crop_x1) when those are set) into accum /
+// accum_sq (full-image arrays).  counts[0] += extend queries,
 // counts[1] += shadow queries.
 void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, const orc_params* p,
                 int64_t p_begin, int64_t p_end, double* accum, double* accum_sq, int64_t* counts) {
@@ -497,6 +499,8 @@ void orc_render(const orc_scene* s, const orc_camera* c, const orc_lights* l, co
   P.nee_emitters = p->nee_emitters;
   P.accel = p->accel;
   P.guide_min_roughness = p->guide_min_roughness;
+  P.crop_x0 = p->crop_x0;
+  P.crop_x1 = p->crop_x1;
   int64_t ne = 0, ns = 0;
   render_pixels(scene_in(s), cam, L, P, p_begin, p_end, accum, accum_sq, &ne, &ns);
   if (counts) {

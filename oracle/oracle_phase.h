@@ -91,6 +91,9 @@ struct RenderParams {
   // Vertices whose base is glossier than this (GGX alpha, or the Disney specular's
   // max(1e-3, roughness^2), below it) scatter by phase sampling alone even with a guide.
   double guide_min_roughness = 0.0;
+  // Columns [crop_x0, crop_x1) of the pixel range only (crop_x1 <= crop_x0: every column), so
+  // that a rectangle of rows and columns can be rendered in one call.
+  int crop_x0 = 0, crop_x1 = 0;
 };
 
 // Next-event estimation toward emissive primitives (not specified by the paper): emitter j is

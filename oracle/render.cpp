@@ -246,6 +246,7 @@ void render_pixels(const SceneIn& s, const Camera& cam, const Lights& L, const R
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : ext, shd)
   for (int64_t p = p_begin; p < p_end; ++p) {
     const int px = int(p % cam.width), py = int(p / cam.width);
+    if (P.crop_x1 > P.crop_x0 && (px < P.crop_x0 || px >= P.crop_x1)) continue;
     double sum[3] = {0, 0, 0}, sq[3] = {0, 0, 0};
     for (int si = 0; si < P.spp; ++si) {
       const uint32_t sample = uint32_t(P.spp_begin + si);

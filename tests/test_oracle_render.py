@@ -254,3 +254,18 @@ def test_render_with_bvh_equals_brute_force(orc):
     b, r, m = orc.render(s, spp=4, max_depth=5, seed=3, accel=True)
     assert n == m and n[0] > 1000
     assert np.array_equal(a, b) and np.array_equal(q, r)
+
+
+def test_render_rectangle_equals_the_full_render(orc):
+    """A rectangle of pixels (the CPU baseline's crops) gets the same sums as the same pixels
+    of a full render, and every other pixel stays zero."""
+    s = scenes.tiny_scene(n=200, seed=3, width=16, height=12)
+    a, q, (ne, ns) = orc.render(s, spp=2, max_depth=2, seed=1)
+    b, qb, (ne2, ns2) = orc.render(s, spp=2, max_depth=2, seed=1, rect=(3, 2, 5, 4))
+    m = np.zeros((12, 16), bool)
+    m[2:6, 3:8] = True
+    assert np.array_equal(b[m], a[m]) and np.array_equal(qb[m], q[m])
+    assert np.all(b[~m] == 0) and np.all(qb[~m] == 0)
+    assert 0 < ne2 < ne
+    with pytest.raises(ValueError):
+        orc.render(s, spp=1, max_depth=1, rect=(10, 0, 8, 2))
