@@ -1,10 +1,13 @@
 // Wavefront path tracer (Table 1, right column) over Gaussian primitives.
 //
-// One path per pixel per sample pass; per bounce three kernels run on the caller's stream:
+// One path per pixel per sample pass; per bounce these kernels run on the caller's stream (the
+// free-flight finish passes of ugp_dense.cu follow k_extend):
 //   k_extend   quad-light clip and free-flight sampling (Sec. 5.2) of every live path
 //   k_shade    emission, light sampling with MIS, phase sampling (Sec. 6); live paths and
 //              shadow rays are appended to queues with warp-aggregated atomics
-//   k_shadow   transmittance of the shadow rays (Sec. 5.3)
+//   k_shadow   transmittance of the shadow rays (Sec. 5.3): one launch for the area light's
+//              samples, one for the emitters' (each path's two contributions then add up in
+//              a fixed order)
 // Queue lengths stay on the device, so a whole frame runs without host synchronisation;
 // kernels walk their queue with grid-stride loops over a grid sized to the GPU.
 //
@@ -14,7 +17,8 @@
 //  * Emissive primitives are pure emitters; escape adds the background, or the area light's
 //    radiance if the ray reaches its front face.
 //  * With an emitter table, each scattering vertex also takes a light sample of an emissive
-//    primitive (ugp_emitters.cuh), balanced against phase sampling; one light sample per vertex.
+//    primitive (ugp_emitters.cuh), balanced against phase sampling; with the area light as well,
+//    a vertex takes one light sample of each, each balanced against phase sampling alone.
 //  * Scattered and shadow rays start at the centre of the chosen primitive's clipped interval
 //    and skip that primitive (Sec. 6).
 //  * With a learned guide, a vertex draws its direction from the guide with probability alpha,
