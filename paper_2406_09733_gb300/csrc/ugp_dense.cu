@@ -1,6 +1,8 @@
 // Finish of free-flight sampling: every ray whose root the scan has bracketed in [lo, hi] (with
-// F(lo) = Flo) is finished here, in three kernels that differ only in how many intervals they
-// hold per ray.
+// F(lo) = Flo) is finished here, in two kernels that differ only in how many intervals they
+// hold per ray. Both keep, per interval collected, its whole term on the bracket and erfc(|tau|)
+// at its clipped start (with tau's sign), so each Newton evaluation takes one erfc per interval
+// that contains t.
 //
 // Main pass (k_dense): each half-warp (16 lanes) finishes one ray, so a warp works on two rays
 // at a time (most brackets hold a few dozen intervals, which would leave lanes of a whole warp
