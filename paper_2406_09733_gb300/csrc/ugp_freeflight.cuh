@@ -39,8 +39,8 @@
 // node steps are held back until the warp holds 32 of them (or a lane's queue is nearly full or
 // its traversal is over), and a leaf step then spreads them over the lanes, one per lane
 // whichever ray it belongs to, so the expensive primitive test and binning run on all lanes
-// (with one primitive per lane of its own ray, the leaf steps of the bench's rays kept 10 of 32
-// lanes busy). A lane bins into the owning ray's bins with shared-memory atomics; the owner
+// (with one primitive per lane of its own ray, the leaf steps of a 5.5M-primitive room's path
+// rays kept 10 of 32 lanes busy). A lane bins into the owning ray's bins with shared-memory atomics; the owner
 // moves its crossing bin after the step. Holding a primitive back can only delay a lowering of
 // the pruning limit, never skip a node that matters.
 #include "ugp_dense.cuh"
