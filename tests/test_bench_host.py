@@ -56,3 +56,19 @@ def test_bench_arguments_and_workload_description():
     assert cfg["n_prims"] == 5_500_000 and cfg["width"] == 1920 and cfg["height"] == 1080
     assert cfg["max_depth"] == 12 and cfg["lighting"] == "A" and cfg["near_specular_frac"] == 0.1
     assert "5500000" in cfg["workload"] and "1920x1080" in cfg["workload"]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` on a tiny workload (the FP64 oracle on the host): one JSON
+    line with the arm's fields, the CPU-baseline block and an e2e block without copies."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n-prims", "2000",
+                          "--width", "64", "--height", "64", "--steps", "1", "--warmup", "0", "--cpu-pixels", "2048"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    d = json.loads(out.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["unit"] == "Mrays/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
